@@ -1,0 +1,172 @@
+"""Pins of the structured reference (oracle/structured.py): Algorithms 1 and 2.
+
+What the paper fixes and is checked here:
+
+* Section 2: the barycentric formula equals the product form; partition of
+  unity; L_r(y_s) = delta_rs; exact interpolation of polynomials of degree < q.
+* Lemma A.1: every interpolated kernel entry is within 2^(1-2q) of exp(-y xi);
+  Lemma A.2 (i), (ii), (iv): the entries set to 1 or 0 are within eps.
+* Algorithm 1 returns exactly K~ c with K~ from eq. (A.1), and Theorem A.3:
+  ||f - f~||_inf <= eps ||c||_1 against the plain oracle.
+* Section 5 experiment shape: E(q) decays faster than 4^(-q).
+* Lemma 4.2 (Hadamard identity) on random dense matrices, to roundoff.
+* Theorem 4.3 / Algorithm 2 (exact NDFT): E <= eps against the plain oracle;
+  Z^0 nodes return c_0; nodes on |z| = 1 reduce to the DFT.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import structured as S
+from paper_1606_03255_gb300 import workloads as W
+
+
+@pytest.mark.parametrize("q", [1, 2, 5, 12, 22])
+def test_barycentric_matches_product_form_and_unity(q):
+    rng = np.random.default_rng(q)
+    a, b = 0.37, 0.74
+    y = a + (b - a) * rng.random(200)
+    Lb = S.lagrange_barycentric(y, a, b, q)
+    Lp = S.lagrange_product(y, a, b, q)
+    assert np.max(np.abs(Lb - Lp)) < 1e-12 * max(1, q)
+    assert np.max(np.abs(Lb.sum(axis=1) - 1.0)) < 1e-13
+    nodes = S.interval_points(a, b, q)
+    assert np.array_equal(S.lagrange_barycentric(nodes, a, b, q), np.eye(q))
+
+
+def test_interpolation_is_exact_on_low_degree_polynomials():
+    q = 9
+    a, b = 2.0, 4.0
+    rng = np.random.default_rng(0)
+    coef = rng.standard_normal(q)            # degree q-1
+    y = a + (b - a) * rng.random(100)
+    nodes = S.interval_points(a, b, q)
+    vals = np.polyval(coef, nodes)
+    interp = S.lagrange_barycentric(y, a, b, q) @ vals
+    assert np.max(np.abs(interp - np.polyval(coef, y))) < 1e-11 * np.max(np.abs(vals))
+    # degree q is not reproduced
+    coef2 = np.concatenate([[1.0], np.zeros(q)])
+    interp2 = S.lagrange_barycentric(y, a, b, q) @ np.polyval(coef2, nodes)
+    assert np.max(np.abs(interp2 - np.polyval(coef2, y))) > 1e-6
+
+
+def test_definition_parameters_hand_computed():
+    # q = ceil(1/2 + log_4(1/eps))
+    assert S.rank_q(1e-6) == 11 and S.rank_q(1e-6 / 3) == 12
+    assert S.rank_q(1e-12 / 3) == 22 and S.rank_q(1e-10 / 3) == 18
+    assert S.rank_q(2.0 ** (1 - 2 * 7)) == 7
+    # y1 * xi1 = 2^10, eps = 2^-10: M = ceil(log2(2^20)) + 1 = 21
+    p = S.laplace_params(2.0 ** -10, 32.0, 32.0)
+    assert p.M == 21
+    # l_m = max(1, floor(10 - m - log2(ln 2^10)) + 1); log2(6.931...) = 2.79...
+    for m in range(1, p.M):
+        assert p.ell[m] == max(1, math.floor(10 - m - math.log2(10 * math.log(2))) + 1)
+        assert p.L[m] == 21 - m
+    assert p.ell[1] == 7 and p.ell[6] == 2 and p.ell[7] == 1
+
+
+def test_band_assignment_edges():
+    M = 6
+    v1 = 10.0
+    v = np.array([10.0, 5.0000001, 5.0, 2.5, 1e-9, 0.0, 10.0 / 32, 10.0 / 32 * 1.0000001])
+    b = S.band_of(v, v1, M)
+    # (5, 10] -> 1 ; (2.5, 5] -> 2 ; (1.25, 2.5] -> 3 ; ... [0, 10/32] -> 6
+    assert list(b) == [1, 1, 2, 3, 6, 6, 6, 5]
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-6, 1e-9])
+def test_kernel_entries_meet_lemma_bounds(eps):
+    rng = np.random.default_rng(7)
+    t = np.sort(rng.random(300))[::-1] * 3.0
+    s = np.sort(rng.random(200))[::-1] * 500.0
+    K, p = S.laplace_tilde_matrix(t, s, eps)
+    exact = np.exp(-np.outer(s, t))
+    bt = S.band_of(t, p.xi1, p.M)
+    bs = S.band_of(s, p.y1, p.M)
+    err = np.abs(K - exact)
+    for j in range(s.size):
+        m = bs[j]
+        for k in range(t.size):
+            l = bt[k]
+            if m < p.M and p.ell[m] <= l <= p.L[m]:
+                assert err[j, k] <= 2.0 ** (1 - 2 * p.q) + 1e-15      # Lemma A.1
+            else:
+                assert err[j, k] <= eps                                # Lemma A.2
+    assert err.max() <= eps
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
+def test_algorithm1_equals_dense_tilde_and_meets_theorem(eps):
+    c, t, s = W.laplace_inputs(400, 300, seed=4)
+    f_alg, p = S.laplace_alg1(c, t, s, eps)
+    K, _ = S.laplace_tilde_matrix(t, s, eps)
+    assert np.max(np.abs(f_alg - K @ c)) <= 1e-12 * np.sum(np.abs(c))
+    f = oracle.laplace_direct(c, t, s)
+    assert oracle.error_E(f, f_alg, c) <= eps                          # Theorem A.3
+
+
+def test_algorithm1_error_decays_faster_than_4_to_minus_q():
+    # Section 5 workload shape (smaller N): y in [0, (2q-1) ln 2] is the paper's
+    # choice; here nodes fill [0, 2N] and [0, 1] as in the Laplace config.
+    c, t, s = W.laplace_inputs(2048, 512, seed=8)
+    f = oracle.laplace_direct(c, t, s)
+    qs = np.arange(2, 11)
+    Es = []
+    for q in qs:
+        eps = 2.0 ** (1 - 2 * q)                 # so that rank_q(eps) == q
+        assert S.rank_q(eps) == q
+        fa, _ = S.laplace_alg1(c, t, s, eps)
+        Es.append(oracle.error_E(f, fa, c))
+        assert Es[-1] <= eps
+    slope = np.polyfit(qs, np.log(np.maximum(Es, 1e-300)), 1)[0]
+    assert -slope > math.log(4.0), (Es, slope)
+
+
+def test_hadamard_identity_lemma_4_2():
+    rng = np.random.default_rng(1)
+    p_, n_, q = 17, 23, 5
+    LY = rng.standard_normal((p_, q))
+    KYO = rng.standard_normal((q, q))
+    LO = rng.standard_normal((n_, q))
+    A = rng.standard_normal((p_, n_)) + 1j * rng.standard_normal((p_, n_))
+    f = rng.standard_normal(n_) + 1j * rng.standard_normal(n_)
+    lhs = (A * (LY @ KYO @ LO.T)) @ f
+    rhs = (LY * (A @ np.diag(f) @ LO @ KYO.T)) @ np.ones(q)
+    assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(lhs))
+    # the transposed coupling block is not the same thing
+    bad = (LY * (A @ np.diag(f) @ LO @ KYO)) @ np.ones(q)
+    assert np.max(np.abs(lhs - bad)) > 1e-3
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
+@pytest.mark.parametrize("kind", ["disk", "clustered", "paper"])
+def test_algorithm2_meets_theorem(eps, kind):
+    N, M = 512, 256
+    c = W.coefficients(N, seed=12)
+    if kind == "disk":
+        w = W.nodes_disk_uniform(M, seed=13)
+    elif kind == "clustered":
+        w = W.nodes_circle_clustered(M, seed=14)
+    else:
+        w = W.nodes_paper_section5(M, S.rank_q(eps), seed=15)
+    f = oracle.flt_direct(c, w)
+    fa, P = S.xflt_alg2(c, w, eps)
+    assert oracle.error_E(f, fa, c) <= eps
+
+
+def test_algorithm2_special_cases():
+    N = 256
+    c = W.coefficients(N, seed=2)
+    # all nodes on the unit circle, equispaced: Z_M band only -> DFT
+    w = W.nodes_equispaced_circle(N)
+    fa, P = S.xflt_alg2(c, w, 1e-8)
+    assert oracle.error_E(np.fft.ifft(c) * N, fa, c) < 1e-14
+    # Z^0 nodes: |z| < eps -> exactly c_0
+    w0 = np.array([[0.25, 5.0], [0.6, 3.0]])          # |z| = e^{-10 pi}, e^{-6 pi}
+    f0, _ = S.xflt_alg2(c, w0, 1e-6)
+    assert np.array_equal(f0, np.full(2, c[0]))
+    # N = 1: f = c_0 everywhere
+    f1, _ = S.xflt_alg2(c[:1], W.nodes_disk_uniform(5, 0), 1e-6)
+    assert np.array_equal(f1, np.full(5, c[0]))
