@@ -1,0 +1,181 @@
+/*
+ * fl.h -- C ABI of the GB300 fast Fourier-Laplace transform library (libfl.so).
+ *
+ * Kunis & Melzer, "Fast evaluation of real and complex exponential sums"
+ * (arXiv 1606.03255).  The library evaluates
+ *
+ *   f_j = sum_{k=0}^{N-1} c_k exp(2 pi i k w_j),   Im w_j >= 0,   j < M,
+ *
+ * i.e. the polynomial sum_k c_k z^k at the nodes z_j = exp(2 pi i w_j) of the
+ * closed unit disk (Section 4, eq. (4.1) with exponents xi_k = k and the polar
+ * split (4.2); this ABI numbers coefficients from 0 where the paper numbers
+ * them from 1), by Algorithm 2 of the paper, and the real discrete Laplace
+ * transform f_j = sum_k c_k exp(-s_j t_k) (Section 3, eq. (3.2)) by
+ * Algorithm 1.  Every step runs in the library's own CUDA kernels on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - All pointers named *_dev are device pointers (e.g. from torch tensors);
+ *     *_host pointers are host memory (pinned memory gives overlapped copies).
+ *     The caller owns every buffer it passes; the plan owns its own scratch.
+ *   - Complex arrays are interleaved (re, im).  The element type follows the
+ *     plan's precision: FL_FP32 -> float pairs (complex64),
+ *     FL_FP64 -> double pairs (complex128).  Nodes are always float64.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  fl_execute / fl_adjoint / fl_laplace_real are asynchronous on
+ *     it; planning synchronises it.
+ *   - Errors are returned as fl_status, never raised or aborted on; a message
+ *     is kept per thread and read with fl_last_error().
+ *   - A plan may be executed any number of times; one plan must not be used by
+ *     two host threads at the same time.
+ */
+#ifndef FL_H
+#define FL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fl_plan_s *fl_plan_t;
+
+typedef enum {
+    FL_OK = 0,
+    FL_EINVAL = 1,        /* invalid argument (sizes, eps, Im w < 0, NaN ...) */
+    FL_ENOMEM = 2,        /* device or host allocation failed                 */
+    FL_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
+    FL_ETIMEOUT = 4,      /* a bounded device-side wait gave up               */
+    FL_EUNSUPPORTED = 5   /* size or parameter outside what is implemented    */
+} fl_status;
+
+typedef enum { FL_FP32 = 0, FL_FP64 = 1 } fl_precision;
+
+#define FL_MAX_LEVELS 128
+
+/* Plan parameters and per-band sizes, filled by fl_get_info. */
+typedef struct {
+    int kind;                 /* 0 = Fourier-Laplace (Alg. 2), 1 = Laplace (Alg. 1) */
+    int precision;            /* fl_precision */
+    int64_t N, M;
+    double eps;               /* target accuracy: ||f - f~||_inf <= eps ||c||_1 */
+    double eps_laplace;       /* accuracy given to the Laplace factor (eps/3 for Alg. 2) */
+    double eps_fourier;       /* accuracy given to each NFFT (eps/3) */
+    int q;                    /* interpolation rank (Definition 3.2) */
+    int levels;               /* number of dyadic levels, the paper's M (Definition 3.2) */
+    int m_w;                  /* Kaiser-Bessel window half-width (taps = 2 m_w) */
+    int sigma;                /* oversampling of every band grid (2) */
+    double y1, xi1;           /* interval ends of Definition 3.2 */
+    int64_t z0_nodes;         /* nodes with |z| < eps (returned as c_0) */
+    int n_bands_fft;          /* bands evaluated with an NFFT */
+    int n_bands_direct;       /* bands evaluated by the direct-sum kernel */
+    /* per band b = 1..levels (index 0 unused): */
+    int band_ell[FL_MAX_LEVELS];      /* l_m (first interpolated frequency band) */
+    int band_route[FL_MAX_LEVELS];    /* 0 empty, 1 NFFT, 2 direct */
+    int64_t band_nodes[FL_MAX_LEVELS];
+    int64_t band_K[FL_MAX_LEVELS];    /* frequencies with nonzero weight */
+    int64_t band_n[FL_MAX_LEVELS];    /* FFT length (oversampled grid) */
+    double model_bytes;       /* algorithmic HBM bytes of one fl_execute */
+    double scratch_bytes;     /* device memory owned by the plan */
+} fl_info;
+
+/* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
+#define FL_MAX_TIMED_KERNELS 16
+typedef struct {
+    int n_kernels;
+    char name[FL_MAX_TIMED_KERNELS][32];
+    int64_t launches[FL_MAX_TIMED_KERNELS];
+    double total_ms[FL_MAX_TIMED_KERNELS];
+    double bytes[FL_MAX_TIMED_KERNELS];   /* algorithmic bytes summed over launches */
+    int64_t total_launches;               /* every kernel launched by execute calls */
+} fl_timing;
+
+/*
+ * fl_plan -- plan Algorithm 2 (Section 4) for N coefficients and M nodes.
+ *   nodes_dev : device, M x {Re w_j, Im w_j} float64, Im w_j >= 0, finite.
+ *               Read during planning only (the plan keeps a sorted copy).
+ *   q         : interpolation rank; 0 = from eps by Definition 3.2,
+ *               q = ceil(1/2 + log_4(3/eps)) (the Laplace factor gets eps/3,
+ *               Lemma 4.1).
+ *   eps       : target accuracy in (0, 1); the result satisfies
+ *               max_j |f_j - f~_j| <= eps * sum_k |c_k| (Theorem 4.3) up to
+ *               the rounding of the chosen precision.
+ *   prec      : FL_FP32 (grids, FFT and recombination in float; phases and
+ *               barycentric differences in double) or FL_FP64.
+ * Returns FL_EINVAL for N < 1, M < 0, eps outside (0, 1), q outside [0, 40] or
+ * a node with Im w < 0 or a non-finite part; FL_EUNSUPPORTED for N > 2^23.
+ * On failure *out is NULL.
+ */
+fl_status fl_plan(fl_plan_t *out, int64_t N, int64_t M, const double *nodes_dev,
+                  int q, double eps, fl_precision prec, void *stream);
+
+/*
+ * fl_execute -- f~ ~= C c with C = (z_j^k), Algorithm 2.
+ *   c_dev : device, N complex (plan precision).
+ *   f_dev : device, M complex (plan precision), fully overwritten.
+ * Asynchronous on `stream`.
+ */
+fl_status fl_execute(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
+
+/*
+ * fl_execute_deriv -- f'_j = sum_k (2 pi i k) c_k z_j^k = d f / d w at w_j, the
+ * same Algorithm 2 applied to the k-weighted coefficients (the derivative of
+ * eq. (4.1) in w).  Same arguments and accuracy scale as fl_execute, with
+ * ||c||_1 replaced by sum_k 2 pi k |c_k|.
+ */
+fl_status fl_execute_deriv(fl_plan_t p, const void *c_dev, void *fprime_dev, void *stream);
+
+/*
+ * fl_execute_host -- fl_execute on host buffers: copies c_host (N complex) to
+ * the device, executes, copies the result to f_host (M complex) and
+ * synchronises `stream`.  Staging buffers are owned by the plan.
+ */
+fl_status fl_execute_host(fl_plan_t p, const void *c_host, void *f_host, void *stream);
+
+/*
+ * fl_adjoint -- c_out = C^* r, (C^* r)_k = sum_j conj(z_j)^k r_j, the adjoint
+ * of Algorithm 2 (Section 4, the remark after Algorithm 2): every step of the
+ * forward transform transposed and conjugated.
+ *   r_dev     : device, M complex.   c_out_dev : device, N complex, overwritten.
+ * Accuracy: |c_out - C^* r|_inf <= eps * sum_j |r_j| up to rounding.
+ */
+fl_status fl_adjoint(fl_plan_t p, const void *r_dev, void *c_out_dev, void *stream);
+
+/*
+ * fl_plan_laplace -- plan Algorithm 1 (Section 3) for the real discrete Laplace
+ * transform f_j = sum_k c_k exp(-s_j t_k).
+ *   t_dev : device, N float64 frequencies t_k >= 0.
+ *   s_dev : device, M float64 nodes s_j >= 0.
+ *   q, eps: as Definition 3.2 (the whole eps goes to the Laplace factor).
+ *   prec  : FL_FP64, or FL_FP32 (float moments/evaluation, double weights).
+ * Data is real: c and f are float64 for FL_FP64 and float32 for FL_FP32.
+ */
+fl_status fl_plan_laplace(fl_plan_t *out, int64_t N, int64_t M, const double *t_dev,
+                          const double *s_dev, int q, double eps, fl_precision prec,
+                          void *stream);
+
+/* fl_laplace_real -- f~ ~= K c (Algorithm 1), c_dev N reals, f_dev M reals. */
+fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
+
+/* Plan parameters and sizes (host call, no device work). */
+fl_status fl_get_info(fl_plan_t p, fl_info *info);
+
+/* Enable (1) or disable (0) per-kernel CUDA-event timing; resets counters. */
+fl_status fl_set_timing(fl_plan_t p, int enable);
+
+/* Read the timing counters (synchronises the events recorded so far). */
+fl_status fl_get_timing(fl_plan_t p, fl_timing *out);
+
+/* Release the plan and its device memory (synchronises the device). */
+void fl_destroy(fl_plan_t p);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *fl_last_error(void);
+
+/* Library version string. */
+const char *fl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FL_H */

@@ -1,0 +1,399 @@
+// fl_api.cu -- the C ABI of libfl.so (include/fl.h): parameter selection
+// (Definition 3.2 and Algorithm 2 of Kunis & Melzer), band sizing, plan
+// construction, execution, timing and error reporting.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+
+#include "fl_plan.cuh"
+
+namespace fl {
+
+static thread_local std::string g_err;
+
+static fl_status fail(fl_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+static fl_status cuda_fail(cudaError_t e, const char* where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? FL_ENOMEM : FL_ECUDA;
+}
+
+#define FL_CUDA(call, where)                          \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+Plan::~Plan() {
+    void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_cheb, d_D, d_grid, d_Y,
+                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_lap};
+    for (void* q : ptrs)
+        if (q) cudaFree(q);
+    for (Timer& t : timers) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+}
+
+void timer_begin(Plan& p, const char* name, double bytes, cudaStream_t st, int* slot) {
+    *slot = -1;
+    if (!p.timing) return;
+    Timer t;
+    t.name = name;
+    t.bytes = bytes;
+    if (cudaEventCreate(&t.start) != cudaSuccess) return;
+    if (cudaEventCreate(&t.stop) != cudaSuccess) {
+        cudaEventDestroy(t.start);
+        return;
+    }
+    cudaEventRecord(t.start, st);
+    p.timers.push_back(t);
+    *slot = (int)p.timers.size() - 1;
+}
+
+void timer_end(Plan& p, int slot, cudaStream_t st) {
+    if (slot >= 0) cudaEventRecord(p.timers[slot].stop, st);
+}
+
+static int ilog2_ceil(int64_t v) {
+    int l = 0;
+    while (((int64_t)1 << l) < v) ++l;
+    return l;
+}
+
+// Smallest Kaiser-Bessel half-width m whose aliasing-plus-truncation estimate
+// 4 pi (sqrt(m) + m) (1 - 1/sigma)^(1/4) exp(-2 pi m sqrt(1 - 1/sigma))
+// (the error bound of the Kaiser-Bessel NFFT) is at most eps.
+static int window_width(double eps, double sigma) {
+    const double a = sqrt(1.0 - 1.0 / sigma);
+    for (int m = 2; m <= 12; ++m) {
+        const double bound = 4.0 * M_PI * (sqrt((double)m) + m) * sqrt(a) * exp(-2.0 * M_PI * m * a);
+        if (bound <= eps) return m;
+    }
+    return 12;
+}
+
+// Parameters of Algorithm 2 (Section 4) with the error split of Lemma 4.1.
+static fl_status select_params(Plan& p, int q_in) {
+    p.eps_K = p.eps / 3.0;
+    p.eps_A = p.eps / 3.0;
+    p.q = q_in > 0 ? q_in : (int)ceil(0.5 + log(1.0 / p.eps_K) / log(4.0));
+    if (p.q > kMaxQ) return fail(FL_EUNSUPPORTED, "interpolation rank q above 40");
+    p.y1 = log(1.0 / p.eps);            // Z^0 removed: y in [0, ln(1/eps)]
+    p.xi1 = (double)(p.N - 1);          // frequencies 0..N-1
+    p.mw = window_width(p.eps_A, 2.0);
+    p.kb_b = M_PI * (2.0 - 1.0 / 2.0);
+    if (p.N == 1) {
+        p.levels = 1;
+    } else {
+        const double lv = ceil(log2(p.y1 * p.xi1 / p.eps_K)) + 1.0;
+        p.levels = (int)std::max(1.0, lv);
+    }
+    if (p.levels > 127) return fail(FL_EUNSUPPORTED, "more than 127 dyadic levels");
+    p.bands.assign(p.levels + 1, BandHost());
+    for (int b = 1; b <= p.levels; ++b) {
+        BandHost& bh = p.bands[b];
+        int64_t K;
+        if (b < p.levels) {
+            const double lg = log2(p.y1 * p.xi1) - b - log2(log(1.0 / p.eps_K));
+            bh.ell = std::max(1, (int)floor(lg) + 1);
+            bh.Lm = p.levels - b;
+            // frequencies k <= xi1 / 2^(l_m - 1) carry weight (Lemma A.2(ii))
+            K = std::min<int64_t>(p.N, (int64_t)floor(ldexp(p.xi1, 1 - bh.ell)) + 1);
+            bh.dev.nrhs = p.q;
+            const double a = ldexp(p.y1, -b);
+            bh.dev.yc = 1.5 * a;
+            bh.dev.yh = 0.5 * a;
+        } else {
+            K = p.N;            // Z_M band: kernel ~ 1, one plain NFFT
+            bh.dev.nrhs = 1;
+        }
+        const int lg = std::max(4, ilog2_ceil(K));
+        bh.dev.K = K;
+        bh.dev.Nm = (int64_t)1 << lg;
+        bh.dev.log2n = lg + 1;
+        bh.dev.n = (int64_t)1 << (lg + 1);
+        if (bh.dev.log2n > kMaxLog2n) return fail(FL_EUNSUPPORTED, "grid above 2^24 points");
+    }
+    return FL_OK;
+}
+
+static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) {
+    fl_status s = select_params(p, q);
+    if (s != FL_OK) return s;
+    const int nb = p.levels + 1;
+    FL_CUDA(cudaMalloc((void**)&p.d_bands, nb * sizeof(BandDev)), "cudaMalloc bands");
+    std::vector<BandDev> hb(nb);
+    for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
+    FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
+            "copy bands");
+    FL_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
+    FL_CUDA(cudaMalloc(&p.d_z0, 2 * sizeof(double)), "cudaMalloc z0");
+
+    // classify and sort the nodes
+    const int64_t M = p.M;
+    std::vector<int64_t> counts(nb, 0);
+    if (M > 0) {
+        FL_CUDA(cudaMalloc((void**)&p.d_ws, M * sizeof(double2)), "cudaMalloc nodes");
+        FL_CUDA(cudaMalloc((void**)&p.d_perm, M * sizeof(int32_t)), "cudaMalloc perm");
+        FL_CUDA(cudaMalloc((void**)&p.d_bandid, M), "cudaMalloc band ids");
+        uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr;
+        int32_t *vals = nullptr, *vals2 = nullptr;
+        int64_t* dcount = nullptr;
+        int* dflag = nullptr;
+        const int64_t nblk = (M + 2047) / 2048;
+        cudaError_t e = cudaSuccess;
+        auto cleanup = [&]() {
+            cudaFree(keys); cudaFree(keys2); cudaFree(hist); cudaFree(vals); cudaFree(vals2);
+            cudaFree(dcount); cudaFree(dflag);
+        };
+        if ((e = cudaMalloc((void**)&keys, M * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&keys2, M * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&vals, M * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&vals2, M * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&hist, 256 * nblk * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&dcount, nb * sizeof(int64_t))) == cudaSuccess &&
+            (e = cudaMalloc((void**)&dflag, sizeof(int))) == cudaSuccess &&
+            (e = cudaMemsetAsync(dcount, 0, nb * sizeof(int64_t), st)) == cudaSuccess &&
+            (e = cudaMemsetAsync(dflag, 0, sizeof(int), st)) == cudaSuccess &&
+            (e = launch_classify(p, nodes, keys, vals, dcount, dflag, st)) == cudaSuccess &&
+            (e = radix_sort_pairs(keys, vals, keys2, vals2, hist, M, 32, st)) == cudaSuccess &&
+            (e = launch_permute(p, nodes, keys, vals, st)) == cudaSuccess) {
+            int flag = 0;
+            e = cudaMemcpyAsync(counts.data(), dcount, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+            if (e == cudaSuccess && flag) {
+                cleanup();
+                return fail(FL_EINVAL, "fl_plan: a node has Im w < 0 or a non-finite part");
+            }
+        }
+        cleanup();
+        if (e != cudaSuccess) return cuda_fail(e, "fl_plan: node classification");
+    }
+
+    // routes, offsets and work lists
+    p.z0_nodes = counts[0];
+    int64_t off = counts[0];
+    p.grid_elems = p.D_elems = p.Y_elems = 0;
+    p.small_work.clear();
+    p.large_bands.clear();
+    for (int b = 1; b <= p.levels; ++b) {
+        BandHost& bh = p.bands[b];
+        bh.nodes = counts[b];
+        bh.node_off = off;
+        off += counts[b];
+        BandDev& d = bh.dev;
+        d.route = bh.nodes > 0 ? 1 : 0;
+        if (d.route != 1) continue;
+        d.grid_off = p.grid_elems;
+        d.D_off = p.D_elems;
+        p.grid_elems += (int64_t)d.nrhs * d.n;
+        p.D_elems += (int64_t)d.nrhs * d.K;
+        if (d.log2n <= kSmallMaxLog2) {
+            const int per = std::max(1, (int)((1 << kSmallMaxLog2) / d.n));
+            for (int s0 = 0; s0 < d.nrhs; s0 += per)
+                p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
+        } else {
+            p.large_bands.push_back(b);
+            p.Y_elems = std::max<int64_t>(p.Y_elems, (int64_t)d.nrhs * d.n);
+        }
+    }
+    for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
+    FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
+            "copy bands");
+    const size_t cs = p.prec == FL_FP64 ? 16 : 8, rs = cs / 2;
+    if (!p.small_work.empty()) {
+        FL_CUDA(cudaMalloc((void**)&p.d_small, p.small_work.size() * sizeof(SmallWork)), "cudaMalloc work");
+        FL_CUDA(cudaMemcpyAsync(p.d_small, p.small_work.data(), p.small_work.size() * sizeof(SmallWork),
+                                cudaMemcpyHostToDevice, st),
+                "copy work");
+    }
+    if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
+    if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
+    if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
+    FL_CUDA(build_tables(p, st), "fl_plan: tables");
+    FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
+    p.scratch_bytes = (double)p.grid_elems * cs + (double)p.D_elems * rs + (double)p.Y_elems * cs +
+                      (double)M * (sizeof(double2) + 5);
+    // algorithmic bytes of one execute: c once, D once, each grid written and read
+    // once per FFT pass, the nodes, and f
+    double mb = (double)p.N * cs + (double)p.D_elems * rs + (double)M * (sizeof(double2) + 5 + cs);
+    for (int b = 1; b <= p.levels; ++b) {
+        const BandDev& d = p.bands[b].dev;
+        if (d.route != 1) continue;
+        const double g = (double)d.nrhs * d.n * cs;
+        mb += (d.log2n <= kSmallMaxLog2) ? g : 3.0 * g;   // small: write; large: Y write+read, grid write
+        mb += std::min<double>(g, (double)p.bands[b].nodes * d.nrhs * 2 * p.mw * cs);   // gather
+    }
+    p.model_bytes = mb;
+    return FL_OK;
+}
+
+}  // namespace fl
+
+using namespace fl;
+
+struct fl_plan_s {
+    Plan p;
+};
+
+extern "C" {
+
+const char* fl_last_error(void) { return g_err.c_str(); }
+
+const char* fl_version(void) { return "fastfl 0.1 (sm_103a)"; }
+
+fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q, double eps,
+                  fl_precision prec, void* stream) {
+    g_err.clear();
+    if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
+    *out = nullptr;
+    if (N < 1 || M < 0) return fail(FL_EINVAL, "fl_plan: need N >= 1 and M >= 0");
+    if (N > ((int64_t)1 << 23)) return fail(FL_EUNSUPPORTED, "fl_plan: N above 2^23");
+    if (M > ((int64_t)1 << 31) - 1) return fail(FL_EUNSUPPORTED, "fl_plan: M above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(FL_EINVAL, "fl_plan: eps must lie in (0, 1)");
+    if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan: q must lie in [0, 40]");
+    if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan: unknown precision");
+    if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return fail(FL_ENOMEM, "fl_plan: host allocation");
+    h->p.kind = 0;
+    h->p.prec = prec;
+    h->p.N = N;
+    h->p.M = M;
+    h->p.eps = eps;
+    fl_status s = plan_flt(h->p, nodes_dev, q, (cudaStream_t)stream);
+    if (s != FL_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+fl_status fl_execute(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute: not a Fourier-Laplace plan");
+    if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute: NULL buffer");
+    cudaError_t e = run_forward(h->p, c_dev, f_dev, false, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_execute");
+    return FL_OK;
+}
+
+fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_deriv: not a Fourier-Laplace plan");
+    if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_deriv: NULL buffer");
+    cudaError_t e = run_forward(h->p, c_dev, f_dev, true, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_execute_deriv");
+    return FL_OK;
+}
+
+fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_host: not a Fourier-Laplace plan");
+    Plan& p = h->p;
+    if (!c_host || (p.M > 0 && !f_host)) return fail(FL_EINVAL, "fl_execute_host: NULL buffer");
+    const size_t cs = p.prec == FL_FP64 ? 16 : 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p.d_stage_c) FL_CUDA(cudaMalloc(&p.d_stage_c, p.N * cs), "cudaMalloc staging");
+    if (!p.d_stage_f && p.M > 0) FL_CUDA(cudaMalloc(&p.d_stage_f, p.M * cs), "cudaMalloc staging");
+    FL_CUDA(cudaMemcpyAsync(p.d_stage_c, c_host, p.N * cs, cudaMemcpyHostToDevice, st), "copy c");
+    FL_CUDA(run_forward(p, p.d_stage_c, p.d_stage_f, false, st), "fl_execute_host");
+    if (p.M > 0)
+        FL_CUDA(cudaMemcpyAsync(f_host, p.d_stage_f, p.M * cs, cudaMemcpyDeviceToHost, st), "copy f");
+    FL_CUDA(cudaStreamSynchronize(st), "fl_execute_host: synchronise");
+    return FL_OK;
+}
+
+fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_adjoint: not a Fourier-Laplace plan");
+    if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
+    cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
+    return FL_OK;
+}
+
+fl_status fl_get_info(fl_plan_t h, fl_info* info) {
+    if (!h || !info) return fail(FL_EINVAL, "fl_get_info: NULL argument");
+    const Plan& p = h->p;
+    memset(info, 0, sizeof(*info));
+    info->kind = p.kind;
+    info->precision = p.prec;
+    info->N = p.N;
+    info->M = p.M;
+    info->eps = p.eps;
+    info->eps_laplace = p.eps_K;
+    info->eps_fourier = p.eps_A;
+    info->q = p.q;
+    info->levels = p.levels;
+    info->m_w = p.mw;
+    info->sigma = 2;
+    info->y1 = p.y1;
+    info->xi1 = p.xi1;
+    info->z0_nodes = p.z0_nodes;
+    for (int b = 1; b < (int)p.bands.size() && b < FL_MAX_LEVELS; ++b) {
+        const BandHost& bh = p.bands[b];
+        info->band_ell[b] = bh.ell;
+        info->band_route[b] = bh.dev.route;
+        info->band_nodes[b] = bh.nodes;
+        info->band_K[b] = bh.dev.K;
+        info->band_n[b] = bh.dev.n;
+        if (bh.dev.route == 1) ++info->n_bands_fft;
+        if (bh.dev.route == 2) ++info->n_bands_direct;
+    }
+    info->model_bytes = p.model_bytes;
+    info->scratch_bytes = p.scratch_bytes;
+    return FL_OK;
+}
+
+fl_status fl_set_timing(fl_plan_t h, int enable) {
+    if (!h) return fail(FL_EINVAL, "fl_set_timing: NULL plan");
+    Plan& p = h->p;
+    for (Timer& t : p.timers) {
+        cudaEventDestroy(t.start);
+        cudaEventDestroy(t.stop);
+    }
+    p.timers.clear();
+    p.timing = enable != 0;
+    p.launches = 0;
+    return FL_OK;
+}
+
+fl_status fl_get_timing(fl_plan_t h, fl_timing* out) {
+    if (!h || !out) return fail(FL_EINVAL, "fl_get_timing: NULL argument");
+    Plan& p = h->p;
+    memset(out, 0, sizeof(*out));
+    for (Timer& t : p.timers) {
+        cudaError_t e = cudaEventSynchronize(t.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "fl_get_timing");
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, t.start, t.stop);
+        if (e != cudaSuccess) return cuda_fail(e, "fl_get_timing");
+        int slot = -1;
+        for (int i = 0; i < out->n_kernels; ++i)
+            if (t.name == out->name[i]) slot = i;
+        if (slot < 0) {
+            if (out->n_kernels >= FL_MAX_TIMED_KERNELS) continue;
+            slot = out->n_kernels++;
+            snprintf(out->name[slot], sizeof(out->name[slot]), "%s", t.name.c_str());
+        }
+        out->launches[slot] += 1;
+        out->total_ms[slot] += ms;
+        out->bytes[slot] += t.bytes;
+    }
+    out->total_launches = p.launches;
+    return FL_OK;
+}
+
+void fl_destroy(fl_plan_t h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+}  // extern "C"

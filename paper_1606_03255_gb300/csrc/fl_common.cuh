@@ -1,0 +1,161 @@
+// fl_common.cuh -- device helpers shared by the kernels of libfl.so:
+// complex arithmetic, sincospi by precision, the per-band descriptor, and the
+// shared-memory Stockham FFT used by every NFFT (Kunis & Melzer, Section 4:
+// each band's Fourier factor A~ is one NFFT, i.e. deconvolution, one FFT of
+// the oversampled grid, and window interpolation).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fl {
+
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using C_t = typename cplx<T>::type;
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { return {a.x * s, a.y * s}; }
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+
+__device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+
+// exp(i * pi * x)
+template <typename T> __device__ __forceinline__ C_t<T> expipi(T x) {
+    T s, c;
+    sincospi_t(x, &s, &c);
+    return {c, s};
+}
+
+// Per-band descriptor (bands 1..levels; band 0 is Z^0).  Built on the host at
+// plan time, read by every kernel of the forward and adjoint transforms.
+struct BandDev {
+    int64_t n;         // oversampled FFT length n_m = 2 N_m (0: band has no grid)
+    int64_t Nm;        // NFFT bandwidth N_m (power of two >= K)
+    int64_t K;         // frequencies 0..K-1 carry nonzero weight
+    int64_t grid_off;  // element offset of the band's grids (nrhs x n) in the grid buffer
+    int64_t D_off;     // element offset of the band's weight table (nrhs x K)
+    int nrhs;          // right-hand sides: q for interpolated bands, 1 for Y_M
+    int log2n;
+    int route;         // 0 empty, 1 NFFT, 2 direct sum
+    int pad;
+    double yc, yh;     // band Y_m = [yc - yh, yc + yh] (paper's y), for barycentric weights
+};
+
+// ---------------------------------------------------------------------------
+// Shared-memory Stockham FFT, radix 8/4/2, 8 elements per thread.
+//
+// Computes X[l] = sum_i x[i] exp(SIGN * 2 pi i * i l / L) in place on a
+// contiguous smem array of length L = 2^log2L (8 <= L), using nthr = L/8
+// threads numbered t = 0..nthr-1.  Each stage with radix R, span Ns takes
+// job jj = (R-point butterfly) reading x[jj + r L/R], twiddling by
+// w^(r k), w = exp(SIGN 2 pi i / (Ns R)), k = jj mod Ns, and writing to
+// (jj - k) R + k + r Ns: the self-sorting Stockham order, so the result is in
+// natural order.  Every thread of the block must call it (it synchronises).
+
+template <int SIGN, typename C> __device__ __forceinline__ C mul_i(C a) {
+    // a * (SIGN * i)
+    return SIGN > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft2(C& a0, C& a1) {
+    C t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+template <int SIGN, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    C u0 = cadd(a0, a2), u1 = csub(a0, a2);
+    C u2 = cadd(a1, a3), u3 = mul_i<SIGN>(csub(a1, a3));
+    a0 = cadd(u0, u2);
+    a2 = csub(u0, u2);
+    a1 = cadd(u1, u3);
+    a3 = csub(u1, u3);
+}
+
+template <int SIGN, typename T> __device__ __forceinline__ void dft8(C_t<T>* a) {
+    using C = C_t<T>;
+    const T h = (T)0.70710678118654752440084436210485;
+    C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+    C o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+    dft4<SIGN>(e0, e1, e2, e3);
+    dft4<SIGN>(o0, o1, o2, o3);
+    // o1 *= w8, o2 *= w8^2 = SIGN i, o3 *= w8^3, w8 = (1 + SIGN i)/sqrt 2
+    C t1 = {(o1.x - SIGN * o1.y) * h, (o1.y + SIGN * o1.x) * h};
+    C t2 = mul_i<SIGN>(o2);
+    C t3 = {(-o3.x - SIGN * o3.y) * h, (-o3.y + SIGN * o3.x) * h};
+    a[0] = cadd(e0, o0);
+    a[4] = csub(e0, o0);
+    a[1] = cadd(e1, t1);
+    a[5] = csub(e1, t1);
+    a[2] = cadd(e2, t2);
+    a[6] = csub(e2, t2);
+    a[3] = cadd(e3, t3);
+    a[7] = csub(e3, t3);
+}
+
+template <int R, int SIGN, typename T>
+__device__ __forceinline__ void fft_stage(C_t<T>* buf, int L, int Ns, int t, int nthr, bool active) {
+    using C = C_t<T>;
+    constexpr int J = 8 / R;
+    C v[8];
+    if (active) {
+#pragma unroll
+        for (int jb = 0; jb < J; ++jb) {
+            const int jj = t + jb * nthr;
+            const int k = jj & (Ns - 1);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[jj + r * (L / R)];
+            if (Ns > 1) {
+                C w1 = expipi<T>((T)(2 * SIGN) * (T)k / (T)(Ns * R));
+                C w = w1;
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    v[jb * R + r] = cmul(v[jb * R + r], w);
+                    w = cmul(w, w1);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+        for (int jb = 0; jb < J; ++jb) {
+            C* a = v + jb * R;
+            if (R == 8) dft8<SIGN, T>(a);
+            if (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
+            if (R == 2) dft2<SIGN>(a[0], a[1]);
+            const int jj = t + jb * nthr;
+            const int k = jj & (Ns - 1);
+            const int base = (jj - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[base + r * Ns] = a[r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int SIGN, typename T>
+__device__ __forceinline__ void fft_smem(C_t<T>* buf, int log2L, int t, bool active) {
+    const int L = 1 << log2L;
+    const int nthr = L >> 3;
+    int Ns = 1, rem = log2L;
+    while (rem >= 3) {
+        fft_stage<8, SIGN, T>(buf, L, Ns, t, nthr, active);
+        Ns <<= 3;
+        rem -= 3;
+    }
+    if (rem == 2) fft_stage<4, SIGN, T>(buf, L, Ns, t, nthr, active);
+    if (rem == 1) fft_stage<2, SIGN, T>(buf, L, Ns, t, nthr, active);
+}
+
+}  // namespace fl

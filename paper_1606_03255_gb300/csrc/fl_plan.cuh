@@ -1,0 +1,108 @@
+// fl_plan.cuh -- host-side plan object and the kernel launchers shared by the
+// translation units of libfl.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "fl.h"
+#include "fl_common.cuh"
+
+namespace fl {
+
+constexpr int kMaxQ = 40;
+constexpr int kMaxMw = 16;
+constexpr int kSmallMaxLog2 = 12;   // grids up to 4096 points: one CTA per FFT
+constexpr int kMaxLog2n = 24;       // two passes of <= 4096 points each
+
+// Work item of the small-grid FFT kernel: FFTs nfft (one per right-hand side
+// s0 .. s0+nfft-1) of band `band`, all of length 2^log2n.
+struct SmallWork {
+    int band;
+    int s0;
+    int nfft;
+    int log2n;
+};
+
+// Per-band plan data on the host.
+struct BandHost {
+    int ell = 0, Lm = 0;    // l_m, L_m (Definition 3.2); 0 for the Y_M band
+    int64_t nodes = 0;      // nodes of the band
+    int64_t node_off = 0;   // first node of the band in sorted order
+    BandDev dev{};
+};
+
+struct Timer {
+    std::string name;
+    cudaEvent_t start, stop;
+    double bytes;
+};
+
+struct Plan {
+    int kind = 0;           // 0 Fourier-Laplace, 1 Laplace
+    fl_precision prec = FL_FP32;
+    int64_t N = 0, M = 0;
+    int q = 0, levels = 1, mw = 0;
+    double eps = 0, eps_K = 0, eps_A = 0, y1 = 0, xi1 = 0, kb_b = 0;
+    std::vector<BandHost> bands;          // index 0 = Z^0, 1..levels
+    int64_t z0_nodes = 0;
+    int64_t grid_elems = 0, D_elems = 0, Y_elems = 0;
+    std::vector<SmallWork> small_work;
+    std::vector<int> large_bands;
+
+    // device memory
+    double2* d_ws = nullptr;       // nodes in sorted order (Re w, Im w)
+    int32_t* d_perm = nullptr;     // sorted position -> original index
+    uint8_t* d_bandid = nullptr;   // band of each sorted node
+    BandDev* d_bands = nullptr;    // levels + 1 descriptors
+    SmallWork* d_small = nullptr;
+    double* d_cheb = nullptr;      // t_s (q), lambda_s (q)
+    void* d_D = nullptr;           // weight tables (T)
+    void* d_grid = nullptr;        // band grids (complex T)
+    void* d_Y = nullptr;           // four-step intermediate (complex T)
+    void* d_stage_c = nullptr;     // staging for fl_execute_host
+    void* d_stage_f = nullptr;
+    void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
+    double scratch_bytes = 0;
+
+    // Laplace (Algorithm 1)
+    double* d_t = nullptr;
+    double* d_s = nullptr;
+    void* d_lap = nullptr;         // moments and partial sums
+    int lap_blocks = 0;
+
+    // timing
+    bool timing = false;
+    std::vector<Timer> timers;
+    int64_t launches = 0;
+    double model_bytes = 0;
+
+    ~Plan();
+};
+
+// Launchers (fl_nodes.cu)
+cudaError_t launch_classify(Plan& p, const double* nodes, uint32_t* keys, int32_t* vals,
+                            int64_t* counts, int* flag, cudaStream_t st);
+cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
+                             int32_t* vals_tmp, uint32_t* hist, int64_t n, int key_bits,
+                             cudaStream_t st);
+cudaError_t launch_permute(Plan& p, const double* nodes, const uint32_t* keys,
+                           const int32_t* vals, cudaStream_t st);
+
+// Launchers (fl_transform.cu)
+cudaError_t build_tables(Plan& p, cudaStream_t st);
+cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st);
+cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
+
+// Launchers (fl_laplace.cu)
+cudaError_t laplace_prepare(Plan& p, cudaStream_t st);
+cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st);
+
+// Timing helpers (fl_api.cu)
+void timer_begin(Plan& p, const char* name, double bytes, cudaStream_t st, int* slot);
+void timer_end(Plan& p, int slot, cudaStream_t st);
+
+}  // namespace fl

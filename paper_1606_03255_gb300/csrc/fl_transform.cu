@@ -1,0 +1,625 @@
+// fl_transform.cu -- the kernels of Algorithm 2 (Kunis & Melzer, Section 4) and
+// of its adjoint.
+//
+// For a band Y_m of nodes the paper evaluates (Algorithm 2, Lemma 4.2)
+//
+//   f~_j = sum_s L_s^{Y_m}(y_j) * [A~ (c (.) W_{.,s})](x_j),
+//   W_{k,s} = sum_r K^{Y_m,Omega_l}_{s r} L_r^{Omega_l}(k)   for l_m <= l(k) <= L_m,
+//   W_{k,s} = 1  for l(k) > L_m (region (iv); folded into every s since
+//               sum_s L_s = 1),   W_{k,s} = 0 for l(k) < l_m (region (ii)),
+//
+// where A~ is one NFFT with q right-hand sides.  Each NFFT here is:
+//   deconvolution  g^_k' = c_k W_{k,s} / Phi(k'/n)      (folded into table D)
+//   FFT            g_l = sum_k' g^_k' exp(+2 pi i k' l / n)
+//   window gather  s(x) = sum_l g_l phi(n x - l),  Kaiser-Bessel phi, 2 m_w taps
+// with centred frequencies k' = k - N_m/2 and the shift exp(pi i N_m x) applied
+// after the gather.  The band's q results are recombined with the barycentric
+// weights L_s^{Y_m}(y_j) (Section 2) in the same gather kernel.
+#include <math.h>
+
+#include "fl_plan.cuh"
+
+namespace fl {
+
+constexpr double kPi = 3.141592653589793238462643383279;
+constexpr double kTwoPiD = 6.283185307179586476925286766559;
+
+// ---------------------------------------------------------------------------
+// Tables (plan time).
+
+__device__ __forceinline__ int band_of_freq(double k, double xi1, int levels) {
+    if (levels <= 1) return 1;
+    if (k > ldexp(xi1, -1)) return 1;
+    if (!(k > ldexp(xi1, -(levels - 1)))) return levels;
+    int b = (int)floor(log2(xi1 / k)) + 1;
+    b = max(1, min(b, levels - 1));
+    while (b > 1 && k > ldexp(xi1, -(b - 1))) --b;
+    while (b < levels - 1 && !(k > ldexp(xi1, -b))) ++b;
+    return b;
+}
+
+// Chebyshev points t_s = cos((2s+1) pi / (2q)) and barycentric weights
+// lambda_s = (-1)^s sin((2s+1) pi / (2q)) (Section 2).
+__global__ void k_cheb(int q, double* cheb) {
+    const int s = threadIdx.x;
+    if (s >= q) return;
+    double sn, cs;
+    sincospi((2.0 * s + 1.0) / (2.0 * q), &sn, &cs);
+    cheb[s] = cs;
+    cheb[q + s] = (s & 1) ? -sn : sn;
+}
+
+// K^{Y_m,Omega_l}_{s r} = exp(-y_s^{Y_m} xi_r^{Omega_l}) for l = l_m..L_m
+// (Definition 3.2), written as Kt[(l - l_m) q^2 + s q + r].
+__global__ void k_coupling(double y1, double xi1, int m, int ellm, int Lm, int q,
+                           const double* __restrict__ cheb, double* __restrict__ Kt) {
+    const int nl = Lm - ellm + 1;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)nl * q * q) return;
+    const int r = (int)(i % q), s = (int)((i / q) % q), l = ellm + (int)(i / ((int64_t)q * q));
+    const double ay = ldexp(y1, -m), ax = ldexp(xi1, -l);
+    const double ys = 1.5 * ay + 0.5 * ay * cheb[s];
+    const double xr = 1.5 * ax + 0.5 * ax * cheb[r];
+    Kt[i] = exp(-ys * xr);
+}
+
+// D[s K + k] = W_{k,s} / Phi(k'/n), k' = k - N_m/2, with the Kaiser-Bessel
+// transform Phi(nu) = pi I_0(m_w sqrt(b^2 - (2 pi nu)^2)) (window in grid units).
+template <typename T>
+__global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int levels,
+                          const double* __restrict__ cheb, const double* __restrict__ Kt,
+                          int mw, double kb_b, T* __restrict__ D) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= B.K) return;
+    const double nu = (double)(k - B.Nm / 2) / (double)B.n;
+    const double arg = kb_b * kb_b - (kTwoPiD * nu) * (kTwoPiD * nu);
+    const double inv_phi = 1.0 / (kPi * cyl_bessel_i0((double)mw * sqrt(fmax(arg, 0.0))));
+    T* Dk = D + B.D_off;
+    if (B.nrhs == 1) {
+        Dk[k] = (T)inv_phi;
+        return;
+    }
+    const int l = band_of_freq((double)k, xi1, levels);
+    if (l > Lm) {   // region (iv): kernel ~ 1
+        for (int s = 0; s < q; ++s) Dk[(int64_t)s * B.K + k] = (T)inv_phi;
+        return;
+    }
+    if (l < ellm) {   // region (ii): kernel ~ 0 (not reached: k < K)
+        for (int s = 0; s < q; ++s) Dk[(int64_t)s * B.K + k] = (T)0;
+        return;
+    }
+    // Lagrange weights L_r^{Omega_l}(k), barycentric form, tau in [-1, 1]
+    const double ax = ldexp(xi1, -l);
+    const double tau = ((double)k - 1.5 * ax) / (0.5 * ax);
+    double Lr[kMaxQ];
+    int hit = -1;
+    double den = 0.0;
+    for (int r = 0; r < q; ++r) {
+        const double d = tau - cheb[r];
+        if (d == 0.0) hit = r;
+        Lr[r] = cheb[q + r] / d;
+        den += Lr[r];
+    }
+    for (int r = 0; r < q; ++r) Lr[r] = (hit >= 0) ? (r == hit ? 1.0 : 0.0) : Lr[r] / den;
+    const double* Kb = Kt + (int64_t)(l - ellm) * q * q;
+    for (int s = 0; s < q; ++s) {
+        double W = 0.0;
+        for (int r = 0; r < q; ++r) W += Kb[s * q + r] * Lr[r];
+        Dk[(int64_t)s * B.K + k] = (T)(W * inv_phi);
+    }
+}
+
+template <typename T>
+static cudaError_t build_tables_t(Plan& p, cudaStream_t st) {
+    double* Kt = nullptr;
+    cudaError_t e = cudaSuccess;
+    k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb);
+    int64_t kt_max = 0;
+    for (int b = 1; b <= p.levels; ++b) {
+        const BandHost& bh = p.bands[b];
+        if (bh.dev.route != 1 || bh.dev.nrhs == 1) continue;
+        kt_max = std::max<int64_t>(kt_max, (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q);
+    }
+    if (kt_max > 0) {
+        e = cudaMallocAsync((void**)&Kt, kt_max * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+    }
+    for (int b = 1; b <= p.levels; ++b) {
+        const BandHost& bh = p.bands[b];
+        if (bh.dev.route != 1) continue;
+        if (bh.dev.nrhs > 1) {
+            const int64_t nk = (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q;
+            k_coupling<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(p.y1, p.xi1, b, bh.ell, bh.Lm,
+                                                                     p.q, p.d_cheb, Kt);
+        }
+        k_weights<T><<<(unsigned)((bh.dev.K + 255) / 256), 256, 0, st>>>(
+            bh.dev, bh.ell, bh.Lm, p.q, p.xi1, p.levels, p.d_cheb, Kt, p.mw, p.kb_b, (T*)p.d_D);
+    }
+    e = cudaGetLastError();
+    if (Kt) {
+        cudaError_t e2 = cudaFreeAsync(Kt, st);
+        if (e == cudaSuccess) e = e2;
+    }
+    return e;
+}
+
+cudaError_t build_tables(Plan& p, cudaStream_t st) {
+    return p.prec == FL_FP64 ? build_tables_t<double>(p, st) : build_tables_t<float>(p, st);
+}
+
+// ---------------------------------------------------------------------------
+// Forward input: grid index i in [0, n) holds frequency k' = i (i < n/2) or
+// i - n, i.e. k = k' + N_m/2; value c_k D[s][k] for 0 <= k < K, else 0.
+template <typename T, bool DERIV>
+__device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
+                                             const C_t<T>* __restrict__ c,
+                                             const T* __restrict__ D) {
+    const int64_t kp = (i < (B.n >> 1)) ? i : i - B.n;
+    const int64_t k = kp + (B.Nm >> 1);
+    if (k < 0 || k >= B.K) return C_t<T>{(T)0, (T)0};
+    const T d = D[B.D_off + (int64_t)s * B.K + k];
+    C_t<T> v = c[k];
+    if (DERIV) {   // (2 pi i k) c_k
+        const T w = (T)(kTwoPiD * (double)k);
+        v = C_t<T>{-v.y * w, v.x * w};
+    }
+    return C_t<T>{v.x * d, v.y * d};
+}
+
+// One CTA per work item: nfft FFTs of one band (one per right-hand side).
+// MODE 0: input generated from c and D (forward), written to the band grid.
+// MODE 1: input read from the band grid and transformed in place (adjoint).
+template <typename T, int SIGN, int MODE, bool DERIV>
+__global__ void __launch_bounds__(512) k_small_fft(const SmallWork* __restrict__ work,
+                                                   const BandDev* __restrict__ bands,
+                                                   const C_t<T>* __restrict__ c,
+                                                   const T* __restrict__ D,
+                                                   C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const SmallWork wk = work[blockIdx.x];
+    const BandDev B = bands[wk.band];
+    const int L = 1 << wk.log2n;
+    const int nthr = L >> 3;
+    const int f = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const bool active = f < wk.nfft;
+    const int s = wk.s0 + f;
+    C* buf = sm + (int64_t)f * L;
+    C* g = grid + B.grid_off + (int64_t)s * L;
+    if (active) {
+        for (int e = t; e < L; e += nthr)
+            buf[e] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c, D) : g[e];
+    }
+    __syncthreads();
+    fft_smem<SIGN, T>(buf, wk.log2n, t, active);
+    if (active)
+        for (int e = t; e < L; e += nthr) g[e] = buf[e];
+}
+
+// Four-step FFT of length n = n1 n2, pass 1: for a tile of TC columns i1, the
+// length-n2 FFTs over i2 of x[i1 + n1 i2], twiddled by exp(SIGN 2 pi i i1 l2/n),
+// stored to Y[l2 n1 + i1].
+template <typename T, int SIGN, int MODE, bool DERIV>
+__global__ void __launch_bounds__(1024) k_fft_pass1(BandDev B, int rhs0, int log2n1, int log2n2,
+                                                    int TC, const C_t<T>* __restrict__ c,
+                                                    const T* __restrict__ D,
+                                                    const C_t<T>* __restrict__ src,
+                                                    C_t<T>* __restrict__ Y) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int n1 = 1 << log2n1, n2 = 1 << log2n2;
+    const int ld = n2 + 1;
+    const int s = rhs0 + blockIdx.y;
+    const int64_t n = (int64_t)n1 * n2;
+    const int i1b = blockIdx.x * TC;
+    const C* in = src + B.grid_off + (int64_t)s * n;
+    for (int idx = threadIdx.x; idx < TC * n2; idx += blockDim.x) {
+        const int col = idx % TC, i2 = idx / TC;
+        const int64_t i = (int64_t)(i1b + col) + (int64_t)n1 * i2;
+        sm[col * ld + i2] = (MODE == 0) ? prep_value<T, DERIV>(i, B, s, c, D) : in[i];
+    }
+    __syncthreads();
+    const int nthr = n2 >> 3;
+    fft_smem<SIGN, T>(sm + (threadIdx.x / nthr) * ld, log2n2, threadIdx.x % nthr, true);
+    C* out = Y + (int64_t)blockIdx.y * n;
+    for (int idx = threadIdx.x; idx < TC * n2; idx += blockDim.x) {
+        const int col = idx % TC, l2 = idx / TC;
+        const int64_t i1 = i1b + col;
+        int64_t e = (i1 * l2) & (n - 1);
+        if (e >= n / 2) e -= n;
+        const C w = expipi<T>((T)((double)(2 * SIGN) * (double)e / (double)n));
+        out[(int64_t)l2 * n1 + i1] = cmul(sm[col * ld + l2], w);
+    }
+}
+
+// Pass 2: for a tile of TR rows l2, the length-n1 FFTs over i1 of Y[l2 n1 + i1],
+// stored to X[l2 + n2 l1] (natural order of the length-n transform).
+template <typename T, int SIGN>
+__global__ void __launch_bounds__(1024) k_fft_pass2(BandDev B, int rhs0, int log2n1, int log2n2,
+                                                    int TR, const C_t<T>* __restrict__ Y,
+                                                    C_t<T>* __restrict__ dst) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int n1 = 1 << log2n1, n2 = 1 << log2n2;
+    const int ld = n1 + 1;
+    const int s = rhs0 + blockIdx.y;
+    const int64_t n = (int64_t)n1 * n2;
+    const int l2b = blockIdx.x * TR;
+    const C* in = Y + (int64_t)blockIdx.y * n;
+    for (int idx = threadIdx.x; idx < TR * n1; idx += blockDim.x) {
+        const int row = idx / n1, i1 = idx % n1;
+        sm[row * ld + i1] = in[(int64_t)(l2b + row) * n1 + i1];
+    }
+    __syncthreads();
+    const int nthr = n1 >> 3;
+    fft_smem<SIGN, T>(sm + (threadIdx.x / nthr) * ld, log2n1, threadIdx.x % nthr, true);
+    C* out = dst + B.grid_off + (int64_t)s * n;
+    for (int idx = threadIdx.x; idx < TR * n1; idx += blockDim.x) {
+        const int row = idx % TR, l1 = idx / TR;
+        out[(int64_t)(l2b + row) + (int64_t)n2 * l1] = sm[row * ld + l1];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Window and barycentric weights of one node.
+
+// Kaiser-Bessel window in grid units, phi(t) = sinh(b sqrt(m^2 - t^2)) / sqrt(m^2 - t^2),
+// |t| <= m (limit b at |t| = m).
+template <typename T> __device__ __forceinline__ T kb_window(T t, T m, T b) {
+    const T s2 = m * m - t * t;
+    if (!(s2 > (T)0)) return b;
+    const T r = sqrt(s2);
+    return sinh(b * r) / r;
+}
+
+// Barycentric weights of y in Y_m = [yc - yh, yc + yh]: tau - t_s in double (the
+// cancellation-prone step), the rest in T.  Returns in Ls[0..q-1].
+template <typename T>
+__device__ __forceinline__ void bary_weights(double y, const BandDev& B, int q,
+                                             const double* __restrict__ cheb, T* Ls) {
+    const double tau = (y - B.yc) / B.yh;
+    T den = 0;
+    int hit = -1;
+    for (int s = 0; s < q; ++s) {
+        const double d = tau - cheb[s];
+        if (d == 0.0) hit = s;
+        Ls[s] = (T)cheb[q + s] / (T)d;
+        den += Ls[s];
+    }
+    const T inv = (T)1 / den;
+    for (int s = 0; s < q; ++s) Ls[s] = (hit >= 0) ? (s == hit ? (T)1 : (T)0) : Ls[s] * inv;
+}
+
+// Gather + barycentric recombination + centring shift, one thread per node in
+// sorted order; writes f[perm[i]].  Z^0 nodes (band 0) receive c_0.
+template <typename T, int MW>
+__global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __restrict__ ws,
+                                                const int32_t* __restrict__ perm,
+                                                const uint8_t* __restrict__ bandid,
+                                                const BandDev* __restrict__ bands,
+                                                const C_t<T>* __restrict__ grid,
+                                                const double* __restrict__ cheb, int q, T kb_b,
+                                                const C_t<T>* __restrict__ c, int deriv,
+                                                C_t<T>* __restrict__ f) {
+    using C = C_t<T>;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int b = bandid[i];
+    const int32_t j = perm[i];
+    if (b == 0) {
+        f[j] = deriv ? C{(T)0, (T)0} : c[0];
+        return;
+    }
+    const BandDev B = bands[b];
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double t0 = (double)B.n * x;
+    const double u = floor(t0);
+    const T fr = (T)(t0 - u);
+    const int64_t lo = (int64_t)u - (MW - 1);
+    T phi[2 * MW];
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+    const int64_t nmask = B.n - 1;
+    const C* g = grid + B.grid_off;
+    C acc = {(T)0, (T)0};
+    if (B.nrhs == 1) {
+#pragma unroll
+        for (int t = 0; t < 2 * MW; ++t) {
+            const C v = g[(lo + t) & nmask];
+            acc.x += phi[t] * v.x;
+            acc.y += phi[t] * v.y;
+        }
+    } else {
+        T Ls[kMaxQ];
+        bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
+        for (int s = 0; s < q; ++s) {
+            const C* gs = g + (int64_t)s * B.n;
+            C a = {(T)0, (T)0};
+#pragma unroll
+            for (int t = 0; t < 2 * MW; ++t) {
+                const C v = gs[(lo + t) & nmask];
+                a.x += phi[t] * v.x;
+                a.y += phi[t] * v.y;
+            }
+            acc.x += Ls[s] * a.x;
+            acc.y += Ls[s] * a.y;
+        }
+    }
+    // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
+    double ph = (double)(B.Nm >> 1) * x;
+    ph -= floor(ph);
+    if (ph >= 0.5) ph -= 1.0;
+    f[j] = cmul(acc, expipi<T>((T)(2.0 * ph)));
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint: spread (transpose of the gather), FFT with sign -, combine.
+
+template <typename T, int MW>
+__global__ void __launch_bounds__(256) k_spread(int64_t M, int64_t z0, const double2* __restrict__ ws,
+                                                const int32_t* __restrict__ perm,
+                                                const uint8_t* __restrict__ bandid,
+                                                const BandDev* __restrict__ bands,
+                                                const C_t<T>* __restrict__ r,
+                                                const double* __restrict__ cheb, int q, T kb_b,
+                                                C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    const int64_t i = z0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int b = bandid[i];
+    const BandDev B = bands[b];
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double t0 = (double)B.n * x;
+    const double u = floor(t0);
+    const T fr = (T)(t0 - u);
+    const int64_t lo = (int64_t)u - (MW - 1);
+    double ph = (double)(B.Nm >> 1) * x;
+    ph -= floor(ph);
+    if (ph >= 0.5) ph -= 1.0;
+    const C rv = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));   // r_j exp(-2 pi i (N_m/2) x_j)
+    T phi[2 * MW];
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+    const int64_t nmask = B.n - 1;
+    C* g = grid + B.grid_off;
+    T Ls[kMaxQ];
+    int nr = B.nrhs;
+    if (nr > 1) bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
+    else Ls[0] = (T)1;
+    for (int s = 0; s < nr; ++s) {
+        C* gs = g + (int64_t)s * B.n;
+        const C a = cscale(rv, Ls[s]);
+#pragma unroll
+        for (int t = 0; t < 2 * MW; ++t) {
+            C* dst = gs + ((lo + t) & nmask);
+            atomicAdd(&dst->x, phi[t] * a.x);
+            atomicAdd(&dst->y, phi[t] * a.y);
+        }
+    }
+}
+
+// Sum of r over the Z^0 nodes (the first z0 sorted nodes): c_out[0] gets it.
+template <typename T>
+__global__ void k_z0_sum(int64_t z0, const int32_t* __restrict__ perm,
+                         const C_t<T>* __restrict__ r, C_t<T>* __restrict__ out) {
+    __shared__ T sx[256], sy[256];
+    T ax = 0, ay = 0;
+    for (int64_t i = threadIdx.x; i < z0; i += 256) {
+        const C_t<T> v = r[perm[i]];
+        ax += v.x;
+        ay += v.y;
+    }
+    sx[threadIdx.x] = ax;
+    sy[threadIdx.x] = ay;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sx[threadIdx.x] += sx[threadIdx.x + h];
+            sy[threadIdx.x] += sy[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = C_t<T>{sx[0], sy[0]};
+}
+
+// c_out[k] = [k == 0] z0sum + sum_bands sum_s D[s][k] b_s[(k - N_m/2) mod n].
+template <typename T>
+__global__ void k_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
+                          const T* __restrict__ D, const C_t<T>* __restrict__ grid,
+                          const C_t<T>* __restrict__ z0sum, C_t<T>* __restrict__ cout) {
+    using C = C_t<T>;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    C acc = (k == 0) ? *z0sum : C{(T)0, (T)0};
+    for (int b = 1; b <= levels; ++b) {
+        const BandDev B = bands[b];
+        if (B.route != 1 || k >= B.K) continue;
+        const int64_t i = (k - (B.Nm >> 1)) & (B.n - 1);
+        const T* Dk = D + B.D_off + k;
+        const C* g = grid + B.grid_off + i;
+        for (int s = 0; s < B.nrhs; ++s) {
+            const T d = Dk[(int64_t)s * B.K];
+            const C v = g[(int64_t)s * B.n];
+            acc.x += d * v.x;
+            acc.y += d * v.y;
+        }
+    }
+    cout[k] = acc;
+}
+
+// ---------------------------------------------------------------------------
+// Orchestration.
+
+static void large_split(int log2n, int* l1, int* l2) {
+    *l1 = (log2n + 1) / 2;
+    *l2 = log2n / 2;
+}
+
+template <typename T>
+static int tile_for(int log2len) {
+    // columns per CTA: <= 1024 threads (len/8 each), >= 64 B contiguous per row
+    const int len = 1 << log2len;
+    int tiles = (int)(64 / sizeof(C_t<T>));
+    while (tiles > 1 && tiles * (len / 8) > 1024) tiles >>= 1;
+    return tiles;
+}
+
+template <typename T, int SIGN, int MODE, bool DERIV>
+static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
+    using C = C_t<T>;
+    C* grid = (C*)p.d_grid;
+    cudaError_t e = cudaSuccess;
+    if (!p.small_work.empty()) {
+        const size_t smem = (size_t)(1 << kSmallMaxLog2) * sizeof(C);
+        auto kern = k_small_fft<T, SIGN, MODE, DERIV>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        double bytes = 0;
+        for (const SmallWork& w : p.small_work) {
+            const BandDev& B = p.bands[w.band].dev;
+            bytes += (double)w.nfft * (B.n * sizeof(C) * (MODE == 0 ? 1 : 2) +
+                                       (MODE == 0 ? B.K * (sizeof(C) + sizeof(T)) : 0));
+        }
+        int slot;
+        timer_begin(p, "small_fft", bytes, st, &slot);
+        kern<<<(unsigned)p.small_work.size(), 512, smem, st>>>(p.d_small, p.d_bands, (const C*)c,
+                                                             (const T*)p.d_D, grid);
+        timer_end(p, slot, st);
+        ++p.launches;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    for (int b : p.large_bands) {
+        const BandDev& B = p.bands[b].dev;
+        int l1, l2;
+        large_split(B.log2n, &l1, &l2);
+        const int tc = tile_for<T>(l2), tr = tile_for<T>(l1);
+        const size_t sm1 = (size_t)tc * ((1 << l2) + 1) * sizeof(C);
+        const size_t sm2 = (size_t)tr * ((1 << l1) + 1) * sizeof(C);
+        auto k1 = k_fft_pass1<T, SIGN, MODE, DERIV>;
+        auto k2 = k_fft_pass2<T, SIGN>;
+        if ((e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) !=
+            cudaSuccess)
+            return e;
+        // right-hand sides in chunks that fit the intermediate buffer
+        const int chunk = (int)std::max<int64_t>(1, p.Y_elems / B.n);
+        for (int s0 = 0; s0 < B.nrhs; s0 += chunk) {
+            const int ns = std::min(chunk, B.nrhs - s0);
+            const double b1 = (double)ns * (B.n * sizeof(C) +
+                                            (MODE == 0 ? B.K * (sizeof(C) + sizeof(T))
+                                                       : B.n * sizeof(C)));
+            const double b2 = (double)ns * 2.0 * B.n * sizeof(C);
+            int slot;
+            timer_begin(p, "fft_pass1", b1, st, &slot);
+            k1<<<dim3((unsigned)((1 << l1) / tc), (unsigned)ns), tc * ((1 << l2) / 8), sm1, st>>>(
+                B, s0, l1, l2, tc, (const C*)c, (const T*)p.d_D, grid, (C*)p.d_Y);
+            timer_end(p, slot, st);
+            timer_begin(p, "fft_pass2", b2, st, &slot);
+            k2<<<dim3((unsigned)((1 << l2) / tr), (unsigned)ns), tr * ((1 << l1) / 8), sm2, st>>>(
+                B, s0, l1, l2, tr, (const C*)p.d_Y, grid);
+            timer_end(p, slot, st);
+            p.launches += 2;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    }
+    return e;
+}
+
+template <typename T, int MW>
+static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+    using C = C_t<T>;
+    double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(C));
+    for (int b = 1; b <= p.levels; ++b) {
+        const BandDev& B = p.bands[b].dev;
+        if (B.route != 1) continue;
+        bytes += std::min<double>((double)B.nrhs * B.n * sizeof(C),
+                                  (double)p.bands[b].nodes * B.nrhs * 2 * MW * sizeof(C));
+    }
+    int slot;
+    timer_begin(p, "gather", bytes, st, &slot);
+    k_gather<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.q,
+        (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (C*)f);
+    timer_end(p, slot, st);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t gather_dispatch(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+    switch (p.mw) {
+#define FL_MW_CASE(W) \
+    case W: return gather_t<T, W>(p, c, f, deriv, st);
+        FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
+        FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
+#undef FL_MW_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T>
+static cudaError_t forward_t(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+    if (p.M == 0) return cudaSuccess;
+    cudaError_t e = deriv ? fft_bands<T, +1, 0, true>(p, c, st) : fft_bands<T, +1, 0, false>(p, c, st);
+    if (e != cudaSuccess) return e;
+    return gather_dispatch<T>(p, c, f, deriv, st);
+}
+
+cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+    return p.prec == FL_FP64 ? forward_t<double>(p, c, f, deriv, st)
+                             : forward_t<float>(p, c, f, deriv, st);
+}
+
+template <typename T, int MW>
+static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
+    using C = C_t<T>;
+    const int64_t cnt = p.M - p.z0_nodes;
+    if (cnt <= 0) return cudaSuccess;
+    int slot;
+    timer_begin(p, "spread", 0.0, st, &slot);
+    k_spread<T, MW><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
+        p.M, p.z0_nodes, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q,
+        (T)p.kb_b, (C*)p.d_grid);
+    timer_end(p, slot, st);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st) {
+    using C = C_t<T>;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(p.d_grid, 0, p.grid_elems * sizeof(C), st)) != cudaSuccess) return e;
+    switch (p.mw) {
+#define FL_MW_CASE(W) \
+    case W: e = spread_t<T, W>(p, r, st); break;
+        FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
+        FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
+#undef FL_MW_CASE
+        default: e = cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    if ((e = fft_bands<T, -1, 1, false>(p, nullptr, st)) != cudaSuccess) return e;
+    C* z0sum = (C*)p.d_z0;
+    k_z0_sum<T><<<1, 256, 0, st>>>(p.z0_nodes, p.d_perm, (const C*)r, z0sum);
+    int slot;
+    timer_begin(p, "combine", 0.0, st, &slot);
+    k_combine<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
+        p.N, p.levels, p.d_bands, (const T*)p.d_D, (const C*)p.d_grid, z0sum, (C*)cout);
+    timer_end(p, slot, st);
+    p.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t run_adjoint(Plan& p, const void* r, void* cout, cudaStream_t st) {
+    return p.prec == FL_FP64 ? adjoint_t<double>(p, r, cout, st) : adjoint_t<float>(p, r, cout, st);
+}
+
+}  // namespace fl

@@ -1,0 +1,370 @@
+"""ctypes binding of libfl.so with the names of the C ABI in include/fl.h.
+
+Argument marshalling only: every step of the transform runs in the library's
+CUDA kernels.  There is no CPU fallback -- if ``_build/libfl.so`` is missing
+the import raises, and ``paper_1606_03255_gb300.build.build()`` creates it.
+
+Two layers:
+
+* ``fl_plan``, ``fl_execute``, ``fl_adjoint``, ... -- the C calls, taking raw
+  pointers (ints) and sizes, returning ``fl_status`` codes;
+* ``Plan`` / ``LaplacePlan`` -- thin owners of a plan handle that take torch
+  tensors, check dtype/device/shape and raise ``FLError`` on a non-zero status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT, FL_EUNSUPPORTED = range(6)
+FL_FP32, FL_FP64 = 0, 1
+FL_MAX_LEVELS = 128
+FL_MAX_TIMED_KERNELS = 16
+
+STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
+                FL_ECUDA: "FL_ECUDA", FL_ETIMEOUT: "FL_ETIMEOUT",
+                FL_EUNSUPPORTED: "FL_EUNSUPPORTED"}
+
+# Every symbol include/fl.h declares.
+EXPORTED = ["fl_plan", "fl_execute", "fl_execute_deriv", "fl_execute_host", "fl_adjoint",
+            "fl_plan_laplace", "fl_laplace_real", "fl_get_info", "fl_set_timing",
+            "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
+
+
+class fl_info(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int), ("precision", ctypes.c_int),
+        ("N", ctypes.c_int64), ("M", ctypes.c_int64),
+        ("eps", ctypes.c_double), ("eps_laplace", ctypes.c_double),
+        ("eps_fourier", ctypes.c_double),
+        ("q", ctypes.c_int), ("levels", ctypes.c_int), ("m_w", ctypes.c_int),
+        ("sigma", ctypes.c_int),
+        ("y1", ctypes.c_double), ("xi1", ctypes.c_double),
+        ("z0_nodes", ctypes.c_int64),
+        ("n_bands_fft", ctypes.c_int), ("n_bands_direct", ctypes.c_int),
+        ("band_ell", ctypes.c_int * FL_MAX_LEVELS),
+        ("band_route", ctypes.c_int * FL_MAX_LEVELS),
+        ("band_nodes", ctypes.c_int64 * FL_MAX_LEVELS),
+        ("band_K", ctypes.c_int64 * FL_MAX_LEVELS),
+        ("band_n", ctypes.c_int64 * FL_MAX_LEVELS),
+        ("model_bytes", ctypes.c_double), ("scratch_bytes", ctypes.c_double),
+    ]
+
+
+class fl_timing(ctypes.Structure):
+    _fields_ = [
+        ("n_kernels", ctypes.c_int),
+        ("name", (ctypes.c_char * 32) * FL_MAX_TIMED_KERNELS),
+        ("launches", ctypes.c_int64 * FL_MAX_TIMED_KERNELS),
+        ("total_ms", ctypes.c_double * FL_MAX_TIMED_KERNELS),
+        ("bytes", ctypes.c_double * FL_MAX_TIMED_KERNELS),
+        ("total_launches", ctypes.c_int64),
+    ]
+
+
+class FLError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libfl.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise OSError(f"libfl.so not built at {path}; run paper_1606_03255_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, ci, cd = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    pp = ctypes.POINTER(vp)
+    sig = {
+        "fl_plan": [pp, i64, i64, vp, ci, cd, ci, vp],
+        "fl_execute": [vp, vp, vp, vp],
+        "fl_execute_deriv": [vp, vp, vp, vp],
+        "fl_execute_host": [vp, vp, vp, vp],
+        "fl_adjoint": [vp, vp, vp, vp],
+        "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
+        "fl_laplace_real": [vp, vp, vp, vp],
+        "fl_get_info": [vp, ctypes.POINTER(fl_info)],
+        "fl_set_timing": [vp, ci],
+        "fl_get_timing": [vp, ctypes.POINTER(fl_timing)],
+        "fl_destroy": [vp],
+        "fl_last_error": [],
+        "fl_version": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ci
+    lib.fl_destroy.restype = None
+    lib.fl_last_error.restype = ctypes.c_char_p
+    lib.fl_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# The C calls, same names and argument order as include/fl.h.
+
+def fl_plan(N, M, nodes_ptr, q, eps, prec, stream):
+    h = ctypes.c_void_p()
+    st = load().fl_plan(ctypes.byref(h), int(N), int(M), nodes_ptr, int(q), float(eps),
+                        int(prec), stream)
+    return st, h
+
+
+def fl_execute(plan, c_ptr, f_ptr, stream):
+    return load().fl_execute(plan, c_ptr, f_ptr, stream)
+
+
+def fl_execute_deriv(plan, c_ptr, f_ptr, stream):
+    return load().fl_execute_deriv(plan, c_ptr, f_ptr, stream)
+
+
+def fl_execute_host(plan, c_ptr, f_ptr, stream):
+    return load().fl_execute_host(plan, c_ptr, f_ptr, stream)
+
+
+def fl_adjoint(plan, r_ptr, c_out_ptr, stream):
+    return load().fl_adjoint(plan, r_ptr, c_out_ptr, stream)
+
+
+def fl_plan_laplace(N, M, t_ptr, s_ptr, q, eps, prec, stream):
+    h = ctypes.c_void_p()
+    st = load().fl_plan_laplace(ctypes.byref(h), int(N), int(M), t_ptr, s_ptr, int(q),
+                                float(eps), int(prec), stream)
+    return st, h
+
+
+def fl_laplace_real(plan, c_ptr, f_ptr, stream):
+    return load().fl_laplace_real(plan, c_ptr, f_ptr, stream)
+
+
+def fl_get_info(plan):
+    info = fl_info()
+    st = load().fl_get_info(plan, ctypes.byref(info))
+    return st, info
+
+
+def fl_set_timing(plan, enable):
+    return load().fl_set_timing(plan, int(bool(enable)))
+
+
+def fl_get_timing(plan):
+    t = fl_timing()
+    st = load().fl_get_timing(plan, ctypes.byref(t))
+    return st, t
+
+
+def fl_destroy(plan):
+    load().fl_destroy(plan)
+
+
+def fl_last_error() -> str:
+    return load().fl_last_error().decode()
+
+
+def fl_version() -> str:
+    return load().fl_version().decode()
+
+
+def check(status: int, what: str = "") -> None:
+    if status != FL_OK:
+        raise FLError(status, f"{what}: {fl_last_error()}" if what else fl_last_error())
+
+
+# ---------------------------------------------------------------------------
+# Tensor-level helpers.
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_handle(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr())
+
+
+def _require(t, dtype, numel: int, name: str):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() != numel or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous with {numel} elements")
+
+
+def info_dict(info: fl_info) -> dict:
+    nb = info.levels + 1
+    return {
+        "kind": info.kind, "precision": info.precision, "N": info.N, "M": info.M,
+        "eps": info.eps, "eps_laplace": info.eps_laplace, "eps_fourier": info.eps_fourier,
+        "q": info.q, "levels": info.levels, "m_w": info.m_w, "sigma": info.sigma,
+        "y1": info.y1, "xi1": info.xi1, "z0_nodes": info.z0_nodes,
+        "n_bands_fft": info.n_bands_fft, "n_bands_direct": info.n_bands_direct,
+        "band_ell": list(info.band_ell[:nb]), "band_route": list(info.band_route[:nb]),
+        "band_nodes": list(info.band_nodes[:nb]), "band_K": list(info.band_K[:nb]),
+        "band_n": list(info.band_n[:nb]),
+        "model_bytes": info.model_bytes, "scratch_bytes": info.scratch_bytes,
+    }
+
+
+def timing_dict(t: fl_timing) -> dict:
+    out = {}
+    for i in range(t.n_kernels):
+        name = bytes(t.name[i]).split(b"\0", 1)[0].decode()
+        out[name] = {"launches": int(t.launches[i]), "total_ms": float(t.total_ms[i]),
+                     "bytes": float(t.bytes[i])}
+    return {"kernels": out, "total_launches": int(t.total_launches)}
+
+
+class Plan:
+    """Owner of an Algorithm-2 plan: f = sum_k c_k exp(2 pi i k w_j).
+
+    nodes: CUDA float64 tensor (M, 2) of (Re w, Im w), or complex128 (M,).
+    precision: "fp32" (complex64 c/f) or "fp64" (complex128 c/f).
+    """
+
+    def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
+                 stream=None):
+        torch = _torch()
+        if nodes.is_complex():
+            nodes = torch.view_as_real(nodes.to(torch.complex128))
+        nodes = nodes.to(torch.float64).contiguous()
+        self.N = int(N)
+        self.M = int(nodes.shape[0]) if nodes.dim() else 0
+        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
+        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self._handle = None
+        st, h = fl_plan(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
+                        _stream_handle(stream))
+        check(st, "fl_plan")
+        self._handle = h
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def execute(self, c, out=None, stream=None, deriv: bool = False):
+        torch = _torch()
+        _require(c, self.cdtype, self.N, "c")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=c.device)
+        _require(out, self.cdtype, self.M, "out")
+        fn = fl_execute_deriv if deriv else fl_execute
+        check(fn(self._handle, _ptr(c), _ptr(out) if self.M else None, _stream_handle(stream)),
+              "fl_execute")
+        return out
+
+    def adjoint(self, r, out=None, stream=None):
+        torch = _torch()
+        _require(r, self.cdtype, self.M, "r")
+        if out is None:
+            out = torch.empty(self.N, dtype=self.cdtype, device=r.device)
+        _require(out, self.cdtype, self.N, "out")
+        check(fl_adjoint(self._handle, _ptr(r) if self.M else None, _ptr(out),
+                         _stream_handle(stream)), "fl_adjoint")
+        return out
+
+    def execute_host(self, c_host, f_host, stream=None):
+        """c_host, f_host: CPU tensors (ideally pinned) of the plan's complex dtype."""
+        check(fl_execute_host(self._handle, _ptr(c_host), _ptr(f_host), _stream_handle(stream)),
+              "fl_execute_host")
+        return f_host
+
+    def info(self) -> dict:
+        st, inf = fl_get_info(self._handle)
+        check(st, "fl_get_info")
+        return info_dict(inf)
+
+    def set_timing(self, enable: bool):
+        check(fl_set_timing(self._handle, enable), "fl_set_timing")
+
+    def timing(self) -> dict:
+        st, t = fl_get_timing(self._handle)
+        check(st, "fl_get_timing")
+        return timing_dict(t)
+
+    def close(self):
+        if self._handle is not None and self._handle.value:
+            fl_destroy(self._handle)
+        self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class LaplacePlan:
+    """Owner of an Algorithm-1 plan: f_j = sum_k c_k exp(-s_j t_k) (real data)."""
+
+    def __init__(self, t, s, eps: float, precision: str = "fp64", q: int = 0, stream=None):
+        torch = _torch()
+        t = t.to(torch.float64).contiguous()
+        s = s.to(torch.float64).contiguous()
+        self.N, self.M = int(t.numel()), int(s.numel())
+        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
+        self.rdtype = torch.float64 if self.prec == FL_FP64 else torch.float32
+        self._handle = None
+        st, h = fl_plan_laplace(self.N, self.M, _ptr(t), _ptr(s), q, eps, self.prec,
+                                _stream_handle(stream))
+        check(st, "fl_plan_laplace")
+        self._handle = h
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def execute(self, c, out=None, stream=None):
+        torch = _torch()
+        _require(c, self.rdtype, self.N, "c")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.rdtype, device=c.device)
+        _require(out, self.rdtype, self.M, "out")
+        check(fl_laplace_real(self._handle, _ptr(c), _ptr(out), _stream_handle(stream)),
+              "fl_laplace_real")
+        return out
+
+    def info(self) -> dict:
+        st, inf = fl_get_info(self._handle)
+        check(st, "fl_get_info")
+        return info_dict(inf)
+
+    def set_timing(self, enable: bool):
+        check(fl_set_timing(self._handle, enable), "fl_set_timing")
+
+    def timing(self) -> dict:
+        st, t = fl_get_timing(self._handle)
+        check(st, "fl_get_timing")
+        return timing_dict(t)
+
+    def close(self):
+        if self._handle is not None and self._handle.value:
+            fl_destroy(self._handle)
+        self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

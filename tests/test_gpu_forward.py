@@ -1,0 +1,175 @@
+"""GPU parity of the forward transform (Algorithm 2) against the CPU oracle.
+
+Element-by-element comparison through the C ABI, with E = ||f - f~||_inf /
+||c||_1 (eq. 5.1) at or below the target accuracy eps of each plan:
+E <= eps is what Theorem 4.3 guarantees for exact arithmetic; the FP32 form
+adds float rounding, which at these sizes stays orders of magnitude below eps
+(grid values ~ sqrt(N) |c|, rounding ~ 1e-7 relative, ||c||_1 ~ N).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import structured as S
+from paper_1606_03255_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_1606_03255_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1606_03255_gb300 import fl as flmod
+    flmod.load()
+    return flmod
+
+
+def _run(fl, c, w, eps, prec, q=0, deriv=False):
+    dev = torch.device("cuda")
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    plan = fl.Plan(len(c), torch.from_numpy(np.ascontiguousarray(w)).to(dev), eps, precision=prec, q=q)
+    f = plan.execute(torch.from_numpy(np.asarray(c)).to(cdt).to(dev), deriv=deriv)
+    torch.cuda.synchronize()
+    out = f.cpu().numpy().astype(np.complex128)
+    info = plan.info()
+    plan.close()
+    return out, info
+
+
+def _nodes(kind, M, seed, eps=1e-6):
+    if kind == "disk":
+        return W.nodes_disk_uniform(M, seed)
+    if kind == "clustered":
+        return W.nodes_circle_clustered(M, seed)
+    if kind == "paper":
+        return W.nodes_paper_section5(M, S.rank_q(eps), seed)
+    if kind == "circle":
+        return W.nodes_equispaced_circle(M)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp32", 1e-6)])
+def test_config0_disk_uniform_1024(fl, prec, eps):
+    c = W.coefficients(1024, seed=0)
+    w = W.nodes_disk_uniform(1024, seed=1)
+    f, info = _run(fl, c, w, eps, prec)
+    E = oracle.error_E(oracle.flt_direct(c, w), f, c)
+    assert E <= eps, E
+
+
+@pytest.mark.parametrize("N,M", [(1, 5), (2, 3), (3, 17), (100, 1), (1000, 999), (4097, 300),
+                                 (20000, 2000), (5, 0)])
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_sizes_and_ragged_tails(fl, N, M, prec, eps):
+    c = W.coefficients(N, seed=N)
+    w = W.nodes_disk_uniform(M, seed=M + 1)
+    f, info = _run(fl, c, w, eps, prec)
+    if M:
+        E = oracle.error_E(oracle.flt_direct(c, w), f, c)
+        assert E <= eps, (E, info["q"], info["m_w"])
+
+
+@pytest.mark.parametrize("kind", ["disk", "clustered", "paper", "circle"])
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp64", 1e-8), ("fp32", 1e-6),
+                                      ("fp32", 1e-4)])
+def test_node_distributions(fl, kind, prec, eps):
+    N, M = 3000, 2500
+    c = W.coefficients(N, seed=7)
+    w = _nodes(kind, M, seed=8, eps=eps)
+    f, _ = _run(fl, c, w, eps, prec)
+    E = oracle.error_E(oracle.flt_direct(c, w), f, c)
+    assert E <= eps, E
+
+
+def test_special_nodes(fl):
+    N = 777
+    c = W.coefficients(N, seed=9)
+    w = np.array([
+        [0.0, 0.0], [0.5, 0.0], [-0.25, 0.0], [3.75, 0.0], [-7.1, 0.01],  # any real x
+        [0.3, 5.0], [0.9, 40.0],                                           # Z^0: |z| < eps
+        [0.123, 1e-15], [0.123, 1e-9], [0.77, 0.3],
+    ])
+    for prec, eps in (("fp64", 1e-12), ("fp32", 1e-6)):
+        f, info = _run(fl, c, w, eps, prec)
+        ref = oracle.flt_direct(c, w)
+        assert oracle.error_E(ref, f, c) <= eps
+        tol = 0 if prec == "fp64" else 1e-7 * abs(c[0])
+        assert abs(f[5] - c[0]) <= tol and abs(f[6] - c[0]) <= tol   # Z^0 -> c_0
+        assert info["z0_nodes"] == 2
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+def test_two_pass_fft_bands(fl, prec, eps):
+    # N = 2^14 and 2^16 put the Y_M band and the top bands on grids of 2^15..2^17
+    # points (the four-step path); clustered nodes fill the near-circle bands.
+    for N in (1 << 14, 1 << 16):
+        c = W.coefficients(N, seed=N)
+        w = W.nodes_circle_clustered(4096, seed=3)
+        f, info = _run(fl, c, w, eps, prec)
+        assert max(info["band_n"]) > 4096
+        E = oracle.error_E(oracle.flt_direct(c, w), f, c)
+        assert E <= eps, E
+
+
+def test_matches_structured_algorithm2(fl):
+    # Same Laplace factorisation with exact NDFTs: the two differ only by the
+    # NFFT error (<= eps/3 per Lemma 4.1) and rounding.
+    N, M, eps = 512, 300, 1e-8
+    c = W.coefficients(N, seed=4)
+    w = W.nodes_circle_clustered(M, seed=5)
+    f, info = _run(fl, c, w, eps, "fp64")
+    fs, P = S.xflt_alg2(c, w, eps)
+    assert info["q"] == P.lap.q and info["levels"] == P.lap.M
+    for b in range(1, info["levels"]):
+        assert info["band_ell"][b] == P.lap.ell[b]
+    assert oracle.error_E(fs, f, c) <= eps / 3
+
+
+def test_parameters_follow_definition(fl):
+    N = 1 << 20
+    w = W.nodes_disk_uniform(8, seed=1)
+    for eps, q in ((1e-6, 12), (1e-10, 18), (1e-12, 22)):
+        _, info = _run(fl, W.coefficients(N, 0)[:N], w, eps, "fp32")
+        assert info["q"] == q == S.rank_q(eps / 3)
+        P = S.xflt_params(N, eps)
+        assert info["levels"] == P.lap.M
+        assert info["y1"] == P.y1 and info["xi1"] == P.xi1
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_derivative_in_w(fl, prec, eps):
+    N, M = 2000, 700
+    c = W.coefficients(N, seed=11)
+    w = W.nodes_disk_uniform(M, seed=12)
+    k = np.arange(N)
+    cd = 2j * np.pi * k * c
+    ref = oracle.flt_direct(cd, w)
+    f, _ = _run(fl, c, w, eps, prec, deriv=True)
+    assert oracle.error_E(ref, f, cd) <= eps
+
+
+def test_invalid_nodes_rejected(fl):
+    w = torch.tensor([[0.1, 0.2], [0.3, -1e-3]], dtype=torch.float64, device="cuda")
+    with pytest.raises(fl.FLError) as ei:
+        fl.Plan(10, w, 1e-6)
+    assert ei.value.status == fl.FL_EINVAL
+    w2 = torch.tensor([[float("nan"), 0.2]], dtype=torch.float64, device="cuda")
+    with pytest.raises(fl.FLError):
+        fl.Plan(10, w2, 1e-6)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_full_size_config2_sampled(fl, prec, eps):
+    # N = M = 2^20, half the nodes on |z| = 1, half clustered near it; the
+    # oracle checks a seeded sample of 512 outputs.
+    N = M = 1 << 20
+    c = W.coefficients(N, seed=0)
+    w = W.nodes_circle_clustered(M, seed=1)
+    f, info = _run(fl, c, w, eps, prec)
+    idx = np.random.default_rng(2).choice(M, 512, replace=False)
+    ref = oracle.flt_direct(c, w[idx])
+    E = oracle.error_E(ref, f[idx], c)
+    assert E <= eps, E
