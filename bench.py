@@ -1,0 +1,396 @@
+"""Benchmark of the fast Fourier-Laplace transform (Algorithm 2) on GB300.
+
+Workload (one step): one fl_execute of the planned transform at N = M = 2^20,
+c complex64 N(0,1), half the nodes exactly on |z| = 1 and half with
+1 - |z| = 10^(-6U) (clustered towards the circle), eps = 1e-6, FP32 form.
+The plan (parameter choice, tables, node banding and sorting) is built once
+before the timed region -- the paper's "precomputation", which it neglects.
+Metric: evaluations per second, N*M / (time of one step).
+
+Also reported on the same inputs: the FP64 form at eps = 1e-12 and at the same
+eps = 1e-6, the error E = ||f - f~||_inf / ||c||_1 of each form on a seeded
+sample of nodes checked by the CPU oracle (the cpu_baseline leg), per-kernel
+roofline figures, plan time, and an end-to-end number through fl_execute_host
+(host buffers, copies inside the timed region).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own full instance (seed offset by rank):
+weak scaling, no collective on the data path; the step time is the maximum
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1606_03255_gb300 import workloads as W  # noqa: E402
+
+N_DEFAULT = 1 << 20
+EPS32 = 1e-6
+EPS64 = 1e-12
+METRIC = "Fourier–Laplace evals/s (N·M/time) at N=M=2^20, FP32 vs FP64 form at stated E"
+WORKLOAD = ("N=M=2^20 Fourier-Laplace transform: c complex64 N(0,1); nodes half on |z|=1, "
+            "half with 1-|z|=10^(-6U); eps=1e-6 FP32 form (FP64 phase reduction)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form lines")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--sample", type=int, default=2048, help="oracle sample size (nodes)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_1606_03255_gb300", "csrc")
+    for name in sorted(os.listdir(src)):
+        with open(os.path.join(src, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    captured from the current sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != source_hash():
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    return None if k is None else float(k["dram_bytes_per_launch"])
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.gpu), "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def oracle_sample(c, w, sample: int, seed: int = 2):
+    """cpu_baseline leg: the oracle on a seeded node sample; returns (idx, ref, sec, cores)."""
+    import oracle
+    idx = np.sort(np.random.default_rng(seed).choice(w.shape[0], sample, replace=False))
+    cores = oracle.default_threads()
+    t0 = time.perf_counter()
+    ref = oracle.flt_direct(c, w[idx], threads=cores)
+    sec = time.perf_counter() - t0
+    return idx, ref, sec, cores
+
+
+def error_E(ref, approx, c) -> float:
+    return float(np.max(np.abs(ref - approx)) / np.sum(np.abs(c)))
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle (plain FP64 direct sum) on the host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    N = args.N
+    c = W.coefficients(N, seed=0).astype(np.complex64).astype(np.complex128)
+    w = W.nodes_circle_clustered(N, seed=1)
+    S = 128                       # nodes per step: a bounded sample of the workload
+    cores = oracle.default_threads()
+    rng = np.random.default_rng(5)
+    for _ in range(args.warmup):
+        oracle.flt_direct(c, w[rng.choice(N, 8, replace=False)], threads=cores)
+    times = []
+    for _ in range(args.steps):
+        idx = rng.choice(N, S, replace=False)
+        t0 = time.perf_counter()
+        oracle.flt_direct(c, w[idx], threads=cores)
+        times.append(time.perf_counter() - t0)
+    sec = float(np.mean(times))
+    value = S * N / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "evals/s",
+        "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M": N, "per_step_sample_nodes": S,
+                   "note": "CPU oracle: term-by-term FP64 direct sum, all host cores"},
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{S} seeded nodes x N={N} terms per step"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    from paper_1606_03255_gb300 import fl
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    N = M = args.N
+    c_np = W.coefficients(N, seed=rank).astype(np.complex64)
+    w_np = W.nodes_circle_clustered(M, seed=1000 + rank)
+    c = torch.from_numpy(c_np).to(dev)
+    nodes = torch.from_numpy(w_np).to(dev)
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = fl.Plan(N, nodes, EPS32, precision="fp32")
+    torch.cuda.synchronize()
+    plan_ms = (time.perf_counter() - t0) * 1e3
+    info = plan.info()
+    f = torch.empty(M, dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > 129 MB of L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(3, args.warmup)):
+        plan.execute(c, out=f)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    plan.set_timing(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        plan.execute(c, out=f)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    timing = plan.timing()
+    plan.set_timing(False)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * N * M / (ms * 1e-3)
+
+    # per-kernel roofline from the live CUDA-event timing
+    peaks = measured_peaks()
+    kern = timing["kernels"]
+    kernel_table = {}
+    for name, kd in kern.items():
+        per = kd["total_ms"] / max(kd["launches"], 1)
+        gbs = kd["bytes"] / max(kd["total_ms"], 1e-12) / 1e6
+        kernel_table[name] = {"launches": kd["launches"], "ms_per_step": kd["total_ms"] / args.steps,
+                              "avg_launch_ms": per, "bytes_per_launch": kd["bytes"] / max(kd["launches"], 1),
+                              "GBps": gbs, "share": kd["total_ms"] / max(sum(v["total_ms"] for v in kern.values()), 1e-12)}
+    top = max(kernel_table, key=lambda k: kernel_table[k]["ms_per_step"]) if kernel_table else None
+    roof = None
+    if top:
+        kt = kernel_table[top]
+        roof = {"kernel": top, "bound": "hbm", "achieved": kt["GBps"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": kt["GBps"] / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(top), "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": kt["bytes_per_launch"]}
+
+    # end-to-end through the host-buffer C call (copies inside the timed region)
+    c_host = torch.from_numpy(c_np).pin_memory()
+    f_host = torch.empty(M, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        plan.execute_host(c_host, f_host)
+    e2e_times = []
+    for _ in range(max(3, args.steps // 2)):
+        t1 = time.perf_counter()
+        plan.execute_host(c_host, f_host)
+        e2e_times.append(time.perf_counter() - t1)
+    e2e_ms = float(np.mean(e2e_times)) * 1e3
+    e2e = {"value": world * N * M / (e2e_ms * 1e-3), "unit": "evals/s",
+           "h2d_bytes_per_step": int(c_host.numel() * c_host.element_size()),
+           "d2h_bytes_per_step": int(f_host.numel() * f_host.element_size()),
+           "ms_per_step": e2e_ms, "api": "fl_execute_host"}
+    f_fp32 = f.cpu().numpy().astype(np.complex128)
+    plan.close()
+
+    # FP64 form: at eps = 1e-12 and at the same eps as the FP32 form
+    fp64 = {}
+    f64_results = {}
+    if not args.no_fp64:
+        c64 = torch.from_numpy(c_np.astype(np.complex128)).to(dev)
+        for tag, eps in (("eps1e-12", EPS64), ("eps1e-6", EPS32)):
+            p64 = fl.Plan(N, nodes, eps, precision="fp64")
+            out = torch.empty(M, dtype=torch.complex128, device=dev)
+            for _ in range(3):
+                p64.execute(c64, out=out)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(5)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                p64.execute(c64, out=out)
+                b.record(stream)
+            torch.cuda.synchronize()
+            ms64 = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+            inf = p64.info()
+            fp64[tag] = {"ms_per_step": ms64, "value": N * M / (ms64 * 1e-3), "q": inf["q"],
+                         "m_w": inf["m_w"], "eps": eps}
+            f64_results[tag] = out.cpu().numpy()
+            p64.close()
+        fp64["fp32_speedup_vs_fp64_same_eps"] = fp64["eps1e-6"]["ms_per_step"] / ms
+        fp64["fp32_speedup_vs_fp64_eps1e-12"] = fp64["eps1e-12"]["ms_per_step"] / ms
+
+    # cpu_baseline leg: the oracle on a seeded sample; the same sample gives E
+    cpu = None
+    errors = {}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        c128 = c_np.astype(np.complex128)
+        idx, ref, sec, cores = oracle_sample(c128, w_np, args.sample)
+        cpu = {"value": len(idx) * N / sec, "unit": "evals/s", "cores": cores, "kind": "oracle",
+               "sample": f"{len(idx)} seeded nodes of the workload x N={N} terms ({sec:.1f} s)"}
+        errors["fp32_eps1e-6"] = error_E(ref, f_fp32[idx], c128)
+        for tag, res in f64_results.items():
+            errors["fp64_" + tag] = error_E(ref, res[idx], c128)
+
+    if dist:
+        dist.barrier()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    launches_total = timing["total_launches"]
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "M": M, "eps": EPS32, "q": info["q"],
+                   "levels": info["levels"], "m_w": info["m_w"], "sigma": info["sigma"],
+                   "bands_fft": info["n_bands_fft"],
+                   "l2": "flushed between steps (256 MiB write); working set > L2",
+                   "plan": "built once before the timed region"},
+        "plan_ms": plan_ms,
+        "E": errors or None,
+        "fp64": fp64 or None,
+        "roofline": roof,
+        "kernels": kernel_table,
+        "model_bytes_per_step": info["model_bytes"],
+        "model_GBps": info["model_bytes"] / (ms * 1e-3) / 1e9,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches_total,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,10 +1,14 @@
 """GPU parity of the forward transform (Algorithm 2) against the CPU oracle.
 
 Element-by-element comparison through the C ABI, with E = ||f - f~||_inf /
-||c||_1 (eq. 5.1) at or below the target accuracy eps of each plan:
-E <= eps is what Theorem 4.3 guarantees for exact arithmetic; the FP32 form
-adds float rounding, which at these sizes stays orders of magnitude below eps
-(grid values ~ sqrt(N) |c|, rounding ~ 1e-7 relative, ||c||_1 ~ N).
+||c||_1 (eq. 5.1).  Tolerance: E <= eps is what Theorem 4.3 guarantees in exact
+arithmetic.  The FP64 form is held to exactly that.  The FP32 form adds float
+rounding, which scales with the magnitude of the values it rounds -- the grids
+and the output, all O(||f||_inf) -- so its bound is
+    E <= eps + 32 u_32 ||f||_inf / ||c||_1,     u_32 = 2^-24,
+(32 ~ log2(n) FFT stages plus the q-term recombination).  For random c at large
+N, ||f||_inf ~ sqrt(N) << ||c||_1 ~ N and the extra term vanishes; at N = 3 it
+is what dominates.
 """
 import numpy as np
 import pytest
@@ -39,6 +43,16 @@ def _run(fl, c, w, eps, prec, q=0, deriv=False):
     return out, info
 
 
+U32 = 2.0 ** -24
+
+
+def tol(eps, prec, fref, c):
+    """Allowed E for a plan of accuracy eps (see the module docstring)."""
+    if prec == "fp64":
+        return eps
+    return eps + 32 * U32 * np.max(np.abs(fref)) / np.sum(np.abs(c))
+
+
 def _nodes(kind, M, seed, eps=1e-6):
     if kind == "disk":
         return W.nodes_disk_uniform(M, seed)
@@ -56,8 +70,9 @@ def test_config0_disk_uniform_1024(fl, prec, eps):
     c = W.coefficients(1024, seed=0)
     w = W.nodes_disk_uniform(1024, seed=1)
     f, info = _run(fl, c, w, eps, prec)
-    E = oracle.error_E(oracle.flt_direct(c, w), f, c)
-    assert E <= eps, E
+    ref = oracle.flt_direct(c, w)
+    E = oracle.error_E(ref, f, c)
+    assert E <= tol(eps, prec, ref, c), E
 
 
 @pytest.mark.parametrize("N,M", [(1, 5), (2, 3), (3, 17), (100, 1), (1000, 999), (4097, 300),
@@ -68,8 +83,9 @@ def test_sizes_and_ragged_tails(fl, N, M, prec, eps):
     w = W.nodes_disk_uniform(M, seed=M + 1)
     f, info = _run(fl, c, w, eps, prec)
     if M:
-        E = oracle.error_E(oracle.flt_direct(c, w), f, c)
-        assert E <= eps, (E, info["q"], info["m_w"])
+        ref = oracle.flt_direct(c, w)
+        E = oracle.error_E(ref, f, c)
+        assert E <= tol(eps, prec, ref, c), (E, info["q"], info["m_w"])
 
 
 @pytest.mark.parametrize("kind", ["disk", "clustered", "paper", "circle"])
@@ -80,8 +96,9 @@ def test_node_distributions(fl, kind, prec, eps):
     c = W.coefficients(N, seed=7)
     w = _nodes(kind, M, seed=8, eps=eps)
     f, _ = _run(fl, c, w, eps, prec)
-    E = oracle.error_E(oracle.flt_direct(c, w), f, c)
-    assert E <= eps, E
+    ref = oracle.flt_direct(c, w)
+    E = oracle.error_E(ref, f, c)
+    assert E <= tol(eps, prec, ref, c), E
 
 
 def test_special_nodes(fl):
@@ -95,9 +112,9 @@ def test_special_nodes(fl):
     for prec, eps in (("fp64", 1e-12), ("fp32", 1e-6)):
         f, info = _run(fl, c, w, eps, prec)
         ref = oracle.flt_direct(c, w)
-        assert oracle.error_E(ref, f, c) <= eps
-        tol = 0 if prec == "fp64" else 1e-7 * abs(c[0])
-        assert abs(f[5] - c[0]) <= tol and abs(f[6] - c[0]) <= tol   # Z^0 -> c_0
+        assert oracle.error_E(ref, f, c) <= tol(eps, prec, ref, c)
+        t0 = 0 if prec == "fp64" else 1e-7 * abs(c[0])
+        assert abs(f[5] - c[0]) <= t0 and abs(f[6] - c[0]) <= t0   # Z^0 -> c_0
         assert info["z0_nodes"] == 2
 
 
@@ -110,8 +127,9 @@ def test_two_pass_fft_bands(fl, prec, eps):
         w = W.nodes_circle_clustered(4096, seed=3)
         f, info = _run(fl, c, w, eps, prec)
         assert max(info["band_n"]) > 4096
-        E = oracle.error_E(oracle.flt_direct(c, w), f, c)
-        assert E <= eps, E
+        ref = oracle.flt_direct(c, w)
+        E = oracle.error_E(ref, f, c)
+        assert E <= tol(eps, prec, ref, c), E
 
 
 def test_matches_structured_algorithm2(fl):
@@ -148,7 +166,7 @@ def test_derivative_in_w(fl, prec, eps):
     cd = 2j * np.pi * k * c
     ref = oracle.flt_direct(cd, w)
     f, _ = _run(fl, c, w, eps, prec, deriv=True)
-    assert oracle.error_E(ref, f, cd) <= eps
+    assert oracle.error_E(ref, f, cd) <= tol(eps, prec, ref, cd)
 
 
 def test_invalid_nodes_rejected(fl):
@@ -172,4 +190,5 @@ def test_full_size_config2_sampled(fl, prec, eps):
     idx = np.random.default_rng(2).choice(M, 512, replace=False)
     ref = oracle.flt_direct(c, w[idx])
     E = oracle.error_E(ref, f[idx], c)
+    assert E <= tol(eps, prec, ref, c), E
     assert E <= eps, E
