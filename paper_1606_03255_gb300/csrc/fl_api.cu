@@ -14,10 +14,14 @@ namespace fl {
 
 static thread_local std::string g_err;
 
-static fl_status fail(fl_status s, const std::string& msg) {
+fl_status set_error(fl_status s, const std::string& msg) {
     g_err = msg;
     return s;
 }
+
+void clear_error() { g_err.clear(); }
+
+static fl_status fail(fl_status s, const std::string& msg) { return set_error(s, msg); }
 
 static fl_status cuda_fail(cudaError_t e, const char* where) {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);
@@ -32,7 +36,7 @@ static fl_status cuda_fail(cudaError_t e, const char* where) {
 
 Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_cheb, d_D, d_grid, d_Y,
-                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_lap};
+                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_lap};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -110,6 +114,7 @@ static fl_status select_params(Plan& p, int q_in) {
             const double a = ldexp(p.y1, -b);
             bh.dev.yc = 1.5 * a;
             bh.dev.yh = 0.5 * a;
+            bh.dev.yh_inv = 1.0 / bh.dev.yh;
         } else {
             K = p.N;            // Z_M band: kernel ~ 1, one plain NFFT
             bh.dev.nrhs = 1;
@@ -239,10 +244,6 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
 }  // namespace fl
 
 using namespace fl;
-
-struct fl_plan_s {
-    Plan p;
-};
 
 extern "C" {
 

@@ -49,6 +49,7 @@ struct BandDev {
     int route;         // 0 empty, 1 NFFT, 2 direct sum
     int pad;
     double yc, yh;     // band Y_m = [yc - yh, yc + yh] (paper's y), for barycentric weights
+    double yh_inv;     // 1 / yh (a power of two times 1/y_1)
 };
 
 // ---------------------------------------------------------------------------
@@ -108,6 +109,7 @@ __device__ __forceinline__ void fft_stage(C_t<T>* buf, int L, int Ns, int t, int
     using C = C_t<T>;
     constexpr int J = 8 / R;
     C v[8];
+    const T inv_span = (T)1 / (T)(Ns * R);   // a power of two
     if (active) {
 #pragma unroll
         for (int jb = 0; jb < J; ++jb) {
@@ -116,7 +118,8 @@ __device__ __forceinline__ void fft_stage(C_t<T>* buf, int L, int Ns, int t, int
 #pragma unroll
             for (int r = 0; r < R; ++r) v[jb * R + r] = buf[jj + r * (L / R)];
             if (Ns > 1) {
-                C w1 = expipi<T>((T)(2 * SIGN) * (T)k / (T)(Ns * R));
+                // k < Ns and 1/(Ns R) is a power of two: exact argument
+                C w1 = expipi<T>((T)(2 * SIGN) * (T)k * inv_span);
                 C w = w1;
 #pragma unroll
                 for (int r = 1; r < R; ++r) {

@@ -1,17 +1,453 @@
-// fl_laplace.cu -- Algorithm 1 (Kunis & Melzer, Section 3): the real discrete
-// Laplace transform.  (Filled in below the C ABI entry points.)
+// fl_laplace.cu -- Algorithm 1 of Kunis & Melzer (Section 3): the real discrete
+// Laplace transform f_j = sum_k c_k exp(-s_j t_k) through the hierarchical
+// factorisation K~ = diag(L^{Y_m}) (K^{Y_m,Omega_l}) diag(L^{Omega_l})^T plus the
+// cumulative sums g_m (Definition 3.2, Theorem A.3):
+//
+//   g_M = sum_{t_k in Omega_M} c_k,  g_m = g_{m+1} + sum_{t_k in Omega_m} c_k
+//   v^{Omega_l}_r = sum_{t_k in Omega_l} L_r^{Omega_l}(t_k) c_k         (moments)
+//   h^{Y_m}_s = sum_{l=l_m}^{L_m} sum_r K^{Y_m,Omega_l}_{s r} v^{Omega_l}_r (coupling)
+//   f~_j = sum_s L_s^{Y_m}(s_j) h^{Y_m}_s + g_{L_m+1}  (s_j in Y_m),  g_1 (s_j in Y_M)
+//
+// Kernels: k_lap_minmax (interval ends y_1 = max s, xi_1 = max t, validity),
+// k_lap_band (band of every t_k and s_j), k_lap_moments (moments and band sums,
+// deterministic: per-warp tables, warp-ordered group sums, block partials
+// reduced in block order by k_lap_reduce), k_lap_couple (h and g), k_lap_eval.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
 #include "fl_plan.cuh"
+
+namespace fl {
+
+constexpr int kLapWarps = 8;          // warps per moment block
+constexpr int kLapMaxBlocks = 128;    // moment blocks (fixed: partial-sum order)
+
+__device__ __forceinline__ int lap_band(double v, double v1, int levels) {
+    if (levels <= 1) return 1;
+    if (v > ldexp(v1, -1)) return 1;
+    if (!(v > ldexp(v1, -(levels - 1)))) return levels;
+    int b = (int)floor(log2(v1 / v)) + 1;
+    b = max(1, min(b, levels - 1));
+    while (b > 1 && v > ldexp(v1, -(b - 1))) --b;
+    while (b < levels - 1 && !(v > ldexp(v1, -b))) ++b;
+    return b;
+}
+
+// max over non-negative doubles by their bit patterns (monotone for x >= 0);
+// flag bit 1: a t_k or s_j is negative or not finite.
+__global__ void k_lap_minmax(int64_t N, const double* __restrict__ t, int64_t M,
+                             const double* __restrict__ s, unsigned long long* __restrict__ mx,
+                             int* __restrict__ flag) {
+    unsigned long long mt = 0, ms = 0;
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
+        const double v = t[i];
+        if (!(v >= 0.0) || !isfinite(v)) bad = 1;
+        else mt = max(mt, (unsigned long long)__double_as_longlong(v));
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const double v = s[i];
+        if (!(v >= 0.0) || !isfinite(v)) bad = 1;
+        else ms = max(ms, (unsigned long long)__double_as_longlong(v));
+    }
+    if (bad) atomicOr(flag, 1);
+    atomicMax(&mx[0], mt);
+    atomicMax(&mx[1], ms);
+}
+
+__global__ void k_lap_band(int64_t n, const double* __restrict__ v, double v1, int levels,
+                           uint8_t* __restrict__ band) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) band[i] = (uint8_t)lap_band(v[i], v1, levels);
+}
+
+// Moments and band sums.  Table row l (1..levels) holds v^{Omega_l}_0..q-1 and,
+// in column q, the band sum sum_{t_k in Omega_l} c_k.  Each warp owns a table;
+// for every 32 consecutive t_k it takes, lanes are grouped by band
+// (match_any) and each group's sum is formed in lane order and added by the
+// group's lowest lane, so the result does not depend on scheduling.
+template <typename T>
+__global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
+                              const uint8_t* __restrict__ tband, const T* __restrict__ c,
+                              int levels, int q, double xi1, const double* __restrict__ cheb,
+                              T* __restrict__ partial) {
+    extern __shared__ unsigned char smem_raw[];
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = q + 1;
+    const int entries = (levels + 1) * row;
+    for (int i = threadIdx.x; i < kLapWarps * entries; i += blockDim.x) tab[i] = (T)0;
+    __syncthreads();
+    T* mytab = tab + w * entries;
+    const int64_t nchunk = (N + 31) / 32;
+    for (int64_t ch = (int64_t)blockIdx.x * kLapWarps + w; ch < nchunk;
+         ch += (int64_t)gridDim.x * kLapWarps) {
+        const int64_t k = ch * 32 + lane;
+        const bool valid = k < N;
+        const int l = valid ? tband[k] : 255;
+        const double cv = valid ? (double)c[k] : 0.0;
+        // barycentric denominator on Omega_l (only for interpolated bands)
+        double tau = 0.0, den = 1.0;
+        int hit = -1;
+        const bool interp = valid && l < levels;
+        if (interp) {
+            const double a = ldexp(xi1, -l);
+            tau = (t[k] - 1.5 * a) / (0.5 * a);
+            den = 0.0;
+            for (int r = 0; r < q; ++r) {
+                const double d = tau - cheb[r];
+                if (d == 0.0) hit = r;
+                den += cheb[q + r] / d;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, l);
+        const bool leader = (peers & ((1u << lane) - 1u)) == 0u;
+        for (int r = 0; r <= q; ++r) {
+            T val = (T)0;
+            if (r == q) {
+                val = (T)cv;
+            } else if (interp) {
+                const double Lr = (hit >= 0) ? (r == hit ? 1.0 : 0.0)
+                                             : (cheb[q + r] / (tau - cheb[r])) / den;
+                val = (T)(Lr * cv);
+            }
+            T acc = (T)0;
+            for (int src = 0; src < 32; ++src) {
+                const T x = __shfl_sync(0xffffffffu, val, src);
+                if ((peers >> src) & 1u) acc += x;
+            }
+            if (valid && leader) mytab[l * row + r] += acc;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < entries; i += blockDim.x) {
+        T s = (T)0;
+        for (int ww = 0; ww < kLapWarps; ++ww) s += tab[ww * entries + i];
+        partial[(int64_t)blockIdx.x * entries + i] = s;
+    }
+}
+
+// vS[i] = sum over blocks (in block order) of partial[b][i].
+template <typename T>
+__global__ void k_lap_reduce(int nblocks, int entries, const T* __restrict__ partial,
+                             double* __restrict__ vS) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= entries) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += (double)partial[(int64_t)b * entries + i];
+    vS[i] = s;
+}
+
+// h^{Y_m}_s for m = blockIdx.x + 1 (threads over s) with
+// K^{Y_m,Omega_l}_{s r} = exp(-y_s xi_r) formed on the fly; block 0 also forms
+// the cumulative sums g_l = sum_{l' >= l} S_{l'}, g_{levels+1} = 0.
+__global__ void k_lap_couple(int levels, int q, double y1, double xi1,
+                             const int* __restrict__ ell, const double* __restrict__ cheb,
+                             const double* __restrict__ vS, double* __restrict__ h,
+                             double* __restrict__ g) {
+    const int m = blockIdx.x + 1;
+    const int row = q + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g[levels + 1] = 0.0;
+        for (int l = levels; l >= 1; --l) g[l] = g[l + 1] + vS[l * row + q];
+    }
+    if (m >= levels) return;
+    const int s = threadIdx.x;
+    if (s >= q) return;
+    const double ay = ldexp(y1, -m);
+    const double ys = 1.5 * ay + 0.5 * ay * cheb[s];
+    double acc = 0.0;
+    for (int l = ell[m]; l <= levels - m; ++l) {
+        const double ax = ldexp(xi1, -l);
+        for (int r = 0; r < q; ++r) {
+            const double xr = 1.5 * ax + 0.5 * ax * cheb[r];
+            acc += exp(-ys * xr) * vS[l * row + r];
+        }
+    }
+    h[m * q + s] = acc;
+}
+
+// f~_j: barycentric weights of s_j on Y_m (double), then sum_s L_s h_s + g_{L_m + 1}.
+template <typename T>
+__global__ void k_lap_eval(int64_t M, const double* __restrict__ sv,
+                           const uint8_t* __restrict__ sband, int levels, int q, double y1,
+                           const double* __restrict__ cheb, const double* __restrict__ h,
+                           const double* __restrict__ g, T* __restrict__ f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int m = sband[j];
+    if (m >= levels) {
+        f[j] = (T)g[1];
+        return;
+    }
+    const double a = ldexp(y1, -m);
+    const double tau = (sv[j] - 1.5 * a) / (0.5 * a);
+    double den = 0.0, num = 0.0;
+    int hit = -1;
+    for (int s = 0; s < q; ++s) {
+        const double d = tau - cheb[s];
+        if (d == 0.0) hit = s;
+        const double wgt = cheb[q + s] / d;
+        den += wgt;
+        num += wgt * h[m * q + s];
+    }
+    const double interp = (hit >= 0) ? h[m * q + hit] : num / den;
+    f[j] = (T)(interp + g[levels - m + 1]);
+}
+
+// Chebyshev points and barycentric weights (Section 2); same table as Algorithm 2.
+__global__ void k_lap_cheb(int q, double* cheb) {
+    const int s = threadIdx.x;
+    if (s >= q) return;
+    double sn, cs;
+    sincospi((2.0 * s + 1.0) / (2.0 * q), &sn, &cs);
+    cheb[s] = cs;
+    cheb[q + s] = (s & 1) ? -sn : sn;
+}
+
+// ---------------------------------------------------------------------------
+// Scratch layout of one Laplace evaluation (all offsets in bytes, 256-aligned).
+struct LapLayout {
+    size_t partial, vS, h, g, ell, total;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static LapLayout lap_layout(int levels, int q, int nblocks, size_t tsize) {
+    LapLayout L;
+    const size_t entries = (size_t)(levels + 1) * (q + 1);
+    size_t off = 0;
+    L.partial = off; off = align256(off + (size_t)nblocks * entries * tsize);
+    L.vS = off;      off = align256(off + entries * sizeof(double));
+    L.h = off;       off = align256(off + (size_t)(levels + 1) * q * sizeof(double));
+    L.g = off;       off = align256(off + (size_t)(levels + 2) * sizeof(double));
+    L.ell = off;     off = align256(off + (size_t)(levels + 1) * sizeof(int));
+    L.total = off;
+    return L;
+}
+
+static int lap_blocks(int64_t N) {
+    const int64_t chunks = (N + 31) / 32;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(kLapMaxBlocks, (chunks + kLapWarps - 1) / kLapWarps));
+}
+
+// Parameters of Definition 3.2 for the whole eps (Algorithm 1).
+struct LapParams {
+    int q, levels;
+    double y1, xi1;
+    int ell[FL_MAX_LEVELS];
+};
+
+static bool lap_params(double eps, int q_in, double y1, double xi1, LapParams* P) {
+    P->q = q_in > 0 ? q_in : (int)ceil(0.5 + log(1.0 / eps) / log(4.0));
+    P->y1 = y1;
+    P->xi1 = xi1;
+    if (!(y1 > 0.0) || !(xi1 > 0.0)) {
+        P->levels = 1;
+    } else {
+        P->levels = (int)std::max(1.0, ceil(log2(y1 * xi1 / eps)) + 1.0);
+    }
+    if (P->levels > 127 || P->q > kMaxQ) return false;
+    for (int m = 0; m < FL_MAX_LEVELS; ++m) P->ell[m] = 0;
+    for (int m = 1; m < P->levels; ++m) {
+        const double lg = log2(y1 * xi1) - m - log2(log(1.0 / eps));
+        P->ell[m] = std::max(1, (int)floor(lg) + 1);
+    }
+    return true;
+}
+
+// Launches moments -> reduce -> couple -> eval on `scratch` (layout above).
+template <typename T>
+static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* s,
+                           const uint8_t* tband, const uint8_t* sband, const LapParams& P,
+                           const double* cheb, const T* c, T* f, unsigned char* scratch,
+                           int nblocks, cudaStream_t st, Plan* timed) {
+    const LapLayout L = lap_layout(P.levels, P.q, nblocks, sizeof(T));
+    const int entries = (P.levels + 1) * (P.q + 1);
+    T* partial = (T*)(scratch + L.partial);
+    double* vS = (double*)(scratch + L.vS);
+    double* h = (double*)(scratch + L.h);
+    double* g = (double*)(scratch + L.g);
+    const int* ell = (const int*)(scratch + L.ell);
+    const size_t smem = (size_t)kLapWarps * entries * sizeof(T);
+    int slot = -1;
+    if (N > 0) {
+        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (timed) timer_begin(*timed, "lap_moments", (double)N * (8 + 1 + sizeof(T)), st, &slot);
+        k_lap_moments<T><<<nblocks, kLapWarps * 32, smem, st>>>(N, t, tband, c, P.levels, P.q, P.xi1,
+                                                                cheb, partial);
+        if (timed) timer_end(*timed, slot, st);
+        k_lap_reduce<T><<<(entries + 255) / 256, 256, 0, st>>>(nblocks, entries, partial, vS);
+    } else {
+        cudaError_t e = cudaMemsetAsync(vS, 0, entries * sizeof(double), st);
+        if (e != cudaSuccess) return e;
+    }
+    k_lap_couple<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
+        P.levels, P.q, P.y1, P.xi1, ell, cheb, vS, h, g);
+    if (M > 0) {
+        if (timed) timer_begin(*timed, "lap_eval", (double)M * (8 + 1 + sizeof(T)), st, &slot);
+        k_lap_eval<T><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, s, sband, P.levels, P.q, P.y1,
+                                                                  cheb, h, g, f);
+        if (timed) timer_end(*timed, slot, st);
+    }
+    if (timed) timed->launches += (N > 0 ? 2 : 0) + 1 + (M > 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+}  // namespace fl
 
 using namespace fl;
 
-extern "C" {
+static fl_status lap_fail(fl_status s, const std::string& m) { return set_error(s, m); }
 
-fl_status fl_plan_laplace(fl_plan_t* out, int64_t, int64_t, const double*, const double*, int,
-                          double, fl_precision, void*) {
-    if (out) *out = nullptr;
-    return FL_EUNSUPPORTED;
+namespace fl {
+
+cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
+    LapParams P;
+    memset(&P, 0, sizeof(P));
+    P.q = p.q;
+    P.levels = p.levels;
+    P.y1 = p.y1;
+    P.xi1 = p.xi1;
+    for (int m = 1; m < p.levels && m < (int)p.bands.size(); ++m) P.ell[m] = p.bands[m].ell;
+    const uint8_t* tband = p.d_tband;
+    if (p.prec == FL_FP64)
+        return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_bandid, P, p.d_cheb,
+                               (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
+                               st, &p);
+    return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_bandid, P, p.d_cheb, (const float*)c,
+                          (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p);
 }
 
-fl_status fl_laplace_real(fl_plan_t, const void*, void*, void*) { return FL_EUNSUPPORTED; }
+}  // namespace fl
+
+#define LAP_CUDA(call, where)                                                      \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return lap_fail(e_ == cudaErrorMemoryAllocation ? FL_ENOMEM : FL_ECUDA, \
+                            std::string(where) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, int q,
+                                   cudaStream_t st) {
+    // interval ends and validity
+    unsigned long long* dmx = nullptr;
+    int* dflag = nullptr;
+    LAP_CUDA(cudaMalloc((void**)&dmx, 2 * sizeof(unsigned long long)), "cudaMalloc");
+    cudaError_t e = cudaMalloc((void**)&dflag, sizeof(int));
+    unsigned long long mx[2] = {0, 0};
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmx, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, sizeof(int), st);
+    if (e == cudaSuccess && (p.N > 0 || p.M > 0)) {
+        k_lap_minmax<<<256, 256, 0, st>>>(p.N, t, p.M, s, dmx, dflag);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx, dmx, sizeof(mx), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dmx);
+    cudaFree(dflag);
+    LAP_CUDA(e, "fl_plan_laplace: node scan");
+    if (flag) return lap_fail(FL_EINVAL, "fl_plan_laplace: a t_k or s_j is negative or not finite");
+    double xi1, y1;
+    memcpy(&xi1, &mx[0], sizeof(double));
+    memcpy(&y1, &mx[1], sizeof(double));
+    LapParams P;
+    if (!lap_params(p.eps, q, y1, xi1, &P))
+        return lap_fail(FL_EUNSUPPORTED, "fl_plan_laplace: more than 127 levels or q above 40");
+    p.q = P.q;
+    p.levels = P.levels;
+    p.y1 = y1;
+    p.xi1 = xi1;
+    p.eps_K = p.eps;
+    p.bands.assign(P.levels + 1, BandHost());
+    for (int m = 1; m < P.levels; ++m) {
+        p.bands[m].ell = P.ell[m];
+        p.bands[m].Lm = P.levels - m;
+    }
+    // copies of the nodes and their band ids
+    const size_t N = (size_t)p.N, M = (size_t)p.M;
+    if (N) {
+        LAP_CUDA(cudaMalloc((void**)&p.d_t, N * sizeof(double)), "cudaMalloc t");
+        LAP_CUDA(cudaMemcpyAsync(p.d_t, t, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy t");
+        LAP_CUDA(cudaMalloc((void**)&p.d_tband, N), "cudaMalloc t bands");
+        k_lap_band<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(p.N, p.d_t, xi1, P.levels, p.d_tband);
+    }
+    if (M) {
+        LAP_CUDA(cudaMalloc((void**)&p.d_s, M * sizeof(double)), "cudaMalloc s");
+        LAP_CUDA(cudaMemcpyAsync(p.d_s, s, M * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy s");
+        LAP_CUDA(cudaMalloc((void**)&p.d_bandid, M), "cudaMalloc s bands");
+        k_lap_band<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(p.M, p.d_s, y1, P.levels, p.d_bandid);
+    }
+    LAP_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
+    k_lap_cheb<<<1, 64, 0, st>>>(P.q, p.d_cheb);
+    p.lap_blocks = lap_blocks(p.N);
+    const size_t tsz = p.prec == FL_FP64 ? 8 : 4;
+    if ((size_t)kLapWarps * (P.levels + 1) * (P.q + 1) * tsz > 200 * 1024)
+        return lap_fail(FL_EUNSUPPORTED, "fl_plan_laplace: moment tables exceed shared memory "
+                                         "(too many levels for this q)");
+    const LapLayout L = lap_layout(P.levels, P.q, p.lap_blocks, p.prec == FL_FP64 ? 8 : 4);
+    LAP_CUDA(cudaMalloc(&p.d_lap, L.total), "cudaMalloc scratch");
+    std::vector<int> ell(P.levels + 1, 0);
+    for (int m = 1; m < P.levels; ++m) ell[m] = P.ell[m];
+    LAP_CUDA(cudaMemcpyAsync((unsigned char*)p.d_lap + L.ell, ell.data(), ell.size() * sizeof(int),
+                             cudaMemcpyHostToDevice, st),
+             "copy l_m");
+    LAP_CUDA(cudaGetLastError(), "fl_plan_laplace: launch");
+    LAP_CUDA(cudaStreamSynchronize(st), "fl_plan_laplace: synchronise");
+    const size_t ts = p.prec == FL_FP64 ? 8 : 4;
+    p.scratch_bytes = (double)L.total + N * 9.0 + M * 9.0;
+    p.model_bytes = (double)N * (8 + 1 + ts) + (double)M * (8 + 1 + ts);
+    return FL_OK;
+}
+
+extern "C" {
+
+fl_status fl_plan_laplace(fl_plan_t* out, int64_t N, int64_t M, const double* t_dev,
+                          const double* s_dev, int q, double eps, fl_precision prec, void* stream) {
+    clear_error();
+    if (!out) return lap_fail(FL_EINVAL, "fl_plan_laplace: out is NULL");
+    *out = nullptr;
+    if (N < 0 || M < 0) return lap_fail(FL_EINVAL, "fl_plan_laplace: need N >= 0 and M >= 0");
+    if (N > ((int64_t)1 << 31) - 1 || M > ((int64_t)1 << 31) - 1)
+        return lap_fail(FL_EUNSUPPORTED, "fl_plan_laplace: N or M above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0)) return lap_fail(FL_EINVAL, "fl_plan_laplace: eps must lie in (0, 1)");
+    if (q < 0 || q > kMaxQ) return lap_fail(FL_EINVAL, "fl_plan_laplace: q must lie in [0, 40]");
+    if (prec != FL_FP32 && prec != FL_FP64) return lap_fail(FL_EINVAL, "fl_plan_laplace: unknown precision");
+    if ((N > 0 && !t_dev) || (M > 0 && !s_dev)) return lap_fail(FL_EINVAL, "fl_plan_laplace: NULL nodes");
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return lap_fail(FL_ENOMEM, "fl_plan_laplace: host allocation");
+    h->p.kind = 1;
+    h->p.prec = prec;
+    h->p.N = N;
+    h->p.M = M;
+    h->p.eps = eps;
+    fl_status s = plan_laplace_impl(h->p, t_dev, s_dev, q, (cudaStream_t)stream);
+    if (s != FL_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+fl_status fl_laplace_real(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
+    clear_error();
+    if (!h || h->p.kind != 1) return lap_fail(FL_EINVAL, "fl_laplace_real: not a Laplace plan");
+    if ((h->p.N > 0 && !c_dev) || (h->p.M > 0 && !f_dev))
+        return lap_fail(FL_EINVAL, "fl_laplace_real: NULL buffer");
+    cudaError_t e = run_laplace(h->p, c_dev, f_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return lap_fail(FL_ECUDA, std::string("fl_laplace_real: ") + cudaGetErrorString(e));
+    return FL_OK;
+}
 
 }  // extern "C"

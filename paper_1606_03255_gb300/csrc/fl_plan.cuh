@@ -71,6 +71,7 @@ struct Plan {
     // Laplace (Algorithm 1)
     double* d_t = nullptr;
     double* d_s = nullptr;
+    uint8_t* d_tband = nullptr;    // band of every t_k
     void* d_lap = nullptr;         // moments and partial sums
     int lap_blocks = 0;
 
@@ -98,11 +99,19 @@ cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_
 cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
 
 // Launchers (fl_laplace.cu)
-cudaError_t laplace_prepare(Plan& p, cudaStream_t st);
 cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st);
+
+// Per-thread error message of the C ABI (fl_api.cu)
+fl_status set_error(fl_status s, const std::string& msg);
+void clear_error();
 
 // Timing helpers (fl_api.cu)
 void timer_begin(Plan& p, const char* name, double bytes, cudaStream_t st, int* slot);
 void timer_end(Plan& p, int slot, cudaStream_t st);
 
 }  // namespace fl
+
+// The opaque handle of include/fl.h.
+struct fl_plan_s {
+    fl::Plan p;
+};

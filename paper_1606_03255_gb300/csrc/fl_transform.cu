@@ -224,12 +224,14 @@ __global__ void __launch_bounds__(1024) k_fft_pass1(BandDev B, int rhs0, int log
     const int nthr = n2 >> 3;
     fft_smem<SIGN, T>(sm + (threadIdx.x / nthr) * ld, log2n2, threadIdx.x % nthr, true);
     C* out = Y + (int64_t)blockIdx.y * n;
+    const T inv_n = (T)1 / (T)n;
     for (int idx = threadIdx.x; idx < TC * n2; idx += blockDim.x) {
         const int col = idx % TC, l2 = idx / TC;
         const int64_t i1 = i1b + col;
         int64_t e = (i1 * l2) & (n - 1);
         if (e >= n / 2) e -= n;
-        const C w = expipi<T>((T)((double)(2 * SIGN) * (double)e / (double)n));
+        // |e| <= n/2 <= 2^23 and 2/n is a power of two: the angle is exact in T
+        const C w = expipi<T>((T)(2 * SIGN) * (T)e * inv_n);
         out[(int64_t)l2 * n1 + i1] = cmul(sm[col * ld + l2], w);
     }
 }
@@ -280,7 +282,7 @@ template <typename T> __device__ __forceinline__ T kb_window(T t, T m, T b) {
 template <typename T>
 __device__ __forceinline__ void bary_weights(double y, const BandDev& B, int q,
                                              const double* __restrict__ cheb, T* Ls) {
-    const double tau = (y - B.yc) / B.yh;
+    const double tau = (y - B.yc) * B.yh_inv;
     T den = 0;
     int hit = -1;
     for (int s = 0; s < q; ++s) {
