@@ -156,6 +156,32 @@ fl_status fl_plan_laplace(fl_plan_t *out, int64_t N, int64_t M, const double *t_
 /* fl_laplace_real -- f~ ~= K c (Algorithm 1), c_dev N reals, f_dev M reals. */
 fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
 
+/*
+ * fl_laplace_real_noalloc -- the real Laplace transform of fl_plan_laplace +
+ * fl_laplace_real in one call that allocates no device memory.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate at
+ * the point where they need the transform -- code running inside another
+ * framework's memory pool that forbids outside allocations, real-time loops
+ * where cudaMalloc (which can synchronise the whole device) is not allowed,
+ * or a device that is already full.
+ *   t_dev, s_dev, c_dev, f_dev, q, eps, prec : as fl_plan_laplace and
+ *               fl_laplace_real (c and f real, float64 for FL_FP64, float32
+ *               for FL_FP32); the result equals theirs.
+ * Scratch: a fixed static device array of 2 MiB, held by every GPU that loads
+ * libfl.so until the process exits.  Its use depends on the number of levels
+ * and on q only (not on N or M); a problem that needs more returns
+ * FL_EUNSUPPORTED with the bytes needed in fl_last_error().
+ * The first call on each device does a one-time set-up (it looks up the
+ * array's device address); make that first call before any stream capture.
+ * The call synchronises `stream` once (it reads max t and max s back to choose
+ * the levels).  Every call on a device shares the one array, which keeps the
+ * last call's contents: calls that overlap on the GPU (two streams, two host
+ * threads) race and give wrong results, so serialise them.
+ */
+fl_status fl_laplace_real_noalloc(int64_t N, int64_t M, const double *t_dev,
+                                  const double *s_dev, const void *c_dev, void *f_dev,
+                                  int q, double eps, fl_precision prec, void *stream);
+
 /* Plan parameters and sizes (host call, no device work). */
 fl_status fl_get_info(fl_plan_t p, fl_info *info);
 

@@ -13,9 +13,11 @@
 // deterministic: per-warp tables, warp-ordered group sums, block partials
 // reduced in block order by k_lap_reduce), k_lap_couple (h and g), k_lap_eval.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,7 +73,7 @@ __global__ void k_lap_band(int64_t n, const double* __restrict__ v, double v1, i
 // for every 32 consecutive t_k it takes, lanes are grouped by band
 // (match_any) and each group's sum is formed in lane order and added by the
 // group's lowest lane, so the result does not depend on scheduling.
-template <typename T>
+template <typename T, bool BANDS_FROM_VALUES = false>
 __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
                               const uint8_t* __restrict__ tband, const T* __restrict__ c,
                               int levels, int q, double xi1, const double* __restrict__ cheb,
@@ -89,7 +91,7 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
          ch += (int64_t)gridDim.x * kLapWarps) {
         const int64_t k = ch * 32 + lane;
         const bool valid = k < N;
-        const int l = valid ? tband[k] : 255;
+        const int l = !valid ? 255 : (BANDS_FROM_VALUES ? lap_band(t[k], xi1, levels) : tband[k]);
         const double cv = valid ? (double)c[k] : 0.0;
         // barycentric denominator on Omega_l (only for interpolated bands)
         double tau = 0.0, den = 1.0;
@@ -173,14 +175,14 @@ __global__ void k_lap_couple(int levels, int q, double y1, double xi1,
 }
 
 // f~_j: barycentric weights of s_j on Y_m (double), then sum_s L_s h_s + g_{L_m + 1}.
-template <typename T>
+template <typename T, bool BANDS_FROM_VALUES = false>
 __global__ void k_lap_eval(int64_t M, const double* __restrict__ sv,
                            const uint8_t* __restrict__ sband, int levels, int q, double y1,
                            const double* __restrict__ cheb, const double* __restrict__ h,
                            const double* __restrict__ g, T* __restrict__ f) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
-    const int m = sband[j];
+    const int m = BANDS_FROM_VALUES ? lap_band(sv[j], y1, levels) : sband[j];
     if (m >= levels) {
         f[j] = (T)g[1];
         return;
@@ -262,7 +264,7 @@ static bool lap_params(double eps, int q_in, double y1, double xi1, LapParams* P
 }
 
 // Launches moments -> reduce -> couple -> eval on `scratch` (layout above).
-template <typename T>
+template <typename T, bool BANDS_FROM_VALUES = false>
 static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* s,
                            const uint8_t* tband, const uint8_t* sband, const LapParams& P,
                            const double* cheb, const T* c, T* f, unsigned char* scratch,
@@ -277,12 +279,12 @@ static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* 
     const size_t smem = (size_t)kLapWarps * entries * sizeof(T);
     int slot = -1;
     if (N > 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T>,
+        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T, BANDS_FROM_VALUES>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         if (timed) timer_begin(*timed, "lap_moments", (double)N * (8 + 1 + sizeof(T)), st, &slot);
-        k_lap_moments<T><<<nblocks, kLapWarps * 32, smem, st>>>(N, t, tband, c, P.levels, P.q, P.xi1,
-                                                                cheb, partial);
+        k_lap_moments<T, BANDS_FROM_VALUES><<<nblocks, kLapWarps * 32, smem, st>>>(
+            N, t, tband, c, P.levels, P.q, P.xi1, cheb, partial);
         if (timed) timer_end(*timed, slot, st);
         k_lap_reduce<T><<<(entries + 255) / 256, 256, 0, st>>>(nblocks, entries, partial, vS);
     } else {
@@ -293,8 +295,8 @@ static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* 
         P.levels, P.q, P.y1, P.xi1, ell, cheb, vS, h, g);
     if (M > 0) {
         if (timed) timer_begin(*timed, "lap_eval", (double)M * (8 + 1 + sizeof(T)), st, &slot);
-        k_lap_eval<T><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, s, sband, P.levels, P.q, P.y1,
-                                                                  cheb, h, g, f);
+        k_lap_eval<T, BANDS_FROM_VALUES><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
+            M, s, sband, P.levels, P.q, P.y1, cheb, h, g, f);
         if (timed) timer_end(*timed, slot, st);
     }
     if (timed) timed->launches += (N > 0 ? 2 : 0) + 1 + (M > 0 ? 1 : 0);
@@ -447,6 +449,143 @@ fl_status fl_laplace_real(fl_plan_t h, const void* c_dev, void* f_dev, void* str
         return lap_fail(FL_EINVAL, "fl_laplace_real: NULL buffer");
     cudaError_t e = run_laplace(h->p, c_dev, f_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return lap_fail(FL_ECUDA, std::string("fl_laplace_real: ") + cudaGetErrorString(e));
+    return FL_OK;
+}
+
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of fl_laplace_real (fl_laplace_real_noalloc).
+//
+// Some callers cannot allocate device memory at the point where they need the
+// transform: code running inside another framework's memory pool that forbids
+// outside allocations, real-time loops where a cudaMalloc (which may
+// synchronise the device) is not allowed, or a device that is already full.
+// For them every buffer this entry point uses beyond the caller's inputs and
+// outputs lives in g_noalloc_scratch, one static device array of
+// kNoAllocScratchBytes that each GPU loading libfl.so holds until the process
+// exits.  Host code cannot pass the array's name to a kernel (on the host it
+// is only a stand-in for the device symbol), so the first call on each device
+// looks up its device address with cudaGetSymbolAddress, with that device
+// current, and keeps it.
+constexpr size_t kNoAllocScratchBytes = (size_t)2 << 20;   // 2 MiB per GPU
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (set up once).
+fl_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return set_error(FL_ECUDA, std::string("fl_laplace_real_noalloc: cudaGetDevice: ") +
+                                       cudaGetErrorString(e));
+    if (dev < 0 || dev >= kNoAllocMaxDevices)
+        return set_error(FL_EUNSUPPORTED, "fl_laplace_real_noalloc: device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(FL_ECUDA, std::string("fl_laplace_real_noalloc: cudaGetSymbolAddress: ") +
+                                           cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FL_OK;
+}
+
+struct EllArg {
+    int v[FL_MAX_LEVELS];
+};
+
+__global__ void k_store_ell(EllArg a, int n, int* __restrict__ dst) {
+    const int i = threadIdx.x;
+    if (i < n) dst[i] = a.v[i];
+}
+
+}  // namespace
+
+extern "C" {
+
+fl_status fl_laplace_real_noalloc(int64_t N, int64_t M, const double* t_dev, const double* s_dev,
+                                  const void* c_dev, void* f_dev, int q, double eps,
+                                  fl_precision prec, void* stream) {
+    clear_error();
+    if (N < 0 || M < 0) return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: need N >= 0 and M >= 0");
+    if (N > ((int64_t)1 << 31) - 1 || M > ((int64_t)1 << 31) - 1)
+        return lap_fail(FL_EUNSUPPORTED, "fl_laplace_real_noalloc: N or M above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0))
+        return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: eps must lie in (0, 1)");
+    if (q < 0 || q > kMaxQ) return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: q must lie in [0, 40]");
+    if (prec != FL_FP32 && prec != FL_FP64)
+        return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: unknown precision");
+    if ((N > 0 && (!t_dev || !c_dev)) || (M > 0 && (!s_dev || !f_dev)))
+        return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: NULL buffer");
+    unsigned char* scratch = nullptr;
+    fl_status st0 = noalloc_scratch(&scratch);
+    if (st0 != FL_OK) return st0;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // [0, 256): interval maxima (2 x u64) and the validity flag; cleared every call
+    unsigned long long* dmx = (unsigned long long*)scratch;
+    int* dflag = (int*)(scratch + 2 * sizeof(unsigned long long));
+    LAP_CUDA(cudaMemsetAsync(scratch, 0, 256, st), "fl_laplace_real_noalloc: clear");
+    if (N > 0 || M > 0) k_lap_minmax<<<256, 256, 0, st>>>(N, t_dev, M, s_dev, dmx, dflag);
+    LAP_CUDA(cudaGetLastError(), "fl_laplace_real_noalloc: launch");
+    unsigned long long mx[2] = {0, 0};
+    int flag = 0;
+    LAP_CUDA(cudaMemcpyAsync(mx, dmx, sizeof(mx), cudaMemcpyDeviceToHost, st), "fl_laplace_real_noalloc: read");
+    LAP_CUDA(cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st),
+             "fl_laplace_real_noalloc: read");
+    LAP_CUDA(cudaStreamSynchronize(st), "fl_laplace_real_noalloc: synchronise");
+    if (flag) return lap_fail(FL_EINVAL, "fl_laplace_real_noalloc: a t_k or s_j is negative or not finite");
+    double xi1, y1;
+    memcpy(&xi1, &mx[0], sizeof(double));
+    memcpy(&y1, &mx[1], sizeof(double));
+    LapParams P;
+    if (!lap_params(eps, q, y1, xi1, &P))
+        return lap_fail(FL_EUNSUPPORTED, "fl_laplace_real_noalloc: more than 127 levels or q above 40");
+    const size_t tsz = prec == FL_FP64 ? 8 : 4;
+    if ((size_t)kLapWarps * (P.levels + 1) * (P.q + 1) * tsz > 200 * 1024)
+        return lap_fail(FL_EUNSUPPORTED, "fl_laplace_real_noalloc: moment tables exceed shared memory");
+
+    // [256, 256 + cheb): Chebyshev table; then the Algorithm 1 layout
+    const size_t cheb_off = 256;
+    const size_t lap_off = align256(cheb_off + 2 * kMaxQ * sizeof(double));
+    const int nblocks = lap_blocks(N);
+    const LapLayout L = lap_layout(P.levels, P.q, nblocks, tsz);
+    if (lap_off + L.total > kNoAllocScratchBytes) {
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "fl_laplace_real_noalloc: this problem needs %zu bytes of scratch (levels = %d, "
+                 "q = %d); the static maximum is %zu bytes -- use fl_plan_laplace, a larger eps "
+                 "or a smaller max(s) * max(t)",
+                 lap_off + L.total, P.levels, P.q, kNoAllocScratchBytes);
+        return lap_fail(FL_EUNSUPPORTED, msg);
+    }
+    double* cheb = (double*)(scratch + cheb_off);
+    unsigned char* lap = scratch + lap_off;
+    k_lap_cheb<<<1, 64, 0, st>>>(P.q, cheb);
+    EllArg ea;
+    for (int m = 0; m < FL_MAX_LEVELS; ++m) ea.v[m] = (m < P.levels) ? P.ell[m] : 0;
+    k_store_ell<<<1, FL_MAX_LEVELS, 0, st>>>(ea, P.levels + 1, (int*)(lap + L.ell));
+    LAP_CUDA(cudaGetLastError(), "fl_laplace_real_noalloc: launch");
+    cudaError_t e;
+    if (prec == FL_FP64)
+        e = lap_run<double, true>(N, M, t_dev, s_dev, nullptr, nullptr, P, cheb, (const double*)c_dev,
+                                  (double*)f_dev, lap, nblocks, st, nullptr);
+    else
+        e = lap_run<float, true>(N, M, t_dev, s_dev, nullptr, nullptr, P, cheb, (const float*)c_dev,
+                                 (float*)f_dev, lap, nblocks, st, nullptr);
+    LAP_CUDA(e, "fl_laplace_real_noalloc");
     return FL_OK;
 }
 

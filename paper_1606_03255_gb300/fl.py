@@ -29,8 +29,8 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
 
 # Every symbol include/fl.h declares.
 EXPORTED = ["fl_plan", "fl_execute", "fl_execute_deriv", "fl_execute_host", "fl_adjoint",
-            "fl_plan_laplace", "fl_laplace_real", "fl_get_info", "fl_set_timing",
-            "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
+            "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
+            "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
 
 
 class fl_info(ctypes.Structure):
@@ -96,6 +96,7 @@ def load(path: str | None = None):
         "fl_adjoint": [vp, vp, vp, vp],
         "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
         "fl_laplace_real": [vp, vp, vp, vp],
+        "fl_laplace_real_noalloc": [i64, i64, vp, vp, vp, vp, ci, cd, ci, vp],
         "fl_get_info": [vp, ctypes.POINTER(fl_info)],
         "fl_set_timing": [vp, ci],
         "fl_get_timing": [vp, ctypes.POINTER(fl_timing)],
@@ -149,6 +150,16 @@ def fl_plan_laplace(N, M, t_ptr, s_ptr, q, eps, prec, stream):
 
 def fl_laplace_real(plan, c_ptr, f_ptr, stream):
     return load().fl_laplace_real(plan, c_ptr, f_ptr, stream)
+
+
+def fl_laplace_real_noalloc(N, M, t_ptr, s_ptr, c_ptr, f_ptr, q, eps, prec, stream):
+    """Laplace transform without any device allocation (static 2 MiB scratch).
+
+    For callers that cannot allocate device memory where they need the
+    transform; see include/fl.h for the limits and the one-time set-up.
+    """
+    return load().fl_laplace_real_noalloc(int(N), int(M), t_ptr, s_ptr, c_ptr, f_ptr, int(q),
+                                          float(eps), int(prec), stream)
 
 
 def fl_get_info(plan):
