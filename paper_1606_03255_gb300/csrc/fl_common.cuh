@@ -56,12 +56,19 @@ struct BandDev {
 // Shared-memory Stockham FFT, radix 8/4/2, 8 elements per thread.
 //
 // Computes X[l] = sum_i x[i] exp(SIGN * 2 pi i * i l / L) in place on a
-// contiguous smem array of length L = 2^log2L (8 <= L), using nthr = L/8
+// smem array holding element i at pad8(i), L = 2^log2L (8 <= L), using nthr = L/8
 // threads numbered t = 0..nthr-1.  Each stage with radix R, span Ns takes
 // job jj = (R-point butterfly) reading x[jj + r L/R], twiddling by
 // w^(r k), w = exp(SIGN 2 pi i / (Ns R)), k = jj mod Ns, and writing to
 // (jj - k) R + k + r Ns: the self-sorting Stockham order, so the result is in
 // natural order.  Every thread of the block must call it (it synchronises).
+
+// Padded shared-memory index: one spare element after every 8.  The Stockham
+// stores of the first stages have strides that are multiples of 8 elements and
+// would fall on two banks; with the pad they spread over all of them.  A
+// buffer for L points needs padded_len(L) elements.
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ __forceinline__ int padded_len(int L) { return L + (L >> 3); }
 
 template <int SIGN, typename C> __device__ __forceinline__ C mul_i(C a) {
     // a * (SIGN * i)
@@ -116,7 +123,7 @@ __device__ __forceinline__ void fft_stage(C_t<T>* buf, int L, int Ns, int t, int
             const int jj = t + jb * nthr;
             const int k = jj & (Ns - 1);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[jj + r * (L / R)];
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[pad8(jj + r * (L / R))];
             if (Ns > 1) {
                 // k < Ns and 1/(Ns R) is a power of two: exact argument
                 C w1 = expipi<T>((T)(2 * SIGN) * (T)k * inv_span);
@@ -141,7 +148,7 @@ __device__ __forceinline__ void fft_stage(C_t<T>* buf, int L, int Ns, int t, int
             const int k = jj & (Ns - 1);
             const int base = (jj - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) buf[base + r * Ns] = a[r];
+            for (int r = 0; r < R; ++r) buf[pad8(base + r * Ns)] = a[r];
         }
     }
     __syncthreads();

@@ -17,7 +17,12 @@
 // weights L_s^{Y_m}(y_j) (Section 2) in the same gather kernel.
 #include <math.h>
 
-#include "fl_plan.cuh"
+#include "fl_fft.cuh"
+
+namespace fl {
+FL_FFT_EXTERN(float)
+FL_FFT_EXTERN(double)
+}  // namespace fl
 
 namespace fl {
 
@@ -147,25 +152,6 @@ cudaError_t build_tables(Plan& p, cudaStream_t st) {
     return p.prec == FL_FP64 ? build_tables_t<double>(p, st) : build_tables_t<float>(p, st);
 }
 
-// ---------------------------------------------------------------------------
-// Forward input: grid index i in [0, n) holds frequency k' = i (i < n/2) or
-// i - n, i.e. k = k' + N_m/2; value c_k D[s][k] for 0 <= k < K, else 0.
-template <typename T, bool DERIV>
-__device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
-                                             const C_t<T>* __restrict__ c,
-                                             const T* __restrict__ D) {
-    const int64_t kp = (i < (B.n >> 1)) ? i : i - B.n;
-    const int64_t k = kp + (B.Nm >> 1);
-    if (k < 0 || k >= B.K) return C_t<T>{(T)0, (T)0};
-    const T d = D[B.D_off + (int64_t)s * B.K + k];
-    C_t<T> v = c[k];
-    if (DERIV) {   // (2 pi i k) c_k
-        const T w = (T)(kTwoPiD * (double)k);
-        v = C_t<T>{-v.y * w, v.x * w};
-    }
-    return C_t<T>{v.x * d, v.y * d};
-}
-
 // One CTA per work item: nfft FFTs of one band (one per right-hand side).
 // MODE 0: input generated from c and D (forward), written to the band grid.
 // MODE 1: input read from the band grid and transformed in place (adjoint).
@@ -185,84 +171,16 @@ __global__ void __launch_bounds__(512) k_small_fft(const SmallWork* __restrict__
     const int f = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const bool active = f < wk.nfft;
     const int s = wk.s0 + f;
-    C* buf = sm + (int64_t)f * L;
+    C* buf = sm + (int64_t)f * padded_len(L);
     C* g = grid + B.grid_off + (int64_t)s * L;
     if (active) {
         for (int e = t; e < L; e += nthr)
-            buf[e] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c, D) : g[e];
+            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c, D) : g[e];
     }
     __syncthreads();
     fft_smem<SIGN, T>(buf, wk.log2n, t, active);
     if (active)
-        for (int e = t; e < L; e += nthr) g[e] = buf[e];
-}
-
-// Four-step FFT of length n = n1 n2, pass 1: for a tile of TC columns i1, the
-// length-n2 FFTs over i2 of x[i1 + n1 i2], twiddled by exp(SIGN 2 pi i i1 l2/n),
-// stored to Y[l2 n1 + i1].
-template <typename T, int SIGN, int MODE, bool DERIV>
-__global__ void __launch_bounds__(1024) k_fft_pass1(BandDev B, int rhs0, int log2n1, int log2n2,
-                                                    int TC, const C_t<T>* __restrict__ c,
-                                                    const T* __restrict__ D,
-                                                    const C_t<T>* __restrict__ src,
-                                                    C_t<T>* __restrict__ Y) {
-    using C = C_t<T>;
-    extern __shared__ unsigned char smem_raw[];
-    C* sm = reinterpret_cast<C*>(smem_raw);
-    const int n1 = 1 << log2n1, n2 = 1 << log2n2;
-    const int ld = n2 + 1;
-    const int s = rhs0 + blockIdx.y;
-    const int64_t n = (int64_t)n1 * n2;
-    const int i1b = blockIdx.x * TC;
-    const C* in = src + B.grid_off + (int64_t)s * n;
-    for (int idx = threadIdx.x; idx < TC * n2; idx += blockDim.x) {
-        const int col = idx % TC, i2 = idx / TC;
-        const int64_t i = (int64_t)(i1b + col) + (int64_t)n1 * i2;
-        sm[col * ld + i2] = (MODE == 0) ? prep_value<T, DERIV>(i, B, s, c, D) : in[i];
-    }
-    __syncthreads();
-    const int nthr = n2 >> 3;
-    fft_smem<SIGN, T>(sm + (threadIdx.x / nthr) * ld, log2n2, threadIdx.x % nthr, true);
-    C* out = Y + (int64_t)blockIdx.y * n;
-    const T inv_n = (T)1 / (T)n;
-    for (int idx = threadIdx.x; idx < TC * n2; idx += blockDim.x) {
-        const int col = idx % TC, l2 = idx / TC;
-        const int64_t i1 = i1b + col;
-        int64_t e = (i1 * l2) & (n - 1);
-        if (e >= n / 2) e -= n;
-        // |e| <= n/2 <= 2^23 and 2/n is a power of two: the angle is exact in T
-        const C w = expipi<T>((T)(2 * SIGN) * (T)e * inv_n);
-        out[(int64_t)l2 * n1 + i1] = cmul(sm[col * ld + l2], w);
-    }
-}
-
-// Pass 2: for a tile of TR rows l2, the length-n1 FFTs over i1 of Y[l2 n1 + i1],
-// stored to X[l2 + n2 l1] (natural order of the length-n transform).
-template <typename T, int SIGN>
-__global__ void __launch_bounds__(1024) k_fft_pass2(BandDev B, int rhs0, int log2n1, int log2n2,
-                                                    int TR, const C_t<T>* __restrict__ Y,
-                                                    C_t<T>* __restrict__ dst) {
-    using C = C_t<T>;
-    extern __shared__ unsigned char smem_raw[];
-    C* sm = reinterpret_cast<C*>(smem_raw);
-    const int n1 = 1 << log2n1, n2 = 1 << log2n2;
-    const int ld = n1 + 1;
-    const int s = rhs0 + blockIdx.y;
-    const int64_t n = (int64_t)n1 * n2;
-    const int l2b = blockIdx.x * TR;
-    const C* in = Y + (int64_t)blockIdx.y * n;
-    for (int idx = threadIdx.x; idx < TR * n1; idx += blockDim.x) {
-        const int row = idx / n1, i1 = idx % n1;
-        sm[row * ld + i1] = in[(int64_t)(l2b + row) * n1 + i1];
-    }
-    __syncthreads();
-    const int nthr = n1 >> 3;
-    fft_smem<SIGN, T>(sm + (threadIdx.x / nthr) * ld, log2n1, threadIdx.x % nthr, true);
-    C* out = dst + B.grid_off + (int64_t)s * n;
-    for (int idx = threadIdx.x; idx < TR * n1; idx += blockDim.x) {
-        const int row = idx % TR, l1 = idx / TR;
-        out[(int64_t)(l2b + row) + (int64_t)n2 * l1] = sm[row * ld + l1];
-    }
+        for (int e = t; e < L; e += nthr) g[e] = buf[pad8(e)];
 }
 
 // ---------------------------------------------------------------------------
@@ -462,22 +380,13 @@ static void large_split(int log2n, int* l1, int* l2) {
     *l2 = log2n / 2;
 }
 
-template <typename T>
-static int tile_for(int log2len) {
-    // columns per CTA: <= 1024 threads (len/8 each), >= 64 B contiguous per row
-    const int len = 1 << log2len;
-    int tiles = (int)(64 / sizeof(C_t<T>));
-    while (tiles > 1 && tiles * (len / 8) > 1024) tiles >>= 1;
-    return tiles;
-}
-
 template <typename T, int SIGN, int MODE, bool DERIV>
 static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
     using C = C_t<T>;
     C* grid = (C*)p.d_grid;
     cudaError_t e = cudaSuccess;
     if (!p.small_work.empty()) {
-        const size_t smem = (size_t)(1 << kSmallMaxLog2) * sizeof(C);
+        const size_t smem = (size_t)padded_len(1 << kSmallMaxLog2) * sizeof(C);
         auto kern = k_small_fft<T, SIGN, MODE, DERIV>;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -499,17 +408,6 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         const BandDev& B = p.bands[b].dev;
         int l1, l2;
         large_split(B.log2n, &l1, &l2);
-        const int tc = tile_for<T>(l2), tr = tile_for<T>(l1);
-        const size_t sm1 = (size_t)tc * ((1 << l2) + 1) * sizeof(C);
-        const size_t sm2 = (size_t)tr * ((1 << l1) + 1) * sizeof(C);
-        auto k1 = k_fft_pass1<T, SIGN, MODE, DERIV>;
-        auto k2 = k_fft_pass2<T, SIGN>;
-        if ((e = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1)) !=
-            cudaSuccess)
-            return e;
-        if ((e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)) !=
-            cudaSuccess)
-            return e;
         // right-hand sides in chunks that fit the intermediate buffer
         const int chunk = (int)std::max<int64_t>(1, p.Y_elems / B.n);
         for (int s0 = 0; s0 < B.nrhs; s0 += chunk) {
@@ -520,15 +418,15 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
             const double b2 = (double)ns * 2.0 * B.n * sizeof(C);
             int slot;
             timer_begin(p, "fft_pass1", b1, st, &slot);
-            k1<<<dim3((unsigned)((1 << l1) / tc), (unsigned)ns), tc * ((1 << l2) / 8), sm1, st>>>(
-                B, s0, l1, l2, tc, (const C*)c, (const T*)p.d_D, grid, (C*)p.d_Y);
+            e = launch_pass1<T, SIGN, MODE, DERIV>(B, s0, ns, l1, l2, (const C*)c, (const T*)p.d_D,
+                                                   grid, (C*)p.d_Y, st);
             timer_end(p, slot, st);
+            if (e != cudaSuccess) return e;
             timer_begin(p, "fft_pass2", b2, st, &slot);
-            k2<<<dim3((unsigned)((1 << l2) / tr), (unsigned)ns), tr * ((1 << l1) / 8), sm2, st>>>(
-                B, s0, l1, l2, tr, (const C*)p.d_Y, grid);
+            e = launch_pass2<T, SIGN>(B, s0, ns, l1, l2, (const C*)p.d_Y, grid, st);
             timer_end(p, slot, st);
             p.launches += 2;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if (e != cudaSuccess) return e;
         }
     }
     return e;
