@@ -125,6 +125,17 @@ fl_status fl_execute(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
 fl_status fl_execute_deriv(fl_plan_t p, const void *c_dev, void *fprime_dev, void *stream);
 
 /*
+ * fl_grad_w -- gw_j = r_j * conj(f'_j), f'_j = sum_k (2 pi i k) c_k z_j^k: the
+ * gradient of a real loss with respect to the nodes w_j, given the upstream
+ * gradient r = dL/dRe f + i dL/dIm f (the chain rule for the holomorphic map
+ * w -> f(w) of eq. (4.1)).  fl_execute_deriv with the product fused into its
+ * last kernel.  c_dev: N complex; r_dev, gw_dev: M complex (plan precision).
+ * Z^0 nodes get 0.
+ */
+fl_status fl_grad_w(fl_plan_t p, const void *c_dev, const void *r_dev, void *gw_dev,
+                    void *stream);
+
+/*
  * fl_execute_host -- fl_execute on host buffers: copies c_host (N complex) to
  * the device, executes, copies the result to f_host (M complex) and
  * synchronises `stream`.  Staging buffers are owned by the plan.

@@ -64,9 +64,10 @@ def _load():
             i64, dp, ci = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int
             lib.oracle_flt_direct.argtypes = [i64, dp, i64, dp, dp, ci]
             lib.oracle_flt_adjoint.argtypes = [i64, dp, i64, dp, dp, ci]
+            lib.oracle_flt_adjoint_at.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_laplace_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_flt_brute_ld.argtypes = [i64, dp, i64, dp, dp]
-            for fn in (lib.oracle_flt_direct, lib.oracle_flt_adjoint,
+            for fn in (lib.oracle_flt_direct, lib.oracle_flt_adjoint, lib.oracle_flt_adjoint_at,
                        lib.oracle_laplace_direct, lib.oracle_flt_brute_ld):
                 fn.restype = ci
             lib.oracle_default_threads.restype = ci
@@ -109,6 +110,18 @@ def flt_adjoint(r, w, N: int, threads: int = 0) -> np.ndarray:
                                     g.ctypes.data, threads)
     if rc != 0:
         raise ValueError("oracle_flt_adjoint: invalid arguments")
+    return g
+
+
+def flt_adjoint_at(r, w, ks, threads: int = 0) -> np.ndarray:
+    """g_i = sum_j conj(z_j)^{ks[i]} r_j: the adjoint C^* r at selected frequencies."""
+    r, w = _c128(r), _nodes(w)
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    g = np.empty(ks.size, dtype=np.complex128)
+    rc = _load().oracle_flt_adjoint_at(ks.size, ks.ctypes.data, r.ctypes.data, w.shape[0],
+                                       w.ctypes.data, g.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle_flt_adjoint_at: invalid arguments")
     return g
 
 

@@ -16,7 +16,8 @@
  *                          (the index is shifted to start at k = 0) and the polar
  *                          split (4.2): z = exp(-y) exp(2 pi i x), y = 2 pi Im w.
  *   oracle_flt_adjoint     g_k = sum_j conj(z_j)^k r_j, the adjoint C^* of the
- *                          same matrix (Section 4, remark after Algorithm 2).
+ *                          same matrix (Section 4, remark after Algorithm 2);
+ *                          oracle_flt_adjoint_at: the same at selected k.
  *   oracle_laplace_direct  f_j = sum_k c_k exp(-s_j t_k), eq. (3.2) (real data).
  *   oracle_flt_brute_ld    oracle_flt_direct in long double, for tiny N.
  *
@@ -165,13 +166,15 @@ typedef struct {
     int64_t M;
     const double *r;   /* 2M */
     const double *w;   /* 2M */
-    double *g;         /* 2N out */
+    double *g;         /* 2 x (number of outputs) */
+    const int64_t *ks; /* NULL: output i is k = i; else k = ks[i] */
 } adj_ctx;
 
 static void adj_range(void *vctx, int64_t lo, int64_t hi)
 {
     const adj_ctx *cx = (const adj_ctx *)vctx;
-    for (int64_t k = lo; k < hi; ++k) {
+    for (int64_t i = lo; i < hi; ++i) {
+        const int64_t k = cx->ks ? cx->ks[i] : i;
         const double dk = (double)k;
         acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
         for (int64_t j = 0; j < cx->M; ++j) {
@@ -187,8 +190,8 @@ static void adj_range(void *vctx, int64_t lo, int64_t hi)
             acc_add(&im, rr * zi);
             acc_add(&im, ri * zr);
         }
-        cx->g[2 * k] = acc_get(&re);
-        cx->g[2 * k + 1] = acc_get(&im);
+        cx->g[2 * i] = acc_get(&re);
+        cx->g[2 * i + 1] = acc_get(&im);
     }
 }
 
@@ -198,8 +201,21 @@ int oracle_flt_adjoint(int64_t N, const double *r, int64_t M, const double *w,
     if (N < 0 || M < 0 || (M > 0 && (!r || !w)) || (N > 0 && !g)) return -1;
     for (int64_t j = 0; j < M; ++j)
         if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
-    adj_ctx cx = {M, r, w, g};
+    adj_ctx cx = {M, r, w, g, NULL};
     run_parallel(adj_range, &cx, N, nthreads);
+    return 0;
+}
+
+/* The adjoint at selected frequencies: g_i = sum_j conj(z_j)^{ks[i]} r_j. */
+int oracle_flt_adjoint_at(int64_t nk, const int64_t *ks, const double *r, int64_t M,
+                          const double *w, double *g, int nthreads)
+{
+    if (nk < 0 || M < 0 || (M > 0 && (!r || !w)) || (nk > 0 && (!g || !ks))) return -1;
+    for (int64_t i = 0; i < nk; ++i) if (ks[i] < 0) return -1;
+    for (int64_t j = 0; j < M; ++j)
+        if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
+    adj_ctx cx = {M, r, w, g, ks};
+    run_parallel(adj_range, &cx, nk, nthreads);
     return 0;
 }
 

@@ -295,6 +295,14 @@ fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* st
     return FL_OK;
 }
 
+fl_status fl_grad_w(fl_plan_t h, const void* c_dev, const void* r_dev, void* gw_dev, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_grad_w: not a Fourier-Laplace plan");
+    if (h->p.M > 0 && (!c_dev || !r_dev || !gw_dev)) return fail(FL_EINVAL, "fl_grad_w: NULL buffer");
+    cudaError_t e = run_forward(h->p, c_dev, gw_dev, true, (cudaStream_t)stream, r_dev);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_grad_w");
+    return FL_OK;
+}
+
 fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* stream) {
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_host: not a Fourier-Laplace plan");
     Plan& p = h->p;

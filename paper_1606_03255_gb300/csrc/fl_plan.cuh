@@ -95,7 +95,9 @@ cudaError_t launch_permute(Plan& p, const double* nodes, const uint32_t* keys,
 
 // Launchers (fl_transform.cu)
 cudaError_t build_tables(Plan& p, cudaStream_t st);
-cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st);
+// rmul != nullptr: f[j] = rmul[j] * conj(result_j) (the node-gradient epilogue)
+cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
+                        const void* rmul = nullptr);
 cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
 
 // Launchers (fl_laplace.cu)

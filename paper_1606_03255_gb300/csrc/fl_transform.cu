@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
                                                 const C_t<T>* __restrict__ grid,
                                                 const double* __restrict__ cheb, int q, T kb_b,
                                                 const C_t<T>* __restrict__ c, int deriv,
+                                                const C_t<T>* __restrict__ rmul,
                                                 C_t<T>* __restrict__ f) {
     using C = C_t<T>;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
         f[j] = deriv ? C{(T)0, (T)0} : c[0];
         return;
     }
+    // with rmul: f[j] = rmul[j] * conj(value) (node gradient, see fl_grad_w)
     const BandDev B = bands[b];
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
@@ -273,7 +275,8 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     double ph = (double)(B.Nm >> 1) * x;
     ph -= floor(ph);
     if (ph >= 0.5) ph -= 1.0;
-    f[j] = cmul(acc, expipi<T>((T)(2.0 * ph)));
+    const C val = cmul(acc, expipi<T>((T)(2.0 * ph)));
+    f[j] = rmul ? cmulc(rmul[j], val) : val;
 }
 
 // ---------------------------------------------------------------------------
@@ -433,7 +436,8 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
 }
 
 template <typename T, int MW>
-static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                            cudaStream_t st) {
     using C = C_t<T>;
     double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(C));
     for (int b = 1; b <= p.levels; ++b) {
@@ -446,17 +450,18 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, cudaStr
     timer_begin(p, "gather", bytes, st, &slot);
     k_gather<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.q,
-        (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (C*)f);
+        (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, (C*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
 }
 
 template <typename T>
-static cudaError_t gather_dispatch(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+static cudaError_t gather_dispatch(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                                   cudaStream_t st) {
     switch (p.mw) {
 #define FL_MW_CASE(W) \
-    case W: return gather_t<T, W>(p, c, f, deriv, st);
+    case W: return gather_t<T, W>(p, c, f, deriv, rmul, st);
         FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
         FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
 #undef FL_MW_CASE
@@ -465,16 +470,18 @@ static cudaError_t gather_dispatch(Plan& p, const void* c, void* f, bool deriv, 
 }
 
 template <typename T>
-static cudaError_t forward_t(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
+static cudaError_t forward_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                             cudaStream_t st) {
     if (p.M == 0) return cudaSuccess;
     cudaError_t e = deriv ? fft_bands<T, +1, 0, true>(p, c, st) : fft_bands<T, +1, 0, false>(p, c, st);
     if (e != cudaSuccess) return e;
-    return gather_dispatch<T>(p, c, f, deriv, st);
+    return gather_dispatch<T>(p, c, f, deriv, rmul, st);
 }
 
-cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st) {
-    return p.prec == FL_FP64 ? forward_t<double>(p, c, f, deriv, st)
-                             : forward_t<float>(p, c, f, deriv, st);
+cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
+                        const void* rmul) {
+    return p.prec == FL_FP64 ? forward_t<double>(p, c, f, deriv, rmul, st)
+                             : forward_t<float>(p, c, f, deriv, rmul, st);
 }
 
 template <typename T, int MW>

@@ -28,7 +28,8 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
                 FL_EUNSUPPORTED: "FL_EUNSUPPORTED"}
 
 # Every symbol include/fl.h declares.
-EXPORTED = ["fl_plan", "fl_execute", "fl_execute_deriv", "fl_execute_host", "fl_adjoint",
+EXPORTED = ["fl_plan", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
+            "fl_adjoint",
             "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
 
@@ -92,6 +93,7 @@ def load(path: str | None = None):
         "fl_plan": [pp, i64, i64, vp, ci, cd, ci, vp],
         "fl_execute": [vp, vp, vp, vp],
         "fl_execute_deriv": [vp, vp, vp, vp],
+        "fl_grad_w": [vp, vp, vp, vp, vp],
         "fl_execute_host": [vp, vp, vp, vp],
         "fl_adjoint": [vp, vp, vp, vp],
         "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
@@ -131,6 +133,10 @@ def fl_execute(plan, c_ptr, f_ptr, stream):
 
 def fl_execute_deriv(plan, c_ptr, f_ptr, stream):
     return load().fl_execute_deriv(plan, c_ptr, f_ptr, stream)
+
+
+def fl_grad_w(plan, c_ptr, r_ptr, gw_ptr, stream):
+    return load().fl_grad_w(plan, c_ptr, r_ptr, gw_ptr, stream)
 
 
 def fl_execute_host(plan, c_ptr, f_ptr, stream):
@@ -283,6 +289,18 @@ class Plan:
         fn = fl_execute_deriv if deriv else fl_execute
         check(fn(self._handle, _ptr(c), _ptr(out) if self.M else None, _stream_handle(stream)),
               "fl_execute")
+        return out
+
+    def grad_w(self, c, r, out=None, stream=None):
+        """gw_j = r_j conj(df/dw (w_j)): node gradient for upstream gradient r."""
+        torch = _torch()
+        _require(c, self.cdtype, self.N, "c")
+        _require(r, self.cdtype, self.M, "r")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=c.device)
+        _require(out, self.cdtype, self.M, "out")
+        check(fl_grad_w(self._handle, _ptr(c), _ptr(r) if self.M else None,
+                        _ptr(out) if self.M else None, _stream_handle(stream)), "fl_grad_w")
         return out
 
     def adjoint(self, r, out=None, stream=None):

@@ -131,6 +131,9 @@ def test_adjoint_inner_product_and_brute_force():
     assert np.max(np.abs(ref - Chr)) <= 1e-11 * np.sum(np.abs(r))
     # transposed without conjugation must fail
     assert np.max(np.abs(C.T @ r - Chr)) > 1e-3
+    # the selected-frequency variant returns the same entries
+    ks = np.array([0, 7, 299, 150, 7])
+    assert np.array_equal(oracle.flt_adjoint_at(r, w, ks), Chr[ks])
 
 
 def test_laplace_geometric_and_single_term():
