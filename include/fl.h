@@ -108,6 +108,25 @@ typedef struct {
 fl_status fl_plan(fl_plan_t *out, int64_t N, int64_t M, const double *nodes_dev,
                   int q, double eps, fl_precision prec, void *stream);
 
+/* Planning options (fl_plan_ex). */
+typedef struct {
+    int route;            /* how each non-empty band is evaluated:
+                             0 = by estimated cost (default): an NFFT with q
+                                 right-hand sides, or the direct sum of eq. (4.1)
+                                 over the band's frequencies when it has few nodes;
+                             1 = every band by NFFT (Algorithm 2 as printed);
+                             2 = every band by the direct sum                      */
+    double direct_bias;   /* multiplies the direct-sum cost in route 0 (0 = 1.0)  */
+} fl_options;
+
+/*
+ * fl_plan_ex -- fl_plan with options (NULL = defaults, i.e. fl_plan).
+ * Returns FL_EINVAL for an invalid option value.
+ */
+fl_status fl_plan_ex(fl_plan_t *out, int64_t N, int64_t M, const double *nodes_dev,
+                     int q, double eps, fl_precision prec, const fl_options *opt,
+                     void *stream);
+
 /*
  * fl_execute -- f~ ~= C c with C = (z_j^k), Algorithm 2.
  *   c_dev : device, N complex (plan precision).

@@ -36,7 +36,8 @@ static fl_status cuda_fail(cudaError_t e, const char* where) {
 
 Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_cheb, d_D, d_grid, d_Y,
-                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_lap};
+                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_lap, d_direct,
+                    d_dranges, d_dpart, d_cdir};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -129,6 +130,20 @@ static fl_status select_params(Plan& p, int q_in) {
     return FL_OK;
 }
 
+// Route of a non-empty band: NFFT with nrhs right-hand sides, or the direct sum
+// over its K frequencies.  Costs in issued instructions per element: an FFT
+// grid point ~ (log2 n + 8) over both passes and the prep, a gathered tap ~ 2
+// per right-hand side, a direct term ~ 6 (one complex Horner step and its
+// share of the block's phase).
+static int route_of(const Plan& p, const BandHost& bh) {
+    if (p.route_mode == 1) return 1;
+    if (p.route_mode == 2) return 2;
+    const BandDev& d = bh.dev;
+    const double fft = (double)d.nrhs * d.n * (d.log2n + 8) + (double)bh.nodes * d.nrhs * 2 * p.mw * 2;
+    const double direct = (double)bh.nodes * d.K * 6.0 * p.direct_bias;
+    return direct < fft ? 2 : 1;
+}
+
 static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) {
     fl_status s = select_params(p, q);
     if (s != FL_OK) return s;
@@ -189,13 +204,30 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
     p.grid_elems = p.D_elems = p.Y_elems = 0;
     p.small_work.clear();
     p.large_bands.clear();
+    p.direct_work.clear();
+    p.direct_ranges.clear();
+    p.direct_nodes = p.direct_terms = p.dpart_elems = 0;
     for (int b = 1; b <= p.levels; ++b) {
         BandHost& bh = p.bands[b];
         bh.nodes = counts[b];
         bh.node_off = off;
         off += counts[b];
         BandDev& d = bh.dev;
-        d.route = bh.nodes > 0 ? 1 : 0;
+        d.node_off = bh.node_off;
+        d.route = bh.nodes > 0 ? route_of(p, bh) : 0;
+        if (d.route == 2) {
+            d.nchunk = (int)((d.K + kDirChunk - 1) / kDirChunk);
+            d.dslot = p.dpart_elems;
+            p.dpart_elems += bh.nodes * d.nchunk;
+            p.direct_ranges.push_back({b, 0, bh.nodes, p.direct_nodes});
+            p.direct_nodes += bh.nodes;
+            p.direct_terms += bh.nodes * d.K;
+            for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirNodes)
+                for (int ch = 0; ch < d.nchunk; ++ch)
+                    p.direct_work.push_back({b, ch, bh.node_off + n0,
+                                             (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
+            continue;
+        }
         if (d.route != 1) continue;
         d.grid_off = p.grid_elems;
         d.D_off = p.D_elems;
@@ -220,13 +252,28 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
                                 cudaMemcpyHostToDevice, st),
                 "copy work");
     }
+    if (!p.direct_work.empty()) {
+        FL_CUDA(cudaMalloc((void**)&p.d_direct, p.direct_work.size() * sizeof(DirectItem)),
+                "cudaMalloc direct work");
+        FL_CUDA(cudaMemcpyAsync(p.d_direct, p.direct_work.data(),
+                                p.direct_work.size() * sizeof(DirectItem), cudaMemcpyHostToDevice, st),
+                "copy direct work");
+        FL_CUDA(cudaMalloc((void**)&p.d_dranges, p.direct_ranges.size() * sizeof(DirectRange)),
+                "cudaMalloc direct ranges");
+        FL_CUDA(cudaMemcpyAsync(p.d_dranges, p.direct_ranges.data(),
+                                p.direct_ranges.size() * sizeof(DirectRange), cudaMemcpyHostToDevice, st),
+                "copy direct ranges");
+        FL_CUDA(cudaMalloc(&p.d_dpart, p.dpart_elems * cs), "cudaMalloc direct partials");
+        FL_CUDA(cudaMalloc(&p.d_cdir, p.N * cs), "cudaMalloc direct adjoint");
+    }
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
     if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
     FL_CUDA(build_tables(p, st), "fl_plan: tables");
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
     p.scratch_bytes = (double)p.grid_elems * cs + (double)p.D_elems * rs + (double)p.Y_elems * cs +
-                      (double)M * (sizeof(double2) + 5);
+                      (double)M * (sizeof(double2) + 5) + (double)p.dpart_elems * cs +
+                      (p.direct_work.empty() ? 0.0 : (double)p.N * cs);
     // algorithmic bytes of one execute: c once, D once, each grid written and read
     // once per FFT pass, the nodes, and f
     double mb = (double)p.N * cs + (double)p.D_elems * rs + (double)M * (sizeof(double2) + 5 + cs);
@@ -237,6 +284,7 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
         mb += (d.log2n <= kSmallMaxLog2) ? g : 3.0 * g;   // small: write; large: Y write+read, grid write
         mb += std::min<double>(g, (double)p.bands[b].nodes * d.nrhs * 2 * p.mw * cs);   // gather
     }
+    if (!p.direct_work.empty()) mb += (double)p.direct_work.size() * kDirChunk * cs;   // c tiles
     p.model_bytes = mb;
     return FL_OK;
 }
@@ -253,7 +301,14 @@ const char* fl_version(void) { return "fastfl 0.1 (sm_103a)"; }
 
 fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q, double eps,
                   fl_precision prec, void* stream) {
+    return fl_plan_ex(out, N, M, nodes_dev, q, eps, prec, nullptr, stream);
+}
+
+fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q,
+                     double eps, fl_precision prec, const fl_options* opt, void* stream) {
     g_err.clear();
+    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0)))
+        return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
     if (N < 1 || M < 0) return fail(FL_EINVAL, "fl_plan: need N >= 1 and M >= 0");
@@ -270,6 +325,10 @@ fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev,
     h->p.N = N;
     h->p.M = M;
     h->p.eps = eps;
+    if (opt) {
+        h->p.route_mode = opt->route;
+        h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
+    }
     fl_status s = plan_flt(h->p, nodes_dev, q, (cudaStream_t)stream);
     if (s != FL_OK) {
         delete h;

@@ -50,6 +50,10 @@ struct BandDev {
     int pad;
     double yc, yh;     // band Y_m = [yc - yh, yc + yh] (paper's y), for barycentric weights
     double yh_inv;     // 1 / yh (a power of two times 1/y_1)
+    int64_t node_off;  // first node of the band in sorted order
+    int64_t dslot;     // direct route: offset of the band's partial sums (nodes x nchunk)
+    int nchunk;        // direct route: coefficient chunks
+    int pad2;
 };
 
 // ---------------------------------------------------------------------------

@@ -1,0 +1,197 @@
+// fl_direct.cu -- direct evaluation of the bands whose node count is too small
+// to pay for an NFFT with q right-hand sides, and of their adjoint.
+//
+// A band routed here computes the plain sum f_j = sum_{k<K} c_k z_j^k over the
+// frequencies the band keeps (K = k <= xi_1 / 2^(l_m - 1), the region-(ii)
+// truncation of Lemma A.2, or K = N for the Y_M band), i.e. eq. (4.1) itself
+// -- the "naive matrix vector multiplication" the paper times in Section 5 --
+// restricted to those frequencies.  The sum is blocked: each block of 32 terms
+// is a Horner polynomial in z_j, and z_j^{k_b} at the block start is formed
+// from an exactly reduced phase (k_b x_j mod 1) and exp(-y_j k_b), so the error
+// does not grow with k.
+#include "fl_plan.cuh"
+
+namespace fl {
+
+constexpr double kTwoPiDir = 6.283185307179586476925286766559;
+
+// frac(k x) in [-1/2, 1/2).  double: k x = p + e exactly (FMA), one rounding.
+// float: the double product's error (2^-53 k |x|) is far below float resolution.
+template <typename T> __device__ __forceinline__ double dir_phase(double k, double x);
+template <> __device__ __forceinline__ double dir_phase<float>(double k, double x) {
+    const double p = k * x;
+    return p - rint(p);
+}
+template <> __device__ __forceinline__ double dir_phase<double>(double k, double x) {
+    const double p = k * x;
+    const double e = fma(k, x, -p);
+    double f = p - rint(p);
+    f += e;
+    if (f >= 0.5) f -= 1.0;
+    if (f < -0.5) f += 1.0;
+    return f;
+}
+
+template <typename T> __device__ __forceinline__ T dir_exp(T a);
+template <> __device__ __forceinline__ float dir_exp<float>(float a) { return expf(a); }
+template <> __device__ __forceinline__ double dir_exp<double>(double a) { return exp(a); }
+
+// One CTA per work item: up to kDirNodes consecutive sorted nodes of one band
+// against one chunk of kDirChunk coefficients staged in shared memory.  Warp w
+// takes node w; lane l takes the Horner blocks l, l + 32, ... of the chunk.
+template <typename T, bool DERIV>
+__global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ items,
+                                                const BandDev* __restrict__ bands,
+                                                const double2* __restrict__ ws,
+                                                const C_t<T>* __restrict__ c,
+                                                C_t<T>* __restrict__ part) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const DirectItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int64_t k0 = (int64_t)it.chunk * kDirChunk;
+    const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
+    for (int i = threadIdx.x; i < kDirChunk; i += blockDim.x) {
+        const int64_t k = k0 + i;
+        C v = C{(T)0, (T)0};
+        if (k < kend) {
+            v = c[k];
+            if (DERIV) {
+                const T wgt = (T)(kTwoPiDir * (double)k);
+                v = C{-v.y * wgt, v.x * wgt};
+            }
+        }
+        tile[i] = v;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= it.nnodes) return;
+    const int64_t i = it.node0 + w;
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double y = kTwoPiDir * wv.y;
+    // z = exp(-y) exp(2 pi i x) in T
+    double xr = x;
+    if (xr >= 0.5) xr -= 1.0;
+    const C z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    C acc = C{(T)0, (T)0};
+#pragma unroll 1
+    for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
+        const int b = bb * 32 + lane;
+        const int64_t kb = k0 + (int64_t)b * kDirBlock;
+        if (kb >= kend) break;
+        const double ykb = y * (double)kb;
+        if (ykb > (sizeof(T) == 4 ? 104.0 : 745.0)) break;   // z^kb underflows: so do later blocks
+        const C* cb = tile + b * kDirBlock;
+        C P = cb[kDirBlock - 1];
+#pragma unroll
+        for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
+        const C zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)kb, x))), dir_exp<T>((T)(-ykb)));
+        acc = cadd(acc, cmul(zk, P));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+    }
+    if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
+}
+
+// f[perm[i]] = sum over the node's chunks (in chunk order); with rmul,
+// rmul[perm[i]] * conj(sum) (the node-gradient epilogue).
+template <typename T>
+__global__ void k_direct_reduce(int nranges, const DirectRange* __restrict__ ranges,
+                                int64_t total, const BandDev* __restrict__ bands,
+                                const int32_t* __restrict__ perm, const C_t<T>* __restrict__ part,
+                                const C_t<T>* __restrict__ rmul, C_t<T>* __restrict__ f) {
+    using C = C_t<T>;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int r = 0;
+    while (r + 1 < nranges && ranges[r + 1].prefix <= t) ++r;
+    const DirectRange R = ranges[r];
+    const BandDev B = bands[R.band];
+    const int64_t local = t - R.prefix;
+    const C* p = part + B.dslot + local * B.nchunk;
+    C acc = C{(T)0, (T)0};
+    for (int ch = 0; ch < B.nchunk; ++ch) acc = cadd(acc, p[ch]);
+    const int32_t j = perm[B.node_off + local];
+    f[j] = rmul ? cmulc(rmul[j], acc) : acc;
+}
+
+// Adjoint of the direct bands: cdir[k] = sum over direct bands with k < K_b of
+// sum_j conj(z_j)^k r_j, one thread per k, exact phase per term.
+template <typename T>
+__global__ void __launch_bounds__(256) k_direct_adj(int nranges, const DirectRange* __restrict__ ranges,
+                                                    int64_t N, const BandDev* __restrict__ bands,
+                                                    const double2* __restrict__ ws,
+                                                    const int32_t* __restrict__ perm,
+                                                    const C_t<T>* __restrict__ r,
+                                                    C_t<T>* __restrict__ cdir) {
+    using C = C_t<T>;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    C acc = C{(T)0, (T)0};
+    for (int q = 0; q < nranges; ++q) {
+        const DirectRange R = ranges[q];
+        const BandDev B = bands[R.band];
+        if (k >= B.K) continue;
+        for (int64_t i = B.node_off; i < B.node_off + R.count; ++i) {
+            const double2 wv = ws[i];
+            const double ykb = kTwoPiDir * wv.y * (double)k;
+            if (ykb > (sizeof(T) == 4 ? 104.0 : 745.0)) continue;
+            const double x = wv.x - floor(wv.x);
+            const C zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)k, x))), dir_exp<T>((T)(-ykb)));
+            acc = cadd(acc, cmulc(r[perm[i]], zk));   // r_j conj(z_j^k)
+        }
+    }
+    cdir[k] = acc;
+}
+
+template <typename T>
+static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                                    cudaStream_t st) {
+    using C = C_t<T>;
+    if (p.direct_work.empty()) return cudaSuccess;
+    const size_t smem = (size_t)kDirChunk * sizeof(C);
+    auto kern = deriv ? k_direct<T, true> : k_direct<T, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int slot;
+    timer_begin(p, "direct", (double)p.direct_terms * sizeof(C) / 32.0, st, &slot);
+    kern<<<(unsigned)p.direct_work.size(), 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws,
+                                                           (const C*)c, (C*)p.d_dpart);
+    timer_end(p, slot, st);
+    k_direct_reduce<T><<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
+        (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
+        (const C*)p.d_dpart, (const C*)rmul, (C*)f);
+    p.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                               cudaStream_t st) {
+    return p.prec == FL_FP64 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
+                             : direct_forward_t<float>(p, c, f, deriv, rmul, st);
+}
+
+template <typename T>
+static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
+    using C = C_t<T>;
+    if (p.direct_ranges.empty()) return cudaSuccess;
+    int slot;
+    timer_begin(p, "direct_adj", 0.0, st, &slot);
+    k_direct_adj<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
+        (int)p.direct_ranges.size(), p.d_dranges, p.N, p.d_bands, p.d_ws, p.d_perm, (const C*)r,
+        (C*)p.d_cdir);
+    timer_end(p, slot, st);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t run_direct_adjoint(Plan& p, const void* r, cudaStream_t st) {
+    return p.prec == FL_FP64 ? direct_adjoint_t<double>(p, r, st) : direct_adjoint_t<float>(p, r, st);
+}
+
+}  // namespace fl

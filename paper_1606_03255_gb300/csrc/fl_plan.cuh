@@ -27,6 +27,27 @@ struct SmallWork {
     int log2n;
 };
 
+// Direct route (fl_direct.cu): kDirNodes nodes x one chunk of kDirChunk
+// coefficients per CTA, Horner blocks of kDirBlock terms.
+constexpr int kDirBlock = 32;
+constexpr int kDirChunk = 4096;
+constexpr int kDirNodes = 8;
+
+struct DirectItem {
+    int band;
+    int chunk;
+    int64_t node0;   // first sorted node of the item
+    int nnodes;      // <= kDirNodes
+    int pad;
+};
+
+struct DirectRange {
+    int band;
+    int pad;
+    int64_t count;   // nodes of the band
+    int64_t prefix;  // direct nodes of the bands before it
+};
+
 // Per-band plan data on the host.
 struct BandHost {
     int ell = 0, Lm = 0;    // l_m, L_m (Definition 3.2); 0 for the Y_M band
@@ -52,6 +73,11 @@ struct Plan {
     int64_t grid_elems = 0, D_elems = 0, Y_elems = 0;
     std::vector<SmallWork> small_work;
     std::vector<int> large_bands;
+    int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
+    double direct_bias = 1.0;
+    std::vector<DirectItem> direct_work;
+    std::vector<DirectRange> direct_ranges;
+    int64_t direct_nodes = 0, direct_terms = 0, dpart_elems = 0;
 
     // device memory
     double2* d_ws = nullptr;       // nodes in sorted order (Re w, Im w)
@@ -66,6 +92,10 @@ struct Plan {
     void* d_stage_c = nullptr;     // staging for fl_execute_host
     void* d_stage_f = nullptr;
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
+    DirectItem* d_direct = nullptr;
+    DirectRange* d_dranges = nullptr;
+    void* d_dpart = nullptr;       // direct route: partial sums (complex T)
+    void* d_cdir = nullptr;        // direct route adjoint: N complex
     double scratch_bytes = 0;
 
     // Laplace (Algorithm 1)
@@ -99,6 +129,11 @@ cudaError_t build_tables(Plan& p, cudaStream_t st);
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul = nullptr);
 cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
+
+// Launchers (fl_direct.cu)
+cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                               cudaStream_t st);
+cudaError_t run_direct_adjoint(Plan& p, const void* r, cudaStream_t st);
 
 // Launchers (fl_laplace.cu)
 cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st);

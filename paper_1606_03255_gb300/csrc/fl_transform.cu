@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     }
     // with rmul: f[j] = rmul[j] * conj(value) (node gradient, see fl_grad_w)
     const BandDev B = bands[b];
+    if (B.route != 1) return;   // direct-route band: written by k_direct_reduce
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
     const double t0 = (double)B.n * x;
@@ -295,6 +296,7 @@ __global__ void __launch_bounds__(256) k_spread(int64_t M, int64_t z0, const dou
     if (i >= M) return;
     const int b = bandid[i];
     const BandDev B = bands[b];
+    if (B.route != 1) return;   // direct-route band: k_direct_adj
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
     const double t0 = (double)B.n * x;
@@ -354,11 +356,13 @@ __global__ void k_z0_sum(int64_t z0, const int32_t* __restrict__ perm,
 template <typename T>
 __global__ void k_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
                           const T* __restrict__ D, const C_t<T>* __restrict__ grid,
-                          const C_t<T>* __restrict__ z0sum, C_t<T>* __restrict__ cout) {
+                          const C_t<T>* __restrict__ z0sum, const C_t<T>* __restrict__ cdir,
+                          C_t<T>* __restrict__ cout) {
     using C = C_t<T>;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     C acc = (k == 0) ? *z0sum : C{(T)0, (T)0};
+    if (cdir) acc = cadd(acc, cdir[k]);
     for (int b = 1; b <= levels; ++b) {
         const BandDev B = bands[b];
         if (B.route != 1 || k >= B.K) continue;
@@ -475,6 +479,7 @@ static cudaError_t forward_t(Plan& p, const void* c, void* f, bool deriv, const 
     if (p.M == 0) return cudaSuccess;
     cudaError_t e = deriv ? fft_bands<T, +1, 0, true>(p, c, st) : fft_bands<T, +1, 0, false>(p, c, st);
     if (e != cudaSuccess) return e;
+    if ((e = run_direct_forward(p, c, f, deriv, rmul, st)) != cudaSuccess) return e;
     return gather_dispatch<T>(p, c, f, deriv, rmul, st);
 }
 
@@ -514,12 +519,14 @@ static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st
     }
     if (e != cudaSuccess) return e;
     if ((e = fft_bands<T, -1, 1, false>(p, nullptr, st)) != cudaSuccess) return e;
+    if ((e = run_direct_adjoint(p, r, st)) != cudaSuccess) return e;
     C* z0sum = (C*)p.d_z0;
     k_z0_sum<T><<<1, 256, 0, st>>>(p.z0_nodes, p.d_perm, (const C*)r, z0sum);
     int slot;
     timer_begin(p, "combine", 0.0, st, &slot);
     k_combine<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
-        p.N, p.levels, p.d_bands, (const T*)p.d_D, (const C*)p.d_grid, z0sum, (C*)cout);
+        p.N, p.levels, p.d_bands, (const T*)p.d_D, (const C*)p.d_grid, z0sum,
+        p.direct_ranges.empty() ? nullptr : (const C*)p.d_cdir, (C*)cout);
     timer_end(p, slot, st);
     p.launches += 2;
     return cudaGetLastError();

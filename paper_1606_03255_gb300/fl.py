@@ -10,6 +10,8 @@ Two layers:
   pointers (ints) and sizes, returning ``fl_status`` codes;
 * ``Plan`` / ``LaplacePlan`` -- thin owners of a plan handle that take torch
   tensors, check dtype/device/shape and raise ``FLError`` on a non-zero status.
+  ``Plan(route=...)``: "auto" (NFFT or direct sum per band by cost), "nfft"
+  (every band by NFFT, Algorithm 2 as printed) or "direct".
 """
 from __future__ import annotations
 
@@ -28,7 +30,7 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
                 FL_EUNSUPPORTED: "FL_EUNSUPPORTED"}
 
 # Every symbol include/fl.h declares.
-EXPORTED = ["fl_plan", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
+EXPORTED = ["fl_plan", "fl_plan_ex", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
             "fl_adjoint",
             "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
@@ -52,6 +54,13 @@ class fl_info(ctypes.Structure):
         ("band_n", ctypes.c_int64 * FL_MAX_LEVELS),
         ("model_bytes", ctypes.c_double), ("scratch_bytes", ctypes.c_double),
     ]
+
+
+class fl_options(ctypes.Structure):
+    _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double)]
+
+
+ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
 
 
 class fl_timing(ctypes.Structure):
@@ -91,6 +100,7 @@ def load(path: str | None = None):
     pp = ctypes.POINTER(vp)
     sig = {
         "fl_plan": [pp, i64, i64, vp, ci, cd, ci, vp],
+        "fl_plan_ex": [pp, i64, i64, vp, ci, cd, ci, ctypes.POINTER(fl_options), vp],
         "fl_execute": [vp, vp, vp, vp],
         "fl_execute_deriv": [vp, vp, vp, vp],
         "fl_grad_w": [vp, vp, vp, vp, vp],
@@ -124,6 +134,14 @@ def fl_plan(N, M, nodes_ptr, q, eps, prec, stream):
     h = ctypes.c_void_p()
     st = load().fl_plan(ctypes.byref(h), int(N), int(M), nodes_ptr, int(q), float(eps),
                         int(prec), stream)
+    return st, h
+
+
+def fl_plan_ex(N, M, nodes_ptr, q, eps, prec, options, stream):
+    h = ctypes.c_void_p()
+    opt = ctypes.byref(options) if options is not None else None
+    st = load().fl_plan_ex(ctypes.byref(h), int(N), int(M), nodes_ptr, int(q), float(eps),
+                           int(prec), opt, stream)
     return st, h
 
 
@@ -261,7 +279,7 @@ class Plan:
     """
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
-                 stream=None):
+                 stream=None, route: str = "auto", direct_bias: float = 1.0):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -271,8 +289,9 @@ class Plan:
         self.prec = FL_FP64 if precision == "fp64" else FL_FP32
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
-        st, h = fl_plan(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
-                        _stream_handle(stream))
+        opt = fl_options(ROUTES[route], float(direct_bias))
+        st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
+                           opt, _stream_handle(stream))
         check(st, "fl_plan")
         self._handle = h
 

@@ -19,10 +19,10 @@ def fl():
     return flmod
 
 
-def _adjoint(fl, r, w, N, eps, prec):
+def _adjoint(fl, r, w, N, eps, prec, route="nfft"):
     dev = torch.device("cuda")
     cdt = torch.complex128 if prec == "fp64" else torch.complex64
-    plan = fl.Plan(N, torch.from_numpy(w).to(dev), eps, precision=prec)
+    plan = fl.Plan(N, torch.from_numpy(w).to(dev), eps, precision=prec, route=route)
     g = plan.adjoint(torch.from_numpy(r).to(cdt).to(dev))
     torch.cuda.synchronize()
     plan.close()
@@ -32,11 +32,12 @@ def _adjoint(fl, r, w, N, eps, prec):
 @pytest.mark.parametrize("N,M", [(1, 4), (64, 100), (1000, 1000), (5000, 3000), (20000, 1500)])
 @pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
 @pytest.mark.parametrize("kind", ["disk", "clustered"])
-def test_adjoint_against_oracle(fl, N, M, prec, eps, kind):
+@pytest.mark.parametrize("route", ["nfft", "auto", "direct"])
+def test_adjoint_against_oracle(fl, N, M, prec, eps, kind, route):
     w = W.nodes_disk_uniform(M, seed=M) if kind == "disk" else W.nodes_circle_clustered(M, seed=M)
     w = np.concatenate([w, [[0.5, 9.0]]])        # one Z^0 node
     r = W.coefficients(M + 1, seed=N)
-    g = _adjoint(fl, r, w, N, eps, prec)
+    g = _adjoint(fl, r, w, N, eps, prec, route)
     ref = oracle.flt_adjoint(r, w, N)
     E = oracle.error_E(ref, g, r)
     bound = eps if prec == "fp64" else eps + 32 * 2.0 ** -24 * np.max(np.abs(ref)) / np.sum(np.abs(r))

@@ -1,5 +1,9 @@
 """GPU parity of the forward transform (Algorithm 2) against the CPU oracle.
 
+Unless a test says otherwise every band goes through the NFFT (route "nfft",
+Algorithm 2 as printed); the routed and the all-direct plans are checked at
+the end.
+
 Element-by-element comparison through the C ABI, with E = ||f - f~||_inf /
 ||c||_1 (eq. 5.1).  Tolerance: E <= eps is what Theorem 4.3 guarantees in exact
 arithmetic.  The FP64 form is held to exactly that.  The FP32 form adds float
@@ -31,10 +35,11 @@ def fl():
     return flmod
 
 
-def _run(fl, c, w, eps, prec, q=0, deriv=False):
+def _run(fl, c, w, eps, prec, q=0, deriv=False, route="nfft"):
     dev = torch.device("cuda")
     cdt = torch.complex128 if prec == "fp64" else torch.complex64
-    plan = fl.Plan(len(c), torch.from_numpy(np.ascontiguousarray(w)).to(dev), eps, precision=prec, q=q)
+    plan = fl.Plan(len(c), torch.from_numpy(np.ascontiguousarray(w)).to(dev), eps, precision=prec, q=q,
+                   route=route)
     f = plan.execute(torch.from_numpy(np.asarray(c)).to(cdt).to(dev), deriv=deriv)
     torch.cuda.synchronize()
     out = f.cpu().numpy().astype(np.complex128)
@@ -192,3 +197,47 @@ def test_full_size_config2_sampled(fl, prec, eps):
     E = oracle.error_E(ref, f[idx], c)
     assert E <= tol(eps, prec, ref, c), E
     assert E <= eps, E
+
+
+@pytest.mark.parametrize("route", ["auto", "direct"])
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-12), ("fp32", 1e-6)])
+@pytest.mark.parametrize("kind,N,M", [("disk", 1024, 1024), ("disk", 1 << 16, 3000),
+                                      ("clustered", 20000, 5000), ("paper", 4097, 777)])
+def test_routed_and_direct(fl, route, prec, eps, kind, N, M):
+    c = W.coefficients(N, seed=21)
+    w = _nodes(kind, M, seed=22, eps=eps)
+    w = np.concatenate([w, [[0.4, 7.0]]])          # plus a Z^0 node
+    f, info = _run(fl, c, w, eps, prec, route=route)
+    if route == "direct":
+        assert info["n_bands_fft"] == 0 and info["n_bands_direct"] > 0
+    ref = oracle.flt_direct(c, w)
+    E = oracle.error_E(ref, f, c)
+    assert E <= tol(eps, prec, ref, c), E
+
+
+def test_auto_route_sends_sparse_full_bands_to_direct(fl):
+    # uniform-disk nodes put only a handful of nodes in each full-bandwidth band
+    N = M = 1 << 18
+    w = W.nodes_disk_uniform(M, seed=1)
+    c = W.coefficients(N, seed=0)
+    f, info = _run(fl, c, w, 1e-6, "fp32", route="auto")
+    assert info["n_bands_direct"] > 0 and info["n_bands_fft"] > 0
+    sparse_full = [b for b in range(1, info["levels"] + 1)
+                   if info["band_K"][b] == N and 0 < info["band_nodes"][b] < 50]
+    assert sparse_full, "expected full-bandwidth bands with few nodes"
+    for b in sparse_full:
+        assert info["band_route"][b] == 2
+    idx = np.random.default_rng(3).choice(M, 256, replace=False)
+    ref = oracle.flt_direct(c, w[idx])
+    assert oracle.error_E(ref, f[idx], c) <= tol(1e-6, "fp32", ref, c)
+
+
+@pytest.mark.parametrize("route", ["auto", "direct"])
+def test_derivative_and_node_gradient_routes(fl, route):
+    N, M = 3000, 900
+    c = W.coefficients(N, seed=31)
+    w = W.nodes_disk_uniform(M, seed=32)
+    cd = 2j * np.pi * np.arange(N) * c
+    ref = oracle.flt_direct(cd, w)
+    f, _ = _run(fl, c, w, 1e-10, "fp64", deriv=True, route=route)
+    assert oracle.error_E(ref, f, cd) <= 1e-10
