@@ -117,6 +117,8 @@ typedef struct {
                              1 = every band by NFFT (Algorithm 2 as printed);
                              2 = every band by the direct sum                      */
     double direct_bias;   /* multiplies the direct-sum cost in route 0 (0 = 1.0)  */
+    int rhs_per_launch;   /* grids of one size per four-step launch pair; small
+                             values keep the intermediate in L2 (0 = all)         */
 } fl_options;
 
 /*

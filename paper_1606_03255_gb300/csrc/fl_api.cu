@@ -35,7 +35,7 @@ static fl_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 Plan::~Plan() {
-    void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_cheb, d_D, d_grid, d_Y,
+    void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir};
     for (void* q : ptrs)
@@ -144,6 +144,40 @@ static int route_of(const Plan& p, const BandHost& bh) {
     return direct < fft ? 2 : 1;
 }
 
+// Four-step work items of the large bands, grouped by grid size into launches
+// of at most rhs_per_launch items (0: a whole size class) and at most
+// kMaxYElems intermediate elements; sets Y_elems.
+constexpr int64_t kMaxYElems = (int64_t)1 << 28;
+
+static void build_pass_groups(Plan& p) {
+    p.pass_items.clear();
+    p.pass_groups.clear();
+    p.Y_elems = 0;
+    for (int lg = kSmallMaxLog2 + 1; lg <= kMaxLog2n; ++lg) {
+        std::vector<PassItem> cls;
+        for (int b : p.large_bands) {
+            const BandDev& d = p.bands[b].dev;
+            if (d.log2n != lg) continue;
+            for (int s = 0; s < d.nrhs; ++s) cls.push_back({b, s, 0});
+        }
+        if (cls.empty()) continue;
+        const int64_t n = (int64_t)1 << lg;
+        int cap = (int)std::min<int64_t>(65535, std::max<int64_t>(1, kMaxYElems / n));
+        if (p.rhs_per_launch > 0) cap = std::min(cap, p.rhs_per_launch);
+        for (size_t i0 = 0; i0 < cls.size(); i0 += cap) {
+            const int cnt = (int)std::min<size_t>(cap, cls.size() - i0);
+            PassGroup g{(int)p.pass_items.size(), cnt, lg};
+            for (int i = 0; i < cnt; ++i) {
+                PassItem it = cls[i0 + i];
+                it.y_off = (int64_t)i * n;
+                p.pass_items.push_back(it);
+            }
+            p.pass_groups.push_back(g);
+            p.Y_elems = std::max<int64_t>(p.Y_elems, (int64_t)cnt * n);
+        }
+    }
+}
+
 static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) {
     fl_status s = select_params(p, q);
     if (s != FL_OK) return s;
@@ -239,9 +273,9 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
                 p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
         } else {
             p.large_bands.push_back(b);
-            p.Y_elems = std::max<int64_t>(p.Y_elems, (int64_t)d.nrhs * d.n);
         }
     }
+    build_pass_groups(p);
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
@@ -251,6 +285,12 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
         FL_CUDA(cudaMemcpyAsync(p.d_small, p.small_work.data(), p.small_work.size() * sizeof(SmallWork),
                                 cudaMemcpyHostToDevice, st),
                 "copy work");
+    }
+    if (!p.pass_items.empty()) {
+        FL_CUDA(cudaMalloc((void**)&p.d_pass, p.pass_items.size() * sizeof(PassItem)), "cudaMalloc pass items");
+        FL_CUDA(cudaMemcpyAsync(p.d_pass, p.pass_items.data(), p.pass_items.size() * sizeof(PassItem),
+                                cudaMemcpyHostToDevice, st),
+                "copy pass items");
     }
     if (!p.direct_work.empty()) {
         FL_CUDA(cudaMalloc((void**)&p.d_direct, p.direct_work.size() * sizeof(DirectItem)),
@@ -307,7 +347,8 @@ fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev,
 fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q,
                      double eps, fl_precision prec, const fl_options* opt, void* stream) {
     g_err.clear();
-    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0)))
+    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
+                opt->rhs_per_launch < 0))
         return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
@@ -328,6 +369,7 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (opt) {
         h->p.route_mode = opt->route;
         h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
+        h->p.rhs_per_launch = opt->rhs_per_launch;
     }
     fl_status s = plan_flt(h->p, nodes_dev, q, (cudaStream_t)stream);
     if (s != FL_OK) {

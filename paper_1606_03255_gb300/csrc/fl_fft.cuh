@@ -5,7 +5,8 @@
 //   of the centred frequency k' = k - N_m/2 (deconvolution and Lagrange /
 //   coupling weights are folded into D), zero elsewhere.
 // * fft_ct: shared-memory Stockham FFT with the length a compile-time constant,
-//   radix 8 (then 4 or 2), 8 elements per thread, every stage unrolled.
+//   radix 16 (then 8, 4 or 2), 16 elements per thread, every stage unrolled,
+//   XOR-swizzled shared memory.
 // * k_pass1 / k_pass2: the two passes of the four-step FFT of length
 //   n = n1 n2 for grids above one CTA (n > 4096).
 #pragma once
@@ -52,35 +53,106 @@ __device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K,
 }
 
 // ---------------------------------------------------------------------------
-// Compile-time-length Stockham FFT (same transform as fft_smem).
+// Compile-time-length Stockham FFT, radix 16 (then 8, 4 or 2), 16 elements per
+// thread.  Same transform and stage structure as fft_smem: stage (R, NS) takes
+// job jj reading x[jj + r L/R], twiddling by w^(r k), w = exp(SIGN 2 pi i /
+// (NS R)), k = jj mod NS, and writing to (jj - k) R + k + r NS.
+//
+// Shared-memory layout: element e lives at swz(e) = e ^ ((e >> 4) & (P - 1)),
+// P = 128 bytes / element size (16 for float2, 8 for double2).  The XOR keeps
+// aligned runs of 16 contiguous elements a permutation of one bank row and
+// spreads the stride-16 stores of the first stage (e = 16 j + r) over P banks,
+// so every stage's loads and stores are free of bank conflicts.
+
+template <typename T> __device__ __forceinline__ int swz(int e) {
+    constexpr int P = (int)(128 / sizeof(C_t<T>));
+    return e ^ ((e >> 4) & (P - 1));
+}
+
+// 16-point DFT in registers (4 x 4 with internal twiddles), sign SIGN.
+template <int SIGN, typename T> __device__ __forceinline__ void dft16(C_t<T>* a) {
+    using C = C_t<T>;
+    const T c1 = (T)0.92387953251128675612818318939679;   // cos(pi/8)
+    const T s1 = (T)0.38268343236508977172845998403040;   // sin(pi/8)
+    const T h = (T)0.70710678118654752440084436210485;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) dft4<SIGN>(a[b], a[4 + b], a[8 + b], a[12 + b]);
+    // a[b + 4 k1] *= W16^(b k1), W16 = exp(SIGN 2 pi i / 16)
+    a[5] = cmul(a[5], C{c1, SIGN * s1});      // W^1
+    a[6] = cmul(a[6], C{h, SIGN * h});        // W^2
+    a[7] = cmul(a[7], C{s1, SIGN * c1});      // W^3
+    a[9] = cmul(a[9], C{h, SIGN * h});        // W^2
+    a[10] = mul_i<SIGN>(a[10]);               // W^4
+    a[11] = cmul(a[11], C{-h, SIGN * h});     // W^6
+    a[13] = cmul(a[13], C{s1, SIGN * c1});    // W^3
+    a[14] = cmul(a[14], C{-h, SIGN * h});     // W^6
+    a[15] = cmul(a[15], C{-c1, -SIGN * s1});  // W^9
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<SIGN>(a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]);
+    // now a[4 k1 + k2] = X[k1 + 4 k2]: transpose to natural order
+    C t;
+    t = a[1]; a[1] = a[4]; a[4] = t;
+    t = a[2]; a[2] = a[8]; a[8] = t;
+    t = a[3]; a[3] = a[12]; a[12] = t;
+    t = a[6]; a[6] = a[9]; a[9] = t;
+    t = a[7]; a[7] = a[13]; a[13] = t;
+    t = a[11]; a[11] = a[14]; a[14] = t;
+}
+
+// Twiddles w^r, r = 0..R-1, of w = exp(i pi x): w and w^4 from sincospi, the
+// rest as products of at most three factors (errors stay a few ulps).
+template <int R, typename T>
+__device__ __forceinline__ void twiddle_powers(T x, C_t<T>* w) {
+    using C = C_t<T>;
+    w[0] = C{(T)1, (T)0};
+    const C w1 = expipi<T>(x);
+    w[1] = w1;
+    if constexpr (R >= 4) {
+        w[2] = cmul(w1, w1);
+        w[3] = cmul(w[2], w1);
+    }
+    if constexpr (R >= 8) {
+        const C w4 = expipi<T>((T)4 * x);
+        w[4] = w4;
+#pragma unroll
+        for (int b = 1; b < 4; ++b) w[4 + b] = cmul(w4, w[b]);
+        if constexpr (R == 16) {
+            const C w8 = cmul(w4, w4);
+            const C w12 = cmul(w8, w4);
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                w[8 + b] = b ? cmul(w8, w[b]) : w8;
+                w[12 + b] = b ? cmul(w12, w[b]) : w12;
+            }
+        }
+    }
+}
 
 template <int R, int NS, int L, int SIGN, typename T>
-__device__ __forceinline__ void fft_stage_ct(C_t<T>* buf, int t) {
+__device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t) {
     using C = C_t<T>;
-    constexpr int J = 8 / R;
-    constexpr int NTHR = L / 8;
-    C v[8];
+    constexpr int J = 16 / R;
+    constexpr int NTHR = L / 16;
+    C v[16];
 #pragma unroll
     for (int jb = 0; jb < J; ++jb) {
         const int jj = t + jb * NTHR;
         const int k = jj & (NS - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[jb * R + r] = buf[pad8(jj + r * (L / R))];
+        for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
         if constexpr (NS > 1) {
             // k < NS and 1/(NS R) is a power of two: exact argument
-            const C w1 = expipi<T>((T)(2 * SIGN) * (T)k * (T)(1.0 / (NS * R)));
-            C w = w1;
+            C w[R];
+            twiddle_powers<R, T>((T)(2 * SIGN) * (T)k * (T)(1.0 / (NS * R)), w);
 #pragma unroll
-            for (int r = 1; r < R; ++r) {
-                v[jb * R + r] = cmul(v[jb * R + r], w);
-                w = cmul(w, w1);
-            }
+            for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], w[r]);
         }
     }
     __syncthreads();
 #pragma unroll
     for (int jb = 0; jb < J; ++jb) {
         C* a = v + jb * R;
+        if constexpr (R == 16) dft16<SIGN, T>(a);
         if constexpr (R == 8) dft8<SIGN, T>(a);
         if constexpr (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
         if constexpr (R == 2) dft2<SIGN>(a[0], a[1]);
@@ -88,42 +160,50 @@ __device__ __forceinline__ void fft_stage_ct(C_t<T>* buf, int t) {
         const int k = jj & (NS - 1);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad8(base + r * NS)] = a[r];
+        for (int r = 0; r < R; ++r) buf[swz<T>(base + r * NS)] = a[r];
     }
     __syncthreads();
 }
 
+// L = 2^LOG2L points (LOG2L >= 4) with L/16 threads t = 0..L/16-1.
 template <int LOG2L, int SIGN, typename T, int DONE = 0>
 __device__ __forceinline__ void fft_ct(C_t<T>* buf, int t) {
     constexpr int L = 1 << LOG2L;
-    if constexpr (LOG2L - DONE >= 3) {
-        fft_stage_ct<8, (1 << DONE), L, SIGN, T>(buf, t);
-        fft_ct<LOG2L, SIGN, T, DONE + 3>(buf, t);
-    } else if constexpr (LOG2L - DONE == 2) {
-        fft_stage_ct<4, (1 << DONE), L, SIGN, T>(buf, t);
-    } else if constexpr (LOG2L - DONE == 1) {
-        fft_stage_ct<2, (1 << DONE), L, SIGN, T>(buf, t);
+    constexpr int REM = LOG2L - DONE;
+    if constexpr (REM >= 4) {
+        fft16_stage<16, (1 << DONE), L, SIGN, T>(buf, t);
+        fft_ct<LOG2L, SIGN, T, DONE + 4>(buf, t);
+    } else if constexpr (REM == 3) {
+        fft16_stage<8, (1 << DONE), L, SIGN, T>(buf, t);
+    } else if constexpr (REM == 2) {
+        fft16_stage<4, (1 << DONE), L, SIGN, T>(buf, t);
+    } else if constexpr (REM == 1) {
+        fft16_stage<2, (1 << DONE), L, SIGN, T>(buf, t);
     }
 }
 
-// Columns (pass 1) or rows (pass 2) per CTA: >= 64 contiguous bytes per global
-// row segment, <= 1024 threads (len/8 per FFT).
+// Columns (pass 1) or rows (pass 2) per CTA: 64 contiguous bytes per global row
+// segment where the thread budget allows (<= 1024 threads for float, <= 512
+// for double, L/16 per FFT).
 template <typename T, int LOG2L>
 struct PassTile {
     static constexpr int L = 1 << LOG2L;
+    static constexpr int EPT = 16;                       // elements per thread
     static constexpr int W0 = (int)(64 / sizeof(C_t<T>));
-    static constexpr int TILES = (W0 * (L / 8) <= 1024) ? W0 : (1024 / (L / 8));
+    static constexpr int TMAX = sizeof(T) == 4 ? 1024 : 512;
+    static constexpr int WMIN = 32 / (L / EPT) > W0 ? 32 / (L / EPT) : W0;   // >= one warp
+    static constexpr int TILES = (WMIN * (L / EPT) <= TMAX) ? WMIN : (TMAX / (L / EPT));
     static constexpr int LOG2T = TILES == 8 ? 3 : TILES == 4 ? 2 : TILES == 2 ? 1 : 0;
-    static constexpr int NT = TILES * (L / 8);
-    // padded length + an offset that puts consecutive tiles P/TILES bank
-    // groups apart (P = 128 bytes / element size), so the transposing
-    // load/store loops (consecutive threads on consecutive tiles) spread over
-    // the banks
+    static_assert(TILES == 1 || TILES == 2 || TILES == 4 || TILES == 8, "tile count");
+    static constexpr int NT = TILES * (L / EPT);
+    // offset between tiles: P/TILES bank groups (P = 128 bytes / element
+    // size), so the transposing load/store loops (consecutive threads on
+    // consecutive tiles) spread over the banks
     static constexpr int P = (int)(128 / sizeof(C_t<T>));
-    static constexpr int LD = L + (L >> 3) + (TILES >= P ? 1 : P / TILES);
+    static constexpr int LD = L + (TILES >= P ? 1 : P / TILES);
     static constexpr size_t SMEM = (size_t)TILES * LD * sizeof(C_t<T>);
-    // 2048 resident threads for float (32 registers), 1024 for double
-    static constexpr int MINB = (sizeof(T) == 4 ? 2048 : 1024) / NT;
+    // register budget: 64 per thread for float, 128 for double
+    static constexpr int MINB = (TMAX / NT) > 0 ? (TMAX / NT) : 1;
 };
 
 // Pass 1 for a tile of TILES columns i1 of one right-hand side s: the
@@ -132,57 +212,62 @@ struct PassTile {
 // MODE 1: x read from the band grid (adjoint).
 template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
 __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MINB)
-    k_pass1(BandDev B, int rhs0, int log2n1, const C_t<T>* __restrict__ c,
-            const T* __restrict__ D, const C_t<T>* __restrict__ src, C_t<T>* __restrict__ Y) {
+    k_pass1(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n1,
+            const C_t<T>* __restrict__ c, const T* __restrict__ D, const C_t<T>* __restrict__ src,
+            C_t<T>* __restrict__ Y) {
     using C = C_t<T>;
     using PT = PassTile<T, LOG2L>;
     constexpr int L = PT::L, TC = PT::TILES, NT = PT::NT, LD = PT::LD;
     extern __shared__ unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
+    const PassItem item = items[blockIdx.y];
+    const BandDev B = bands[item.band];
     const int n1 = 1 << log2n1;
     const int n = n1 << LOG2L;
-    const int s = rhs0 + blockIdx.y;
+    const int s = item.rhs;
     const int i1b = blockIdx.x * TC;
     const int tid = threadIdx.x;
     if constexpr (MODE == 0) {
         const T* Ds = D + B.D_off + (int64_t)s * B.K;
         const int K = (int)B.K, half = (int)(B.Nm >> 1);
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < PT::EPT; ++it) {
             const int idx = tid + it * NT;
             const int col = idx & (TC - 1), i2 = idx >> PT::LOG2T;
-            sm[col * LD + pad8(i2)] =
+            sm[col * LD + swz<T>(i2)] =
                 prep_value32<T, DERIV>(i1b + col + (i2 << log2n1), n, half, K, c, Ds);
         }
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
+        for (int it = 0; it < PT::EPT; ++it) {
             const int idx = tid + it * NT;
             const int col = idx & (TC - 1), i2 = idx >> PT::LOG2T;
-            sm[col * LD + pad8(i2)] = in[i1b + col + (i2 << log2n1)];
+            sm[col * LD + swz<T>(i2)] = in[i1b + col + (i2 << log2n1)];
         }
     }
     __syncthreads();
-    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 8)) * LD, tid & (L / 8 - 1));
-    // twiddles exp(SIGN 2 pi i i1 l2 / n) by recurrence along this thread's l2
+    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 16)) * LD, tid & (L / 16 - 1));
+    // twiddles exp(SIGN 2 pi i i1 l2 / n) along this thread's l2 = l20 + it S:
+    // exp(.. i1 l20) times the powers (it = 4a + b) of exp(.. i1 S), all exact
+    // sincospi values or products of at most three of them
     const int col = tid & (TC - 1);
     const int l20 = tid >> PT::LOG2T;
-    constexpr int S = NT / TC;                    // = L/8, the l2 step between iterations
+    constexpr int S = NT / TC;                    // = L/16, the l2 step between iterations
     const int i1 = i1b + col;
     const T inv_n = (T)1 / (T)n;                  // a power of two
     int e0 = i1 * l20;                            // < n
     if (e0 >= n / 2) e0 -= n;
     int es = (i1 * S) & (n - 1);
     if (es >= n / 2) es -= n;
-    C w = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
-    const C step = expipi<T>((T)(2 * SIGN) * (T)es * inv_n);
-    C* out = Y + (int64_t)blockIdx.y * n;
+    const C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
+    C ws[16];
+    twiddle_powers<16, T>((T)(2 * SIGN) * (T)es * inv_n, ws);
+    C* out = Y + item.y_off;
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < PT::EPT; ++it) {
         const int l2 = l20 + it * S;
-        out[(int64_t)l2 * n1 + i1] = cmul(sm[col * LD + pad8(l2)], w);
-        w = cmul(w, step);
+        out[(int64_t)l2 * n1 + i1] = cmul(sm[col * LD + swz<T>(l2)], cmul(w0, ws[it]));
     }
 }
 
@@ -191,73 +276,78 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
 // transform) in the band grid.
 template <typename T, int SIGN, int LOG2L>
 __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MINB)
-    k_pass2(BandDev B, int rhs0, int log2n2, const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst) {
+    k_pass2(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n2,
+            const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst) {
     using C = C_t<T>;
     using PT = PassTile<T, LOG2L>;
     constexpr int L = PT::L, TR = PT::TILES, NT = PT::NT, LD = PT::LD;
     extern __shared__ unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
+    const PassItem item = items[blockIdx.y];
+    const BandDev B = bands[item.band];
     const int n = L << log2n2;
-    const int s = rhs0 + blockIdx.y;
+    const int s = item.rhs;
     const int l2b = blockIdx.x * TR;
     const int tid = threadIdx.x;
-    const C* in = Y + (int64_t)blockIdx.y * n + (int64_t)l2b * L;
+    const C* in = Y + item.y_off + (int64_t)l2b * L;
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < PT::EPT; ++it) {
         const int idx = tid + it * NT;
         const int row = idx >> LOG2L, i1 = idx & (L - 1);
-        sm[row * LD + pad8(i1)] = in[idx];
+        sm[row * LD + swz<T>(i1)] = in[idx];
     }
     __syncthreads();
-    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 8)) * LD, tid & (L / 8 - 1));
+    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 16)) * LD, tid & (L / 16 - 1));
     C* out = dst + B.grid_off + (int64_t)s * n + l2b;
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < PT::EPT; ++it) {
         const int idx = tid + it * NT;
         const int row = idx & (TR - 1), l1 = idx >> PT::LOG2T;
-        out[row + ((int64_t)l1 << log2n2)] = sm[row * LD + pad8(l1)];
+        out[row + ((int64_t)l1 << log2n2)] = sm[row * LD + swz<T>(l1)];
     }
 }
 
-// Host launchers of one band's passes for right-hand sides rhs0..rhs0+ns-1;
-// the pass length picks the compiled instantiation.
+// Host launchers: one launch covers the work items items[0..nitems) (one per
+// (band, right-hand side) of one grid size); the pass length picks the compiled
+// instantiation.
 
 template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
-static cudaError_t pass1_ct(const BandDev& B, int rhs0, int ns, int log2n1, const C_t<T>* c,
-                            const T* D, const C_t<T>* src, C_t<T>* Y, cudaStream_t st) {
+static cudaError_t pass1_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
+                            const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
+                            cudaStream_t st) {
     using PT = PassTile<T, LOG2L>;
     auto k = k_pass1<T, SIGN, MODE, DERIV, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    k<<<dim3((unsigned)((1 << log2n1) / PT::TILES), (unsigned)ns), PT::NT, PT::SMEM, st>>>(
-        B, rhs0, log2n1, c, D, src, Y);
+    k<<<dim3((unsigned)((1 << log2n1) / PT::TILES), (unsigned)nitems), PT::NT, PT::SMEM, st>>>(
+        items, bands, log2n1, c, D, src, Y);
     return cudaGetLastError();
 }
 
 template <typename T, int SIGN, int LOG2L>
-static cudaError_t pass2_ct(const BandDev& B, int rhs0, int ns, int log2n2, const C_t<T>* Y,
-                            C_t<T>* dst, cudaStream_t st) {
+static cudaError_t pass2_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n2,
+                            const C_t<T>* Y, C_t<T>* dst, cudaStream_t st) {
     using PT = PassTile<T, LOG2L>;
     auto k = k_pass2<T, SIGN, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
-    k<<<dim3((unsigned)((1 << log2n2) / PT::TILES), (unsigned)ns), PT::NT, PT::SMEM, st>>>(
-        B, rhs0, log2n2, Y, dst);
+    k<<<dim3((unsigned)((1 << log2n2) / PT::TILES), (unsigned)nitems), PT::NT, PT::SMEM, st>>>(
+        items, bands, log2n2, Y, dst);
     return cudaGetLastError();
 }
 
 // Pass 1 (length n2 = 2^log2n2, 6..12) over all n1 = 2^log2n1 columns.
 template <typename T, int SIGN, int MODE, bool DERIV>
-cudaError_t launch_pass1(const BandDev& B, int rhs0, int ns, int log2n1, int log2n2,
-                         const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
+cudaError_t launch_pass1(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
+                         int log2n2, const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
                          cudaStream_t st) {
     switch (log2n2) {
 #define FL_P1(LG) \
-    case LG: return pass1_ct<T, SIGN, MODE, DERIV, LG>(B, rhs0, ns, log2n1, c, D, src, Y, st);
+    case LG: return pass1_ct<T, SIGN, MODE, DERIV, LG>(items, nitems, bands, log2n1, c, D, src, Y, st);
         FL_P1(6) FL_P1(7) FL_P1(8) FL_P1(9) FL_P1(10) FL_P1(11) FL_P1(12)
 #undef FL_P1
         default: return cudaErrorInvalidValue;
@@ -266,33 +356,26 @@ cudaError_t launch_pass1(const BandDev& B, int rhs0, int ns, int log2n1, int log
 
 // Pass 2 (length n1 = 2^log2n1, 7..12) over all n2 = 2^log2n2 rows.
 template <typename T, int SIGN>
-cudaError_t launch_pass2(const BandDev& B, int rhs0, int ns, int log2n1, int log2n2,
-                         const C_t<T>* Y, C_t<T>* dst, cudaStream_t st) {
+cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
+                         int log2n2, const C_t<T>* Y, C_t<T>* dst, cudaStream_t st) {
     switch (log2n1) {
 #define FL_P2(LG) \
-    case LG: return pass2_ct<T, SIGN, LG>(B, rhs0, ns, log2n2, Y, dst, st);
+    case LG: return pass2_ct<T, SIGN, LG>(items, nitems, bands, log2n2, Y, dst, st);
         FL_P2(6) FL_P2(7) FL_P2(8) FL_P2(9) FL_P2(10) FL_P2(11) FL_P2(12)
 #undef FL_P2
         default: return cudaErrorInvalidValue;
     }
 }
 
-#define FL_FFT_EXTERN(T)                                                                    \
-    extern template cudaError_t launch_pass1<T, 1, 0, false>(const BandDev&, int, int, int, int, \
-                                                             const C_t<T>*, const T*,         \
-                                                             const C_t<T>*, C_t<T>*,          \
-                                                             cudaStream_t);                   \
-    extern template cudaError_t launch_pass1<T, 1, 0, true>(const BandDev&, int, int, int, int,  \
-                                                            const C_t<T>*, const T*,          \
-                                                            const C_t<T>*, C_t<T>*,           \
-                                                            cudaStream_t);                    \
-    extern template cudaError_t launch_pass1<T, -1, 1, false>(const BandDev&, int, int, int,     \
-                                                              int, const C_t<T>*, const T*,   \
-                                                              const C_t<T>*, C_t<T>*,         \
-                                                              cudaStream_t);                  \
-    extern template cudaError_t launch_pass2<T, 1>(const BandDev&, int, int, int, int,          \
-                                                   const C_t<T>*, C_t<T>*, cudaStream_t);     \
-    extern template cudaError_t launch_pass2<T, -1>(const BandDev&, int, int, int, int,         \
-                                                    const C_t<T>*, C_t<T>*, cudaStream_t);
+#define FL_P1_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, const T*, \
+                     const C_t<T>*, C_t<T>*, cudaStream_t
+#define FL_P2_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, C_t<T>*, \
+                     cudaStream_t
+#define FL_FFT_EXTERN(T)                                                   \
+    extern template cudaError_t launch_pass1<T, 1, 0, false>(FL_P1_SIG(T)); \
+    extern template cudaError_t launch_pass1<T, 1, 0, true>(FL_P1_SIG(T));  \
+    extern template cudaError_t launch_pass1<T, -1, 1, false>(FL_P1_SIG(T)); \
+    extern template cudaError_t launch_pass2<T, 1>(FL_P2_SIG(T));          \
+    extern template cudaError_t launch_pass2<T, -1>(FL_P2_SIG(T));
 
 }  // namespace fl

@@ -4,18 +4,10 @@
 
 namespace fl {
 
-template cudaError_t launch_pass1<float, 1, 0, false>(const BandDev&, int, int, int, int,
-                                                  const C_t<float>*, const float*, const C_t<float>*,
-                                                  C_t<float>*, cudaStream_t);
-template cudaError_t launch_pass1<float, 1, 0, true>(const BandDev&, int, int, int, int,
-                                                 const C_t<float>*, const float*, const C_t<float>*,
-                                                 C_t<float>*, cudaStream_t);
-template cudaError_t launch_pass1<float, -1, 1, false>(const BandDev&, int, int, int, int,
-                                                   const C_t<float>*, const float*, const C_t<float>*,
-                                                   C_t<float>*, cudaStream_t);
-template cudaError_t launch_pass2<float, 1>(const BandDev&, int, int, int, int, const C_t<float>*,
-                                        C_t<float>*, cudaStream_t);
-template cudaError_t launch_pass2<float, -1>(const BandDev&, int, int, int, int, const C_t<float>*,
-                                         C_t<float>*, cudaStream_t);
+template cudaError_t launch_pass1<float, 1, 0, false>(FL_P1_SIG(float));
+template cudaError_t launch_pass1<float, 1, 0, true>(FL_P1_SIG(float));
+template cudaError_t launch_pass1<float, -1, 1, false>(FL_P1_SIG(float));
+template cudaError_t launch_pass2<float, 1>(FL_P2_SIG(float));
+template cudaError_t launch_pass2<float, -1>(FL_P2_SIG(float));
 
 }  // namespace fl

@@ -4,18 +4,10 @@
 
 namespace fl {
 
-template cudaError_t launch_pass1<double, 1, 0, false>(const BandDev&, int, int, int, int,
-                                                  const C_t<double>*, const double*, const C_t<double>*,
-                                                  C_t<double>*, cudaStream_t);
-template cudaError_t launch_pass1<double, 1, 0, true>(const BandDev&, int, int, int, int,
-                                                 const C_t<double>*, const double*, const C_t<double>*,
-                                                 C_t<double>*, cudaStream_t);
-template cudaError_t launch_pass1<double, -1, 1, false>(const BandDev&, int, int, int, int,
-                                                   const C_t<double>*, const double*, const C_t<double>*,
-                                                   C_t<double>*, cudaStream_t);
-template cudaError_t launch_pass2<double, 1>(const BandDev&, int, int, int, int, const C_t<double>*,
-                                        C_t<double>*, cudaStream_t);
-template cudaError_t launch_pass2<double, -1>(const BandDev&, int, int, int, int, const C_t<double>*,
-                                         C_t<double>*, cudaStream_t);
+template cudaError_t launch_pass1<double, 1, 0, false>(FL_P1_SIG(double));
+template cudaError_t launch_pass1<double, 1, 0, true>(FL_P1_SIG(double));
+template cudaError_t launch_pass1<double, -1, 1, false>(FL_P1_SIG(double));
+template cudaError_t launch_pass2<double, 1>(FL_P2_SIG(double));
+template cudaError_t launch_pass2<double, -1>(FL_P2_SIG(double));
 
 }  // namespace fl

@@ -27,6 +27,20 @@ struct SmallWork {
     int log2n;
 };
 
+// One (band, right-hand side) of a four-step FFT launch, with the offset of
+// its slice of the intermediate buffer.
+struct PassItem {
+    int band;
+    int rhs;
+    int64_t y_off;
+};
+
+// A launch of the two four-step passes over items[start, start + count), all
+// of grid length 2^log2n.
+struct PassGroup {
+    int start, count, log2n;
+};
+
 // Direct route (fl_direct.cu): kDirNodes nodes x one chunk of kDirChunk
 // coefficients per CTA, Horner blocks of kDirBlock terms.
 constexpr int kDirBlock = 32;
@@ -73,6 +87,9 @@ struct Plan {
     int64_t grid_elems = 0, D_elems = 0, Y_elems = 0;
     std::vector<SmallWork> small_work;
     std::vector<int> large_bands;
+    std::vector<PassItem> pass_items;
+    std::vector<PassGroup> pass_groups;
+    int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
     double direct_bias = 1.0;
     std::vector<DirectItem> direct_work;
@@ -85,6 +102,7 @@ struct Plan {
     uint8_t* d_bandid = nullptr;   // band of each sorted node
     BandDev* d_bands = nullptr;    // levels + 1 descriptors
     SmallWork* d_small = nullptr;
+    PassItem* d_pass = nullptr;
     double* d_cheb = nullptr;      // t_s (q), lambda_s (q)
     void* d_D = nullptr;           // weight tables (T)
     void* d_grid = nullptr;        // band grids (complex T)

@@ -411,30 +411,27 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         ++p.launches;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    for (int b : p.large_bands) {
-        const BandDev& B = p.bands[b].dev;
+    for (const PassGroup& g : p.pass_groups) {
         int l1, l2;
-        large_split(B.log2n, &l1, &l2);
-        // right-hand sides in chunks that fit the intermediate buffer
-        const int chunk = (int)std::max<int64_t>(1, p.Y_elems / B.n);
-        for (int s0 = 0; s0 < B.nrhs; s0 += chunk) {
-            const int ns = std::min(chunk, B.nrhs - s0);
-            const double b1 = (double)ns * (B.n * sizeof(C) +
-                                            (MODE == 0 ? B.K * (sizeof(C) + sizeof(T))
-                                                       : B.n * sizeof(C)));
-            const double b2 = (double)ns * 2.0 * B.n * sizeof(C);
-            int slot;
-            timer_begin(p, "fft_pass1", b1, st, &slot);
-            e = launch_pass1<T, SIGN, MODE, DERIV>(B, s0, ns, l1, l2, (const C*)c, (const T*)p.d_D,
-                                                   grid, (C*)p.d_Y, st);
-            timer_end(p, slot, st);
-            if (e != cudaSuccess) return e;
-            timer_begin(p, "fft_pass2", b2, st, &slot);
-            e = launch_pass2<T, SIGN>(B, s0, ns, l1, l2, (const C*)p.d_Y, grid, st);
-            timer_end(p, slot, st);
-            p.launches += 2;
-            if (e != cudaSuccess) return e;
-        }
+        large_split(g.log2n, &l1, &l2);
+        const int64_t n = (int64_t)1 << g.log2n;
+        double kbytes = 0;   // forward input reads: c and D over the items' K
+        for (int i = 0; i < g.count; ++i) kbytes += (double)p.bands[p.pass_items[g.start + i].band].dev.K;
+        const double b1 = (double)g.count * n * sizeof(C) +
+                          (MODE == 0 ? kbytes * (sizeof(C) + sizeof(T)) : (double)g.count * n * sizeof(C));
+        const double b2 = (double)g.count * 2.0 * n * sizeof(C);
+        int slot;
+        timer_begin(p, "fft_pass1", b1, st, &slot);
+        e = launch_pass1<T, SIGN, MODE, DERIV>(p.d_pass + g.start, g.count, p.d_bands, l1, l2,
+                                               (const C*)c, (const T*)p.d_D, grid, (C*)p.d_Y, st);
+        timer_end(p, slot, st);
+        if (e != cudaSuccess) return e;
+        timer_begin(p, "fft_pass2", b2, st, &slot);
+        e = launch_pass2<T, SIGN>(p.d_pass + g.start, g.count, p.d_bands, l1, l2, (const C*)p.d_Y,
+                                  grid, st);
+        timer_end(p, slot, st);
+        p.launches += 2;
+        if (e != cudaSuccess) return e;
     }
     return e;
 }

@@ -57,7 +57,8 @@ class fl_info(ctypes.Structure):
 
 
 class fl_options(ctypes.Structure):
-    _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double)]
+    _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
+                ("rhs_per_launch", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
@@ -279,7 +280,8 @@ class Plan:
     """
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
-                 stream=None, route: str = "auto", direct_bias: float = 1.0):
+                 stream=None, route: str = "auto", direct_bias: float = 1.0,
+                 rhs_per_launch: int = 0):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -289,7 +291,7 @@ class Plan:
         self.prec = FL_FP64 if precision == "fp64" else FL_FP32
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
-        opt = fl_options(ROUTES[route], float(direct_bias))
+        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch))
         st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
                            opt, _stream_handle(stream))
         check(st, "fl_plan")
