@@ -182,6 +182,59 @@ __device__ __forceinline__ void fft_ct(C_t<T>* buf, int t) {
     }
 }
 
+// The same transform split so that its first stage can take its inputs from
+// registers and its last stage can leave its outputs in registers (for
+// LOG2L >= 5: radix 16 first, radix 16 middles, radix LAST_R last).
+template <int LOG2L> struct StagePlan {
+    static constexpr int NSTAGE = (LOG2L + 3) / 4;
+    static constexpr int LAST_LOG = LOG2L - 4 * (NSTAGE - 1);   // 1..4
+    static constexpr int LAST_R = 1 << LAST_LOG;
+    static constexpr int LAST_NS = 1 << (LOG2L - LAST_LOG);
+};
+
+// First stage (radix 16, span 1) on v[r] = x[t + r L/16], stored to smem.
+template <int LOG2L, int SIGN, typename T>
+__device__ __forceinline__ void fft_first_from_regs(C_t<T>* v, C_t<T>* buf, int t) {
+    dft16<SIGN, T>(v);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[swz<T>(t * 16 + r)] = v[r];
+    __syncthreads();
+}
+
+// Middle stages (radix 16, smem to smem) from span 2^DONE up to the last stage.
+template <int LOG2L, int SIGN, typename T, int DONE = 4>
+__device__ __forceinline__ void fft_middle(C_t<T>* buf, int t) {
+    constexpr int L = 1 << LOG2L;
+    if constexpr (DONE < LOG2L - StagePlan<LOG2L>::LAST_LOG) {
+        fft16_stage<16, (1 << DONE), L, SIGN, T>(buf, t);
+        fft_middle<LOG2L, SIGN, T, DONE + 4>(buf, t);
+    }
+}
+
+// Last stage (radix LAST_R, span LAST_NS = L / LAST_R) from smem into
+// registers: v[jb R + r] is output jj + r LAST_NS, jj = t + jb L/16.
+template <int LOG2L, int SIGN, typename T>
+__device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T>* v) {
+    using C = C_t<T>;
+    using SP = StagePlan<LOG2L>;
+    constexpr int L = 1 << LOG2L, R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R, NTHR = L / 16;
+#pragma unroll
+    for (int jb = 0; jb < J; ++jb) {
+        const int jj = t + jb * NTHR;   // < NS, so k = jj
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
+        C w[R];
+        twiddle_powers<R, T>((T)(2 * SIGN) * (T)jj * (T)(1.0 / L), w);
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], w[r]);
+        C* a = v + jb * R;
+        if constexpr (R == 16) dft16<SIGN, T>(a);
+        if constexpr (R == 8) dft8<SIGN, T>(a);
+        if constexpr (R == 4) dft4<SIGN>(a[0], a[1], a[2], a[3]);
+        if constexpr (R == 2) dft2<SIGN>(a[0], a[1]);
+    }
+}
+
 // Columns (pass 1) or rows (pass 2) per CTA: 64 contiguous bytes per global row
 // segment where the thread budget allows (<= 1024 threads for float, <= 512
 // for double, L/16 per FFT).
@@ -217,7 +270,8 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
             C_t<T>* __restrict__ Y) {
     using C = C_t<T>;
     using PT = PassTile<T, LOG2L>;
-    constexpr int L = PT::L, TC = PT::TILES, NT = PT::NT, LD = PT::LD;
+    using SP = StagePlan<LOG2L>;
+    constexpr int L = PT::L, TC = PT::TILES, LD = PT::LD;
     extern __shared__ unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     const PassItem item = items[blockIdx.y];
@@ -225,49 +279,46 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
     const int n1 = 1 << log2n1;
     const int n = n1 << LOG2L;
     const int s = item.rhs;
-    const int i1b = blockIdx.x * TC;
-    const int tid = threadIdx.x;
+    // columns fastest: the warp's global accesses are TC-column segments
+    const int col = threadIdx.x & (TC - 1);
+    const int t = threadIdx.x >> PT::LOG2T;        // thread within the column FFT
+    const int i1 = blockIdx.x * TC + col;
+    C* buf = sm + col * LD;
+    C v[16];
     if constexpr (MODE == 0) {
         const T* Ds = D + B.D_off + (int64_t)s * B.K;
         const int K = (int)B.K, half = (int)(B.Nm >> 1);
 #pragma unroll
-        for (int it = 0; it < PT::EPT; ++it) {
-            const int idx = tid + it * NT;
-            const int col = idx & (TC - 1), i2 = idx >> PT::LOG2T;
-            sm[col * LD + swz<T>(i2)] =
-                prep_value32<T, DERIV>(i1b + col + (i2 << log2n1), n, half, K, c, Ds);
-        }
+        for (int r = 0; r < 16; ++r)
+            v[r] = prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, c, Ds);
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
 #pragma unroll
-        for (int it = 0; it < PT::EPT; ++it) {
-            const int idx = tid + it * NT;
-            const int col = idx & (TC - 1), i2 = idx >> PT::LOG2T;
-            sm[col * LD + swz<T>(i2)] = in[i1b + col + (i2 << log2n1)];
-        }
+        for (int r = 0; r < 16; ++r) v[r] = in[i1 + ((t + r * (L / 16)) << log2n1)];
     }
-    __syncthreads();
-    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 16)) * LD, tid & (L / 16 - 1));
-    // twiddles exp(SIGN 2 pi i i1 l2 / n) along this thread's l2 = l20 + it S:
-    // exp(.. i1 l20) times the powers (it = 4a + b) of exp(.. i1 S), all exact
-    // sincospi values or products of at most three of them
-    const int col = tid & (TC - 1);
-    const int l20 = tid >> PT::LOG2T;
-    constexpr int S = NT / TC;                    // = L/16, the l2 step between iterations
-    const int i1 = i1b + col;
+    fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
+    fft_middle<LOG2L, SIGN, T>(buf, t);
+    fft_last_to_regs<LOG2L, SIGN, T>(buf, t, v);
+    // outputs l2 = jj + r NS, twiddled by exp(SIGN 2 pi i i1 l2 / n) =
+    // exp(.. i1 jj) * exp(.. i1 NS)^r (sincospi values and short products)
+    constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
     const T inv_n = (T)1 / (T)n;                  // a power of two
-    int e0 = i1 * l20;                            // < n
-    if (e0 >= n / 2) e0 -= n;
-    int es = (i1 * S) & (n - 1);
+    int es = (i1 * NS) & (n - 1);                 // i1 NS < n
     if (es >= n / 2) es -= n;
-    const C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
-    C ws[16];
-    twiddle_powers<16, T>((T)(2 * SIGN) * (T)es * inv_n, ws);
+    C step[R];
+    twiddle_powers<R, T>((T)(2 * SIGN) * (T)es * inv_n, step);
     C* out = Y + item.y_off;
 #pragma unroll
-    for (int it = 0; it < PT::EPT; ++it) {
-        const int l2 = l20 + it * S;
-        out[(int64_t)l2 * n1 + i1] = cmul(sm[col * LD + swz<T>(l2)], cmul(w0, ws[it]));
+    for (int jb = 0; jb < J; ++jb) {
+        const int jj = t + jb * (L / 16);
+        int e0 = i1 * jj;                         // < n
+        if (e0 >= n / 2) e0 -= n;
+        const C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int l2 = jj + r * NS;
+            out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], cmul(w0, step[r]));
+        }
     }
 }
 
@@ -290,14 +341,16 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
     const int l2b = blockIdx.x * TR;
     const int tid = threadIdx.x;
     const C* in = Y + item.y_off + (int64_t)l2b * L;
+    // first stage straight from the rows (consecutive threads, consecutive i1)
+    {
+        const int row = tid / (L / 16), t = tid & (L / 16 - 1);
+        C v[16];
 #pragma unroll
-    for (int it = 0; it < PT::EPT; ++it) {
-        const int idx = tid + it * NT;
-        const int row = idx >> LOG2L, i1 = idx & (L - 1);
-        sm[row * LD + swz<T>(i1)] = in[idx];
+        for (int r = 0; r < 16; ++r) v[r] = in[(int64_t)row * L + t + r * (L / 16)];
+        C* buf = sm + row * LD;
+        fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
+        fft_ct<LOG2L, SIGN, T, 4>(buf, t);
     }
-    __syncthreads();
-    fft_ct<LOG2L, SIGN, T>(sm + (tid / (L / 16)) * LD, tid & (L / 16 - 1));
     C* out = dst + B.grid_off + (int64_t)s * n + l2b;
 #pragma unroll
     for (int it = 0; it < PT::EPT; ++it) {
