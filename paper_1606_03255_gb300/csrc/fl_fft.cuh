@@ -288,9 +288,13 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
     if constexpr (MODE == 0) {
         const T* Ds = D + B.D_off + (int64_t)s * B.K;
         const int K = (int)B.K, half = (int)(B.Nm >> 1);
+        // i2 = t + r L/16 in [n2/4, 3 n2/4) (r = 4..11) holds grid indices in
+        // [n/4, 3n/4): centred frequencies with k >= N_m or k < 0, always zero
 #pragma unroll
         for (int r = 0; r < 16; ++r)
-            v[r] = prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, c, Ds);
+            v[r] = (r >= 4 && r < 12)
+                       ? C{(T)0, (T)0}
+                       : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, c, Ds);
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
 #pragma unroll
@@ -349,16 +353,25 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
         for (int r = 0; r < 16; ++r) v[r] = in[(int64_t)row * L + t + r * (L / 16)];
         C* buf = sm + row * LD;
         fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
-        fft_ct<LOG2L, SIGN, T, 4>(buf, t);
+        fft_middle<LOG2L, SIGN, T>(buf, t);
     }
-    C* out = dst + B.grid_off + (int64_t)s * n + l2b;
+    // last stage with rows fastest: the warp's stores are TR-row segments of X
+    {
+        using SP = StagePlan<LOG2L>;
+        constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
+        const int row = tid & (TR - 1), t = tid >> PT::LOG2T;
+        C v[16];
+        fft_last_to_regs<LOG2L, SIGN, T>(sm + row * LD, t, v);
+        C* out = dst + B.grid_off + (int64_t)s * n + l2b + row;
 #pragma unroll
-    for (int it = 0; it < PT::EPT; ++it) {
-        const int idx = tid + it * NT;
-        const int row = idx & (TR - 1), l1 = idx >> PT::LOG2T;
-        out[row + ((int64_t)l1 << log2n2)] = sm[row * LD + swz<T>(l1)];
+        for (int jb = 0; jb < J; ++jb) {
+            const int jj = t + jb * (L / 16);
+#pragma unroll
+            for (int r = 0; r < R; ++r) out[(int64_t)(jj + r * NS) << log2n2] = v[jb * R + r];
+        }
     }
 }
+
 
 // Host launchers: one launch covers the work items items[0..nitems) (one per
 // (band, right-hand side) of one grid size); the pass length picks the compiled
