@@ -66,9 +66,10 @@ typedef struct {
     int sigma;                /* oversampling of every band grid (2) */
     double y1, xi1;           /* interval ends of Definition 3.2 */
     int64_t z0_nodes;         /* nodes with |z| < eps (returned as c_0) */
-    int n_bands_fft;          /* bands evaluated with an NFFT */
-    int n_bands_direct;       /* bands evaluated by the direct-sum kernel */
-    /* per band b = 1..levels (index 0 unused): */
+    int batch;                /* transforms in the plan (fl_plan_batched), else 1 */
+    int n_bands_fft;          /* bands evaluated with an NFFT (all transforms) */
+    int n_bands_direct;       /* bands evaluated by the direct-sum kernel (all transforms) */
+    /* per band b = 1..levels of the (first) transform (index 0 unused): */
     int band_ell[FL_MAX_LEVELS];      /* l_m (first interpolated frequency band) */
     int band_route[FL_MAX_LEVELS];    /* 0 empty, 1 NFFT, 2 direct */
     int64_t band_nodes[FL_MAX_LEVELS];
@@ -119,6 +120,11 @@ typedef struct {
     double direct_bias;   /* multiplies the direct-sum cost in route 0 (0 = 1.0)  */
     int rhs_per_launch;   /* grids of one size per four-step launch pair; small
                              values keep the intermediate in L2 (0 = all)         */
+    int use_graph;        /* fl_execute: 1 = capture the launches in a CUDA graph
+                             on the first call and replay it (re-captured when the
+                             buffers or the stream change; not on the legacy
+                             default stream).  fl_plan_batched: graphs are on
+                             unless this is -1.  0 = plain launches.             */
 } fl_options;
 
 /*
@@ -128,6 +134,26 @@ typedef struct {
 fl_status fl_plan_ex(fl_plan_t *out, int64_t N, int64_t M, const double *nodes_dev,
                      int q, double eps, fl_precision prec, const fl_options *opt,
                      void *stream);
+
+/*
+ * fl_plan_batched -- one plan for B independent transforms of sizes
+ * N_host[i] x M_host[i] (host arrays), i < B, with the same eps, q and
+ * precision.  nodes_dev holds the nodes of transform 0, then 1, ... (sum M_i
+ * rows of {Re w, Im w}, float64).  Every kernel launch of fl_execute_batched
+ * covers all B transforms (one global band table; the four-step FFTs of all
+ * transforms of one grid size share a launch), and the launches are captured
+ * in a CUDA graph and replayed (see fl_options.use_graph).  Forward only.
+ */
+fl_status fl_plan_batched(fl_plan_t *out, int B, const int64_t *N_host, const int64_t *M_host,
+                          const double *nodes_dev, int q, double eps, fl_precision prec,
+                          const fl_options *opt, void *stream);
+
+/*
+ * fl_execute_batched -- all transforms of a batched plan: c_dev holds the
+ * coefficients of transform 0, 1, ... (sum N_i complex), f_dev receives the
+ * results in the same order (sum M_i complex).
+ */
+fl_status fl_execute_batched(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
 
 /*
  * fl_execute -- f~ ~= C c with C = (z_j^k), Algorithm 2.

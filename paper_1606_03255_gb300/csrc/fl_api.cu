@@ -35,8 +35,9 @@ static fl_status cuda_fail(cudaError_t e, const char* where) {
     } while (0)
 
 Plan::~Plan() {
+    if (gexec) cudaGraphExecDestroy(gexec);
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
-                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_lap, d_direct,
+                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -84,40 +85,54 @@ static int window_width(double eps, double sigma) {
     return 12;
 }
 
-// Parameters of Algorithm 2 (Section 4) with the error split of Lemma 4.1.
-static fl_status select_params(Plan& p, int q_in) {
+// Parameters of Algorithm 2 (Section 4) with the error split of Lemma 4.1 that
+// do not depend on N: q, y_1 = ln(1/eps), the window.
+static fl_status select_common(Plan& p, int q_in) {
     p.eps_K = p.eps / 3.0;
     p.eps_A = p.eps / 3.0;
     p.q = q_in > 0 ? q_in : (int)ceil(0.5 + log(1.0 / p.eps_K) / log(4.0));
     if (p.q > kMaxQ) return fail(FL_EUNSUPPORTED, "interpolation rank q above 40");
     p.y1 = log(1.0 / p.eps);            // Z^0 removed: y in [0, ln(1/eps)]
-    p.xi1 = (double)(p.N - 1);          // frequencies 0..N-1
     p.mw = window_width(p.eps_A, 2.0);
     p.kb_b = M_PI * (2.0 - 1.0 / 2.0);
-    if (p.N == 1) {
-        p.levels = 1;
+    return FL_OK;
+}
+
+// The dyadic partition of one transform (Definition 3.2 with xi_1 = N - 1):
+// appends its bands 0..levels to p.bands.
+static fl_status select_bands(Plan& p, Instance& in, int inst_index) {
+    in.xi1 = (double)(in.N - 1);        // frequencies 0..N-1
+    if (in.N == 1) {
+        in.levels = 1;
     } else {
-        const double lv = ceil(log2(p.y1 * p.xi1 / p.eps_K)) + 1.0;
-        p.levels = (int)std::max(1.0, lv);
+        const double lv = ceil(log2(p.y1 * in.xi1 / p.eps_K)) + 1.0;
+        in.levels = (int)std::max(1.0, lv);
     }
-    if (p.levels > 127) return fail(FL_EUNSUPPORTED, "more than 127 dyadic levels");
-    p.bands.assign(p.levels + 1, BandHost());
-    for (int b = 1; b <= p.levels; ++b) {
-        BandHost& bh = p.bands[b];
+    if (in.levels > 127) return fail(FL_EUNSUPPORTED, "more than 127 dyadic levels");
+    in.band_base = (int)p.bands.size();
+    for (int b = 0; b <= in.levels; ++b) {
+        BandHost bh;
+        bh.inst = inst_index;
+        bh.local = b;
+        bh.dev.c_off = in.noff;
+        if (b == 0) {
+            p.bands.push_back(bh);
+            continue;
+        }
         int64_t K;
-        if (b < p.levels) {
-            const double lg = log2(p.y1 * p.xi1) - b - log2(log(1.0 / p.eps_K));
+        if (b < in.levels) {
+            const double lg = log2(p.y1 * in.xi1) - b - log2(log(1.0 / p.eps_K));
             bh.ell = std::max(1, (int)floor(lg) + 1);
-            bh.Lm = p.levels - b;
+            bh.Lm = in.levels - b;
             // frequencies k <= xi1 / 2^(l_m - 1) carry weight (Lemma A.2(ii))
-            K = std::min<int64_t>(p.N, (int64_t)floor(ldexp(p.xi1, 1 - bh.ell)) + 1);
+            K = std::min<int64_t>(in.N, (int64_t)floor(ldexp(in.xi1, 1 - bh.ell)) + 1);
             bh.dev.nrhs = p.q;
             const double a = ldexp(p.y1, -b);
             bh.dev.yc = 1.5 * a;
             bh.dev.yh = 0.5 * a;
             bh.dev.yh_inv = 1.0 / bh.dev.yh;
         } else {
-            K = p.N;            // Z_M band: kernel ~ 1, one plain NFFT
+            K = in.N;           // Z_M band: kernel ~ 1, one plain NFFT
             bh.dev.nrhs = 1;
         }
         const int lg = std::max(4, ilog2_ceil(K));
@@ -126,6 +141,7 @@ static fl_status select_params(Plan& p, int q_in) {
         bh.dev.log2n = lg + 1;
         bh.dev.n = (int64_t)1 << (lg + 1);
         if (bh.dev.log2n > kMaxLog2n) return fail(FL_EUNSUPPORTED, "grid above 2^24 points");
+        p.bands.push_back(bh);
     }
     return FL_OK;
 }
@@ -178,10 +194,33 @@ static void build_pass_groups(Plan& p) {
     }
 }
 
-static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) {
-    fl_status s = select_params(p, q);
+// Plans the transforms Ns[i] x Ms[i], i < B, whose nodes are consecutive in
+// `nodes` (a single plan is B = 1).  Every band of every transform gets an
+// entry of one global band table, and each kernel launch of fl_execute covers
+// all transforms at once.
+static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms,
+                            const double* nodes, int q, cudaStream_t st) {
+    fl_status s = select_common(p, q);
     if (s != FL_OK) return s;
-    const int nb = p.levels + 1;
+    p.bands.clear();
+    p.inst.assign(B, Instance());
+    int64_t noff = 0, moff = 0, maxM = 0;
+    for (int i = 0; i < B; ++i) {
+        Instance& in = p.inst[i];
+        in.N = Ns[i];
+        in.M = Ms[i];
+        in.noff = noff;
+        in.moff = moff;
+        noff += in.N;
+        moff += in.M;
+        maxM = std::max(maxM, in.M);
+        if ((s = select_bands(p, in, i)) != FL_OK) return s;
+    }
+    p.N = noff;
+    p.M = moff;
+    p.levels = p.inst[0].levels;
+    p.xi1 = p.inst[0].xi1;
+    const int nb = (int)p.bands.size();
     FL_CUDA(cudaMalloc((void**)&p.d_bands, nb * sizeof(BandDev)), "cudaMalloc bands");
     std::vector<BandDev> hb(nb);
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
@@ -190,37 +229,41 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
     FL_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
     FL_CUDA(cudaMalloc(&p.d_z0, 2 * sizeof(double)), "cudaMalloc z0");
 
-    // classify and sort the nodes
+    // classify and sort the nodes of every transform into its slice
     const int64_t M = p.M;
     std::vector<int64_t> counts(nb, 0);
     if (M > 0) {
         FL_CUDA(cudaMalloc((void**)&p.d_ws, M * sizeof(double2)), "cudaMalloc nodes");
         FL_CUDA(cudaMalloc((void**)&p.d_perm, M * sizeof(int32_t)), "cudaMalloc perm");
-        FL_CUDA(cudaMalloc((void**)&p.d_bandid, M), "cudaMalloc band ids");
+        FL_CUDA(cudaMalloc((void**)&p.d_bandid, M * sizeof(int32_t)), "cudaMalloc band ids");
         uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr;
         int32_t *vals = nullptr, *vals2 = nullptr;
         int64_t* dcount = nullptr;
         int* dflag = nullptr;
-        const int64_t nblk = (M + 2047) / 2048;
+        const int64_t nblk = (maxM + 2047) / 2048;
         cudaError_t e = cudaSuccess;
         auto cleanup = [&]() {
             cudaFree(keys); cudaFree(keys2); cudaFree(hist); cudaFree(vals); cudaFree(vals2);
             cudaFree(dcount); cudaFree(dflag);
         };
-        if ((e = cudaMalloc((void**)&keys, M * 4)) == cudaSuccess &&
-            (e = cudaMalloc((void**)&keys2, M * 4)) == cudaSuccess &&
-            (e = cudaMalloc((void**)&vals, M * 4)) == cudaSuccess &&
-            (e = cudaMalloc((void**)&vals2, M * 4)) == cudaSuccess &&
+        if ((e = cudaMalloc((void**)&keys, maxM * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&keys2, maxM * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&vals, maxM * 4)) == cudaSuccess &&
+            (e = cudaMalloc((void**)&vals2, maxM * 4)) == cudaSuccess &&
             (e = cudaMalloc((void**)&hist, 256 * nblk * 4)) == cudaSuccess &&
             (e = cudaMalloc((void**)&dcount, nb * sizeof(int64_t))) == cudaSuccess &&
             (e = cudaMalloc((void**)&dflag, sizeof(int))) == cudaSuccess &&
             (e = cudaMemsetAsync(dcount, 0, nb * sizeof(int64_t), st)) == cudaSuccess &&
-            (e = cudaMemsetAsync(dflag, 0, sizeof(int), st)) == cudaSuccess &&
-            (e = launch_classify(p, nodes, keys, vals, dcount, dflag, st)) == cudaSuccess &&
-            (e = radix_sort_pairs(keys, vals, keys2, vals2, hist, M, 32, st)) == cudaSuccess &&
-            (e = launch_permute(p, nodes, keys, vals, st)) == cudaSuccess) {
+            (e = cudaMemsetAsync(dflag, 0, sizeof(int), st)) == cudaSuccess) {
+            for (int i = 0; i < B && e == cudaSuccess; ++i) {
+                const Instance& in = p.inst[i];
+                if ((e = launch_classify(p, in, nodes, keys, vals, dcount, dflag, st)) == cudaSuccess &&
+                    (e = radix_sort_pairs(keys, vals, keys2, vals2, hist, in.M, 32, st)) == cudaSuccess)
+                    e = launch_permute(p, in, nodes, keys, vals, st);
+            }
             int flag = 0;
-            e = cudaMemcpyAsync(counts.data(), dcount, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(counts.data(), dcount, nb * sizeof(int64_t), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, dflag, sizeof(int), cudaMemcpyDeviceToHost, st);
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e == cudaSuccess && flag) {
@@ -233,46 +276,55 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
     }
 
     // routes, offsets and work lists
-    p.z0_nodes = counts[0];
-    int64_t off = counts[0];
     p.grid_elems = p.D_elems = p.Y_elems = 0;
     p.small_work.clear();
     p.large_bands.clear();
     p.direct_work.clear();
     p.direct_ranges.clear();
     p.direct_nodes = p.direct_terms = p.dpart_elems = 0;
-    for (int b = 1; b <= p.levels; ++b) {
-        BandHost& bh = p.bands[b];
-        bh.nodes = counts[b];
-        bh.node_off = off;
-        off += counts[b];
-        BandDev& d = bh.dev;
-        d.node_off = bh.node_off;
-        d.route = bh.nodes > 0 ? route_of(p, bh) : 0;
-        if (d.route == 2) {
-            d.nchunk = (int)((d.K + kDirChunk - 1) / kDirChunk);
-            d.dslot = p.dpart_elems;
-            p.dpart_elems += bh.nodes * d.nchunk;
-            p.direct_ranges.push_back({b, 0, bh.nodes, p.direct_nodes});
-            p.direct_nodes += bh.nodes;
-            p.direct_terms += bh.nodes * d.K;
-            for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirNodes)
-                for (int ch = 0; ch < d.nchunk; ++ch)
-                    p.direct_work.push_back({b, ch, bh.node_off + n0,
-                                             (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
-            continue;
-        }
-        if (d.route != 1) continue;
-        d.grid_off = p.grid_elems;
-        d.D_off = p.D_elems;
-        p.grid_elems += (int64_t)d.nrhs * d.n;
-        p.D_elems += (int64_t)d.nrhs * d.K;
-        if (d.log2n <= kSmallMaxLog2) {
-            const int per = std::max(1, (int)((1 << kSmallMaxLog2) / d.n));
-            for (int s0 = 0; s0 < d.nrhs; s0 += per)
-                p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
-        } else {
-            p.large_bands.push_back(b);
+    p.z0_nodes = 0;
+    for (int i = 0; i < B; ++i) {
+        Instance& in = p.inst[i];
+        in.z0_nodes = counts[in.band_base];
+        p.z0_nodes += in.z0_nodes;
+        int64_t off = in.moff + in.z0_nodes;
+        p.bands[in.band_base].node_off = in.moff;
+        p.bands[in.band_base].dev.node_off = in.moff;
+        p.bands[in.band_base].nodes = in.z0_nodes;
+        for (int lb = 1; lb <= in.levels; ++lb) {
+            const int b = in.band_base + lb;
+            BandHost& bh = p.bands[b];
+            bh.nodes = counts[b];
+            bh.node_off = off;
+            off += counts[b];
+            BandDev& d = bh.dev;
+            d.node_off = bh.node_off;
+            d.route = bh.nodes > 0 ? route_of(p, bh) : 0;
+            if (d.route == 2) {
+                d.nchunk = (int)((d.K + kDirChunk - 1) / kDirChunk);
+                d.dslot = p.dpart_elems;
+                p.dpart_elems += bh.nodes * d.nchunk;
+                p.direct_ranges.push_back({b, 0, bh.nodes, p.direct_nodes});
+                p.direct_nodes += bh.nodes;
+                p.direct_terms += bh.nodes * d.K;
+                for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirNodes)
+                    for (int ch = 0; ch < d.nchunk; ++ch)
+                        p.direct_work.push_back({b, ch, bh.node_off + n0,
+                                                 (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
+                continue;
+            }
+            if (d.route != 1) continue;
+            d.grid_off = p.grid_elems;
+            d.D_off = p.D_elems;
+            p.grid_elems += (int64_t)d.nrhs * d.n;
+            p.D_elems += (int64_t)d.nrhs * d.K;
+            if (d.log2n <= kSmallMaxLog2) {
+                const int per = std::max(1, (int)((1 << kSmallMaxLog2) / d.n));
+                for (int s0 = 0; s0 < d.nrhs; s0 += per)
+                    p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
+            } else {
+                p.large_bands.push_back(b);
+            }
         }
     }
     build_pass_groups(p);
@@ -309,15 +361,16 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
     if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
-    FL_CUDA(build_tables(p, st), "fl_plan: tables");
+    FL_CUDA(build_cheb(p, st), "fl_plan: tables");
+    for (int i = 0; i < B; ++i) FL_CUDA(build_tables(p, p.inst[i], st), "fl_plan: tables");
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
     p.scratch_bytes = (double)p.grid_elems * cs + (double)p.D_elems * rs + (double)p.Y_elems * cs +
-                      (double)M * (sizeof(double2) + 5) + (double)p.dpart_elems * cs +
+                      (double)M * (sizeof(double2) + 8) + (double)p.dpart_elems * cs +
                       (p.direct_work.empty() ? 0.0 : (double)p.N * cs);
     // algorithmic bytes of one execute: c once, D once, each grid written and read
     // once per FFT pass, the nodes, and f
-    double mb = (double)p.N * cs + (double)p.D_elems * rs + (double)M * (sizeof(double2) + 5 + cs);
-    for (int b = 1; b <= p.levels; ++b) {
+    double mb = (double)p.N * cs + (double)p.D_elems * rs + (double)M * (sizeof(double2) + 8 + cs);
+    for (int b = 0; b < nb; ++b) {
         const BandDev& d = p.bands[b].dev;
         if (d.route != 1) continue;
         const double g = (double)d.nrhs * d.n * cs;
@@ -327,6 +380,43 @@ static fl_status plan_flt(Plan& p, const double* nodes, int q, cudaStream_t st) 
     if (!p.direct_work.empty()) mb += (double)p.direct_work.size() * kDirChunk * cs;   // c tiles
     p.model_bytes = mb;
     return FL_OK;
+}
+
+
+// fl_execute through a CUDA graph of its launches, captured on the first call
+// (and again when the buffers or the stream change), then replayed.
+static cudaError_t forward_graphed(Plan& p, const void* c, void* f, cudaStream_t st) {
+    if (!p.use_graph || p.timing || st == nullptr) return run_forward(p, c, f, false, st);
+    if (!p.gexec || p.g_c != c || p.g_f != f || p.g_st != st) {
+        if (p.gexec) {
+            cudaGraphExecDestroy(p.gexec);
+            p.gexec = nullptr;
+        }
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        const int64_t launches = p.launches;
+        cudaError_t er = run_forward(p, c, f, false, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (er != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return er;
+        }
+        if (e != cudaSuccess) return e;
+        e = cudaGraphInstantiate(&p.gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            p.gexec = nullptr;
+            return e;
+        }
+        p.graph_launches = p.launches - launches;
+        p.launches = launches;
+        p.g_c = c;
+        p.g_f = f;
+        p.g_st = st;
+    }
+    p.launches += p.graph_launches;
+    return cudaGraphLaunch(p.gexec, st);
 }
 
 }  // namespace fl
@@ -370,8 +460,9 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
         h->p.route_mode = opt->route;
         h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
         h->p.rhs_per_launch = opt->rhs_per_launch;
+        h->p.use_graph = opt->use_graph != 0;
     }
-    fl_status s = plan_flt(h->p, nodes_dev, q, (cudaStream_t)stream);
+    fl_status s = plan_multi(h->p, 1, &N, &M, nodes_dev, q, (cudaStream_t)stream);
     if (s != FL_OK) {
         delete h;
         return s;
@@ -383,7 +474,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
 fl_status fl_execute(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute: NULL buffer");
-    cudaError_t e = run_forward(h->p, c_dev, f_dev, false, (cudaStream_t)stream);
+    if (h->p.batched) return fail(FL_EINVAL, "fl_execute: batched plan (use fl_execute_batched)");
+    cudaError_t e = forward_graphed(h->p, c_dev, f_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute");
     return FL_OK;
 }
@@ -391,6 +483,7 @@ fl_status fl_execute(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) 
 fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_deriv: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_deriv: NULL buffer");
+    if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: batched plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, f_dev, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute_deriv");
     return FL_OK;
@@ -399,6 +492,7 @@ fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* st
 fl_status fl_grad_w(fl_plan_t h, const void* c_dev, const void* r_dev, void* gw_dev, void* stream) {
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_grad_w: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !r_dev || !gw_dev)) return fail(FL_EINVAL, "fl_grad_w: NULL buffer");
+    if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_grad_w: batched plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, gw_dev, true, (cudaStream_t)stream, r_dev);
     if (e != cudaSuccess) return cuda_fail(e, "fl_grad_w");
     return FL_OK;
@@ -413,7 +507,7 @@ fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* s
     if (!p.d_stage_c) FL_CUDA(cudaMalloc(&p.d_stage_c, p.N * cs), "cudaMalloc staging");
     if (!p.d_stage_f && p.M > 0) FL_CUDA(cudaMalloc(&p.d_stage_f, p.M * cs), "cudaMalloc staging");
     FL_CUDA(cudaMemcpyAsync(p.d_stage_c, c_host, p.N * cs, cudaMemcpyHostToDevice, st), "copy c");
-    FL_CUDA(run_forward(p, p.d_stage_c, p.d_stage_f, false, st), "fl_execute_host");
+    FL_CUDA(forward_graphed(p, p.d_stage_c, p.d_stage_f, st), "fl_execute_host");
     if (p.M > 0)
         FL_CUDA(cudaMemcpyAsync(f_host, p.d_stage_f, p.M * cs, cudaMemcpyDeviceToHost, st), "copy f");
     FL_CUDA(cudaStreamSynchronize(st), "fl_execute_host: synchronise");
@@ -423,8 +517,64 @@ fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* s
 fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stream) {
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_adjoint: not a Fourier-Laplace plan");
     if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
+    if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
+    return FL_OK;
+}
+
+fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const int64_t* M_host,
+                          const double* nodes_dev, int q, double eps, fl_precision prec,
+                          const fl_options* opt, void* stream) {
+    g_err.clear();
+    if (!out) return fail(FL_EINVAL, "fl_plan_batched: out is NULL");
+    *out = nullptr;
+    if (B < 1 || !N_host || !M_host) return fail(FL_EINVAL, "fl_plan_batched: need B >= 1 and sizes");
+    int64_t Mtot = 0, Ntot = 0;
+    for (int i = 0; i < B; ++i) {
+        if (N_host[i] < 1 || M_host[i] < 0)
+            return fail(FL_EINVAL, "fl_plan_batched: need N_i >= 1 and M_i >= 0");
+        if (N_host[i] > ((int64_t)1 << 23)) return fail(FL_EUNSUPPORTED, "fl_plan_batched: N_i above 2^23");
+        Ntot += N_host[i];
+        Mtot += M_host[i];
+    }
+    if (Mtot > ((int64_t)1 << 31) - 1 || Ntot > ((int64_t)1 << 40))
+        return fail(FL_EUNSUPPORTED, "fl_plan_batched: sum of M_i above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(FL_EINVAL, "fl_plan_batched: eps must lie in (0, 1)");
+    if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan_batched: q must lie in [0, 40]");
+    if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
+    if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
+    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
+                opt->rhs_per_launch < 0))
+        return fail(FL_EINVAL, "fl_plan_batched: invalid options");
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return fail(FL_ENOMEM, "fl_plan_batched: host allocation");
+    h->p.kind = 0;
+    h->p.batched = true;
+    h->p.prec = prec;
+    h->p.eps = eps;
+    h->p.use_graph = true;
+    if (opt) {
+        h->p.route_mode = opt->route;
+        h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
+        h->p.rhs_per_launch = opt->rhs_per_launch;
+        h->p.use_graph = opt->use_graph >= 0;
+    }
+    fl_status s = plan_multi(h->p, B, N_host, M_host, nodes_dev, q, (cudaStream_t)stream);
+    if (s != FL_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+fl_status fl_execute_batched(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) {
+    if (!h || h->p.kind != 0 || !h->p.batched)
+        return fail(FL_EINVAL, "fl_execute_batched: not a batched Fourier-Laplace plan");
+    if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_batched: NULL buffer");
+    cudaError_t e = forward_graphed(h->p, c_dev, f_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_execute_batched");
     return FL_OK;
 }
 
@@ -446,15 +596,22 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->y1 = p.y1;
     info->xi1 = p.xi1;
     info->z0_nodes = p.z0_nodes;
-    for (int b = 1; b < (int)p.bands.size() && b < FL_MAX_LEVELS; ++b) {
+    info->batch = p.batched ? (int)p.inst.size() : 1;
+    if (p.kind == 0) {   // bands of all transforms: routes counted over the batch
+        for (const BandHost& bh : p.bands) {
+            if (bh.local == 0) continue;
+            if (bh.dev.route == 1) ++info->n_bands_fft;
+            if (bh.dev.route == 2) ++info->n_bands_direct;
+        }
+    }
+    const int nb_first = p.kind == 0 && !p.inst.empty() ? p.inst[0].levels + 1 : (int)p.bands.size();
+    for (int b = 1; b < nb_first && b < (int)p.bands.size() && b < FL_MAX_LEVELS; ++b) {
         const BandHost& bh = p.bands[b];
         info->band_ell[b] = bh.ell;
         info->band_route[b] = bh.dev.route;
         info->band_nodes[b] = bh.nodes;
         info->band_K[b] = bh.dev.K;
         info->band_n[b] = bh.dev.n;
-        if (bh.dev.route == 1) ++info->n_bands_fft;
-        if (bh.dev.route == 2) ++info->n_bands_direct;
     }
     info->model_bytes = p.model_bytes;
     info->scratch_bytes = p.scratch_bytes;

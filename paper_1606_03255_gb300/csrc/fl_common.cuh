@@ -54,6 +54,7 @@ struct BandDev {
     int64_t dslot;     // direct route: offset of the band's partial sums (nodes x nchunk)
     int nchunk;        // direct route: coefficient chunks
     int pad2;
+    int64_t c_off;     // offset of the band's transform in the coefficient buffer (batches)
 };
 
 // ---------------------------------------------------------------------------

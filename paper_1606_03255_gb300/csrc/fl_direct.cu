@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
         const int64_t k = k0 + i;
         C v = C{(T)0, (T)0};
         if (k < kend) {
-            v = c[k];
+            v = c[B.c_off + k];
             if (DERIV) {
                 const T wgt = (T)(kTwoPiDir * (double)k);
                 v = C{-v.y * wgt, v.x * wgt};

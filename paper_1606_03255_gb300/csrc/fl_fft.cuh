@@ -294,7 +294,8 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
         for (int r = 0; r < 16; ++r)
             v[r] = (r >= 4 && r < 12)
                        ? C{(T)0, (T)0}
-                       : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, c, Ds);
+                       : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K,
+                                                c + B.c_off, Ds);
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
 #pragma unroll

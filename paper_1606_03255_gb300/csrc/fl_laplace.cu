@@ -321,10 +321,10 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
     for (int m = 1; m < p.levels && m < (int)p.bands.size(); ++m) P.ell[m] = p.bands[m].ell;
     const uint8_t* tband = p.d_tband;
     if (p.prec == FL_FP64)
-        return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_bandid, P, p.d_cheb,
+        return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb,
                                (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
                                st, &p);
-    return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_bandid, P, p.d_cheb, (const float*)c,
+    return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb, (const float*)c,
                           (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p);
 }
 
@@ -387,8 +387,8 @@ static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, in
     if (M) {
         LAP_CUDA(cudaMalloc((void**)&p.d_s, M * sizeof(double)), "cudaMalloc s");
         LAP_CUDA(cudaMemcpyAsync(p.d_s, s, M * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy s");
-        LAP_CUDA(cudaMalloc((void**)&p.d_bandid, M), "cudaMalloc s bands");
-        k_lap_band<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(p.M, p.d_s, y1, P.levels, p.d_bandid);
+        LAP_CUDA(cudaMalloc((void**)&p.d_sband, M), "cudaMalloc s bands");
+        k_lap_band<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(p.M, p.d_s, y1, P.levels, p.d_sband);
     }
     LAP_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
     k_lap_cheb<<<1, 64, 0, st>>>(P.q, p.d_cheb);

@@ -56,14 +56,14 @@ __global__ void k_classify(int64_t M, const double* __restrict__ w,
         if (cnt[i]) atomicAdd(&counts[i], (unsigned long long)cnt[i]);
 }
 
-cudaError_t launch_classify(Plan& p, const double* nodes, uint32_t* keys, int32_t* vals,
-                            int64_t* counts, int* flag, cudaStream_t st) {
-    if (p.M == 0) return cudaSuccess;
+cudaError_t launch_classify(const Plan& p, const Instance& in, const double* nodes, uint32_t* keys,
+                            int32_t* vals, int64_t* counts, int* flag, cudaStream_t st) {
+    if (in.M == 0) return cudaSuccess;
     const int bs = 256;
-    const int64_t grid = (p.M + bs - 1) / bs;
-    k_classify<<<(unsigned)grid, bs, 0, st>>>(p.M, nodes, p.d_bands, p.levels, p.y1,
-                                              p.N == 1 ? 1 : 0, keys, vals,
-                                              (unsigned long long*)counts, flag);
+    const int64_t grid = (in.M + bs - 1) / bs;
+    k_classify<<<(unsigned)grid, bs, 0, st>>>(in.M, nodes + 2 * in.moff, p.d_bands + in.band_base,
+                                              in.levels, p.y1, in.N == 1 ? 1 : 0, keys, vals,
+                                              (unsigned long long*)(counts + in.band_base), flag);
     return cudaGetLastError();
 }
 
@@ -177,23 +177,27 @@ cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
     return e;
 }
 
+// Sorted slice of one transform: node (Re w, Im w), result index moff + j and
+// global band id band_base + local band.
 __global__ void k_permute(int64_t M, const double* __restrict__ w, const uint32_t* __restrict__ keys,
-                          const int32_t* __restrict__ vals, double2* __restrict__ ws,
-                          int32_t* __restrict__ perm, uint8_t* __restrict__ bandid) {
+                          const int32_t* __restrict__ vals, int32_t moff, int32_t band_base,
+                          double2* __restrict__ ws, int32_t* __restrict__ perm,
+                          int32_t* __restrict__ bandid) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int32_t j = vals[i];
     ws[i] = make_double2(w[2 * (int64_t)j], w[2 * (int64_t)j + 1]);
-    perm[i] = j;
-    bandid[i] = (uint8_t)(keys[i] >> 25);
+    perm[i] = moff + j;
+    bandid[i] = band_base + (int32_t)(keys[i] >> 25);
 }
 
-cudaError_t launch_permute(Plan& p, const double* nodes, const uint32_t* keys,
+cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, const uint32_t* keys,
                            const int32_t* vals, cudaStream_t st) {
-    if (p.M == 0) return cudaSuccess;
+    if (in.M == 0) return cudaSuccess;
     const int bs = 256;
-    k_permute<<<(unsigned)((p.M + bs - 1) / bs), bs, 0, st>>>(p.M, nodes, keys, vals, p.d_ws,
-                                                              p.d_perm, p.d_bandid);
+    k_permute<<<(unsigned)((in.M + bs - 1) / bs), bs, 0, st>>>(
+        in.M, nodes + 2 * in.moff, keys, vals, (int32_t)in.moff, in.band_base, p.d_ws + in.moff,
+        p.d_perm + in.moff, p.d_bandid + in.moff);
     return cudaGetLastError();
 }
 

@@ -65,9 +65,22 @@ struct DirectRange {
 // Per-band plan data on the host.
 struct BandHost {
     int ell = 0, Lm = 0;    // l_m, L_m (Definition 3.2); 0 for the Y_M band
+    int inst = 0;           // transform of the batch the band belongs to
+    int local = 0;          // band index within its transform (0 = Z^0, 1..levels)
     int64_t nodes = 0;      // nodes of the band
     int64_t node_off = 0;   // first node of the band in sorted order
     BandDev dev{};
+};
+
+// One transform of a plan (a single plan has one; a batched plan has many).
+// Its bands occupy bands[band_base .. band_base + levels] of the plan.
+struct Instance {
+    int64_t N = 0, M = 0;
+    int64_t noff = 0, moff = 0;   // offsets of its coefficients and nodes/results
+    int band_base = 0;
+    int levels = 1;
+    double xi1 = 0;
+    int64_t z0_nodes = 0;
 };
 
 struct Timer {
@@ -82,7 +95,9 @@ struct Plan {
     int64_t N = 0, M = 0;
     int q = 0, levels = 1, mw = 0;
     double eps = 0, eps_K = 0, eps_A = 0, y1 = 0, xi1 = 0, kb_b = 0;
-    std::vector<BandHost> bands;          // index 0 = Z^0, 1..levels
+    std::vector<BandHost> bands;          // per transform: Z^0, 1..levels (see Instance)
+    std::vector<Instance> inst;
+    bool batched = false;
     int64_t z0_nodes = 0;
     int64_t grid_elems = 0, D_elems = 0, Y_elems = 0;
     std::vector<SmallWork> small_work;
@@ -99,7 +114,7 @@ struct Plan {
     // device memory
     double2* d_ws = nullptr;       // nodes in sorted order (Re w, Im w)
     int32_t* d_perm = nullptr;     // sorted position -> original index
-    uint8_t* d_bandid = nullptr;   // band of each sorted node
+    int32_t* d_bandid = nullptr;   // band (global index) of each sorted node
     BandDev* d_bands = nullptr;    // levels + 1 descriptors
     SmallWork* d_small = nullptr;
     PassItem* d_pass = nullptr;
@@ -120,8 +135,17 @@ struct Plan {
     double* d_t = nullptr;
     double* d_s = nullptr;
     uint8_t* d_tband = nullptr;    // band of every t_k
+    uint8_t* d_sband = nullptr;    // band of every s_j
     void* d_lap = nullptr;         // moments and partial sums
     int lap_blocks = 0;
+
+    // CUDA-graph replay of fl_execute / fl_execute_batched
+    bool use_graph = false;
+    cudaGraphExec_t gexec = nullptr;
+    const void* g_c = nullptr;
+    void* g_f = nullptr;
+    cudaStream_t g_st = nullptr;
+    int64_t graph_launches = 0;
 
     // timing
     bool timing = false;
@@ -132,17 +156,20 @@ struct Plan {
     ~Plan();
 };
 
-// Launchers (fl_nodes.cu)
-cudaError_t launch_classify(Plan& p, const double* nodes, uint32_t* keys, int32_t* vals,
-                            int64_t* counts, int* flag, cudaStream_t st);
+// Launchers (fl_nodes.cu).  For transform `in` of the plan: classify its M
+// nodes (keys: local band << 25 | grid cell), sort, and write its slice of the
+// sorted node arrays with global band ids and result indices.
+cudaError_t launch_classify(const Plan& p, const Instance& in, const double* nodes, uint32_t* keys,
+                            int32_t* vals, int64_t* counts, int* flag, cudaStream_t st);
 cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
                              int32_t* vals_tmp, uint32_t* hist, int64_t n, int key_bits,
                              cudaStream_t st);
-cudaError_t launch_permute(Plan& p, const double* nodes, const uint32_t* keys,
+cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, const uint32_t* keys,
                            const int32_t* vals, cudaStream_t st);
 
 // Launchers (fl_transform.cu)
-cudaError_t build_tables(Plan& p, cudaStream_t st);
+cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st);
+cudaError_t build_cheb(Plan& p, cudaStream_t st);
 // rmul != nullptr: f[j] = rmul[j] * conj(result_j) (the node-gradient epilogue)
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul = nullptr);

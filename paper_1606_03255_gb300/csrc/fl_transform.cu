@@ -115,13 +115,12 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
 }
 
 template <typename T>
-static cudaError_t build_tables_t(Plan& p, cudaStream_t st) {
+static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) {
     double* Kt = nullptr;
     cudaError_t e = cudaSuccess;
-    k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb);
     int64_t kt_max = 0;
-    for (int b = 1; b <= p.levels; ++b) {
-        const BandHost& bh = p.bands[b];
+    for (int lb = 1; lb <= in.levels; ++lb) {
+        const BandHost& bh = p.bands[in.band_base + lb];
         if (bh.dev.route != 1 || bh.dev.nrhs == 1) continue;
         kt_max = std::max<int64_t>(kt_max, (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q);
     }
@@ -129,16 +128,16 @@ static cudaError_t build_tables_t(Plan& p, cudaStream_t st) {
         e = cudaMallocAsync((void**)&Kt, kt_max * sizeof(double), st);
         if (e != cudaSuccess) return e;
     }
-    for (int b = 1; b <= p.levels; ++b) {
-        const BandHost& bh = p.bands[b];
+    for (int lb = 1; lb <= in.levels; ++lb) {
+        const BandHost& bh = p.bands[in.band_base + lb];
         if (bh.dev.route != 1) continue;
         if (bh.dev.nrhs > 1) {
             const int64_t nk = (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q;
-            k_coupling<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(p.y1, p.xi1, b, bh.ell, bh.Lm,
+            k_coupling<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(p.y1, in.xi1, lb, bh.ell, bh.Lm,
                                                                      p.q, p.d_cheb, Kt);
         }
         k_weights<T><<<(unsigned)((bh.dev.K + 255) / 256), 256, 0, st>>>(
-            bh.dev, bh.ell, bh.Lm, p.q, p.xi1, p.levels, p.d_cheb, Kt, p.mw, p.kb_b, (T*)p.d_D);
+            bh.dev, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, (T*)p.d_D);
     }
     e = cudaGetLastError();
     if (Kt) {
@@ -148,8 +147,13 @@ static cudaError_t build_tables_t(Plan& p, cudaStream_t st) {
     return e;
 }
 
-cudaError_t build_tables(Plan& p, cudaStream_t st) {
-    return p.prec == FL_FP64 ? build_tables_t<double>(p, st) : build_tables_t<float>(p, st);
+cudaError_t build_cheb(Plan& p, cudaStream_t st) {
+    k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb);
+    return cudaGetLastError();
+}
+
+cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st) {
+    return p.prec == FL_FP64 ? build_tables_t<double>(p, in, st) : build_tables_t<float>(p, in, st);
 }
 
 // One CTA per work item: nfft FFTs of one band (one per right-hand side).
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(512) k_small_fft(const SmallWork* __restrict__
     C* g = grid + B.grid_off + (int64_t)s * L;
     if (active) {
         for (int e = t; e < L; e += nthr)
-            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c, D) : g[e];
+            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c + B.c_off, D) : g[e];
     }
     __syncthreads();
     fft_smem<SIGN, T>(buf, wk.log2n, t, active);
@@ -218,7 +222,7 @@ __device__ __forceinline__ void bary_weights(double y, const BandDev& B, int q,
 template <typename T, int MW>
 __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __restrict__ ws,
                                                 const int32_t* __restrict__ perm,
-                                                const uint8_t* __restrict__ bandid,
+                                                const int32_t* __restrict__ bandid,
                                                 const BandDev* __restrict__ bands,
                                                 const C_t<T>* __restrict__ grid,
                                                 const double* __restrict__ cheb, int q, T kb_b,
@@ -230,12 +234,12 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     if (i >= M) return;
     const int b = bandid[i];
     const int32_t j = perm[i];
-    if (b == 0) {
-        f[j] = deriv ? C{(T)0, (T)0} : c[0];
+    const BandDev B = bands[b];
+    if (B.K == 0) {   // Z^0 (band 0 of its transform): c_0
+        f[j] = deriv ? C{(T)0, (T)0} : c[B.c_off];
         return;
     }
     // with rmul: f[j] = rmul[j] * conj(value) (node gradient, see fl_grad_w)
-    const BandDev B = bands[b];
     if (B.route != 1) return;   // direct-route band: written by k_direct_reduce
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 template <typename T, int MW>
 __global__ void __launch_bounds__(256) k_spread(int64_t M, int64_t z0, const double2* __restrict__ ws,
                                                 const int32_t* __restrict__ perm,
-                                                const uint8_t* __restrict__ bandid,
+                                                const int32_t* __restrict__ bandid,
                                                 const BandDev* __restrict__ bands,
                                                 const C_t<T>* __restrict__ r,
                                                 const double* __restrict__ cheb, int q, T kb_b,

@@ -30,7 +30,7 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
                 FL_EUNSUPPORTED: "FL_EUNSUPPORTED"}
 
 # Every symbol include/fl.h declares.
-EXPORTED = ["fl_plan", "fl_plan_ex", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
+EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
             "fl_adjoint",
             "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
@@ -45,7 +45,7 @@ class fl_info(ctypes.Structure):
         ("q", ctypes.c_int), ("levels", ctypes.c_int), ("m_w", ctypes.c_int),
         ("sigma", ctypes.c_int),
         ("y1", ctypes.c_double), ("xi1", ctypes.c_double),
-        ("z0_nodes", ctypes.c_int64),
+        ("z0_nodes", ctypes.c_int64), ("batch", ctypes.c_int),
         ("n_bands_fft", ctypes.c_int), ("n_bands_direct", ctypes.c_int),
         ("band_ell", ctypes.c_int * FL_MAX_LEVELS),
         ("band_route", ctypes.c_int * FL_MAX_LEVELS),
@@ -58,7 +58,7 @@ class fl_info(ctypes.Structure):
 
 class fl_options(ctypes.Structure):
     _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
-                ("rhs_per_launch", ctypes.c_int)]
+                ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
@@ -102,6 +102,9 @@ def load(path: str | None = None):
     sig = {
         "fl_plan": [pp, i64, i64, vp, ci, cd, ci, vp],
         "fl_plan_ex": [pp, i64, i64, vp, ci, cd, ci, ctypes.POINTER(fl_options), vp],
+        "fl_plan_batched": [pp, ci, ctypes.POINTER(i64), ctypes.POINTER(i64), vp, ci, cd, ci,
+                            ctypes.POINTER(fl_options), vp],
+        "fl_execute_batched": [vp, vp, vp, vp],
         "fl_execute": [vp, vp, vp, vp],
         "fl_execute_deriv": [vp, vp, vp, vp],
         "fl_grad_w": [vp, vp, vp, vp, vp],
@@ -144,6 +147,21 @@ def fl_plan_ex(N, M, nodes_ptr, q, eps, prec, options, stream):
     st = load().fl_plan_ex(ctypes.byref(h), int(N), int(M), nodes_ptr, int(q), float(eps),
                            int(prec), opt, stream)
     return st, h
+
+
+def fl_plan_batched(Ns, Ms, nodes_ptr, q, eps, prec, options, stream):
+    h = ctypes.c_void_p()
+    B = len(Ns)
+    na = (ctypes.c_int64 * B)(*[int(x) for x in Ns])
+    ma = (ctypes.c_int64 * B)(*[int(x) for x in Ms])
+    opt = ctypes.byref(options) if options is not None else None
+    st = load().fl_plan_batched(ctypes.byref(h), B, na, ma, nodes_ptr, int(q), float(eps),
+                                int(prec), opt, stream)
+    return st, h
+
+
+def fl_execute_batched(plan, c_ptr, f_ptr, stream):
+    return load().fl_execute_batched(plan, c_ptr, f_ptr, stream)
 
 
 def fl_execute(plan, c_ptr, f_ptr, stream):
@@ -254,7 +272,7 @@ def info_dict(info: fl_info) -> dict:
         "kind": info.kind, "precision": info.precision, "N": info.N, "M": info.M,
         "eps": info.eps, "eps_laplace": info.eps_laplace, "eps_fourier": info.eps_fourier,
         "q": info.q, "levels": info.levels, "m_w": info.m_w, "sigma": info.sigma,
-        "y1": info.y1, "xi1": info.xi1, "z0_nodes": info.z0_nodes,
+        "y1": info.y1, "xi1": info.xi1, "z0_nodes": info.z0_nodes, "batch": info.batch,
         "n_bands_fft": info.n_bands_fft, "n_bands_direct": info.n_bands_direct,
         "band_ell": list(info.band_ell[:nb]), "band_route": list(info.band_route[:nb]),
         "band_nodes": list(info.band_nodes[:nb]), "band_K": list(info.band_K[:nb]),
@@ -281,7 +299,7 @@ class Plan:
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
-                 rhs_per_launch: int = 0):
+                 rhs_per_launch: int = 0, use_graph: bool = False):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -291,7 +309,7 @@ class Plan:
         self.prec = FL_FP64 if precision == "fp64" else FL_FP32
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
-        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch))
+        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)))
         st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
                            opt, _stream_handle(stream))
         check(st, "fl_plan")
@@ -339,6 +357,71 @@ class Plan:
         check(fl_execute_host(self._handle, _ptr(c_host), _ptr(f_host), _stream_handle(stream)),
               "fl_execute_host")
         return f_host
+
+    def info(self) -> dict:
+        st, inf = fl_get_info(self._handle)
+        check(st, "fl_get_info")
+        return info_dict(inf)
+
+    def set_timing(self, enable: bool):
+        check(fl_set_timing(self._handle, enable), "fl_set_timing")
+
+    def timing(self) -> dict:
+        st, t = fl_get_timing(self._handle)
+        check(st, "fl_get_timing")
+        return timing_dict(t)
+
+    def close(self):
+        if self._handle is not None and self._handle.value:
+            fl_destroy(self._handle)
+        self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchedPlan:
+    """B independent transforms f_i = C_i c_i in one plan (fl_plan_batched).
+
+    Ns, Ms: sizes per transform; nodes: CUDA float64 (sum Ms, 2), the nodes of
+    transform 0, 1, ... in order.  execute(c) takes the coefficients of all
+    transforms concatenated (sum Ns) and returns the results concatenated.
+    """
+
+    def __init__(self, Ns, Ms, nodes, eps: float, precision: str = "fp32", q: int = 0,
+                 stream=None, route: str = "auto", direct_bias: float = 1.0,
+                 rhs_per_launch: int = 0, use_graph: bool = True):
+        torch = _torch()
+        nodes = nodes.to(torch.float64).contiguous()
+        self.Ns = [int(x) for x in Ns]
+        self.Ms = [int(x) for x in Ms]
+        self.N, self.M = sum(self.Ns), sum(self.Ms)
+        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
+        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self._handle = None
+        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
+                         1 if use_graph else -1)
+        st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
+                                self.prec, opt, _stream_handle(stream))
+        check(st, "fl_plan_batched")
+        self._handle = h
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def execute(self, c, out=None, stream=None):
+        torch = _torch()
+        _require(c, self.cdtype, self.N, "c")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=c.device)
+        _require(out, self.cdtype, self.M, "out")
+        check(fl_execute_batched(self._handle, _ptr(c), _ptr(out) if self.M else None,
+                                 _stream_handle(stream)), "fl_execute_batched")
+        return out
 
     def info(self) -> dict:
         st, inf = fl_get_info(self._handle)
