@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-form lines")
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--sample", type=int, default=2048, help="oracle sample size (nodes)")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the secondary workloads (Laplace, batched, gradients, N=1024)")
     return ap.parse_args()
 
 
@@ -173,6 +175,136 @@ def oracle_sample(c, w, sample: int, seed: int = 2):
 
 def error_E(ref, approx, c) -> float:
     return float(np.max(np.abs(ref - approx)) / np.sum(np.abs(c)))
+
+
+def _time_cuda(fn, reps, flush=None):
+    """Mean milliseconds of fn() over reps calls, CUDA events, optional L2 flush between."""
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.mean(ts))
+
+
+def secondary_workloads(dev, flush, rank):
+    """The other workloads of the method, each timed on its own (not the headline)."""
+    import torch
+    from paper_1606_03255_gb300 import fl
+    from paper_1606_03255_gb300.autograd import FourierLaplace
+    out = {}
+    # N = M = 1024, disk-uniform, FP64, eps = 1e-10 (latency-bound; CUDA-graph replay)
+    N = M = 1024
+    c = torch.from_numpy(W.coefficients(N, seed=rank)).to(dev)
+    w = torch.from_numpy(W.nodes_disk_uniform(M, seed=100 + rank)).to(dev)
+    p = fl.Plan(N, w, 1e-10, precision="fp64", use_graph=True)
+    f = torch.empty(M, dtype=torch.complex128, device=dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(5):
+            p.execute(c, out=f)
+        s.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(200):
+            p.execute(c, out=f)
+        b.record(s)
+    s.synchronize()
+    us = a.elapsed_time(b) * 1e3 / 200
+    out["disk_1024_fp64_eps1e-10"] = {"us_per_call": us, "value": N * M / (us * 1e-6),
+                                       "unit": "evals/s", "graph": True}
+    p.close()
+    # Laplace, N = M = 2^16, FP64 and FP32 forms, eps = 1e-6
+    N = M = 1 << 16
+    cl, t, sv = W.laplace_inputs(N, M, seed=rank)
+    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+        lp = fl.LaplacePlan(torch.from_numpy(t).to(dev), torch.from_numpy(sv).to(dev), 1e-6,
+                            precision=prec)
+        cc = torch.from_numpy(cl).to(dt).to(dev)
+        ff = torch.empty(M, dtype=dt, device=dev)
+        for _ in range(3):
+            lp.execute(cc, out=ff)
+        ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
+        out[f"laplace_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s"}
+        lp.close()
+    # batched: 512 transforms, N_i = floor(2^U), U ~ U[8,16], M_i = N_i, FP32, eps = 1e-6:
+    # one plan + CUDA graph vs 512 separate plans with plain launches
+    Ns = W.batched_degrees(512, seed=rank)
+    cs = np.concatenate([W.coefficients(int(n), seed=7 + i).astype(np.complex64)
+                         for i, n in enumerate(Ns)])
+    ws = [W.nodes_disk_uniform(int(n), seed=9000 + i) for i, n in enumerate(Ns)]
+    evals = float(np.sum(Ns.astype(np.float64) ** 2))
+    t0 = time.perf_counter()
+    bp = fl.BatchedPlan(Ns, Ns, torch.from_numpy(np.concatenate(ws)).to(dev), 1e-6)
+    torch.cuda.synchronize()
+    plan_s = time.perf_counter() - t0
+    cb = torch.from_numpy(cs).to(dev)
+    fb = torch.empty(int(Ns.sum()), dtype=torch.complex64, device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            bp.execute(cb, out=fb)
+        s.synchronize()
+        ms_b = []
+        for _ in range(10):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            bp.execute(cb, out=fb)
+            b.record(s)
+            s.synchronize()
+            ms_b.append(a.elapsed_time(b))
+    ms_b = float(np.mean(ms_b))
+    info_b = bp.info()
+    bp.close()
+    plans = []
+    off = 0
+    for i, n in enumerate(Ns):
+        plans.append((fl.Plan(int(n), torch.from_numpy(ws[i]).to(dev), 1e-6), off, int(n)))
+        off += int(n)
+
+    def run_separate():
+        for pl, o, n in plans:
+            pl.execute(cb[o:o + n], out=fb[o:o + n])
+    for _ in range(2):
+        run_separate()
+    ms_s = _time_cuda(run_separate, 5, flush)
+    for pl, _, _ in plans:
+        pl.close()
+    out["batched_512"] = {"ms": ms_b, "value": evals / (ms_b * 1e-3), "unit": "evals/s",
+                          "separate_plans_ms": ms_s,
+                          "separate_plans_value": evals / (ms_s * 1e-3),
+                          "speedup_vs_separate": ms_s / ms_b, "plan_s": plan_s,
+                          "sum_N_i": int(Ns.sum()), "sum_NiMi": evals,
+                          "bands_fft": info_b["n_bands_fft"], "bands_direct": info_b["n_bands_direct"]}
+    # gradients: N = M = 2^18, disk-uniform, FP32 (eps 1e-7), loss sum |f - g|^2
+    N = M = 1 << 18
+    c = torch.from_numpy(W.coefficients(N, seed=rank)).to(torch.complex64).to(dev).requires_grad_(True)
+    w = torch.from_numpy(W.nodes_disk_uniform(M, seed=200 + rank)).to(dev).requires_grad_(True)
+    g = torch.from_numpy(W.targets(M, seed=300 + rank)).to(torch.complex64).to(dev)
+    op = FourierLaplace(N, eps=1e-7, precision="fp32")
+    op.plan_for(w)
+
+    def fwd_bwd():
+        c.grad = None
+        w.grad = None
+        loss = torch.sum(torch.abs(op(c, w) - g) ** 2)
+        loss.backward()
+    for _ in range(3):
+        fwd_bwd()
+    ms = _time_cuda(fwd_bwd, 10, flush)
+    fwd = _time_cuda(lambda: op(c.detach(), w.detach()), 10, flush)
+    out["gradients_2^18_fp32"] = {"ms_fwd_bwd": ms, "ms_fwd": fwd, "unit": "ms",
+                                  "note": "forward + adjoint (grad c) + k-weighted transform (grad w)"}
+    return out
 
 
 def run_reference(args):
@@ -338,6 +470,10 @@ def run_ours(args):
         fp64["fp32_speedup_vs_fp64_same_eps"] = fp64["eps1e-6"]["ms_per_step"] / ms
         fp64["fp32_speedup_vs_fp64_eps1e-12"] = fp64["eps1e-12"]["ms_per_step"] / ms
 
+    configs = None
+    if not args.no_configs:
+        configs = secondary_workloads(dev, flush, rank)
+
     # cpu_baseline leg: the oracle on a seeded sample; the same sample gives E
     cpu = None
     errors = {}
@@ -378,6 +514,7 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": launches_total,
         "clocks": clocks,
+        "other_workloads": configs,
     }
     print(json.dumps(line), flush=True)
     if dist:
