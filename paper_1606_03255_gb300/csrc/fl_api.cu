@@ -38,7 +38,8 @@ Plan::~Plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
-                    d_dranges, d_dpart, d_cdir};
+                    d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
+                    d_sp_L, d_sp_rv, d_cell_bands};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -236,6 +237,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
         FL_CUDA(cudaMalloc((void**)&p.d_ws, M * sizeof(double2)), "cudaMalloc nodes");
         FL_CUDA(cudaMalloc((void**)&p.d_perm, M * sizeof(int32_t)), "cudaMalloc perm");
         FL_CUDA(cudaMalloc((void**)&p.d_bandid, M * sizeof(int32_t)), "cudaMalloc band ids");
+        FL_CUDA(cudaMalloc((void**)&p.d_cell, M * sizeof(int32_t)), "cudaMalloc cells");
         uint32_t *keys = nullptr, *keys2 = nullptr, *hist = nullptr;
         int32_t *vals = nullptr, *vals2 = nullptr;
         int64_t* dcount = nullptr;
@@ -281,6 +283,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.large_bands.clear();
     p.direct_work.clear();
     p.direct_ranges.clear();
+    p.dadj_work32.clear();
+    p.dadj_work64.clear();
     p.direct_nodes = p.direct_terms = p.dpart_elems = 0;
     p.z0_nodes = 0;
     for (int i = 0; i < B; ++i) {
@@ -299,6 +303,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             off += counts[b];
             BandDev& d = bh.dev;
             d.node_off = bh.node_off;
+            d.nodes = bh.nodes;
             d.route = bh.nodes > 0 ? route_of(p, bh) : 0;
             if (d.route == 2) {
                 d.nchunk = (int)((d.K + kDirChunk - 1) / kDirChunk);
@@ -311,6 +316,16 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                     for (int ch = 0; ch < d.nchunk; ++ch)
                         p.direct_work.push_back({b, ch, bh.node_off + n0,
                                                  (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
+                if (!p.batched) {
+                    for (int kl : {32, 16}) {
+                        std::vector<DirectAdjItem>& v = kl == 32 ? p.dadj_work32 : p.dadj_work64;
+                        const int64_t kc = (d.K + 32 * kl - 1) / (32 * kl);
+                        for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirAdjNodes)
+                            for (int64_t ch = 0; ch < kc; ++ch)
+                                v.push_back({b, (int)ch, bh.node_off + n0,
+                                             (int)std::min<int64_t>(kDirAdjNodes, bh.nodes - n0), 0});
+                    }
+                }
                 continue;
             }
             if (d.route != 1) continue;
@@ -356,7 +371,46 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                                 p.direct_ranges.size() * sizeof(DirectRange), cudaMemcpyHostToDevice, st),
                 "copy direct ranges");
         FL_CUDA(cudaMalloc(&p.d_dpart, p.dpart_elems * cs), "cudaMalloc direct partials");
+        std::vector<DirectAdjItem>& adj = p.prec == FL_FP64 ? p.dadj_work64 : p.dadj_work32;
+        DirectAdjItem*& d_adj = p.prec == FL_FP64 ? p.d_dadj64 : p.d_dadj32;
+        if (!adj.empty()) {
+            FL_CUDA(cudaMalloc((void**)&d_adj, adj.size() * sizeof(DirectAdjItem)), "cudaMalloc adjoint work");
+            FL_CUDA(cudaMemcpyAsync(d_adj, adj.data(), adj.size() * sizeof(DirectAdjItem),
+                                    cudaMemcpyHostToDevice, st),
+                    "copy adjoint work");
+        }
         FL_CUDA(cudaMalloc(&p.d_cdir, p.N * cs), "cudaMalloc direct adjoint");
+    }
+    // adjoint of the NFFT bands (single plans): per-node taps and weights, cell list
+    p.cell_bands.clear();
+    p.cells_total = p.cells_dense = 0;
+    p.n_sparse_cb = 0;
+    if (!p.batched && M > 0) {
+        // dense: on average >= 32 window contributions per cell (warp per cell)
+        auto dense = [&](const BandHost& bh) { return bh.nodes * 2 * p.mw >= 32 * bh.dev.n; };
+        for (int b = 0; b < nb; ++b) {
+            const BandDev& d = p.bands[b].dev;
+            if (d.route != 1 || dense(p.bands[b])) continue;
+            p.cell_bands.push_back({b, 0, p.cells_total});
+            p.cells_total += d.n;
+        }
+        p.n_sparse_cb = (int)p.cell_bands.size();
+        for (int b = 0; b < nb; ++b) {
+            const BandDev& d = p.bands[b].dev;
+            if (d.route != 1 || !dense(p.bands[b])) continue;
+            p.cell_bands.push_back({b, 0, p.cells_dense});
+            p.cells_dense += d.n;
+        }
+        if (!p.cell_bands.empty()) {
+            FL_CUDA(cudaMalloc((void**)&p.d_cell_bands, p.cell_bands.size() * sizeof(Plan::CellBand)),
+                    "cudaMalloc cell bands");
+            FL_CUDA(cudaMemcpyAsync(p.d_cell_bands, p.cell_bands.data(),
+                                    p.cell_bands.size() * sizeof(Plan::CellBand), cudaMemcpyHostToDevice, st),
+                    "copy cell bands");
+            FL_CUDA(cudaMalloc(&p.d_sp_phi, (size_t)M * 2 * p.mw * rs), "cudaMalloc adjoint taps");
+            FL_CUDA(cudaMalloc(&p.d_sp_L, (size_t)M * p.q * rs), "cudaMalloc adjoint weights");
+            FL_CUDA(cudaMalloc(&p.d_sp_rv, (size_t)M * cs), "cudaMalloc adjoint residuals");
+        }
     }
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");

@@ -55,6 +55,7 @@ struct BandDev {
     int nchunk;        // direct route: coefficient chunks
     int pad2;
     int64_t c_off;     // offset of the band's transform in the coefficient buffer (batches)
+    int64_t nodes;     // nodes of the band (sorted positions node_off .. node_off + nodes)
 };
 
 // ---------------------------------------------------------------------------

@@ -120,33 +120,72 @@ __global__ void k_direct_reduce(int nranges, const DirectRange* __restrict__ ran
     f[j] = rmul ? cmulc(rmul[j], acc) : acc;
 }
 
-// Adjoint of the direct bands: cdir[k] = sum over direct bands with k < K_b of
-// sum_j conj(z_j)^k r_j, one thread per k, exact phase per term.
+// Adjoint of the direct bands, cdir[k] += sum_{j in band} r_j conj(z_j)^k for
+// k < K_b: the transpose of the blocked Horner sum.  One warp per work item
+// (band, chunk of 32 KL frequencies, up to kDirAdjNodes nodes); lane l owns
+// the KL frequencies k0 = chunk 32 KL + l KL .. k0 + KL - 1.  For each node
+// (broadcast across the warp by shuffles) the lane forms conj(z_j)^k0 from an
+// exactly reduced phase, then steps through its frequencies multiplying by
+// conj(z_j).  Chunks of different node groups meet in cdir through atomics.
+template <typename T> struct AdjKL { static constexpr int KL = sizeof(T) == 4 ? 32 : 16; };
+
 template <typename T>
-__global__ void __launch_bounds__(256) k_direct_adj(int nranges, const DirectRange* __restrict__ ranges,
-                                                    int64_t N, const BandDev* __restrict__ bands,
-                                                    const double2* __restrict__ ws,
-                                                    const int32_t* __restrict__ perm,
-                                                    const C_t<T>* __restrict__ r,
-                                                    C_t<T>* __restrict__ cdir) {
+__global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restrict__ items,
+                                                   const BandDev* __restrict__ bands,
+                                                   const double2* __restrict__ ws,
+                                                   const int32_t* __restrict__ perm,
+                                                   const C_t<T>* __restrict__ r,
+                                                   C_t<T>* __restrict__ cdir) {
     using C = C_t<T>;
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= N) return;
-    C acc = C{(T)0, (T)0};
-    for (int q = 0; q < nranges; ++q) {
-        const DirectRange R = ranges[q];
-        const BandDev B = bands[R.band];
-        if (k >= B.K) continue;
-        for (int64_t i = B.node_off; i < B.node_off + R.count; ++i) {
+    constexpr int KL = AdjKL<T>::KL;
+    const DirectAdjItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int lane = threadIdx.x;
+    const int64_t k0 = (int64_t)it.kchunk * (32 * KL) + (int64_t)lane * KL;
+    const bool active = k0 < B.K;
+    C acc[KL];
+#pragma unroll
+    for (int t = 0; t < KL; ++t) acc[t] = C{(T)0, (T)0};
+    for (int nb = 0; nb < it.nnodes; nb += 32) {
+        // lane loads node nb + lane: x, y, r_j and conj(z_j) in T
+        double xl = 0.0, yl = 0.0;
+        C rl = C{(T)0, (T)0}, zl = C{(T)0, (T)0};
+        if (nb + lane < it.nnodes) {
+            const int64_t i = it.node0 + nb + lane;
             const double2 wv = ws[i];
-            const double ykb = kTwoPiDir * wv.y * (double)k;
-            if (ykb > (sizeof(T) == 4 ? 104.0 : 745.0)) continue;
-            const double x = wv.x - floor(wv.x);
-            const C zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)k, x))), dir_exp<T>((T)(-ykb)));
-            acc = cadd(acc, cmulc(r[perm[i]], zk));   // r_j conj(z_j^k)
+            xl = wv.x - floor(wv.x);
+            yl = kTwoPiDir * wv.y;
+            rl = r[perm[i]];
+            double xr = xl >= 0.5 ? xl - 1.0 : xl;
+            zl = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-yl)));
+        }
+        const int cnt = min(32, it.nnodes - nb);
+        for (int q = 0; q < cnt; ++q) {
+            const double x = __shfl_sync(0xffffffffu, xl, q);
+            const double y = __shfl_sync(0xffffffffu, yl, q);
+            const C rq = C{__shfl_sync(0xffffffffu, rl.x, q), __shfl_sync(0xffffffffu, rl.y, q)};
+            const C zq = C{__shfl_sync(0xffffffffu, zl.x, q), __shfl_sync(0xffffffffu, zl.y, q)};
+            if (!active) continue;
+            const double yk = y * (double)k0;
+            if (yk > (sizeof(T) == 4 ? 104.0 : 745.0)) continue;
+            const C w0 = cscale(expipi<T>((T)(-2.0 * dir_phase<T>((double)k0, x))), dir_exp<T>((T)(-yk)));
+            C rw = cmul(rq, w0);
+#pragma unroll
+            for (int t = 0; t < KL; ++t) {
+                acc[t] = cadd(acc[t], rw);
+                rw = cmul(rw, zq);
+            }
         }
     }
-    cdir[k] = acc;
+    if (!active) return;
+#pragma unroll
+    for (int t = 0; t < KL; ++t) {
+        const int64_t k = k0 + t;
+        if (k < B.K) {
+            atomicAdd(&cdir[k].x, acc[t].x);
+            atomicAdd(&cdir[k].y, acc[t].y);
+        }
+    }
 }
 
 template <typename T>
@@ -180,11 +219,15 @@ template <typename T>
 static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
     using C = C_t<T>;
     if (p.direct_ranges.empty()) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p.d_cdir, 0, p.N * sizeof(C), st);
+    if (e != cudaSuccess) return e;
+    const bool dbl = sizeof(T) == 8;
+    const std::vector<DirectAdjItem>& items = dbl ? p.dadj_work64 : p.dadj_work32;
+    const DirectAdjItem* d_items = dbl ? p.d_dadj64 : p.d_dadj32;
     int slot;
     timer_begin(p, "direct_adj", 0.0, st, &slot);
-    k_direct_adj<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
-        (int)p.direct_ranges.size(), p.d_dranges, p.N, p.d_bands, p.d_ws, p.d_perm, (const C*)r,
-        (C*)p.d_cdir);
+    k_direct_adj<T><<<(unsigned)items.size(), 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
+                                                         (const C*)r, (C*)p.d_cdir);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();

@@ -182,13 +182,14 @@ cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
 __global__ void k_permute(int64_t M, const double* __restrict__ w, const uint32_t* __restrict__ keys,
                           const int32_t* __restrict__ vals, int32_t moff, int32_t band_base,
                           double2* __restrict__ ws, int32_t* __restrict__ perm,
-                          int32_t* __restrict__ bandid) {
+                          int32_t* __restrict__ bandid, int32_t* __restrict__ cell) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int32_t j = vals[i];
     ws[i] = make_double2(w[2 * (int64_t)j], w[2 * (int64_t)j + 1]);
     perm[i] = moff + j;
     bandid[i] = band_base + (int32_t)(keys[i] >> 25);
+    cell[i] = (int32_t)(keys[i] & ((1u << 25) - 1u));
 }
 
 cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, const uint32_t* keys,
@@ -197,7 +198,7 @@ cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, con
     const int bs = 256;
     k_permute<<<(unsigned)((in.M + bs - 1) / bs), bs, 0, st>>>(
         in.M, nodes + 2 * in.moff, keys, vals, (int32_t)in.moff, in.band_base, p.d_ws + in.moff,
-        p.d_perm + in.moff, p.d_bandid + in.moff);
+        p.d_perm + in.moff, p.d_bandid + in.moff, p.d_cell + in.moff);
     return cudaGetLastError();
 }
 

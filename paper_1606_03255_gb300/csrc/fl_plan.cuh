@@ -55,6 +55,16 @@ struct DirectItem {
     int pad;
 };
 
+// Direct route adjoint: a warp per (band, frequency chunk of 32 KL, node group).
+constexpr int kDirAdjNodes = 256;
+struct DirectAdjItem {
+    int band;
+    int kchunk;
+    int64_t node0;
+    int nnodes;
+    int pad;
+};
+
 struct DirectRange {
     int band;
     int pad;
@@ -109,12 +119,27 @@ struct Plan {
     double direct_bias = 1.0;
     std::vector<DirectItem> direct_work;
     std::vector<DirectRange> direct_ranges;
+    std::vector<DirectAdjItem> dadj_work32, dadj_work64;   // adjoint items for KL = 32 / 16
     int64_t direct_nodes = 0, direct_terms = 0, dpart_elems = 0;
 
     // device memory
     double2* d_ws = nullptr;       // nodes in sorted order (Re w, Im w)
     int32_t* d_perm = nullptr;     // sorted position -> original index
     int32_t* d_bandid = nullptr;   // band (global index) of each sorted node
+    int32_t* d_cell = nullptr;     // grid cell floor(n_m x) of each sorted node
+    void* d_sp_phi = nullptr;      // adjoint: window taps per node (M x 2 m_w, T)
+    void* d_sp_L = nullptr;        // adjoint: barycentric weights per node (M x q, T)
+    void* d_sp_rv = nullptr;       // adjoint: shifted residual per node (M, complex T)
+    struct CellBand {              // adjoint: the cells of one NFFT band
+        int band;
+        int pad;
+        int64_t prefix;            // cells of the NFFT bands before it
+    };
+    std::vector<CellBand> cell_bands;   // sparse bands first, then dense ones
+    CellBand* d_cell_bands = nullptr;
+    int n_sparse_cb = 0;
+    int64_t cells_total = 0;            // cells of the sparse bands
+    int64_t cells_dense = 0;            // cells of the dense bands
     BandDev* d_bands = nullptr;    // levels + 1 descriptors
     SmallWork* d_small = nullptr;
     PassItem* d_pass = nullptr;
@@ -127,6 +152,8 @@ struct Plan {
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
     DirectItem* d_direct = nullptr;
     DirectRange* d_dranges = nullptr;
+    DirectAdjItem* d_dadj32 = nullptr;
+    DirectAdjItem* d_dadj64 = nullptr;
     void* d_dpart = nullptr;       // direct route: partial sums (complex T)
     void* d_cdir = nullptr;        // direct route adjoint: N complex
     double scratch_bytes = 0;

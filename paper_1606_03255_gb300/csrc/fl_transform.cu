@@ -287,48 +287,166 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 // ---------------------------------------------------------------------------
 // Adjoint: spread (transpose of the gather), FFT with sign -, combine.
 
+// Adjoint spreading, the transpose of the gather, without atomics in two
+// steps.  k_spread_prep: for every sorted node of an NFFT band its 2 m_w window
+// taps, its barycentric weights L_s(y_j) and rv_j = r_j exp(-2 pi i (N_m/2) x_j).
 template <typename T, int MW>
-__global__ void __launch_bounds__(256) k_spread(int64_t M, int64_t z0, const double2* __restrict__ ws,
-                                                const int32_t* __restrict__ perm,
-                                                const int32_t* __restrict__ bandid,
-                                                const BandDev* __restrict__ bands,
-                                                const C_t<T>* __restrict__ r,
-                                                const double* __restrict__ cheb, int q, T kb_b,
-                                                C_t<T>* __restrict__ grid) {
+__global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* __restrict__ ws,
+                                                     const int32_t* __restrict__ perm,
+                                                     const int32_t* __restrict__ bandid,
+                                                     const BandDev* __restrict__ bands,
+                                                     const C_t<T>* __restrict__ r,
+                                                     const double* __restrict__ cheb, int q, T kb_b,
+                                                     T* __restrict__ sp_phi, T* __restrict__ sp_L,
+                                                     C_t<T>* __restrict__ sp_rv) {
     using C = C_t<T>;
-    const int64_t i = z0 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    const int b = bandid[i];
-    const BandDev B = bands[b];
-    if (B.route != 1) return;   // direct-route band: k_direct_adj
+    const BandDev B = bands[bandid[i]];
+    if (B.route != 1) return;
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
     const double t0 = (double)B.n * x;
-    const double u = floor(t0);
-    const T fr = (T)(t0 - u);
-    const int64_t lo = (int64_t)u - (MW - 1);
+    const T fr = (T)(t0 - floor(t0));
     double ph = (double)(B.Nm >> 1) * x;
     ph -= floor(ph);
     if (ph >= 0.5) ph -= 1.0;
-    const C rv = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));   // r_j exp(-2 pi i (N_m/2) x_j)
-    T phi[2 * MW];
+    sp_rv[i] = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
 #pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
-    const int64_t nmask = B.n - 1;
-    C* g = grid + B.grid_off;
-    T Ls[kMaxQ];
-    int nr = B.nrhs;
-    if (nr > 1) bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
-    else Ls[0] = (T)1;
-    for (int s = 0; s < nr; ++s) {
-        C* gs = g + (int64_t)s * B.n;
-        const C a = cscale(rv, Ls[s]);
-#pragma unroll
-        for (int t = 0; t < 2 * MW; ++t) {
-            C* dst = gs + ((lo + t) & nmask);
-            atomicAdd(&dst->x, phi[t] * a.x);
-            atomicAdd(&dst->y, phi[t] * a.y);
+    for (int t = 0; t < 2 * MW; ++t)
+        sp_phi[i * (2 * MW) + t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+    if (B.nrhs > 1) {
+        T Ls[kMaxQ];
+        bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
+        for (int s = 0; s < q; ++s) sp_L[i * q + s] = Ls[s];
+    }
+}
+
+// First sorted node of [lo, hi) whose cell is >= v (cells ascend within a band).
+__device__ __forceinline__ int64_t lower_cell(const int32_t* __restrict__ cell, int64_t lo,
+                                              int64_t hi, int64_t v) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cell[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Sum over the nodes that cover grid cell l of one NFFT band: the nodes whose
+// cell u lies in [l - m_w, l + m_w - 1] (mod n) form a contiguous range of the
+// band's cell-sorted nodes (two near the ends); node j adds window tap
+// t = l - u + m_w - 1 times rv_j, times L_s(y_j) for right-hand side s.  The
+// lanes lane, lane + stride, ... of the range are summed into acc.
+template <typename T, int MW>
+__device__ __forceinline__ void spread_cell_sum(const BandDev& B, int64_t l,
+                                                const int32_t* __restrict__ cell,
+                                                const T* __restrict__ sp_phi,
+                                                const T* __restrict__ sp_L,
+                                                const C_t<T>* __restrict__ sp_rv, int q,
+                                                int lane, int stride, C_t<T>* acc) {
+    using C = C_t<T>;
+    const int64_t n = B.n, nb0 = B.node_off, nend = B.node_off + B.nodes;
+    int64_t ra[2][2];
+    int nrange = 0;
+    const int64_t c0 = l - MW, c1 = l + MW - 1;
+    if (c0 < 0) {
+        ra[0][0] = n + c0; ra[0][1] = n - 1;
+        ra[1][0] = 0; ra[1][1] = c1;
+        nrange = 2;
+    } else if (c1 >= n) {
+        ra[0][0] = c0; ra[0][1] = n - 1;
+        ra[1][0] = 0; ra[1][1] = c1 - n;
+        nrange = 2;
+    } else {
+        ra[0][0] = c0; ra[0][1] = c1;
+        nrange = 1;
+    }
+    const int nr = B.nrhs;
+    for (int rr = 0; rr < nrange; ++rr) {
+        const int64_t j0 = lower_cell(cell, nb0, nend, ra[rr][0]);
+        const int64_t j1 = lower_cell(cell, j0, nend, ra[rr][1] + 1);
+        for (int64_t j = j0 + lane; j < j1; j += stride) {
+            int64_t t = (l - cell[j] + MW - 1) % n;
+            if (t < 0) t += n;
+            const C w = cscale(sp_rv[j], sp_phi[j * (2 * MW) + t]);
+            if (nr == 1) {
+                acc[0] = cadd(acc[0], w);
+            } else {
+                for (int s = 0; s < nr; ++s) {
+                    const T L = sp_L[j * q + s];
+                    acc[s].x += L * w.x;
+                    acc[s].y += L * w.y;
+                }
+            }
         }
+    }
+}
+
+__device__ __forceinline__ int find_cell_band(const Plan::CellBand* __restrict__ cbs, int ncb,
+                                              int64_t g) {
+    int lo = 0, hi = ncb;   // last entry with prefix <= g
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (cbs[mid].prefix <= g) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// k_spread_cells: one thread per (sparse NFFT band, grid cell l); writes a_s[l]
+// for every right-hand side s.
+template <typename T, int MW>
+__global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellBand* __restrict__ cbs,
+                                                      int64_t total, const BandDev* __restrict__ bands,
+                                                      const int32_t* __restrict__ cell,
+                                                      const T* __restrict__ sp_phi,
+                                                      const T* __restrict__ sp_L,
+                                                      const C_t<T>* __restrict__ sp_rv, int q,
+                                                      C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= total) return;
+    const int cb = find_cell_band(cbs, ncb, g);
+    const BandDev B = bands[cbs[cb].band];
+    const int64_t l = g - cbs[cb].prefix;
+    C acc[kMaxQ];
+    for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
+    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, 0, 1, acc);
+    C* gb = grid + B.grid_off + l;
+    for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = acc[s];
+}
+
+// Dense NFFT bands (many nodes per cell): one warp per cell, lanes strided
+// over the covering nodes, lane sums combined in a fixed shuffle order.
+template <typename T, int MW>
+__global__ void __launch_bounds__(256) k_spread_cells_warp(int ncb, const Plan::CellBand* __restrict__ cbs,
+                                                           int64_t total,
+                                                           const BandDev* __restrict__ bands,
+                                                           const int32_t* __restrict__ cell,
+                                                           const T* __restrict__ sp_phi,
+                                                           const T* __restrict__ sp_L,
+                                                           const C_t<T>* __restrict__ sp_rv, int q,
+                                                           C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (g >= total) return;
+    const int cb = find_cell_band(cbs, ncb, g);
+    const BandDev B = bands[cbs[cb].band];
+    const int64_t l = g - cbs[cb].prefix;
+    C acc[kMaxQ];
+    for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
+    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, lane, 32, acc);
+    C* gb = grid + B.grid_off + l;
+    for (int s = 0; s < B.nrhs; ++s) {
+        T x = acc[s].x, y = acc[s].y;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, off);
+            y += __shfl_xor_sync(0xffffffffu, y, off);
+        }
+        if (lane == 0) gb[(int64_t)s * B.n] = C{x, y};
     }
 }
 
@@ -493,15 +611,23 @@ cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_
 template <typename T, int MW>
 static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     using C = C_t<T>;
-    const int64_t cnt = p.M - p.z0_nodes;
-    if (cnt <= 0) return cudaSuccess;
+    if (p.cell_bands.empty()) return cudaSuccess;
     int slot;
     timer_begin(p, "spread", 0.0, st, &slot);
-    k_spread<T, MW><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(
-        p.M, p.z0_nodes, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q,
-        (T)p.kb_b, (C*)p.d_grid);
+    k_spread_prep<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q, (T)p.kb_b,
+        (T*)p.d_sp_phi, (T*)p.d_sp_L, (C*)p.d_sp_rv);
+    if (p.cells_total > 0)
+        k_spread_cells<T, MW><<<(unsigned)((p.cells_total + 255) / 256), 256, 0, st>>>(
+            (int)p.n_sparse_cb, p.d_cell_bands, p.cells_total, p.d_bands, p.d_cell,
+            (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
+    if (p.cells_dense > 0)
+        k_spread_cells_warp<T, MW><<<(unsigned)((p.cells_dense * 32 + 255) / 256), 256, 0, st>>>(
+            (int)(p.cell_bands.size() - p.n_sparse_cb), p.d_cell_bands + p.n_sparse_cb,
+            p.cells_dense, p.d_bands, p.d_cell, (const T*)p.d_sp_phi, (const T*)p.d_sp_L,
+            (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
     timer_end(p, slot, st);
-    ++p.launches;
+    p.launches += 1 + (p.cells_total > 0) + (p.cells_dense > 0);
     return cudaGetLastError();
 }
 
@@ -509,7 +635,6 @@ template <typename T>
 static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st) {
     using C = C_t<T>;
     cudaError_t e;
-    if ((e = cudaMemsetAsync(p.d_grid, 0, p.grid_elems * sizeof(C), st)) != cudaSuccess) return e;
     switch (p.mw) {
 #define FL_MW_CASE(W) \
     case W: e = spread_t<T, W>(p, r, st); break;
