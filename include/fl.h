@@ -76,6 +76,7 @@ typedef struct {
     int64_t band_K[FL_MAX_LEVELS];    /* frequencies with nonzero weight */
     int64_t band_n[FL_MAX_LEVELS];    /* FFT length (oversampled grid) */
     double model_bytes;       /* algorithmic HBM bytes of one fl_execute */
+    double direct_bias;       /* route bias in use (the autotuner's choice if tuned) */
     double scratch_bytes;     /* device memory owned by the plan */
 } fl_info;
 
@@ -125,6 +126,10 @@ typedef struct {
                              buffers or the stream change; not on the legacy
                              default stream).  fl_plan_batched: graphs are on
                              unless this is -1.  0 = plain launches.             */
+    int autotune;         /* 1 = with route 0, plan the workload for several
+                             values of direct_bias, time an execute of each on
+                             `stream` and keep the fastest (cached per workload
+                             signature for the process); 0 = off              */
 } fl_options;
 
 /*

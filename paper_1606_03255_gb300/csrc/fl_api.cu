@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <mutex>
 #include <string>
 
 #include "fl_plan.cuh"
@@ -39,7 +40,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands};
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -148,15 +149,21 @@ static fl_status select_bands(Plan& p, Instance& in, int inst_index) {
 }
 
 // Route of a non-empty band: NFFT with nrhs right-hand sides, or the direct sum
-// over its K frequencies.  Costs in issued instructions per element: an FFT
-// grid point ~ (log2 n + 8) over both passes and the prep, a gathered tap ~ 2
-// per right-hand side, a direct term ~ 6 (one complex Horner step and its
-// share of the block's phase).
+// over its K frequencies.  Costs in issued instructions: an FFT grid point
+// ~ (log2 n + 8) over both passes and the prep (twice that in double, whose
+// twiddles come from double sincospi); per gathered node, 2 per tap and
+// right-hand side plus the window (2 m_w sinh/sqrt) and the barycentric
+// divisions, both several times dearer in double on this part; a fixed launch
+// and latency share per NFFT band; a direct term ~ 6 (one complex Horner step
+// and its share of the block's phase).
 static int route_of(const Plan& p, const BandHost& bh) {
     if (p.route_mode == 1) return 1;
     if (p.route_mode == 2) return 2;
     const BandDev& d = bh.dev;
-    const double fft = (double)d.nrhs * d.n * (d.log2n + 8) + (double)bh.nodes * d.nrhs * 2 * p.mw * 2;
+    const bool dbl = p.prec == FL_FP64;
+    const double fft_pt = dbl ? 2.0 : 1.0, win = dbl ? 150.0 : 20.0, div = dbl ? 40.0 : 4.0;
+    const double per_node = (double)d.nrhs * 2 * p.mw * 2 + 2.0 * p.mw * win + (d.nrhs > 1 ? p.q * div : 0.0);
+    const double fft = (double)d.nrhs * d.n * (d.log2n + 8) * fft_pt + (double)bh.nodes * per_node + 2.0e5;
     const double direct = (double)bh.nodes * d.K * 6.0 * p.direct_bias;
     return direct < fft ? 2 : 1;
 }
@@ -437,6 +444,152 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
 }
 
 
+// Everything that defines a Fourier-Laplace plan besides the route bias.
+struct PlanSpec {
+    int B;
+    const int64_t* Ns;
+    const int64_t* Ms;
+    const double* nodes;
+    int q;
+    double eps;
+    fl_precision prec;
+    bool batched;
+    int route_mode;
+    int rhs_per_launch;
+    bool use_graph;
+};
+
+static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cudaStream_t st) {
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return fail(FL_ENOMEM, "fl_plan: host allocation");
+    h->p.kind = 0;
+    h->p.batched = sp.batched;
+    h->p.prec = sp.prec;
+    h->p.eps = sp.eps;
+    h->p.route_mode = sp.route_mode;
+    h->p.direct_bias = bias;
+    h->p.rhs_per_launch = sp.rhs_per_launch;
+    h->p.use_graph = sp.use_graph;
+    fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, st);
+    if (s != FL_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+// Route-bias autotuner: plans the workload for each candidate bias, times
+// three executes of each (CUDA events on the caller's stream, after one
+// warm-up, on zero coefficients: the work does not depend on the values), and
+// keeps the fastest.  The choice is cached for the process by a signature of
+// the workload (sizes, eps, precision and the node count of every band), so
+// planning the same workload again costs one plan.
+static std::vector<std::pair<uint64_t, double>> g_tuned;
+static std::mutex g_tuned_mutex;
+
+static uint64_t plan_signature(const Plan& p) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+    mix((uint64_t)p.N);
+    mix((uint64_t)p.M);
+    mix((uint64_t)p.inst.size());
+    mix((uint64_t)p.prec);
+    uint64_t e;
+    memcpy(&e, &p.eps, sizeof(e));
+    mix(e);
+    for (const BandHost& bh : p.bands) mix((uint64_t)bh.nodes * 131 + (uint64_t)bh.local);
+    return h;
+}
+
+static fl_status time_plan(Plan& p, cudaStream_t st, double* ms) {
+    const size_t cs = p.prec == FL_FP64 ? 16 : 8;
+    void *c = nullptr, *f = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaMalloc(&c, std::max<int64_t>(1, p.N) * cs);
+    if (e == cudaSuccess) e = cudaMalloc(&f, std::max<int64_t>(1, p.M) * cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c, 0, std::max<int64_t>(1, p.N) * cs, st);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int64_t launches = p.launches;
+    if (e == cudaSuccess) e = run_forward(p, c, f, false, st);
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = run_forward(p, c, f, false, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    p.launches = launches;
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(c);
+    cudaFree(f);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_plan: autotune");
+    *ms = t / 3.0;
+    return FL_OK;
+}
+
+static fl_status build_plan_tuned(const PlanSpec& sp, double bias, bool autotune, fl_plan_s** out,
+                                  cudaStream_t st) {
+    fl_plan_s* h = nullptr;
+    fl_status s = build_plan(sp, bias, &h, st);
+    if (s != FL_OK || !autotune || sp.route_mode != 0) {
+        *out = h;
+        return s;
+    }
+    const uint64_t sig = plan_signature(h->p);
+    double cached = 0.0;
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mutex);
+        for (const auto& kv : g_tuned)
+            if (kv.first == sig) cached = kv.second;
+    }
+    if (cached > 0.0) {
+        if (cached != bias) {
+            delete h;
+            h = nullptr;
+            if ((s = build_plan(sp, cached, &h, st)) != FL_OK) return s;
+        }
+        h->p.tuned_bias = cached;
+        *out = h;
+        return FL_OK;
+    }
+    double best_ms = 0;
+    if ((s = time_plan(h->p, st, &best_ms)) != FL_OK) {
+        delete h;
+        return s;
+    }
+    double best_bias = bias;
+    for (double cand : {0.125, 0.25, 0.5, 2.0, 4.0, 8.0}) {
+        fl_plan_s* c = nullptr;
+        if ((s = build_plan(sp, cand, &c, st)) != FL_OK) {
+            delete h;
+            return s;
+        }
+        double ms = 0;
+        if ((s = time_plan(c->p, st, &ms)) != FL_OK) {
+            delete c;
+            delete h;
+            return s;
+        }
+        if (ms < best_ms) {
+            delete h;
+            h = c;
+            best_ms = ms;
+            best_bias = cand;
+        } else {
+            delete c;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_tuned_mutex);
+        g_tuned.push_back({sig, best_bias});
+    }
+    h->p.tuned_bias = best_bias;
+    *out = h;
+    return FL_OK;
+}
+
 // fl_execute through a CUDA graph of its launches, captured on the first call
 // (and again when the buffers or the stream change), then replayed.
 static cudaError_t forward_graphed(Plan& p, const void* c, void* f, cudaStream_t st) {
@@ -503,24 +656,12 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan: q must lie in [0, 40]");
     if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan: unknown precision");
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
-    fl_plan_s* h = new (std::nothrow) fl_plan_s();
-    if (!h) return fail(FL_ENOMEM, "fl_plan: host allocation");
-    h->p.kind = 0;
-    h->p.prec = prec;
-    h->p.N = N;
-    h->p.M = M;
-    h->p.eps = eps;
-    if (opt) {
-        h->p.route_mode = opt->route;
-        h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
-        h->p.rhs_per_launch = opt->rhs_per_launch;
-        h->p.use_graph = opt->use_graph != 0;
-    }
-    fl_status s = plan_multi(h->p, 1, &N, &M, nodes_dev, q, (cudaStream_t)stream);
-    if (s != FL_OK) {
-        delete h;
-        return s;
-    }
+    PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
+                 opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false};
+    const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
+    fl_plan_s* h = nullptr;
+    fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
+    if (s != FL_OK) return s;
     *out = h;
     return FL_OK;
 }
@@ -601,24 +742,12 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
                 opt->rhs_per_launch < 0))
         return fail(FL_EINVAL, "fl_plan_batched: invalid options");
-    fl_plan_s* h = new (std::nothrow) fl_plan_s();
-    if (!h) return fail(FL_ENOMEM, "fl_plan_batched: host allocation");
-    h->p.kind = 0;
-    h->p.batched = true;
-    h->p.prec = prec;
-    h->p.eps = eps;
-    h->p.use_graph = true;
-    if (opt) {
-        h->p.route_mode = opt->route;
-        h->p.direct_bias = opt->direct_bias > 0.0 ? opt->direct_bias : 1.0;
-        h->p.rhs_per_launch = opt->rhs_per_launch;
-        h->p.use_graph = opt->use_graph >= 0;
-    }
-    fl_status s = plan_multi(h->p, B, N_host, M_host, nodes_dev, q, (cudaStream_t)stream);
-    if (s != FL_OK) {
-        delete h;
-        return s;
-    }
+    PlanSpec sp{B, N_host, M_host, nodes_dev, q, eps, prec, true, opt ? opt->route : 0,
+                 opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true};
+    const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
+    fl_plan_s* h = nullptr;
+    fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
+    if (s != FL_OK) return s;
     *out = h;
     return FL_OK;
 }
@@ -668,6 +797,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
         info->band_n[b] = bh.dev.n;
     }
     info->model_bytes = p.model_bytes;
+    info->direct_bias = p.tuned_bias > 0 ? p.tuned_bias : p.direct_bias;
     info->scratch_bytes = p.scratch_bytes;
     return FL_OK;
 }

@@ -94,18 +94,19 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
         const int l = !valid ? 255 : (BANDS_FROM_VALUES ? lap_band(t[k], xi1, levels) : tband[k]);
         const double cv = valid ? (double)c[k] : 0.0;
         // barycentric denominator on Omega_l (only for interpolated bands)
-        double tau = 0.0, den = 1.0;
+        double tau = 0.0, inv_den = 1.0;
         int hit = -1;
         const bool interp = valid && l < levels;
         if (interp) {
             const double a = ldexp(xi1, -l);
             tau = (t[k] - 1.5 * a) / (0.5 * a);
-            den = 0.0;
+            double den = 0.0;
             for (int r = 0; r < q; ++r) {
                 const double d = tau - cheb[r];
                 if (d == 0.0) hit = r;
                 den += cheb[q + r] / d;
             }
+            inv_den = 1.0 / den;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, l);
         const bool leader = (peers & ((1u << lane) - 1u)) == 0u;
@@ -115,7 +116,7 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
                 val = (T)cv;
             } else if (interp) {
                 const double Lr = (hit >= 0) ? (r == hit ? 1.0 : 0.0)
-                                             : (cheb[q + r] / (tau - cheb[r])) / den;
+                                             : (cheb[q + r] / (tau - cheb[r])) * inv_den;
                 val = (T)(Lr * cv);
             }
             T acc = (T)0;
@@ -170,6 +171,48 @@ __global__ void k_lap_couple(int levels, int q, double y1, double xi1,
             const double xr = 1.5 * ax + 0.5 * ax * cheb[r];
             acc += exp(-ys * xr) * vS[l * row + r];
         }
+    }
+    h[m * q + s] = acc;
+}
+
+// Plan-time table of the coupling blocks: Kt[koff[m] + ((l - l_m) q + s) q + r]
+// = exp(-y_s^{Y_m} xi_r^{Omega_l}), the same expression k_lap_couple evaluates.
+__global__ void k_lap_ktable(int levels, int q, double y1, double xi1, const int* __restrict__ ell,
+                             const int64_t* __restrict__ koff, const double* __restrict__ cheb,
+                             double* __restrict__ Kt) {
+    const int m = blockIdx.x + 1;
+    if (m >= levels) return;
+    const int nl = levels - m - ell[m] + 1;
+    const double ay = ldexp(y1, -m);
+    for (int i = threadIdx.x; i < nl * q * q; i += blockDim.x) {
+        const int r = i % q, s = (i / q) % q, l = ell[m] + i / (q * q);
+        const double ys = 1.5 * ay + 0.5 * ay * cheb[s];
+        const double ax = ldexp(xi1, -l);
+        const double xr = 1.5 * ax + 0.5 * ax * cheb[r];
+        Kt[koff[m] + i] = exp(-ys * xr);
+    }
+}
+
+// k_lap_couple with the coupling blocks read from the plan's table (same
+// summation order, so the same h).
+__global__ void k_lap_couple_tab(int levels, int q, const int* __restrict__ ell,
+                                 const int64_t* __restrict__ koff, const double* __restrict__ Kt,
+                                 const double* __restrict__ vS, double* __restrict__ h,
+                                 double* __restrict__ g) {
+    const int m = blockIdx.x + 1;
+    const int row = q + 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        g[levels + 1] = 0.0;
+        for (int l = levels; l >= 1; --l) g[l] = g[l + 1] + vS[l * row + q];
+    }
+    if (m >= levels) return;
+    const int s = threadIdx.x;
+    if (s >= q) return;
+    double acc = 0.0;
+    const double* K = Kt + koff[m];
+    for (int l = ell[m]; l <= levels - m; ++l) {
+        const double* Kb = K + ((int64_t)(l - ell[m]) * q + s) * q;
+        for (int r = 0; r < q; ++r) acc += Kb[r] * vS[l * row + r];
     }
     h[m * q + s] = acc;
 }
@@ -268,7 +311,8 @@ template <typename T, bool BANDS_FROM_VALUES = false>
 static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* s,
                            const uint8_t* tband, const uint8_t* sband, const LapParams& P,
                            const double* cheb, const T* c, T* f, unsigned char* scratch,
-                           int nblocks, cudaStream_t st, Plan* timed) {
+                           int nblocks, cudaStream_t st, Plan* timed,
+                           const double* Kt = nullptr, const int64_t* koff = nullptr) {
     const LapLayout L = lap_layout(P.levels, P.q, nblocks, sizeof(T));
     const int entries = (P.levels + 1) * (P.q + 1);
     T* partial = (T*)(scratch + L.partial);
@@ -291,8 +335,12 @@ static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* 
         cudaError_t e = cudaMemsetAsync(vS, 0, entries * sizeof(double), st);
         if (e != cudaSuccess) return e;
     }
-    k_lap_couple<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
-        P.levels, P.q, P.y1, P.xi1, ell, cheb, vS, h, g);
+    if (Kt)
+        k_lap_couple_tab<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
+            P.levels, P.q, ell, koff, Kt, vS, h, g);
+    else
+        k_lap_couple<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
+            P.levels, P.q, P.y1, P.xi1, ell, cheb, vS, h, g);
     if (M > 0) {
         if (timed) timer_begin(*timed, "lap_eval", (double)M * (8 + 1 + sizeof(T)), st, &slot);
         k_lap_eval<T, BANDS_FROM_VALUES><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(
@@ -323,9 +371,10 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
     if (p.prec == FL_FP64)
         return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb,
                                (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
-                               st, &p);
+                               st, &p, p.d_lapK, p.d_lapKoff);
     return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb, (const float*)c,
-                          (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p);
+                          (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p, p.d_lapK,
+                          p.d_lapKoff);
 }
 
 }  // namespace fl
@@ -404,6 +453,23 @@ static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, in
     LAP_CUDA(cudaMemcpyAsync((unsigned char*)p.d_lap + L.ell, ell.data(), ell.size() * sizeof(int),
                              cudaMemcpyHostToDevice, st),
              "copy l_m");
+    // coupling blocks K^{Y_m, Omega_l}, l = l_m .. L_m, as a table
+    std::vector<int64_t> koff(P.levels + 1, 0);
+    int64_t ktot = 0;
+    for (int m = 1; m < P.levels; ++m) {
+        koff[m] = ktot;
+        ktot += (int64_t)std::max(0, P.levels - m - P.ell[m] + 1) * P.q * P.q;
+    }
+    if (ktot > 0) {
+        LAP_CUDA(cudaMalloc((void**)&p.d_lapK, ktot * sizeof(double)), "cudaMalloc coupling table");
+        LAP_CUDA(cudaMalloc((void**)&p.d_lapKoff, koff.size() * sizeof(int64_t)), "cudaMalloc coupling offsets");
+        LAP_CUDA(cudaMemcpyAsync(p.d_lapKoff, koff.data(), koff.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st),
+                 "copy coupling offsets");
+        k_lap_ktable<<<P.levels - 1, 256, 0, st>>>(P.levels, P.q, y1, xi1,
+                                                   (const int*)((unsigned char*)p.d_lap + L.ell),
+                                                   p.d_lapKoff, p.d_cheb, p.d_lapK);
+    }
     LAP_CUDA(cudaGetLastError(), "fl_plan_laplace: launch");
     LAP_CUDA(cudaStreamSynchronize(st), "fl_plan_laplace: synchronise");
     const size_t ts = p.prec == FL_FP64 ? 8 : 4;

@@ -117,6 +117,7 @@ struct Plan {
     int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
     double direct_bias = 1.0;
+    double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)
     std::vector<DirectItem> direct_work;
     std::vector<DirectRange> direct_ranges;
     std::vector<DirectAdjItem> dadj_work32, dadj_work64;   // adjoint items for KL = 32 / 16
@@ -164,6 +165,8 @@ struct Plan {
     uint8_t* d_tband = nullptr;    // band of every t_k
     uint8_t* d_sband = nullptr;    // band of every s_j
     void* d_lap = nullptr;         // moments and partial sums
+    double* d_lapK = nullptr;      // coupling blocks K^{Y_m, Omega_l} (plan-time table)
+    int64_t* d_lapKoff = nullptr;  // offset of band m's blocks in d_lapK
     int lap_blocks = 0;
 
     // CUDA-graph replay of fl_execute / fl_execute_batched

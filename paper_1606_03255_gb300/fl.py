@@ -52,13 +52,15 @@ class fl_info(ctypes.Structure):
         ("band_nodes", ctypes.c_int64 * FL_MAX_LEVELS),
         ("band_K", ctypes.c_int64 * FL_MAX_LEVELS),
         ("band_n", ctypes.c_int64 * FL_MAX_LEVELS),
-        ("model_bytes", ctypes.c_double), ("scratch_bytes", ctypes.c_double),
+        ("model_bytes", ctypes.c_double), ("direct_bias", ctypes.c_double),
+        ("scratch_bytes", ctypes.c_double),
     ]
 
 
 class fl_options(ctypes.Structure):
     _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
-                ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
@@ -277,7 +279,8 @@ def info_dict(info: fl_info) -> dict:
         "band_ell": list(info.band_ell[:nb]), "band_route": list(info.band_route[:nb]),
         "band_nodes": list(info.band_nodes[:nb]), "band_K": list(info.band_K[:nb]),
         "band_n": list(info.band_n[:nb]),
-        "model_bytes": info.model_bytes, "scratch_bytes": info.scratch_bytes,
+        "model_bytes": info.model_bytes, "direct_bias": info.direct_bias,
+        "scratch_bytes": info.scratch_bytes,
     }
 
 
@@ -299,7 +302,7 @@ class Plan:
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
-                 rhs_per_launch: int = 0, use_graph: bool = False):
+                 rhs_per_launch: int = 0, use_graph: bool = False, autotune: bool = False):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -309,7 +312,8 @@ class Plan:
         self.prec = FL_FP64 if precision == "fp64" else FL_FP32
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
-        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)))
+        opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)),
+                         int(bool(autotune)))
         st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
                            opt, _stream_handle(stream))
         check(st, "fl_plan")
@@ -393,7 +397,7 @@ class BatchedPlan:
 
     def __init__(self, Ns, Ms, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
-                 rhs_per_launch: int = 0, use_graph: bool = True):
+                 rhs_per_launch: int = 0, use_graph: bool = True, autotune: bool = False):
         torch = _torch()
         nodes = nodes.to(torch.float64).contiguous()
         self.Ns = [int(x) for x in Ns]
@@ -403,7 +407,7 @@ class BatchedPlan:
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
-                         1 if use_graph else -1)
+                         1 if use_graph else -1, int(bool(autotune)))
         st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
                                 self.prec, opt, _stream_handle(stream))
         check(st, "fl_plan_batched")

@@ -149,3 +149,30 @@ def test_batched_is_forward_only(fl):
     st = fl.fl_adjoint(plan.handle, r.data_ptr(), out.data_ptr(), None)
     assert st == fl.FL_EUNSUPPORTED
     plan.close()
+
+
+def test_autotuned_plans(fl):
+    # the autotuner keeps the fastest route bias; results stay within the bound
+    Ns = W.batched_degrees(32, seed=3)
+    cs, ws = _batch(Ns, Ns, seed=50)
+    dev = torch.device("cuda")
+    nodes = torch.from_numpy(np.concatenate(ws)).to(dev)
+    plan = fl.BatchedPlan(Ns, Ns, nodes, 1e-6, autotune=True)
+    bias = plan.info()["direct_bias"]
+    assert bias in (0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
+    f = plan.execute(torch.from_numpy(np.concatenate(cs)).to(torch.complex64).to(dev)).cpu().numpy()
+    moff = 0
+    for c, w, M in zip(cs, ws, Ns):
+        idx = np.arange(0, M, max(1, M // 64))
+        ref = oracle.flt_direct(c, w[idx])
+        assert oracle.error_E(ref, f[moff:moff + M][idx], c) <= _tol(1e-6, "fp32", ref, c)
+        moff += M
+    # the same workload again: the cached choice is reused
+    plan2 = fl.BatchedPlan(Ns, Ns, nodes, 1e-6, autotune=True)
+    assert plan2.info()["direct_bias"] == bias
+    single = fl.Plan(int(Ns[0]), torch.from_numpy(ws[0]).to(dev), 1e-6, autotune=True)
+    fs = single.execute(torch.from_numpy(cs[0]).to(torch.complex64).to(dev)).cpu().numpy()
+    ref = oracle.flt_direct(cs[0], ws[0])
+    assert oracle.error_E(ref, fs, cs[0]) <= _tol(1e-6, "fp32", ref, cs[0])
+    for p in (plan, plan2, single):
+        p.close()
