@@ -40,7 +40,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff};
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -421,7 +421,11 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     }
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
-    if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
+    if (p.Y_elems) {
+        FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
+        FL_CUDA(cudaMalloc(&p.d_tw, (size_t)kTwEntries * cs), "cudaMalloc twiddles");
+        FL_CUDA(build_twiddles(p, st), "fl_plan: twiddles");
+    }
     FL_CUDA(build_cheb(p, st), "fl_plan: tables");
     for (int i = 0; i < B; ++i) FL_CUDA(build_tables(p, p.inst[i], st), "fl_plan: tables");
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");

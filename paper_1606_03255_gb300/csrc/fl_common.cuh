@@ -36,6 +36,33 @@ template <typename T> __device__ __forceinline__ C_t<T> expipi(T x) {
     return {c, s};
 }
 
+// Stage twiddle tables.  In a length-L transform whose first stage has radix
+// 2^FIRST, every later stage (radix R, span NS = 2^d) multiplies input r of job
+// jj by w^(r k), w = exp(SIGN 2 pi i / (NS R)), k = jj mod NS.  Those values are
+// tabulated at plan time (FP64, rounded once) for SIGN = +1 as
+//   tab[tw_region(LOG2L, FIRST) + tw_off(LOG2L, FIRST, d) + (r - 1) NS + k],
+// so a job reads its R - 1 factors at stride NS from its k (consecutive jobs,
+// consecutive entries) and SIGN = -1 takes the conjugate.
+constexpr int kTwMinLog = 6, kTwMaxLog = 12;
+constexpr int kTwRegion = 1 << kTwMaxLog;                   // entries per (LOG2L, FIRST)
+constexpr int kTwEntries = (kTwMaxLog - kTwMinLog + 1) * 2 * kTwRegion;
+
+__host__ __device__ constexpr int tw_last_log(int LOG2L, int FIRST) {
+    return (LOG2L - FIRST) - 4 * (((LOG2L - FIRST) + 3) / 4 - 1);
+}
+// log2 of the radix of the stage of span 2^d (d = FIRST, FIRST + 4, ...)
+__host__ __device__ constexpr int tw_stage_log(int LOG2L, int FIRST, int d) {
+    return d == LOG2L - tw_last_log(LOG2L, FIRST) ? tw_last_log(LOG2L, FIRST) : 4;
+}
+__host__ __device__ constexpr int tw_off(int LOG2L, int FIRST, int d) {
+    int off = 0;
+    for (int e = FIRST; e < d; e += 4) off += ((1 << tw_stage_log(LOG2L, FIRST, e)) - 1) << e;
+    return off;
+}
+__host__ __device__ constexpr int tw_region(int LOG2L, int FIRST) {
+    return ((LOG2L - kTwMinLog) * 2 + (FIRST - 3)) * kTwRegion;
+}
+
 // Per-band descriptor (bands 1..levels; band 0 is Z^0).  Built on the host at
 // plan time, read by every kernel of the forward and adjoint transforms.
 struct BandDev {

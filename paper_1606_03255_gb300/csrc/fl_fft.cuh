@@ -128,8 +128,16 @@ __device__ __forceinline__ void twiddle_powers(T x, C_t<T>* w) {
     }
 }
 
+// Stage twiddles come from the plan-time table laid out by tw_region / tw_off
+// (fl_common.cuh); SIGN = -1 takes the conjugate.
+template <int SIGN, typename C> __device__ __forceinline__ C tw_load(const C* p) {
+    C w = __ldg(p);
+    if (SIGN < 0) w.y = -w.y;
+    return w;
+}
+
 template <int R, int NS, int L, int SIGN, typename T>
-__device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t) {
+__device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __restrict__ tws) {
     using C = C_t<T>;
     constexpr int J = 16 / R;
     constexpr int NTHR = L / 16;
@@ -141,11 +149,9 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t) {
 #pragma unroll
         for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
         if constexpr (NS > 1) {
-            // k < NS and 1/(NS R) is a power of two: exact argument
-            C w[R];
-            twiddle_powers<R, T>((T)(2 * SIGN) * (T)k * (T)(1.0 / (NS * R)), w);
+            const C* tk = tws + k;
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], w[r]);
+            for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], tw_load<SIGN>(tk + (r - 1) * NS));
         }
     }
     __syncthreads();
@@ -165,29 +171,14 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t) {
     __syncthreads();
 }
 
-// L = 2^LOG2L points (LOG2L >= 4) with L/16 threads t = 0..L/16-1.
-template <int LOG2L, int SIGN, typename T, int DONE = 0>
-__device__ __forceinline__ void fft_ct(C_t<T>* buf, int t) {
-    constexpr int L = 1 << LOG2L;
-    constexpr int REM = LOG2L - DONE;
-    if constexpr (REM >= 4) {
-        fft16_stage<16, (1 << DONE), L, SIGN, T>(buf, t);
-        fft_ct<LOG2L, SIGN, T, DONE + 4>(buf, t);
-    } else if constexpr (REM == 3) {
-        fft16_stage<8, (1 << DONE), L, SIGN, T>(buf, t);
-    } else if constexpr (REM == 2) {
-        fft16_stage<4, (1 << DONE), L, SIGN, T>(buf, t);
-    } else if constexpr (REM == 1) {
-        fft16_stage<2, (1 << DONE), L, SIGN, T>(buf, t);
-    }
-}
-
 // The same transform split so that its first stage can take its inputs from
-// registers and its last stage can leave its outputs in registers (for
-// LOG2L >= 5: radix 16 first, radix 16 middles, radix LAST_R last).
-template <int LOG2L> struct StagePlan {
-    static constexpr int NSTAGE = (LOG2L + 3) / 4;
-    static constexpr int LAST_LOG = LOG2L - 4 * (NSTAGE - 1);   // 1..4
+// registers and its last stage can leave its outputs in registers: a first
+// stage of radix 2^FIRST (16, or 8 with two butterflies per thread), radix-16
+// middle stages, and a last stage of radix LAST_R.
+template <int LOG2L, int FIRST = 4> struct StagePlan {
+    static constexpr int REST = LOG2L - FIRST;                  // >= 1
+    static constexpr int NSTAGE = 1 + (REST + 3) / 4;
+    static constexpr int LAST_LOG = REST - 4 * ((REST + 3) / 4 - 1);   // 1..4
     static constexpr int LAST_R = 1 << LAST_LOG;
     static constexpr int LAST_NS = 1 << (LOG2L - LAST_LOG);
 };
@@ -201,32 +192,46 @@ __device__ __forceinline__ void fft_first_from_regs(C_t<T>* v, C_t<T>* buf, int 
     __syncthreads();
 }
 
-// Middle stages (radix 16, smem to smem) from span 2^DONE up to the last stage.
-template <int LOG2L, int SIGN, typename T, int DONE = 4>
-__device__ __forceinline__ void fft_middle(C_t<T>* buf, int t) {
+// First stage as radix 8 (span 1) with the two butterflies jj = 2t and 2t + 1
+// of one thread: v[8 b + r] = x[2t + b + r L/8].  Butterfly jj writes jj 8 + r,
+// so the thread's 16 outputs are again the contiguous run 16 t .. 16 t + 15, and
+// its inputs are 8 pairs of adjacent elements (16-byte loads for float).
+template <int LOG2L, int SIGN, typename T>
+__device__ __forceinline__ void fft_first8x2_from_regs(C_t<T>* v, C_t<T>* buf, int t) {
+    dft8<SIGN, T>(v);
+    dft8<SIGN, T>(v + 8);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) buf[swz<T>(t * 16 + r)] = v[r];
+    __syncthreads();
+}
+
+// Middle stages (radix 16, smem to smem) from span 2^DONE up to the last stage;
+// twr = the twiddle table region of (LOG2L, FIRST).
+template <int LOG2L, int FIRST, int SIGN, typename T, int DONE = FIRST>
+__device__ __forceinline__ void fft_middle(C_t<T>* buf, int t, const C_t<T>* __restrict__ twr) {
     constexpr int L = 1 << LOG2L;
-    if constexpr (DONE < LOG2L - StagePlan<LOG2L>::LAST_LOG) {
-        fft16_stage<16, (1 << DONE), L, SIGN, T>(buf, t);
-        fft_middle<LOG2L, SIGN, T, DONE + 4>(buf, t);
+    if constexpr (DONE < LOG2L - StagePlan<LOG2L, FIRST>::LAST_LOG) {
+        fft16_stage<16, (1 << DONE), L, SIGN, T>(buf, t, twr + tw_off(LOG2L, FIRST, DONE));
+        fft_middle<LOG2L, FIRST, SIGN, T, DONE + 4>(buf, t, twr);
     }
 }
 
 // Last stage (radix LAST_R, span LAST_NS = L / LAST_R) from smem into
 // registers: v[jb R + r] is output jj + r LAST_NS, jj = t + jb L/16.
-template <int LOG2L, int SIGN, typename T>
-__device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T>* v) {
+template <int LOG2L, int FIRST, int SIGN, typename T>
+__device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T>* v,
+                                                 const C_t<T>* __restrict__ twr) {
     using C = C_t<T>;
-    using SP = StagePlan<LOG2L>;
+    using SP = StagePlan<LOG2L, FIRST>;
     constexpr int L = 1 << LOG2L, R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R, NTHR = L / 16;
+    const C* tws = twr + tw_off(LOG2L, FIRST, LOG2L - SP::LAST_LOG);
 #pragma unroll
     for (int jb = 0; jb < J; ++jb) {
-        const int jj = t + jb * NTHR;   // < NS, so k = jj
+        const int jj = t + jb * NTHR;   // < LAST_NS, so k = jj
 #pragma unroll
         for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
-        C w[R];
-        twiddle_powers<R, T>((T)(2 * SIGN) * (T)jj * (T)(1.0 / L), w);
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], w[r]);
+        for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], tw_load<SIGN>(tws + (r - 1) * NS + jj));
         C* a = v + jb * R;
         if constexpr (R == 16) dft16<SIGN, T>(a);
         if constexpr (R == 8) dft8<SIGN, T>(a);
@@ -235,15 +240,32 @@ __device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T
     }
 }
 
-// Columns (pass 1) or rows (pass 2) per CTA: 64 contiguous bytes per global row
-// segment where the thread budget allows (<= 1024 threads for float, <= 512
-// for double, L/16 per FFT).
-template <typename T, int LOG2L>
+// Thread budgets per CTA of the two passes (float / double).  Pass 2 runs two
+// CTAs per SM so that one CTA's loads overlap the other's shared-memory stages.
+#ifndef FL_P1_THREADS_F32
+#define FL_P1_THREADS_F32 1024
+#endif
+#ifndef FL_P2_THREADS_F32
+#define FL_P2_THREADS_F32 512
+#endif
+#ifndef FL_P1_THREADS_F64
+#define FL_P1_THREADS_F64 512
+#endif
+#ifndef FL_P2_THREADS_F64
+#define FL_P2_THREADS_F64 512
+#endif
+template <typename T> struct PassBudget {
+    static constexpr int P1 = sizeof(T) == 4 ? FL_P1_THREADS_F32 : FL_P1_THREADS_F64;
+    static constexpr int P2 = sizeof(T) == 4 ? FL_P2_THREADS_F32 : FL_P2_THREADS_F64;
+};
+
+// Columns (pass 1) or rows (pass 2) per CTA: up to 64 contiguous bytes per
+// global row segment within the thread budget TMAX (L/16 threads per FFT).
+template <typename T, int LOG2L, int TMAX>
 struct PassTile {
     static constexpr int L = 1 << LOG2L;
     static constexpr int EPT = 16;                       // elements per thread
     static constexpr int W0 = (int)(64 / sizeof(C_t<T>));
-    static constexpr int TMAX = sizeof(T) == 4 ? 1024 : 512;
     static constexpr int WMIN = 32 / (L / EPT) > W0 ? 32 / (L / EPT) : W0;   // >= one warp
     static constexpr int TILES = (WMIN * (L / EPT) <= TMAX) ? WMIN : (TMAX / (L / EPT));
     static constexpr int LOG2T = TILES == 8 ? 3 : TILES == 4 ? 2 : TILES == 2 ? 1 : 0;
@@ -255,8 +277,10 @@ struct PassTile {
     static constexpr int P = (int)(128 / sizeof(C_t<T>));
     static constexpr int LD = L + (TILES >= P ? 1 : P / TILES);
     static constexpr size_t SMEM = (size_t)TILES * LD * sizeof(C_t<T>);
-    // register budget: 64 per thread for float, 128 for double
-    static constexpr int MINB = (TMAX / NT) > 0 ? (TMAX / NT) : 1;
+    // register budget: 64 per thread for float (1024 threads per SM), 128 for
+    // double (512)
+    static constexpr int REGT = sizeof(T) == 4 ? 1024 : 512;
+    static constexpr int MINB = (REGT / NT) > 0 ? (REGT / NT) : 1;
 };
 
 // Pass 1 for a tile of TILES columns i1 of one right-hand side s: the
@@ -264,12 +288,13 @@ struct PassTile {
 // stored to Y[l2 n1 + i1].  MODE 0: x generated by prep_value (forward);
 // MODE 1: x read from the band grid (adjoint).
 template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
-__global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MINB)
+__global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
+                                  PassTile<T, LOG2L, PassBudget<T>::P1>::MINB)
     k_pass1(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n1,
             const C_t<T>* __restrict__ c, const T* __restrict__ D, const C_t<T>* __restrict__ src,
-            C_t<T>* __restrict__ Y) {
+            C_t<T>* __restrict__ Y, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
-    using PT = PassTile<T, LOG2L>;
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P1>;
     using SP = StagePlan<LOG2L>;
     constexpr int L = PT::L, TC = PT::TILES, LD = PT::LD;
     extern __shared__ unsigned char smem_raw[];
@@ -301,24 +326,33 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
 #pragma unroll
         for (int r = 0; r < 16; ++r) v[r] = in[i1 + ((t + r * (L / 16)) << log2n1)];
     }
+    const C* twr = tw + tw_region(LOG2L, 4);
     fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
-    fft_middle<LOG2L, SIGN, T>(buf, t);
-    fft_last_to_regs<LOG2L, SIGN, T>(buf, t, v);
-    // outputs l2 = jj + r NS, twiddled by exp(SIGN 2 pi i i1 l2 / n) =
-    // exp(.. i1 jj) * exp(.. i1 NS)^r (sincospi values and short products)
+    fft_middle<LOG2L, 4, SIGN, T>(buf, t, twr);
+    fft_last_to_regs<LOG2L, 4, SIGN, T>(buf, t, v, twr);
+    // outputs l2 = jj + r NS, jj = t + jb L/16, twiddled by exp(SIGN 2 pi i i1 l2 / n)
+    // = w0 rho^jb step^r with w0 = exp(.. i1 t), rho = exp(.. i1 L/16) and
+    // step = exp(.. i1 NS): three sincospi values and short products
     constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
     const T inv_n = (T)1 / (T)n;                  // a power of two
     int es = (i1 * NS) & (n - 1);                 // i1 NS < n
     if (es >= n / 2) es -= n;
     C step[R];
     twiddle_powers<R, T>((T)(2 * SIGN) * (T)es * inv_n, step);
+    int e0 = i1 * t;                              // < n
+    if (e0 >= n / 2) e0 -= n;
+    C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
+    C rho = C{(T)1, (T)0};
+    if constexpr (J > 1) {
+        int er = i1 * (L / 16);                   // < n / 16
+        if (er >= n / 2) er -= n;
+        rho = expipi<T>((T)(2 * SIGN) * (T)er * inv_n);
+    }
     C* out = Y + item.y_off;
 #pragma unroll
     for (int jb = 0; jb < J; ++jb) {
         const int jj = t + jb * (L / 16);
-        int e0 = i1 * jj;                         // < n
-        if (e0 >= n / 2) e0 -= n;
-        const C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
+        if (jb > 0) w0 = cmul(w0, rho);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int l2 = jj + r * NS;
@@ -329,14 +363,18 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
 
 // Pass 2 for a tile of TILES rows l2: the length-n1 FFTs over i1 of
 // Y[l2 n1 + i1], stored to X[l2 + n2 l1] (natural order of the length-n
-// transform) in the band grid.
+// transform) in the band grid.  For float rows of 2^(4j+3) points the first
+// stage is radix 8 with two butterflies per thread, so each thread reads 8
+// pairs of adjacent elements with 16-byte loads.
 template <typename T, int SIGN, int LOG2L>
-__global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MINB)
+__global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P2>::NT,
+                                  PassTile<T, LOG2L, PassBudget<T>::P2>::MINB)
     k_pass2(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n2,
-            const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst) {
+            const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
-    using PT = PassTile<T, LOG2L>;
-    constexpr int L = PT::L, TR = PT::TILES, NT = PT::NT, LD = PT::LD;
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P2>;
+    constexpr int L = PT::L, TR = PT::TILES, LD = PT::LD;
+    constexpr int FIRST = (sizeof(T) == 4 && LOG2L % 4 == 3) ? 3 : 4;
     extern __shared__ unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     const PassItem item = items[blockIdx.y];
@@ -346,23 +384,36 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
     const int l2b = blockIdx.x * TR;
     const int tid = threadIdx.x;
     const C* in = Y + item.y_off + (int64_t)l2b * L;
+    const C* twr = tw + tw_region(LOG2L, FIRST);
     // first stage straight from the rows (consecutive threads, consecutive i1)
     {
         const int row = tid / (L / 16), t = tid & (L / 16 - 1);
         C v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = in[(int64_t)row * L + t + r * (L / 16)];
         C* buf = sm + row * LD;
-        fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
-        fft_middle<LOG2L, SIGN, T>(buf, t);
+        if constexpr (FIRST == 3) {
+            // pair t + r L/16 holds elements 2t + r L/8 and 2t + 1 + r L/8
+            const float4* in4 = reinterpret_cast<const float4*>(in + (int64_t)row * L);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 q2 = in4[t + r * (L / 16)];
+                v[r] = C{q2.x, q2.y};
+                v[8 + r] = C{q2.z, q2.w};
+            }
+            fft_first8x2_from_regs<LOG2L, SIGN, T>(v, buf, t);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[r] = in[(int64_t)row * L + t + r * (L / 16)];
+            fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
+        }
+        fft_middle<LOG2L, FIRST, SIGN, T>(buf, t, twr);
     }
     // last stage with rows fastest: the warp's stores are TR-row segments of X
     {
-        using SP = StagePlan<LOG2L>;
+        using SP = StagePlan<LOG2L, FIRST>;
         constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
         const int row = tid & (TR - 1), t = tid >> PT::LOG2T;
         C v[16];
-        fft_last_to_regs<LOG2L, SIGN, T>(sm + row * LD, t, v);
+        fft_last_to_regs<LOG2L, FIRST, SIGN, T>(sm + row * LD, t, v, twr);
         C* out = dst + B.grid_off + (int64_t)s * n + l2b + row;
 #pragma unroll
         for (int jb = 0; jb < J; ++jb) {
@@ -381,29 +432,29 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L>::NT, PassTile<T, LOG2L>::MI
 template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
 static cudaError_t pass1_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
                             const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
-                            cudaStream_t st) {
-    using PT = PassTile<T, LOG2L>;
+                            const C_t<T>* tw, cudaStream_t st) {
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P1>;
     auto k = k_pass1<T, SIGN, MODE, DERIV, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     k<<<dim3((unsigned)((1 << log2n1) / PT::TILES), (unsigned)nitems), PT::NT, PT::SMEM, st>>>(
-        items, bands, log2n1, c, D, src, Y);
+        items, bands, log2n1, c, D, src, Y, tw);
     return cudaGetLastError();
 }
 
 template <typename T, int SIGN, int LOG2L>
 static cudaError_t pass2_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n2,
-                            const C_t<T>* Y, C_t<T>* dst, cudaStream_t st) {
-    using PT = PassTile<T, LOG2L>;
+                            const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw, cudaStream_t st) {
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P2>;
     auto k = k_pass2<T, SIGN, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     k<<<dim3((unsigned)((1 << log2n2) / PT::TILES), (unsigned)nitems), PT::NT, PT::SMEM, st>>>(
-        items, bands, log2n2, Y, dst);
+        items, bands, log2n2, Y, dst, tw);
     return cudaGetLastError();
 }
 
@@ -411,10 +462,10 @@ static cudaError_t pass2_ct(const PassItem* items, int nitems, const BandDev* ba
 template <typename T, int SIGN, int MODE, bool DERIV>
 cudaError_t launch_pass1(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
                          int log2n2, const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
-                         cudaStream_t st) {
+                         const C_t<T>* tw, cudaStream_t st) {
     switch (log2n2) {
 #define FL_P1(LG) \
-    case LG: return pass1_ct<T, SIGN, MODE, DERIV, LG>(items, nitems, bands, log2n1, c, D, src, Y, st);
+    case LG: return pass1_ct<T, SIGN, MODE, DERIV, LG>(items, nitems, bands, log2n1, c, D, src, Y, tw, st);
         FL_P1(6) FL_P1(7) FL_P1(8) FL_P1(9) FL_P1(10) FL_P1(11) FL_P1(12)
 #undef FL_P1
         default: return cudaErrorInvalidValue;
@@ -424,10 +475,11 @@ cudaError_t launch_pass1(const PassItem* items, int nitems, const BandDev* bands
 // Pass 2 (length n1 = 2^log2n1, 7..12) over all n2 = 2^log2n2 rows.
 template <typename T, int SIGN>
 cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
-                         int log2n2, const C_t<T>* Y, C_t<T>* dst, cudaStream_t st) {
+                         int log2n2, const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw,
+                         cudaStream_t st) {
     switch (log2n1) {
 #define FL_P2(LG) \
-    case LG: return pass2_ct<T, SIGN, LG>(items, nitems, bands, log2n2, Y, dst, st);
+    case LG: return pass2_ct<T, SIGN, LG>(items, nitems, bands, log2n2, Y, dst, tw, st);
         FL_P2(6) FL_P2(7) FL_P2(8) FL_P2(9) FL_P2(10) FL_P2(11) FL_P2(12)
 #undef FL_P2
         default: return cudaErrorInvalidValue;
@@ -435,9 +487,9 @@ cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands
 }
 
 #define FL_P1_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, const T*, \
-                     const C_t<T>*, C_t<T>*, cudaStream_t
+                     const C_t<T>*, C_t<T>*, const C_t<T>*, cudaStream_t
 #define FL_P2_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, C_t<T>*, \
-                     cudaStream_t
+                     const C_t<T>*, cudaStream_t
 #define FL_FFT_EXTERN(T)                                                   \
     extern template cudaError_t launch_pass1<T, 1, 0, false>(FL_P1_SIG(T)); \
     extern template cudaError_t launch_pass1<T, 1, 0, true>(FL_P1_SIG(T));  \

@@ -148,6 +148,7 @@ struct Plan {
     void* d_D = nullptr;           // weight tables (T)
     void* d_grid = nullptr;        // band grids (complex T)
     void* d_Y = nullptr;           // four-step intermediate (complex T)
+    void* d_tw = nullptr;          // four-step stage twiddles (complex T, kTwEntries)
     void* d_stage_c = nullptr;     // staging for fl_execute_host
     void* d_stage_f = nullptr;
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
@@ -200,6 +201,7 @@ cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, con
 // Launchers (fl_transform.cu)
 cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st);
 cudaError_t build_cheb(Plan& p, cudaStream_t st);
+cudaError_t build_twiddles(Plan& p, cudaStream_t st);
 // rmul != nullptr: f[j] = rmul[j] * conj(result_j) (the node-gradient epilogue)
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul = nullptr);

@@ -147,6 +147,41 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
     return e;
 }
 
+// Stage twiddles of the four-step passes: entry (r - 1) NS + k of the stage of
+// span NS = 2^d and radix R in region (LOG2L, FIRST) is exp(2 pi i r k / (NS R)),
+// computed in FP64 (exact argument: r k < NS R, a power of two) and rounded
+// once to T.  Unused entries are zero.
+template <typename T>
+__global__ void k_twiddles(C_t<T>* __restrict__ tw) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kTwEntries) return;
+    const int region = (int)(i / kTwRegion), e = (int)(i % kTwRegion);
+    const int LOG2L = kTwMinLog + region / 2, FIRST = 3 + region % 2;
+    C_t<T> v{(T)0, (T)0};
+    if (LOG2L > FIRST) {
+        for (int d = FIRST; d < LOG2L; d += 4) {
+            const int NS = 1 << d, R = 1 << tw_stage_log(LOG2L, FIRST, d);
+            const int off = tw_off(LOG2L, FIRST, d);
+            if (e >= off && e < off + (R - 1) * NS) {
+                const int r = (e - off) / NS + 1, k = (e - off) % NS;
+                double sn, cs;
+                sincospi(2.0 * (double)(r * k) / (double)(NS * R), &sn, &cs);
+                v = C_t<T>{(T)cs, (T)sn};
+            }
+        }
+    }
+    tw[i] = v;
+}
+
+cudaError_t build_twiddles(Plan& p, cudaStream_t st) {
+    const unsigned blocks = (unsigned)((kTwEntries + 255) / 256);
+    if (p.prec == FL_FP64)
+        k_twiddles<double><<<blocks, 256, 0, st>>>((C_t<double>*)p.d_tw);
+    else
+        k_twiddles<float><<<blocks, 256, 0, st>>>((C_t<float>*)p.d_tw);
+    return cudaGetLastError();
+}
+
 cudaError_t build_cheb(Plan& p, cudaStream_t st) {
     k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb);
     return cudaGetLastError();
@@ -545,12 +580,13 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         int slot;
         timer_begin(p, "fft_pass1", b1, st, &slot);
         e = launch_pass1<T, SIGN, MODE, DERIV>(p.d_pass + g.start, g.count, p.d_bands, l1, l2,
-                                               (const C*)c, (const T*)p.d_D, grid, (C*)p.d_Y, st);
+                                               (const C*)c, (const T*)p.d_D, grid, (C*)p.d_Y,
+                                               (const C*)p.d_tw, st);
         timer_end(p, slot, st);
         if (e != cudaSuccess) return e;
         timer_begin(p, "fft_pass2", b2, st, &slot);
         e = launch_pass2<T, SIGN>(p.d_pass + g.start, g.count, p.d_bands, l1, l2, (const C*)p.d_Y,
-                                  grid, st);
+                                  grid, (const C*)p.d_tw, st);
         timer_end(p, slot, st);
         p.launches += 2;
         if (e != cudaSuccess) return e;
