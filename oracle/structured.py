@@ -312,3 +312,75 @@ def xflt_alg2(c, w, eps: float, q: int | None = None):
             fm = fm + (Ly * F).sum(axis=1)
         f[sel] = fm
     return f, P
+
+
+# --------------------------------------------------------------------------
+# One-sided variant of Algorithm 2: interpolation in y only.
+#
+# For fixed frequency k, g(y) = exp(-y k) on A = Y_m = (a, 2a] is replaced by
+# its Chebyshev interpolant sum_s L_s^A(y) exp(-y_s^A k) -- the first of the
+# two interpolations in the proof of Theorem 3.1 (asymptotically smooth
+# kernels).  The error formula of Section 2 with diam A = a and
+# max_A |g^(q)| = k^q exp(-a k) bounds one entry by
+#     2 (k a / 4)^q exp(-k a) / q!  <=  2 q^q exp(-q) / (4^q q!)
+# (the maximum over k a >= 0 is at k a = q).  Frequencies with k a >
+# ln(1/eps_K) are dropped exactly as region (ii) of Algorithm 2 (l < l_m).
+
+def onesided_entry_bound(ka, q: int) -> np.ndarray:
+    """2 (ka/4)^q exp(-ka) / q!: per-entry bound of the one-sided interpolation."""
+    ka = np.asarray(ka, dtype=np.float64)
+    return np.exp(math.log(2.0) + q * np.log(np.maximum(ka, 1e-300) / 4.0) - ka
+                  - math.lgamma(q + 1.0)) * (ka > 0)
+
+
+def rank_q_onesided(eps: float, qmax: int = 64) -> int:
+    """Smallest q with 2 q^q e^-q / (4^q q!) <= eps (the bound maximised over k a)."""
+    for q in range(1, qmax + 1):
+        if float(onesided_entry_bound(float(q), q)) <= eps:
+            return q
+    raise ValueError("eps too small")
+
+
+def xflt_alg2_onesided(c, w, eps: float, q: int | None = None):
+    """The one-sided variant step by step with exact NDFTs; returns (f~, q).
+
+    Bands, Z^0 and the Y_M band as in xflt_alg2; band m < M keeps the
+    frequencies of Omega_l, l >= l_m, and weights frequency k of right-hand
+    side s by exp(-y_s k) at the Chebyshev points y_s of Y_m.
+    """
+    c = np.asarray(c, dtype=np.complex128)
+    w = np.asarray(w)
+    if not np.iscomplexobj(w):
+        w = np.asarray(w, dtype=np.float64).reshape(-1, 2)
+        x, yim = w[:, 0], w[:, 1]
+    else:
+        x, yim = w.real, w.imag
+    N = c.size
+    P = xflt_params(N, eps)
+    p = P.lap
+    qq = rank_q_onesided(P.eps_K) if q is None else int(q)
+    y = 2.0 * np.pi * yim
+    f = np.zeros(x.shape, dtype=np.complex128)
+    kall = np.arange(N)
+    if N == 1:
+        f[:] = c[0]
+        return f, qq
+    z0 = y > P.y1
+    f[z0] = c[0]
+    bx = np.where(z0, 0, band_of(y, P.y1, p.M))
+    bk = band_of(kall.astype(np.float64), P.xi1, p.M)
+    sel = bx == p.M
+    if sel.any():
+        f[sel] = ndft(c, kall, x[sel])
+    for m in range(1, p.M):
+        sel = bx == m
+        if not sel.any():
+            continue
+        ya, yb = band_interval(P.y1, m)
+        ys = interval_points(ya, yb, qq)
+        kk = kall[bk >= p.ell[m]]
+        W = np.exp(-np.outer(kk.astype(np.float64), ys))          # (K, q)
+        F = ndft(c[kk][:, None] * W, kk, x[sel])                   # (M_m, q)
+        Ly = lagrange_barycentric(y[sel], ya, yb, qq)
+        f[sel] = (Ly * F).sum(axis=1)
+    return f, qq

@@ -12,6 +12,11 @@ What the paper fixes and is checked here:
 * Lemma 4.2 (Hadamard identity) on random dense matrices, to roundoff.
 * Theorem 4.3 / Algorithm 2 (exact NDFT): E <= eps against the plain oracle;
   Z^0 nodes return c_0; nodes on |z| = 1 reduce to the DFT.
+* One-sided variant (interpolation in y only, first term of the proof of
+  Theorem 3.1): every entry within the bound 2 (ka/4)^q e^-ka / q! of the
+  error formula of Section 2 (checked on a dense y grid); the rank rule is the
+  smallest q whose bound, maximised over ka by brute force, is <= eps/3;
+  E <= eps on three node distributions; E decreases with q.
 """
 import math
 
@@ -170,3 +175,65 @@ def test_algorithm2_special_cases():
     # N = 1: f = c_0 everywhere
     f1, _ = S.xflt_alg2(c[:1], W.nodes_disk_uniform(5, 0), 1e-6)
     assert np.array_equal(f1, np.full(5, c[0]))
+
+
+# --------------------------------------------------------------------------
+# One-sided variant
+
+@pytest.mark.parametrize("q", [4, 8, 10, 14])
+def test_onesided_entries_within_interpolation_bound(q):
+    y1 = math.log(1e6)
+    for m in (3, 9, 17):
+        a, b = S.band_interval(y1, m)
+        ys = S.interval_points(a, b, q)
+        yg = np.linspace(a, b, 2001)
+        L = S.lagrange_barycentric(yg, a, b, q)
+        for ka in (0.1, 1.0, q / 2.0, float(q), 2.0 * q, 40.0):
+            k = ka / a
+            err = np.max(np.abs(np.exp(-yg * k) - L @ np.exp(-ys * k)))
+            assert err <= float(S.onesided_entry_bound(ka, q)) * (1 + 1e-9) + 1e-15, (m, ka, err)
+            if ka == 1.0 and q <= 10:
+                # for small k a the derivative bound is nearly attained: the
+                # formula's constant is not loose by more than a small factor
+                assert err >= float(S.onesided_entry_bound(ka, q)) / 3.0, (m, q, err)
+
+
+def test_onesided_rank_rule_by_brute_force():
+    kag = np.linspace(0.0, 200.0, 400001)
+    for eps in (1e-3, 1e-6 / 3, 1e-10 / 3, 1e-12 / 3):
+        q = S.rank_q_onesided(eps)
+        worst = lambda qq: float(np.max(S.onesided_entry_bound(kag, qq)))
+        assert worst(q) <= eps * (1 + 1e-6)
+        assert worst(q - 1) > eps
+    assert S.rank_q_onesided(1e-6 / 3) == 10 and S.rank_q_onesided(1e-12 / 3) == 20
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
+@pytest.mark.parametrize("kind", ["disk", "clustered", "paper"])
+def test_onesided_meets_eps(eps, kind):
+    N, M = 512, 256
+    c = W.coefficients(N, seed=22)
+    if kind == "disk":
+        w = W.nodes_disk_uniform(M, seed=23)
+    elif kind == "clustered":
+        w = W.nodes_circle_clustered(M, seed=24)
+    else:
+        w = W.nodes_paper_section5(M, S.rank_q(eps), seed=25)
+    f = oracle.flt_direct(c, w)
+    fa, q = S.xflt_alg2_onesided(c, w, eps)
+    assert q == S.rank_q_onesided(eps / 3)
+    assert oracle.error_E(f, fa, c) <= eps
+
+
+def test_onesided_error_decreases_with_q():
+    N, M = 400, 300
+    c = W.coefficients(N, seed=31)
+    w = W.nodes_disk_uniform(M, seed=32)
+    f = oracle.flt_direct(c, w)
+    errs = [oracle.error_E(f, S.xflt_alg2_onesided(c, w, 1e-12, q=q)[0], c) for q in (3, 5, 7, 9)]
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    # Z^0 and the Y_M band are those of Algorithm 2
+    w0 = np.array([[0.25, 5.0], [0.5, 0.0]])
+    f0, _ = S.xflt_alg2_onesided(c, w0, 1e-6)
+    assert f0[0] == c[0]
+    assert abs(f0[1] - np.sum(c * (-1.0) ** np.arange(N))) < 1e-12 * np.sum(np.abs(c))
