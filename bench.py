@@ -492,6 +492,29 @@ def run_ours(args):
         fp64["fp32_speedup_vs_fp64_same_eps"] = fp64["eps1e-6"]["ms_per_step"] / ms
         fp64["fp32_speedup_vs_fp64_eps1e-12"] = fp64["eps1e-12"]["ms_per_step"] / ms
 
+    # one-sided variant (interpolation in y only; q from its own bound), FP32
+    onesided = None
+    f_os = None
+    if not args.no_configs:
+        pos = fl.Plan(N, nodes, EPS32, precision="fp32", autotune=True, variant="onesided")
+        out = torch.empty(M, dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            pos.execute(c, out=out)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(max(3, args.steps // 2))]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            pos.execute(c, out=out)
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms_os = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+        onesided = {"ms_per_step": ms_os, "value": job_value(1, N, M, ms_os), "q": pos.info()["q"],
+                    "eps": EPS32, "speedup_vs_alg2": ms / ms_os}
+        f_os = out.cpu().numpy().astype(np.complex128)
+        pos.close()
+
     configs = None
     if not args.no_configs:
         configs = secondary_workloads(dev, flush, rank)
@@ -507,6 +530,8 @@ def run_ours(args):
         errors["fp32_eps1e-6"] = error_E(ref, f_fp32[idx], c128)
         for tag, res in f64_results.items():
             errors["fp64_" + tag] = error_E(ref, res[idx], c128)
+        if f_os is not None:
+            errors["fp32_onesided_eps1e-6"] = error_E(ref, f_os[idx], c128)
 
     if dist:
         dist.barrier()
@@ -529,6 +554,7 @@ def run_ours(args):
         "plan_ms": plan_ms,
         "E": errors or None,
         "fp64": fp64 or None,
+        "onesided_fp32": onesided,
         "roofline": roof,
         "kernels": kernel_table,
         "model_bytes_per_step": info["model_bytes"],

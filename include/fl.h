@@ -78,6 +78,7 @@ typedef struct {
     double model_bytes;       /* algorithmic HBM bytes of one fl_execute */
     double direct_bias;       /* route bias in use (the autotuner's choice if tuned) */
     double scratch_bytes;     /* device memory owned by the plan */
+    int variant;              /* fl_options.variant in use */
 } fl_info;
 
 /* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
@@ -130,6 +131,17 @@ typedef struct {
                              values of direct_bias, time an execute of each on
                              `stream` and keep the fastest (cached per workload
                              signature for the process); 0 = off              */
+    int variant;          /* weights of an interpolated band Y_m:
+                             0 = Algorithm 2 (default): Chebyshev interpolation
+                                 in y and in the frequency (Lemma 4.2, q from
+                                 Definition 3.2);
+                             1 = one-sided: interpolation in y only, each
+                                 frequency k weighted by the exact
+                                 exp(-y_s k) at the band's Chebyshev points y_s
+                                 (the first term of the proof of Theorem 3.1);
+                                 q = 0 then means the smallest q with
+                                 2 q^q e^-q / (4^q q!) <= eps/3, the
+                                 per-entry bound of that interpolation.       */
 } fl_options;
 
 /*

@@ -89,10 +89,28 @@ static int window_width(double eps, double sigma) {
 
 // Parameters of Algorithm 2 (Section 4) with the error split of Lemma 4.1 that
 // do not depend on N: q, y_1 = ln(1/eps), the window.
+// One-sided interpolation rank: the smallest q whose per-entry bound
+// max_k |exp(-y k) - sum_s L_s(y) exp(-y_s k)| <= 2 q^q e^-q / (4^q q!) on a
+// band (a, 2a] is at most eps_K.  The bound is the interpolation error formula
+// of Section 2 with diam = a and max |d^q/dy^q exp(-y k)| = k^q exp(-a k),
+// maximised over k a = q.
+static int onesided_rank(double eps_K) {
+    for (int q = 1; q <= kMaxQ; ++q) {
+        const double lb = log(2.0) + q * log((double)q) - q - q * log(4.0) - lgamma(q + 1.0);
+        if (lb <= log(eps_K)) return q;
+    }
+    return kMaxQ + 1;
+}
+
 static fl_status select_common(Plan& p, int q_in) {
     p.eps_K = p.eps / 3.0;
     p.eps_A = p.eps / 3.0;
-    p.q = q_in > 0 ? q_in : (int)ceil(0.5 + log(1.0 / p.eps_K) / log(4.0));
+    if (q_in > 0)
+        p.q = q_in;
+    else if (p.variant == 1)
+        p.q = onesided_rank(p.eps_K);
+    else
+        p.q = (int)ceil(0.5 + log(1.0 / p.eps_K) / log(4.0));
     if (p.q > kMaxQ) return fail(FL_EUNSUPPORTED, "interpolation rank q above 40");
     p.y1 = log(1.0 / p.eps);            // Z^0 removed: y in [0, ln(1/eps)]
     p.mw = window_width(p.eps_A, 2.0);
@@ -461,6 +479,7 @@ struct PlanSpec {
     int route_mode;
     int rhs_per_launch;
     bool use_graph;
+    int variant;
 };
 
 static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cudaStream_t st) {
@@ -474,6 +493,7 @@ static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cu
     h->p.direct_bias = bias;
     h->p.rhs_per_launch = sp.rhs_per_launch;
     h->p.use_graph = sp.use_graph;
+    h->p.variant = sp.variant;
     fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, st);
     if (s != FL_OK) {
         delete h;
@@ -502,6 +522,8 @@ static uint64_t plan_signature(const Plan& p) {
     uint64_t e;
     memcpy(&e, &p.eps, sizeof(e));
     mix(e);
+    mix((uint64_t)p.q);
+    mix((uint64_t)p.variant);
     for (const BandHost& bh : p.bands) mix((uint64_t)bh.nodes * 131 + (uint64_t)bh.local);
     return h;
 }
@@ -649,7 +671,7 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
                      double eps, fl_precision prec, const fl_options* opt, void* stream) {
     g_err.clear();
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0))
+                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1))
         return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
@@ -661,7 +683,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan: unknown precision");
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
     PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
-                 opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false};
+                 opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false,
+                 opt ? opt->variant : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -744,10 +767,11 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
     if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
     if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0))
+                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1))
         return fail(FL_EINVAL, "fl_plan_batched: invalid options");
     PlanSpec sp{B, N_host, M_host, nodes_dev, q, eps, prec, true, opt ? opt->route : 0,
-                 opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true};
+                 opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true,
+                 opt ? opt->variant : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -803,6 +827,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->model_bytes = p.model_bytes;
     info->direct_bias = p.tuned_bias > 0 ? p.tuned_bias : p.direct_bias;
     info->scratch_bytes = p.scratch_bytes;
+    info->variant = p.variant;
     return FL_OK;
 }
 

@@ -116,6 +116,7 @@ struct Plan {
     std::vector<PassGroup> pass_groups;
     int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
+    int variant = 0;               // 0 Algorithm 2 weights, 1 one-sided interpolation
     double direct_bias = 1.0;
     double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)
     std::vector<DirectItem> direct_work;

@@ -70,10 +70,12 @@ __global__ void k_coupling(double y1, double xi1, int m, int ellm, int Lm, int q
 
 // D[s K + k] = W_{k,s} / Phi(k'/n), k' = k - N_m/2, with the Kaiser-Bessel
 // transform Phi(nu) = pi I_0(m_w sqrt(b^2 - (2 pi nu)^2)) (window in grid units).
+// one_sided: W_{k,s} = exp(-y_s k) at the band's Chebyshev points y_s (the
+// interpolation in y alone, first term of the proof of Theorem 3.1).
 template <typename T>
 __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int levels,
                           const double* __restrict__ cheb, const double* __restrict__ Kt,
-                          int mw, double kb_b, T* __restrict__ D) {
+                          int mw, double kb_b, int one_sided, T* __restrict__ D) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= B.K) return;
     const double nu = (double)(k - B.Nm / 2) / (double)B.n;
@@ -82,6 +84,13 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
     T* Dk = D + B.D_off;
     if (B.nrhs == 1) {
         Dk[k] = (T)inv_phi;
+        return;
+    }
+    if (one_sided) {
+        for (int s = 0; s < q; ++s) {
+            const double ys = B.yc + B.yh * cheb[s];
+            Dk[(int64_t)s * B.K + k] = (T)(exp(-ys * (double)k) * inv_phi);
+        }
         return;
     }
     const int l = band_of_freq((double)k, xi1, levels);
@@ -121,7 +130,7 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
     int64_t kt_max = 0;
     for (int lb = 1; lb <= in.levels; ++lb) {
         const BandHost& bh = p.bands[in.band_base + lb];
-        if (bh.dev.route != 1 || bh.dev.nrhs == 1) continue;
+        if (bh.dev.route != 1 || bh.dev.nrhs == 1 || p.variant == 1) continue;
         kt_max = std::max<int64_t>(kt_max, (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q);
     }
     if (kt_max > 0) {
@@ -131,13 +140,14 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
     for (int lb = 1; lb <= in.levels; ++lb) {
         const BandHost& bh = p.bands[in.band_base + lb];
         if (bh.dev.route != 1) continue;
-        if (bh.dev.nrhs > 1) {
+        if (bh.dev.nrhs > 1 && p.variant == 0) {
             const int64_t nk = (int64_t)(bh.Lm - bh.ell + 1) * p.q * p.q;
             k_coupling<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(p.y1, in.xi1, lb, bh.ell, bh.Lm,
                                                                      p.q, p.d_cheb, Kt);
         }
         k_weights<T><<<(unsigned)((bh.dev.K + 255) / 256), 256, 0, st>>>(
-            bh.dev, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, (T*)p.d_D);
+            bh.dev, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, p.variant,
+            (T*)p.d_D);
     }
     e = cudaGetLastError();
     if (Kt) {

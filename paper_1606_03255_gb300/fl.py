@@ -53,17 +53,19 @@ class fl_info(ctypes.Structure):
         ("band_K", ctypes.c_int64 * FL_MAX_LEVELS),
         ("band_n", ctypes.c_int64 * FL_MAX_LEVELS),
         ("model_bytes", ctypes.c_double), ("direct_bias", ctypes.c_double),
-        ("scratch_bytes", ctypes.c_double),
+        ("scratch_bytes", ctypes.c_double), ("variant", ctypes.c_int),
     ]
 
 
 class fl_options(ctypes.Structure):
     _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
                 ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("variant", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
+# band weights: Algorithm 2 (two-sided interpolation) or the one-sided variant
+VARIANTS = {"alg2": 0, "onesided": 1}
 
 
 class fl_timing(ctypes.Structure):
@@ -281,6 +283,7 @@ def info_dict(info: fl_info) -> dict:
         "band_n": list(info.band_n[:nb]),
         "model_bytes": info.model_bytes, "direct_bias": info.direct_bias,
         "scratch_bytes": info.scratch_bytes,
+        "variant": {v: k for k, v in VARIANTS.items()}.get(info.variant, info.variant),
     }
 
 
@@ -302,7 +305,8 @@ class Plan:
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
-                 rhs_per_launch: int = 0, use_graph: bool = False, autotune: bool = False):
+                 rhs_per_launch: int = 0, use_graph: bool = False, autotune: bool = False,
+                 variant: str = "alg2"):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -313,7 +317,7 @@ class Plan:
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)),
-                         int(bool(autotune)))
+                         int(bool(autotune)), VARIANTS[variant])
         st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
                            opt, _stream_handle(stream))
         check(st, "fl_plan")
@@ -397,7 +401,8 @@ class BatchedPlan:
 
     def __init__(self, Ns, Ms, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
-                 rhs_per_launch: int = 0, use_graph: bool = True, autotune: bool = False):
+                 rhs_per_launch: int = 0, use_graph: bool = True, autotune: bool = False,
+                 variant: str = "alg2"):
         torch = _torch()
         nodes = nodes.to(torch.float64).contiguous()
         self.Ns = [int(x) for x in Ns]
@@ -407,7 +412,7 @@ class BatchedPlan:
         self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
-                         1 if use_graph else -1, int(bool(autotune)))
+                         1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant])
         st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
                                 self.prec, opt, _stream_handle(stream))
         check(st, "fl_plan_batched")
