@@ -216,6 +216,18 @@ fl_status fl_execute_host(fl_plan_t p, const void *c_host, void *f_host, void *s
 fl_status fl_adjoint(fl_plan_t p, const void *r_dev, void *c_out_dev, void *stream);
 
 /*
+ * fl_transposed -- g_k = sum_j ghat_j z_j^k for k = 0 .. N-1, i.e. C^T ghat:
+ * the evaluation of g(xi) = sum_j ghat_j z_j^xi at the integer exponents
+ * xi = k that the remark after Algorithm 2 (Section 4) obtains from the
+ * adjoint algorithms; computed as conj(C^* conj(ghat)).
+ *   g_dev   : device, M complex (plan precision).
+ *   out_dev : device, N complex, overwritten.
+ * Accuracy as fl_adjoint.  The plan keeps an M-element staging buffer
+ * (allocated on the first call).  Not for batched plans (FL_EUNSUPPORTED).
+ */
+fl_status fl_transposed(fl_plan_t p, const void *g_dev, void *out_dev, void *stream);
+
+/*
  * fl_plan_laplace -- plan Algorithm 1 (Section 3) for the real discrete Laplace
  * transform f_j = sum_k c_k exp(-s_j t_k).
  *   t_dev : device, N float64 frequencies t_k >= 0.

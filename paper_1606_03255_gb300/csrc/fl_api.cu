@@ -38,7 +38,7 @@ static fl_status cuda_fail(cudaError_t e, const char* where) {
 Plan::~Plan() {
     if (gexec) cudaGraphExecDestroy(gexec);
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
-                    d_stage_c, d_stage_f, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
+                    d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
                     d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw};
     for (void* q : ptrs)
@@ -742,6 +742,15 @@ fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stre
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
+    return FL_OK;
+}
+
+fl_status fl_transposed(fl_plan_t h, const void* g_dev, void* out_dev, void* stream) {
+    if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_transposed: not a Fourier-Laplace plan");
+    if (!out_dev || (h->p.M > 0 && !g_dev)) return fail(FL_EINVAL, "fl_transposed: NULL buffer");
+    if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_transposed: batched plans are forward only");
+    cudaError_t e = run_transposed(h->p, g_dev, out_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fl_transposed");
     return FL_OK;
 }
 

@@ -39,12 +39,14 @@ template <typename T> __device__ __forceinline__ C_t<T> expipi(T x) {
 // Stage twiddle tables.  In a length-L transform whose first stage has radix
 // 2^FIRST, every later stage (radix R, span NS = 2^d) multiplies input r of job
 // jj by w^(r k), w = exp(SIGN 2 pi i / (NS R)), k = jj mod NS.  Those values are
-// tabulated at plan time (FP64, rounded once) for SIGN = +1 as
-//   tab[tw_region(LOG2L, FIRST) + tw_off(LOG2L, FIRST, d) + (r - 1) NS + k],
-// so a job reads its R - 1 factors at stride NS from its k (consecutive jobs,
-// consecutive entries) and SIGN = -1 takes the conjugate.
+// tabulated at plan time (FP64, rounded once) for SIGN = +1 in pairs
+// (r, r + 1) = (2p + 1, 2p + 2):
+//   tab[tw_region(LOG2L, FIRST) + tw_off(LOG2L, FIRST, d) + 2 NS p + 2 k + (r - 1) % 2],
+// so a job reads its R - 1 factors as R/2 adjacent pairs (one 16-byte load
+// each in float; consecutive jobs, consecutive pairs) and SIGN = -1 takes the
+// conjugate.  The pair slot of r = R (beyond the last factor) holds zero.
 constexpr int kTwMinLog = 6, kTwMaxLog = 12;
-constexpr int kTwRegion = 1 << kTwMaxLog;                   // entries per (LOG2L, FIRST)
+constexpr int kTwRegion = 2 << kTwMaxLog;                   // entries per (LOG2L, FIRST)
 constexpr int kTwEntries = (kTwMaxLog - kTwMinLog + 1) * 2 * kTwRegion;
 
 __host__ __device__ constexpr int tw_last_log(int LOG2L, int FIRST) {
@@ -56,7 +58,7 @@ __host__ __device__ constexpr int tw_stage_log(int LOG2L, int FIRST, int d) {
 }
 __host__ __device__ constexpr int tw_off(int LOG2L, int FIRST, int d) {
     int off = 0;
-    for (int e = FIRST; e < d; e += 4) off += ((1 << tw_stage_log(LOG2L, FIRST, e)) - 1) << e;
+    for (int e = FIRST; e < d; e += 4) off += (1 << tw_stage_log(LOG2L, FIRST, e)) << e;
     return off;
 }
 __host__ __device__ constexpr int tw_region(int LOG2L, int FIRST) {

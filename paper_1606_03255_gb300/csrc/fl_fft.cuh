@@ -130,10 +130,32 @@ __device__ __forceinline__ void twiddle_powers(T x, C_t<T>* w) {
 
 // Stage twiddles come from the plan-time table laid out by tw_region / tw_off
 // (fl_common.cuh); SIGN = -1 takes the conjugate.
-template <int SIGN, typename C> __device__ __forceinline__ C tw_load(const C* p) {
-    C w = __ldg(p);
-    if (SIGN < 0) w.y = -w.y;
-    return w;
+// The twiddle pair at p (entries p[0], p[1]): one 16-byte load in float.
+template <int SIGN> __device__ __forceinline__ void tw_load2(const float2* p, float2& a, float2& b) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    a = float2{q.x, SIGN < 0 ? -q.y : q.y};
+    b = float2{q.z, SIGN < 0 ? -q.w : q.w};
+}
+template <int SIGN> __device__ __forceinline__ void tw_load2(const double2* p, double2& a, double2& b) {
+    a = __ldg(p);
+    b = __ldg(p + 1);
+    if (SIGN < 0) {
+        a.y = -a.y;
+        b.y = -b.y;
+    }
+}
+
+// v[1 .. R-1] *= w^(r k) from the stage table tws (pairs, see fl_common.cuh).
+template <int R, int NS, int SIGN, typename C>
+__device__ __forceinline__ void apply_stage_twiddles(C* v, const C* __restrict__ tws, int k) {
+    const C* tk = tws + 2 * k;
+#pragma unroll
+    for (int p = 0; p < R / 2; ++p) {
+        C w1, w2;
+        tw_load2<SIGN>(tk + p * 2 * NS, w1, w2);
+        v[2 * p + 1] = cmul(v[2 * p + 1], w1);
+        if (2 * p + 2 < R) v[2 * p + 2] = cmul(v[2 * p + 2], w2);
+    }
 }
 
 template <int R, int NS, int L, int SIGN, typename T>
@@ -148,11 +170,7 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __
         const int k = jj & (NS - 1);
 #pragma unroll
         for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
-        if constexpr (NS > 1) {
-            const C* tk = tws + k;
-#pragma unroll
-            for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], tw_load<SIGN>(tk + (r - 1) * NS));
-        }
+        if constexpr (NS > 1) apply_stage_twiddles<R, NS, SIGN>(v + jb * R, tws, k);
     }
     __syncthreads();
 #pragma unroll
@@ -230,8 +248,7 @@ __device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T
         const int jj = t + jb * NTHR;   // < LAST_NS, so k = jj
 #pragma unroll
         for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
-#pragma unroll
-        for (int r = 1; r < R; ++r) v[jb * R + r] = cmul(v[jb * R + r], tw_load<SIGN>(tws + (r - 1) * NS + jj));
+        apply_stage_twiddles<R, NS, SIGN>(v + jb * R, tws, jj);
         C* a = v + jb * R;
         if constexpr (R == 16) dft16<SIGN, T>(a);
         if constexpr (R == 8) dft8<SIGN, T>(a);

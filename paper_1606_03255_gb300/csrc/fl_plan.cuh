@@ -152,6 +152,7 @@ struct Plan {
     void* d_tw = nullptr;          // four-step stage twiddles (complex T, kTwEntries)
     void* d_stage_c = nullptr;     // staging for fl_execute_host
     void* d_stage_f = nullptr;
+    void* d_stage_r = nullptr;     // fl_transposed: conj of the node values
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
     DirectItem* d_direct = nullptr;
     DirectRange* d_dranges = nullptr;
@@ -207,6 +208,7 @@ cudaError_t build_twiddles(Plan& p, cudaStream_t st);
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul = nullptr);
 cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
+cudaError_t run_transposed(Plan& p, const void* g, void* out, cudaStream_t st);
 
 // Launchers (fl_direct.cu)
 cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,

@@ -157,10 +157,11 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
     return e;
 }
 
-// Stage twiddles of the four-step passes: entry (r - 1) NS + k of the stage of
-// span NS = 2^d and radix R in region (LOG2L, FIRST) is exp(2 pi i r k / (NS R)),
-// computed in FP64 (exact argument: r k < NS R, a power of two) and rounded
-// once to T.  Unused entries are zero.
+// Stage twiddles of the four-step passes (layout in fl_common.cuh): entry
+// 2 NS p + 2 k + h of the stage of span NS = 2^d and radix R in region
+// (LOG2L, FIRST) is exp(2 pi i r k / (NS R)) with r = 2p + 1 + h < R, computed in
+// FP64 (exact argument: r k < NS R, a power of two) and rounded once to T.
+// Unused entries are zero.
 template <typename T>
 __global__ void k_twiddles(C_t<T>* __restrict__ tw) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -172,11 +173,14 @@ __global__ void k_twiddles(C_t<T>* __restrict__ tw) {
         for (int d = FIRST; d < LOG2L; d += 4) {
             const int NS = 1 << d, R = 1 << tw_stage_log(LOG2L, FIRST, d);
             const int off = tw_off(LOG2L, FIRST, d);
-            if (e >= off && e < off + (R - 1) * NS) {
-                const int r = (e - off) / NS + 1, k = (e - off) % NS;
-                double sn, cs;
-                sincospi(2.0 * (double)(r * k) / (double)(NS * R), &sn, &cs);
-                v = C_t<T>{(T)cs, (T)sn};
+            if (e >= off && e < off + R * NS) {
+                const int rel = e - off, pr = rel / (2 * NS), rem = rel % (2 * NS);
+                const int k = rem / 2, r = 2 * pr + 1 + rem % 2;
+                if (r < R) {
+                    double sn, cs;
+                    sincospi(2.0 * (double)(r * k) / (double)(NS * R), &sn, &cs);
+                    v = C_t<T>{(T)cs, (T)sn};
+                }
             }
         }
     }
@@ -706,6 +710,39 @@ static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st
 
 cudaError_t run_adjoint(Plan& p, const void* r, void* cout, cudaStream_t st) {
     return p.prec == FL_FP64 ? adjoint_t<double>(p, r, cout, st) : adjoint_t<float>(p, r, cout, st);
+}
+
+// out[i] = conj(in[i]) (in == out allowed)
+template <typename T>
+__global__ void k_conj(int64_t n, const C_t<T>* in, C_t<T>* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const C_t<T> v = in[i];
+        out[i] = C_t<T>{v.x, -v.y};
+    }
+}
+
+template <typename T>
+static cudaError_t transposed_t(Plan& p, const void* g, void* out, cudaStream_t st) {
+    using C = C_t<T>;
+    if (p.M > 0) {
+        if (!p.d_stage_r) {
+            cudaError_t e = cudaMalloc(&p.d_stage_r, (size_t)p.M * sizeof(C));
+            if (e != cudaSuccess) return e;
+        }
+        k_conj<T><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(p.M, (const C*)g, (C*)p.d_stage_r);
+        ++p.launches;
+    }
+    cudaError_t e = adjoint_t<T>(p, p.M > 0 ? p.d_stage_r : g, out, st);
+    if (e != cudaSuccess) return e;
+    k_conj<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, (const C*)out, (C*)out);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+// g_k = sum_j ghat_j z_j^k, k = 0..N-1 (C^T ghat = conj(C^* conj(ghat))).
+cudaError_t run_transposed(Plan& p, const void* g, void* out, cudaStream_t st) {
+    return p.prec == FL_FP64 ? transposed_t<double>(p, g, out, st) : transposed_t<float>(p, g, out, st);
 }
 
 }  // namespace fl

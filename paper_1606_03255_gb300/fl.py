@@ -31,7 +31,7 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
 
 # Every symbol include/fl.h declares.
 EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
-            "fl_adjoint",
+            "fl_adjoint", "fl_transposed",
             "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
 
@@ -114,6 +114,7 @@ def load(path: str | None = None):
         "fl_grad_w": [vp, vp, vp, vp, vp],
         "fl_execute_host": [vp, vp, vp, vp],
         "fl_adjoint": [vp, vp, vp, vp],
+        "fl_transposed": [vp, vp, vp, vp],
         "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
         "fl_laplace_real": [vp, vp, vp, vp],
         "fl_laplace_real_noalloc": [i64, i64, vp, vp, vp, vp, ci, cd, ci, vp],
@@ -186,6 +187,10 @@ def fl_execute_host(plan, c_ptr, f_ptr, stream):
 
 def fl_adjoint(plan, r_ptr, c_out_ptr, stream):
     return load().fl_adjoint(plan, r_ptr, c_out_ptr, stream)
+
+
+def fl_transposed(plan, g_ptr, out_ptr, stream):
+    return load().fl_transposed(plan, g_ptr, out_ptr, stream)
 
 
 def fl_plan_laplace(N, M, t_ptr, s_ptr, q, eps, prec, stream):
@@ -358,6 +363,17 @@ class Plan:
         _require(out, self.cdtype, self.N, "out")
         check(fl_adjoint(self._handle, _ptr(r) if self.M else None, _ptr(out),
                          _stream_handle(stream)), "fl_adjoint")
+        return out
+
+    def transposed(self, g, out=None, stream=None):
+        """out_k = sum_j g_j z_j^k, k < N (C^T g)."""
+        torch = _torch()
+        _require(g, self.cdtype, self.M, "g")
+        if out is None:
+            out = torch.empty(self.N, dtype=self.cdtype, device=g.device)
+        _require(out, self.cdtype, self.N, "out")
+        check(fl_transposed(self._handle, _ptr(g) if self.M else None, _ptr(out),
+                            _stream_handle(stream)), "fl_transposed")
         return out
 
     def execute_host(self, c_host, f_host, stream=None):
