@@ -66,9 +66,10 @@ def _load():
             lib.oracle_flt_adjoint.argtypes = [i64, dp, i64, dp, dp, ci]
             lib.oracle_flt_adjoint_at.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_laplace_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
+            lib.oracle_kernel_direct.argtypes = [ci, i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_flt_brute_ld.argtypes = [i64, dp, i64, dp, dp]
             for fn in (lib.oracle_flt_direct, lib.oracle_flt_adjoint, lib.oracle_flt_adjoint_at,
-                       lib.oracle_laplace_direct, lib.oracle_flt_brute_ld):
+                       lib.oracle_laplace_direct, lib.oracle_kernel_direct, lib.oracle_flt_brute_ld):
                 fn.restype = ci
             lib.oracle_default_threads.restype = ci
             _lib = lib
@@ -135,6 +136,24 @@ def laplace_direct(c, t, s, threads: int = 0) -> np.ndarray:
                                        s.ctypes.data, f.ctypes.data, threads)
     if rc != 0:
         raise ValueError("oracle_laplace_direct: invalid arguments")
+    return f
+
+
+KERNELS = {"exp": 1, "bessel_half": 2}
+
+
+def kernel_direct(kind: str, c, t, s, threads: int = 0) -> np.ndarray:
+    """f_j = sum_k c_k kappa(s_j, t_k), FP64 term by term, for the kernels of the
+    generalised Algorithm 1: "exp" exp(-s t), "bessel_half" K_{1/2}(s t) =
+    sqrt(pi/(2 s t)) exp(-s t) (s, t > 0)."""
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    t = np.ascontiguousarray(t, dtype=np.float64)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    f = np.empty(s.size, dtype=np.float64)
+    rc = _load().oracle_kernel_direct(KERNELS[kind], c.size, c.ctypes.data, t.ctypes.data, s.size,
+                                      s.ctypes.data, f.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle_kernel_direct: invalid arguments")
     return f
 
 

@@ -19,6 +19,10 @@
  *                          same matrix (Section 4, remark after Algorithm 2);
  *                          oracle_flt_adjoint_at: the same at selected k.
  *   oracle_laplace_direct  f_j = sum_k c_k exp(-s_j t_k), eq. (3.2) (real data).
+ *   oracle_kernel_direct   f_j = sum_k c_k kappa(s_j, t_k) for the kernels of the
+ *                          generalised Algorithm 1 (Section 3, after Algorithm 1):
+ *                          kind 1 exp(-s t), kind 2 the Bessel kernel of the
+ *                          example there, K_{1/2}(s t) = sqrt(pi / (2 s t)) exp(-s t).
  *   oracle_flt_brute_ld    oracle_flt_direct in long double, for tiny N.
  *
  * Phase reduction: the phase k*x is split exactly into p + e with an FMA
@@ -249,6 +253,51 @@ int oracle_laplace_direct(int64_t N, const double *c, const double *t,
     for (int64_t j = 0; j < M; ++j) if (!(s[j] >= 0.0)) return -1;
     lap_ctx cx = {N, c, t, s, f};
     run_parallel(lap_range, &cx, M, nthreads);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Asymptotically smooth kernels of the generalised Algorithm 1.             */
+
+static double kernel_value(int kind, double y, double xi)
+{
+    const double x = y * xi;
+    if (kind == 2) return sqrt(1.5707963267948966192313216916398 / x) * exp(-x);
+    return exp(-x);
+}
+
+typedef struct {
+    int kind;
+    int64_t N;
+    const double *c, *t, *s;
+    double *f;
+} ker_ctx;
+
+static void ker_range(void *vctx, int64_t lo, int64_t hi)
+{
+    const ker_ctx *cx = (const ker_ctx *)vctx;
+    for (int64_t j = lo; j < hi; ++j) {
+        acc_t a = {0.0, 0.0};
+        const double sj = cx->s[j];
+        for (int64_t k = 0; k < cx->N; ++k)
+            acc_add(&a, cx->c[k] * kernel_value(cx->kind, sj, cx->t[k]));
+        cx->f[j] = acc_get(&a);
+    }
+}
+
+int oracle_kernel_direct(int kind, int64_t N, const double *c, const double *t,
+                         int64_t M, const double *s, double *f, int nthreads)
+{
+    if ((kind != 1 && kind != 2) || N < 0 || M < 0 || (N > 0 && (!c || !t)) ||
+        (M > 0 && (!s || !f)))
+        return -1;
+    /* nodes finite; s, t >= 0 (kind 1) or > 0 (kind 2, singular at s t = 0) */
+    for (int64_t k = 0; k < N; ++k)
+        if (!isfinite(t[k]) || t[k] < 0.0 || (kind == 2 && t[k] == 0.0)) return -1;
+    for (int64_t j = 0; j < M; ++j)
+        if (!isfinite(s[j]) || s[j] < 0.0 || (kind == 2 && s[j] == 0.0)) return -1;
+    ker_ctx cx = {kind, N, c, t, s, f};
+    run_parallel(ker_range, &cx, M, nthreads);
     return 0;
 }
 

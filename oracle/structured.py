@@ -384,3 +384,106 @@ def xflt_alg2_onesided(c, w, eps: float, q: int | None = None):
         Ly = lagrange_barycentric(y[sel], ya, yb, qq)
         f[sel] = (Ly * F).sum(axis=1)
     return f, qq
+
+
+# --------------------------------------------------------------------------
+# Generalised Algorithm 1 (Section 3, the theorem after Algorithm 1):
+# asymptotically smooth kernels kappa(y, xi), all blocks Y_m x Omega_l with
+# 1 <= m, l <= M - 1 interpolated (no blocks are replaced by 0 or 1), the near
+# fields Y_M (every frequency) and Omega_M (every node) summed directly, and
+# M = ceil(log2(y_1 xi_1 N / eps)) + 1.
+#
+# Asymptotic smoothness |d^q/dy^q kappa| <= C q! mu^q q^nu y^-q (y xi)^-s with
+#   exp(-y xi):       C = 1,            mu = 1, nu = 0, s = 0
+#                     (xi^q e^(-y xi) = y^-q (y xi)^q e^(-y xi) <= y^-q q^q e^-q <= y^-q q!);
+#   K_1/2(y xi) = sqrt(pi / (2 y xi)) e^(-y xi):
+#                     C = sqrt(pi/2),   mu = 1, nu = 0, s = 1/2   (the example there).
+# The proof of Theorem 3.1 bounds one block by
+#   C mu^q q^nu 2^(1-2q) (2 + (2/pi) ln q) (dist(A,0) dist(B,0))^-s,
+# and dist(A,0) dist(B,0) >= (y_1 / 2^(M-1)) (xi_1 / 2^(M-1)) on the far field;
+# q is the smallest value whose bound is <= eps.
+
+SMOOTH_CONSTANTS = {"exp": (1.0, 1.0, 0.0, 0.0),
+                    "bessel_half": (math.sqrt(math.pi / 2.0), 1.0, 0.0, 0.5)}
+
+
+def smooth_kernel(kind: str, y, xi):
+    """kappa(y, xi) of the generalised Algorithm 1."""
+    x = np.multiply.outer(np.asarray(y, dtype=np.float64), np.asarray(xi, dtype=np.float64))
+    if kind == "bessel_half":
+        return np.sqrt(math.pi / (2.0 * x)) * np.exp(-x)
+    if kind == "exp":
+        return np.exp(-x)
+    raise ValueError(kind)
+
+
+def general_block_bound(kind: str, q: int, dist_product: float) -> float:
+    C, mu, nu, s = SMOOTH_CONSTANTS[kind]
+    return C * mu ** q * q ** nu * 2.0 ** (1 - 2 * q) * (2.0 + 2.0 / math.pi * math.log(q)) \
+        * dist_product ** (-s)
+
+
+@dataclass
+class GeneralParams:
+    kind: str
+    eps: float
+    y1: float
+    xi1: float
+    q: int
+    M: int
+
+
+def general_params(kind: str, eps: float, y1: float, xi1: float, N: int,
+                   q: int | None = None) -> GeneralParams:
+    if y1 <= 0.0 or xi1 <= 0.0 or N < 1:
+        return GeneralParams(kind, eps, y1, xi1, q or 1, 1)
+    M = max(1, int(math.ceil(math.log2(y1 * xi1 * N / eps))) + 1)
+    if q is None:
+        dmin = (y1 / 2.0 ** (M - 1)) * (xi1 / 2.0 ** (M - 1))
+        q = 1
+        while general_block_bound(kind, q, dmin) > eps:
+            q += 1
+    return GeneralParams(kind, eps, y1, xi1, int(q), M)
+
+
+def laplace_alg1_general(kind: str, c, t, s, eps: float, q: int | None = None):
+    """The generalised Algorithm 1 step by step; returns (f~, params)."""
+    c = np.asarray(c)
+    t = np.asarray(t, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    xi1 = float(t.max()) if t.size else 0.0
+    y1 = float(s.max()) if s.size else 0.0
+    p = general_params(kind, eps, y1, xi1, t.size, q)
+    f = np.zeros(s.shape, dtype=np.result_type(c.dtype, np.float64))
+    if p.M == 1 or t.size == 0:
+        if t.size:
+            f[:] = smooth_kernel(kind, s, t) @ c
+        return f, p
+    bt = band_of(t, xi1, p.M)
+    bs = band_of(s, y1, p.M)
+    # near field in y: every frequency directly
+    near_y = bs == p.M
+    if near_y.any():
+        f[near_y] = smooth_kernel(kind, s[near_y], t) @ c
+    # moments v^{Omega_l} = (L^{Omega_l})^T c^{Omega_l}, l = 1 .. M-1
+    v = {}
+    for l in range(1, p.M):
+        sel = bt == l
+        a, b = band_interval(xi1, l)
+        v[l] = lagrange_barycentric(t[sel], a, b, p.q).T @ c[sel]
+    near_t = bt == p.M
+    for m in range(1, p.M):
+        sel = bs == m
+        if not sel.any():
+            continue
+        ya, yb = band_interval(y1, m)
+        ys = interval_points(ya, yb, p.q)
+        h = np.zeros(p.q, dtype=f.dtype)
+        for l in range(1, p.M):
+            xa, xb = band_interval(xi1, l)
+            h = h + smooth_kernel(kind, ys, interval_points(xa, xb, p.q)) @ v[l]
+        fm = lagrange_barycentric(s[sel], ya, yb, p.q) @ h
+        if near_t.any():   # near field in xi: directly for every node
+            fm = fm + smooth_kernel(kind, s[sel], t[near_t]) @ c[near_t]
+        f[sel] = fm
+    return f, p

@@ -161,3 +161,27 @@ def test_error_measure():
     c = np.array([1 + 1j, -2.0, 0.5j])
     assert oracle.error_E([1, 2], [1, 2.5], c) == pytest.approx(0.5 / (math.sqrt(2) + 2.5))
     assert cmath.isclose(1, 1)
+
+
+def test_kernel_direct_pins():
+    # kind "exp" is eq. (3.2) itself; "bessel_half" single terms against the
+    # library Bessel function K_{1/2} and a 40-digit brute force.
+    special = pytest.importorskip("scipy.special")
+    mpmath = pytest.importorskip("mpmath")
+    rng = np.random.default_rng(3)
+    t = rng.uniform(0.01, 1.0, 50)
+    s = rng.uniform(0.01, 100.0, 30)
+    c = rng.standard_normal(50)
+    assert np.array_equal(oracle.kernel_direct("exp", c, t, s), oracle.laplace_direct(c, t, s))
+    for k in (0, 17, 49):
+        e = np.zeros(50)
+        e[k] = 1.0
+        got = oracle.kernel_direct("bessel_half", e, t, s)
+        assert np.allclose(got, special.kv(0.5, s * t[k]), rtol=1e-13, atol=0)
+    mpmath.mp.dps = 40
+    ref = [sum(mpmath.mpf(c[k]) * mpmath.besselk(0.5, mpmath.mpf(sj) * mpmath.mpf(t[k]))
+               for k in range(50)) for sj in s[:5]]
+    got = oracle.kernel_direct("bessel_half", c, t, s[:5])
+    assert np.max(np.abs(got - np.array([float(r) for r in ref]))) <= 1e-13 * np.sum(np.abs(c))
+    with pytest.raises(ValueError):
+        oracle.kernel_direct("bessel_half", c, np.zeros(50), s)   # singular at s t = 0

@@ -237,3 +237,90 @@ def test_onesided_error_decreases_with_q():
     f0, _ = S.xflt_alg2_onesided(c, w0, 1e-6)
     assert f0[0] == c[0]
     assert abs(f0[1] - np.sum(c * (-1.0) ** np.arange(N))) < 1e-12 * np.sum(np.abs(c))
+
+
+# --------------------------------------------------------------------------
+# Generalised Algorithm 1 (asymptotically smooth kernels)
+
+def test_bessel_half_kernel_closed_form():
+    special = pytest.importorskip("scipy.special")
+    x = np.geomspace(1e-6, 50.0, 200)
+    got = S.smooth_kernel("bessel_half", x, np.ones(1))[:, 0]
+    assert np.allclose(got, special.kv(0.5, x), rtol=1e-13, atol=0)
+    # the Laplace kernel of the generalised algorithm is the plain exponential
+    assert np.array_equal(S.smooth_kernel("exp", x, np.ones(1))[:, 0], np.exp(-x))
+
+
+def test_bessel_half_derivative_identity_and_smoothness():
+    sympy = pytest.importorskip("sympy")
+    y, xi = sympy.symbols("y xi", positive=True)
+    kappa = sympy.sqrt(sympy.pi / (2 * y * xi)) * sympy.exp(-y * xi)
+    for q in range(0, 7):
+        d = sympy.diff(kappa, y, q)
+        # the identity of the example: sqrt(pi/2) (-xi)^q e^(-y xi)
+        #   * sum_k binom(q,k) prod_{j<k} (2j+1) / 2^k (y xi)^(-(2k+1)/2)
+        ident = sympy.sqrt(sympy.pi / 2) * (-xi) ** q * sympy.exp(-y * xi) * sum(
+            sympy.binomial(q, k) * sympy.prod([2 * j + 1 for j in range(k)]) / 2 ** k
+            * (y * xi) ** (-sympy.Rational(2 * k + 1, 2)) for k in range(q + 1))
+        for yv, xv in ((0.3, 2.0), (1.7, 0.25), (5.0, 3.0)):
+            dv = float(d.subs({y: yv, xi: xv}))
+            iv = float(ident.subs({y: yv, xi: xv}))
+            assert abs(dv - iv) <= 1e-12 * max(1.0, abs(dv))
+            # asymptotic smoothness: C = sqrt(pi/2), mu = 1, nu = 0, s = 1/2
+            bound = math.sqrt(math.pi / 2) * math.factorial(q) * (yv * xv) ** -0.5 * yv ** -q
+            assert abs(dv) <= bound * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("kind", ["exp", "bessel_half"])
+def test_general_blocks_within_bound(kind):
+    # every interpolated block of a small partition, checked on a dense grid
+    q = 8
+    P = S.general_params(kind, 1e-6, 40.0, 1.0, 64, q=q)
+    dmin = (P.y1 / 2.0 ** (P.M - 1)) * (P.xi1 / 2.0 ** (P.M - 1))
+    bound = S.general_block_bound(kind, q, dmin)
+    worst = 0.0
+    for m in (1, 5, P.M - 1):
+        ya, yb = S.band_interval(P.y1, m)
+        yg = np.linspace(ya, yb, 60)
+        Ly = S.lagrange_barycentric(yg, ya, yb, q)
+        ys = S.interval_points(ya, yb, q)
+        for l in (1, 7, P.M - 1):
+            xa, xb = S.band_interval(P.xi1, l)
+            xg = np.linspace(xa, xb, 60)
+            Lx = S.lagrange_barycentric(xg, xa, xb, q)
+            xs = S.interval_points(xa, xb, q)
+            approx = Ly @ S.smooth_kernel(kind, ys, xs) @ Lx.T
+            err = np.max(np.abs(S.smooth_kernel(kind, yg, xg) - approx))
+            local = S.general_block_bound(kind, q, ya * xa)
+            assert err <= local * (1 + 1e-9) + 1e-14, (m, l, err, local)
+            worst = max(worst, err)
+    assert worst <= bound
+
+
+@pytest.mark.parametrize("kind", ["exp", "bessel_half"])
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
+def test_general_algorithm1_meets_eps(kind, eps):
+    rng = np.random.default_rng(7)
+    N, M = 700, 400
+    t = rng.uniform(0.0, 1.0, N)
+    s = rng.uniform(0.0, 2.0 * N, M)
+    # near fields: a few t in Omega_M and s in Y_M (tiny but positive)
+    t[:3] = [1e-12, 3e-13, 1e-11]
+    s[:3] = [1e-9, 2e-10, 5e-9]
+    t[t == 0] = 0.5
+    s[s == 0] = 1.0
+    c = rng.standard_normal(N)
+    f, P = S.laplace_alg1_general(kind, c, t, s, eps)
+    assert P.M == int(math.ceil(math.log2(s.max() * t.max() * N / eps))) + 1
+    ref = oracle.kernel_direct(kind, c, t, s)
+    # Theorem (generalised Algorithm 1): E <= eps in exact arithmetic.  Both
+    # sides round sums whose terms reach |c_k kappa| ~ 1e10 next to the
+    # singularity (s t ~ 1e-21 in the near fields), so rounding of order
+    # u * sum_k |c_k kappa(s_j, t_k)| is allowed on top.
+    absum = np.abs(S.smooth_kernel(kind, s, t)) @ np.abs(c)
+    allow = 64 * 2.0 ** -53 * np.max(absum)
+    assert np.max(np.abs(f - ref)) <= eps * np.sum(np.abs(c)) + allow
+    # the generalised algorithm on exp(-s t) agrees with Algorithm 1
+    if kind == "exp":
+        f1, _ = S.laplace_alg1(c, t, s, eps)
+        assert np.max(np.abs(f - f1)) <= 2 * eps * np.sum(np.abs(c))
