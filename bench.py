@@ -259,6 +259,20 @@ def secondary_workloads(dev, flush, rank):
         ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
         out[f"laplace_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s"}
         lp.close()
+    # generalised Algorithm 1 on the same inputs (t, s > 0): the K_1/2 Bessel kernel
+    tp, sp = np.where(t > 0, t, 0.5), np.where(sv > 0, sv, 1.0)
+    for prec, dt in (("fp64", torch.float64),):
+        lp = fl.LaplacePlan(torch.from_numpy(tp).to(dev), torch.from_numpy(sp).to(dev), 1e-6,
+                            precision=prec, kernel="bessel_half")
+        cc = torch.from_numpy(cl).to(dt).to(dev)
+        ff = torch.empty(M, dtype=dt, device=dev)
+        for _ in range(3):
+            lp.execute(cc, out=ff)
+        ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
+        inf = lp.info()
+        out[f"bessel_half_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s",
+                                           "q": inf["q"], "levels": inf["levels"]}
+        lp.close()
     # batched: 512 transforms, N_i = floor(2^U), U ~ U[8,16], M_i = N_i, FP32, eps = 1e-6:
     # one plan + CUDA graph vs 512 separate plans with plain launches
     Ns = W.batched_degrees(512, seed=rank)

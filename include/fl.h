@@ -79,6 +79,7 @@ typedef struct {
     double direct_bias;       /* route bias in use (the autotuner's choice if tuned) */
     double scratch_bytes;     /* device memory owned by the plan */
     int variant;              /* fl_options.variant in use */
+    int kernel;               /* Laplace plans: the fl_kernel */
 } fl_info;
 
 /* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
@@ -240,7 +241,37 @@ fl_status fl_plan_laplace(fl_plan_t *out, int64_t N, int64_t M, const double *t_
                           const double *s_dev, int q, double eps, fl_precision prec,
                           void *stream);
 
-/* fl_laplace_real -- f~ ~= K c (Algorithm 1), c_dev N reals, f_dev M reals. */
+/* Kernels of fl_plan_kernel. */
+typedef enum {
+    FL_KERNEL_LAPLACE = 0,        /* exp(-s t) by Algorithm 1 (= fl_plan_laplace)     */
+    FL_KERNEL_EXP_GENERAL = 1,    /* exp(-s t) by the generalised Algorithm 1         */
+    FL_KERNEL_BESSEL_K_HALF = 2   /* K_{1/2}(s t) = sqrt(pi / (2 s t)) exp(-s t),
+                                     s, t > 0 (the example after that theorem)       */
+} fl_kernel;
+
+/*
+ * fl_plan_kernel -- plan f_j = sum_k c_k kappa(s_j, t_k) for an asymptotically
+ * smooth kernel by the generalised Algorithm 1 (Section 3, the theorem after
+ * Algorithm 1): every block Y_m x Omega_l, 1 <= m, l <= M - 1, interpolated
+ * with q Chebyshev points per side, the near fields Y_M (all frequencies) and
+ * Omega_M (all nodes) summed directly, M = ceil(log2(y_1 xi_1 N / eps)) + 1
+ * (y_1 = max s_j, xi_1 = max t_k).
+ *   kernel : fl_kernel; FL_KERNEL_LAPLACE forwards to fl_plan_laplace.
+ *   q      : 0 = the smallest q whose block bound from the proof of Theorem 3.1,
+ *            C mu^q q^nu 2^(1-2q) (2 + (2/pi) ln q) (y_1 xi_1 / 4^(M-1))^-s
+ *            (exp: C = 1, s = 0; K_1/2: C = sqrt(pi/2), s = 1/2; mu = 1, nu = 0),
+ *            is at most eps; else 1 .. 64.
+ *   t_dev, s_dev, eps, prec : as fl_plan_laplace.
+ * Execute with fl_laplace_real.  Cost: O(N q + M q + (M - 1)^2 q^2), plus the
+ * direct near fields (|Y_M| N + M |Omega_M| kernel evaluations).
+ * Returns FL_EINVAL for a negative, non-finite (or, for K_1/2, zero) node,
+ * FL_EUNSUPPORTED for a rank above 64 or more than 127 levels.
+ */
+fl_status fl_plan_kernel(fl_plan_t *out, int kernel, int64_t N, int64_t M, const double *t_dev,
+                         const double *s_dev, int q, double eps, fl_precision prec, void *stream);
+
+/* fl_laplace_real -- f~ ~= K c (Algorithm 1, or the generalised Algorithm 1
+ * of a fl_plan_kernel plan), c_dev N reals, f_dev M reals. */
 fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
 
 /*

@@ -40,7 +40,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw};
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -837,6 +837,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->direct_bias = p.tuned_bias > 0 ? p.tuned_bias : p.direct_bias;
     info->scratch_bytes = p.scratch_bytes;
     info->variant = p.variant;
+    info->kernel = p.kind == 1 ? p.lap_kernel : 0;
     return FL_OK;
 }
 

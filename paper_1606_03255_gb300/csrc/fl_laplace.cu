@@ -81,14 +81,14 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
     extern __shared__ unsigned char smem_raw[];
     T* tab = reinterpret_cast<T*>(smem_raw);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;   // warps (tables) per block
     const int row = q + 1;
     const int entries = (levels + 1) * row;
-    for (int i = threadIdx.x; i < kLapWarps * entries; i += blockDim.x) tab[i] = (T)0;
+    for (int i = threadIdx.x; i < nw * entries; i += blockDim.x) tab[i] = (T)0;
     __syncthreads();
     T* mytab = tab + w * entries;
     const int64_t nchunk = (N + 31) / 32;
-    for (int64_t ch = (int64_t)blockIdx.x * kLapWarps + w; ch < nchunk;
-         ch += (int64_t)gridDim.x * kLapWarps) {
+    for (int64_t ch = (int64_t)blockIdx.x * nw + w; ch < nchunk; ch += (int64_t)gridDim.x * nw) {
         const int64_t k = ch * 32 + lane;
         const bool valid = k < N;
         const int l = !valid ? 255 : (BANDS_FROM_VALUES ? lap_band(t[k], xi1, levels) : tband[k]);
@@ -130,7 +130,7 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
     __syncthreads();
     for (int i = threadIdx.x; i < entries; i += blockDim.x) {
         T s = (T)0;
-        for (int ww = 0; ww < kLapWarps; ++ww) s += tab[ww * entries + i];
+        for (int ww = 0; ww < nw; ++ww) s += tab[ww * entries + i];
         partial[(int64_t)blockIdx.x * entries + i] = s;
     }
 }
@@ -256,6 +256,98 @@ __global__ void k_lap_cheb(int q, double* cheb) {
 }
 
 // ---------------------------------------------------------------------------
+// Generalised Algorithm 1 (Section 3, the theorem after Algorithm 1): an
+// asymptotically smooth kernel kappa(y, xi) in place of exp(-y xi).  Every
+// block Y_m x Omega_l with 1 <= m, l <= M - 1 is interpolated (no block is
+// replaced by 0 or 1), the near fields Y_M (every frequency) and Omega_M (every
+// node) are summed directly, and M = ceil(log2(y_1 xi_1 N / eps)) + 1.
+// Kernels: kind 1 exp(-y xi); kind 2 K_{1/2}(y xi) = sqrt(pi / (2 y xi)) exp(-y xi)
+// (the example there, y, xi > 0).
+
+constexpr int kGenMaxQ = 64;
+
+__device__ __forceinline__ double gen_kappa(int kind, double y, double xi) {
+    const double x = y * xi;
+    return kind == 2 ? sqrt(1.5707963267948966192313216916398 / x) * exp(-x) : exp(-x);
+}
+
+// Kt[((m - 1)(M - 1) + l - 1) q^2 + s q + r] = kappa(y_s^{Y_m}, xi_r^{Omega_l}), block m.
+__global__ void k_gen_ktable(int kind, int levels, int q, double y1, double xi1,
+                             const double* __restrict__ cheb, double* __restrict__ Kt) {
+    const int m = blockIdx.x + 1;
+    const int nb = levels - 1;
+    const double ay = ldexp(y1, -m);
+    for (int i = threadIdx.x; i < nb * q * q; i += blockDim.x) {
+        const int r = i % q, s = (i / q) % q, l = 1 + i / (q * q);
+        const double ys = 1.5 * ay + 0.5 * ay * cheb[s];
+        const double ax = ldexp(xi1, -l);
+        const double xr = 1.5 * ax + 0.5 * ax * cheb[r];
+        Kt[(int64_t)(m - 1) * nb * q * q + i] = gen_kappa(kind, ys, xr);
+    }
+}
+
+// h^{Y_m}_s = sum_{l = 1}^{M - 1} sum_r Kt(m, l)_{s r} v^{Omega_l}_r, m = blockIdx.x + 1.
+__global__ void k_gen_couple(int levels, int q, const double* __restrict__ Kt,
+                             const double* __restrict__ vS, double* __restrict__ h) {
+    const int m = blockIdx.x + 1, s = threadIdx.x, row = q + 1, nb = levels - 1;
+    if (m >= levels || s >= q) return;
+    double acc = 0.0;
+    for (int l = 1; l < levels; ++l) {
+        const double* Kb = Kt + (((int64_t)(m - 1) * nb + (l - 1)) * q + s) * q;
+        for (int r = 0; r < q; ++r) acc += Kb[r] * vS[l * row + r];
+    }
+    h[m * q + s] = acc;
+}
+
+// f~_j: s_j in Y_m (m < M): sum_s L_s^{Y_m}(s_j) h^{Y_m}_s plus the Omega_M near
+// field sum_{t_k in Omega_M} c_k kappa(s_j, t_k); s_j in Y_M: the direct sum.
+template <typename T, int KIND>
+__global__ void k_gen_eval(int64_t M, const double* __restrict__ sv,
+                           const uint8_t* __restrict__ sband, int levels, int q, double y1,
+                           const double* __restrict__ cheb, const double* __restrict__ h, int64_t N,
+                           const double* __restrict__ t, const T* __restrict__ c,
+                           const int32_t* __restrict__ nearT, int64_t nnear, T* __restrict__ f) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    const int m = sband[j];
+    const double sj = sv[j];
+    double acc = 0.0;
+    if (m >= levels) {
+        for (int64_t k = 0; k < N; ++k) acc += (double)c[k] * gen_kappa(KIND, sj, t[k]);
+    } else {
+        const double a = ldexp(y1, -m);
+        const double tau = (sj - 1.5 * a) / (0.5 * a);
+        double den = 0.0, num = 0.0;
+        int hit = -1;
+        for (int s = 0; s < q; ++s) {
+            const double d = tau - cheb[s];
+            if (d == 0.0) hit = s;
+            const double wgt = cheb[q + s] / d;
+            den += wgt;
+            num += wgt * h[m * q + s];
+        }
+        acc = (hit >= 0) ? h[m * q + hit] : num / den;
+        for (int64_t i = 0; i < nnear; ++i) {
+            const int32_t k = nearT[i];
+            acc += (double)c[k] * gen_kappa(KIND, sj, t[k]);
+        }
+    }
+    f[j] = (T)acc;
+}
+
+// flag bit 1: a t_k or s_j is zero (kind 2 is singular at y xi = 0)
+__global__ void k_gen_positive(int64_t N, const double* __restrict__ t, int64_t M,
+                               const double* __restrict__ s, int* __restrict__ flag) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride)
+        if (!(t[i] > 0.0)) bad = 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride)
+        if (!(s[i] > 0.0)) bad = 1;
+    if (bad) atomicOr(flag, 1);
+}
+
+// ---------------------------------------------------------------------------
 // Scratch layout of one Laplace evaluation (all offsets in bytes, 256-aligned).
 struct LapLayout {
     size_t partial, vS, h, g, ell, total;
@@ -359,7 +451,56 @@ static fl_status lap_fail(fl_status s, const std::string& m) { return set_error(
 
 namespace fl {
 
+// Moment tables per block for the generalised algorithm: up to kLapWarps, as
+// many as fit 200 KB of shared memory (0: the tables do not fit).
+static int gen_moment_warps(int entries, size_t tsize) {
+    const size_t per = (size_t)entries * tsize;
+    return (int)std::min<size_t>(kLapWarps, (size_t)(200 * 1024) / per);
+}
+
+template <typename T>
+static cudaError_t gen_run(Plan& p, const T* c, T* f, cudaStream_t st) {
+    const LapLayout L = lap_layout(p.levels, p.q, p.lap_blocks, sizeof(T));
+    const int entries = (p.levels + 1) * (p.q + 1);
+    unsigned char* scratch = (unsigned char*)p.d_lap;
+    T* partial = (T*)(scratch + L.partial);
+    double* vS = (double*)(scratch + L.vS);
+    double* h = (double*)(scratch + L.h);
+    const int nw = gen_moment_warps(entries, sizeof(T));
+    const size_t smem = (size_t)nw * entries * sizeof(T);
+    int slot = -1;
+    if (p.N > 0 && p.levels > 1) {
+        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        timer_begin(p, "lap_moments", (double)p.N * (8 + 1 + sizeof(T)), st, &slot);
+        k_lap_moments<T, false><<<p.lap_blocks, nw * 32, smem, st>>>(
+            p.N, p.d_t, p.d_tband, c, p.levels, p.q, p.xi1, p.d_cheb, partial);
+        timer_end(p, slot, st);
+        k_lap_reduce<T><<<(entries + 255) / 256, 256, 0, st>>>(p.lap_blocks, entries, partial, vS);
+        k_gen_couple<<<p.levels - 1, ((p.q + 31) / 32) * 32, 0, st>>>(p.levels, p.q, p.d_lapK, vS, h);
+        p.launches += 3;
+    }
+    if (p.M > 0) {
+        timer_begin(p, "lap_eval", (double)p.M * (8 + 1 + sizeof(T)), st, &slot);
+        if (p.lap_kernel == 2)
+            k_gen_eval<T, 2><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+                p.M, p.d_s, p.d_sband, p.levels, p.q, p.y1, p.d_cheb, h, p.N, p.d_t, c, p.d_nearT,
+                p.n_nearT, f);
+        else
+            k_gen_eval<T, 1><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+                p.M, p.d_s, p.d_sband, p.levels, p.q, p.y1, p.d_cheb, h, p.N, p.d_t, c, p.d_nearT,
+                p.n_nearT, f);
+        timer_end(p, slot, st);
+        p.launches += 1;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
+    if (p.lap_kernel != 0)
+        return p.prec == FL_FP64 ? gen_run<double>(p, (const double*)c, (double*)f, st)
+                                 : gen_run<float>(p, (const float*)c, (float*)f, st);
     LapParams P;
     memset(&P, 0, sizeof(P));
     P.q = p.q;
@@ -478,6 +619,108 @@ static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, in
     return FL_OK;
 }
 
+// Generalised Algorithm 1: rank from the block bound of the proof of
+// Theorem 3.1, C mu^q q^nu 2^(1-2q) (2 + (2/pi) ln q) (dist(A,0) dist(B,0))^-s
+// <= eps, with dist(A,0) dist(B,0) >= (y_1 / 2^(M-1)) (xi_1 / 2^(M-1)) and the
+// asymptotic-smoothness constants of the kernel (exp: C = 1, mu = 1, nu = 0,
+// s = 0; K_1/2: C = sqrt(pi/2), mu = 1, nu = 0, s = 1/2).
+static int gen_rank(int kind, double eps, double dmin) {
+    const double C = kind == 2 ? sqrt(M_PI / 2.0) : 1.0, sexp = kind == 2 ? 0.5 : 0.0;
+    for (int q = 1; q <= kGenMaxQ; ++q) {
+        const double b = C * pow(2.0, 1 - 2 * q) * (2.0 + 2.0 / M_PI * log((double)q)) * pow(dmin, -sexp);
+        if (b <= eps) return q;
+    }
+    return kGenMaxQ + 1;
+}
+
+static fl_status plan_general_impl(Plan& p, int kind, const double* t, const double* s, int q,
+                                   cudaStream_t st) {
+    unsigned long long* dmx = nullptr;
+    int* dflag = nullptr;
+    LAP_CUDA(cudaMalloc((void**)&dmx, 2 * sizeof(unsigned long long)), "cudaMalloc");
+    cudaError_t e = cudaMalloc((void**)&dflag, 2 * sizeof(int));
+    unsigned long long mx[2] = {0, 0};
+    int flag[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemsetAsync(dmx, 0, 2 * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dflag, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess && (p.N > 0 || p.M > 0)) {
+        k_lap_minmax<<<256, 256, 0, st>>>(p.N, t, p.M, s, dmx, dflag);
+        if (kind == 2) k_gen_positive<<<256, 256, 0, st>>>(p.N, t, p.M, s, dflag + 1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mx, dmx, sizeof(mx), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(flag, dflag, sizeof(flag), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(dmx);
+    cudaFree(dflag);
+    LAP_CUDA(e, "fl_plan_kernel: node scan");
+    if (flag[0]) return lap_fail(FL_EINVAL, "fl_plan_kernel: a t_k or s_j is negative or not finite");
+    if (flag[1]) return lap_fail(FL_EINVAL, "fl_plan_kernel: the K_1/2 kernel needs every t_k, s_j > 0");
+    double xi1, y1;
+    memcpy(&xi1, &mx[0], sizeof(double));
+    memcpy(&y1, &mx[1], sizeof(double));
+    int levels = 1;
+    if (y1 > 0.0 && xi1 > 0.0 && p.N > 0)
+        levels = (int)std::max(1.0, ceil(log2(y1 * xi1 * (double)p.N / p.eps)) + 1.0);
+    if (levels > 127) return lap_fail(FL_EUNSUPPORTED, "fl_plan_kernel: more than 127 levels");
+    const double dmin = ldexp(y1, 1 - levels) * ldexp(xi1, 1 - levels);
+    const int qq = q > 0 ? q : gen_rank(kind, p.eps, dmin);
+    if (qq > kGenMaxQ) return lap_fail(FL_EUNSUPPORTED, "fl_plan_kernel: rank above 64 for this eps");
+    p.lap_kernel = kind;
+    p.q = qq;
+    p.levels = levels;
+    p.y1 = y1;
+    p.xi1 = xi1;
+    p.eps_K = p.eps;
+    p.bands.assign(levels + 1, BandHost());
+    const size_t N = (size_t)p.N, M = (size_t)p.M;
+    if (N) {
+        LAP_CUDA(cudaMalloc((void**)&p.d_t, N * sizeof(double)), "cudaMalloc t");
+        LAP_CUDA(cudaMemcpyAsync(p.d_t, t, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy t");
+        LAP_CUDA(cudaMalloc((void**)&p.d_tband, N), "cudaMalloc t bands");
+        k_lap_band<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(p.N, p.d_t, xi1, levels, p.d_tband);
+    }
+    if (M) {
+        LAP_CUDA(cudaMalloc((void**)&p.d_s, M * sizeof(double)), "cudaMalloc s");
+        LAP_CUDA(cudaMemcpyAsync(p.d_s, s, M * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy s");
+        LAP_CUDA(cudaMalloc((void**)&p.d_sband, M), "cudaMalloc s bands");
+        k_lap_band<<<(unsigned)((M + 255) / 256), 256, 0, st>>>(p.M, p.d_s, y1, levels, p.d_sband);
+    }
+    LAP_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kGenMaxQ * sizeof(double)), "cudaMalloc cheb");
+    k_lap_cheb<<<1, kGenMaxQ, 0, st>>>(qq, p.d_cheb);
+    p.lap_blocks = lap_blocks(p.N);
+    const size_t tsz = p.prec == FL_FP64 ? 8 : 4;
+    if (gen_moment_warps((levels + 1) * (qq + 1), tsz) < 1)
+        return lap_fail(FL_EUNSUPPORTED, "fl_plan_kernel: moment tables exceed shared memory");
+    const LapLayout L = lap_layout(levels, qq, p.lap_blocks, tsz);
+    LAP_CUDA(cudaMalloc(&p.d_lap, L.total), "cudaMalloc scratch");
+    // the Omega_M near field: indices of the t_k in the last frequency band
+    if (N && levels > 1) {
+        std::vector<uint8_t> tb(N);
+        LAP_CUDA(cudaMemcpyAsync(tb.data(), p.d_tband, N, cudaMemcpyDeviceToHost, st), "copy t bands");
+        LAP_CUDA(cudaStreamSynchronize(st), "fl_plan_kernel: synchronise");
+        std::vector<int32_t> near;
+        for (size_t k = 0; k < N; ++k)
+            if (tb[k] == levels) near.push_back((int32_t)k);
+        p.n_nearT = (int64_t)near.size();
+        if (!near.empty()) {
+            LAP_CUDA(cudaMalloc((void**)&p.d_nearT, near.size() * sizeof(int32_t)), "cudaMalloc near field");
+            LAP_CUDA(cudaMemcpyAsync(p.d_nearT, near.data(), near.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st),
+                     "copy near field");
+        }
+        const int64_t ktot = (int64_t)(levels - 1) * (levels - 1) * qq * qq;
+        LAP_CUDA(cudaMalloc((void**)&p.d_lapK, ktot * sizeof(double)), "cudaMalloc coupling table");
+        k_gen_ktable<<<levels - 1, 256, 0, st>>>(kind, levels, qq, y1, xi1, p.d_cheb, p.d_lapK);
+    }
+    LAP_CUDA(cudaGetLastError(), "fl_plan_kernel: launch");
+    LAP_CUDA(cudaStreamSynchronize(st), "fl_plan_kernel: synchronise");
+    p.scratch_bytes = (double)L.total + N * 9.0 + M * 9.0 +
+                      (levels > 1 ? (double)(levels - 1) * (levels - 1) * qq * qq * 8.0 : 0.0);
+    p.model_bytes = (double)N * (8 + 1 + tsz) + (double)M * (8 + 1 + tsz);
+    return FL_OK;
+}
+
 extern "C" {
 
 fl_status fl_plan_laplace(fl_plan_t* out, int64_t N, int64_t M, const double* t_dev,
@@ -500,6 +743,37 @@ fl_status fl_plan_laplace(fl_plan_t* out, int64_t N, int64_t M, const double* t_
     h->p.M = M;
     h->p.eps = eps;
     fl_status s = plan_laplace_impl(h->p, t_dev, s_dev, q, (cudaStream_t)stream);
+    if (s != FL_OK) {
+        delete h;
+        return s;
+    }
+    *out = h;
+    return FL_OK;
+}
+
+fl_status fl_plan_kernel(fl_plan_t* out, int kernel, int64_t N, int64_t M, const double* t_dev,
+                         const double* s_dev, int q, double eps, fl_precision prec, void* stream) {
+    clear_error();
+    if (kernel == FL_KERNEL_LAPLACE) return fl_plan_laplace(out, N, M, t_dev, s_dev, q, eps, prec, stream);
+    if (!out) return lap_fail(FL_EINVAL, "fl_plan_kernel: out is NULL");
+    *out = nullptr;
+    if (kernel != FL_KERNEL_EXP_GENERAL && kernel != FL_KERNEL_BESSEL_K_HALF)
+        return lap_fail(FL_EINVAL, "fl_plan_kernel: unknown kernel");
+    if (N < 0 || M < 0) return lap_fail(FL_EINVAL, "fl_plan_kernel: need N >= 0 and M >= 0");
+    if (N > ((int64_t)1 << 31) - 1 || M > ((int64_t)1 << 31) - 1)
+        return lap_fail(FL_EUNSUPPORTED, "fl_plan_kernel: N or M above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0)) return lap_fail(FL_EINVAL, "fl_plan_kernel: eps must lie in (0, 1)");
+    if (q < 0 || q > kGenMaxQ) return lap_fail(FL_EINVAL, "fl_plan_kernel: q must lie in [0, 64]");
+    if (prec != FL_FP32 && prec != FL_FP64) return lap_fail(FL_EINVAL, "fl_plan_kernel: unknown precision");
+    if ((N > 0 && !t_dev) || (M > 0 && !s_dev)) return lap_fail(FL_EINVAL, "fl_plan_kernel: NULL nodes");
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return lap_fail(FL_ENOMEM, "fl_plan_kernel: host allocation");
+    h->p.kind = 1;
+    h->p.prec = prec;
+    h->p.N = N;
+    h->p.M = M;
+    h->p.eps = eps;
+    fl_status s = plan_general_impl(h->p, kernel, t_dev, s_dev, q, (cudaStream_t)stream);
     if (s != FL_OK) {
         delete h;
         return s;

@@ -171,6 +171,9 @@ struct Plan {
     double* d_lapK = nullptr;      // coupling blocks K^{Y_m, Omega_l} (plan-time table)
     int64_t* d_lapKoff = nullptr;  // offset of band m's blocks in d_lapK
     int lap_blocks = 0;
+    int lap_kernel = 0;            // 0 Algorithm 1 (exp), 1 generalised exp, 2 generalised K_1/2
+    int32_t* d_nearT = nullptr;    // generalised Algorithm 1: the t_k in Omega_M
+    int64_t n_nearT = 0;
 
     // CUDA-graph replay of fl_execute / fl_execute_batched
     bool use_graph = false;

@@ -32,7 +32,7 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
 # Every symbol include/fl.h declares.
 EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
             "fl_adjoint", "fl_transposed",
-            "fl_plan_laplace", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
+            "fl_plan_laplace", "fl_plan_kernel", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
 
 
@@ -53,7 +53,7 @@ class fl_info(ctypes.Structure):
         ("band_K", ctypes.c_int64 * FL_MAX_LEVELS),
         ("band_n", ctypes.c_int64 * FL_MAX_LEVELS),
         ("model_bytes", ctypes.c_double), ("direct_bias", ctypes.c_double),
-        ("scratch_bytes", ctypes.c_double), ("variant", ctypes.c_int),
+        ("scratch_bytes", ctypes.c_double), ("variant", ctypes.c_int), ("kernel", ctypes.c_int),
     ]
 
 
@@ -66,6 +66,8 @@ class fl_options(ctypes.Structure):
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
 # band weights: Algorithm 2 (two-sided interpolation) or the one-sided variant
 VARIANTS = {"alg2": 0, "onesided": 1}
+# kernels of fl_plan_kernel (generalised Algorithm 1)
+KERNELS = {"laplace": 0, "exp": 1, "bessel_half": 2}
 
 
 class fl_timing(ctypes.Structure):
@@ -116,6 +118,7 @@ def load(path: str | None = None):
         "fl_adjoint": [vp, vp, vp, vp],
         "fl_transposed": [vp, vp, vp, vp],
         "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
+        "fl_plan_kernel": [pp, ci, i64, i64, vp, vp, ci, cd, ci, vp],
         "fl_laplace_real": [vp, vp, vp, vp],
         "fl_laplace_real_noalloc": [i64, i64, vp, vp, vp, vp, ci, cd, ci, vp],
         "fl_get_info": [vp, ctypes.POINTER(fl_info)],
@@ -197,6 +200,13 @@ def fl_plan_laplace(N, M, t_ptr, s_ptr, q, eps, prec, stream):
     h = ctypes.c_void_p()
     st = load().fl_plan_laplace(ctypes.byref(h), int(N), int(M), t_ptr, s_ptr, int(q),
                                 float(eps), int(prec), stream)
+    return st, h
+
+
+def fl_plan_kernel(kernel, N, M, t_ptr, s_ptr, q, eps, prec, stream):
+    h = ctypes.c_void_p()
+    st = load().fl_plan_kernel(ctypes.byref(h), int(kernel), int(N), int(M), t_ptr, s_ptr, int(q),
+                               float(eps), int(prec), stream)
     return st, h
 
 
@@ -289,6 +299,7 @@ def info_dict(info: fl_info) -> dict:
         "model_bytes": info.model_bytes, "direct_bias": info.direct_bias,
         "scratch_bytes": info.scratch_bytes,
         "variant": {v: k for k, v in VARIANTS.items()}.get(info.variant, info.variant),
+        "kernel": {v: k for k, v in KERNELS.items()}.get(info.kernel, info.kernel),
     }
 
 
@@ -474,9 +485,15 @@ class BatchedPlan:
 
 
 class LaplacePlan:
-    """Owner of an Algorithm-1 plan: f_j = sum_k c_k exp(-s_j t_k) (real data)."""
+    """Owner of an Algorithm-1 plan: f_j = sum_k c_k kappa(s_j, t_k) (real data).
 
-    def __init__(self, t, s, eps: float, precision: str = "fp64", q: int = 0, stream=None):
+    kernel: "laplace" (exp(-s t) by Algorithm 1, the default), or a kernel of
+    the generalised Algorithm 1: "exp" (exp(-s t)) or "bessel_half"
+    (K_{1/2}(s t) = sqrt(pi / (2 s t)) exp(-s t), s, t > 0).
+    """
+
+    def __init__(self, t, s, eps: float, precision: str = "fp64", q: int = 0, stream=None,
+                 kernel: str = "laplace"):
         torch = _torch()
         t = t.to(torch.float64).contiguous()
         s = s.to(torch.float64).contiguous()
@@ -484,9 +501,13 @@ class LaplacePlan:
         self.prec = FL_FP64 if precision == "fp64" else FL_FP32
         self.rdtype = torch.float64 if self.prec == FL_FP64 else torch.float32
         self._handle = None
-        st, h = fl_plan_laplace(self.N, self.M, _ptr(t), _ptr(s), q, eps, self.prec,
-                                _stream_handle(stream))
-        check(st, "fl_plan_laplace")
+        if kernel == "laplace":
+            st, h = fl_plan_laplace(self.N, self.M, _ptr(t), _ptr(s), q, eps, self.prec,
+                                    _stream_handle(stream))
+        else:
+            st, h = fl_plan_kernel(KERNELS[kernel], self.N, self.M, _ptr(t), _ptr(s), q, eps,
+                                   self.prec, _stream_handle(stream))
+        check(st, "fl_plan_laplace" if kernel == "laplace" else "fl_plan_kernel")
         self._handle = h
 
     @property

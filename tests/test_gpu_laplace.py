@@ -136,3 +136,80 @@ def test_deterministic(fl):
     a, _ = _run(fl, c, t, s, 1e-6, "fp32")
     b, _ = _run(fl, c, t, s, 1e-6, "fp32")
     assert np.array_equal(a, b)
+
+
+# --------------------------------------------------------------------------
+# Generalised Algorithm 1 (fl_plan_kernel): exp(-s t) and K_{1/2}(s t)
+
+def _run_kernel(fl, kernel, c, t, s, eps, prec, q=0):
+    dev = torch.device("cuda")
+    rdt = torch.float64 if prec == "fp64" else torch.float32
+    plan = fl.LaplacePlan(torch.from_numpy(t).to(dev), torch.from_numpy(s).to(dev), eps,
+                          precision=prec, q=q, kernel=kernel)
+    f = plan.execute(torch.from_numpy(np.asarray(c)).to(rdt).to(dev))
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    return f.cpu().numpy().astype(np.float64), info
+
+
+def _kernel_inputs(N, M, seed, near=True):
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(0.0, 1.0, N)
+    s = rng.uniform(0.0, 2.0 * N, M)
+    if near:   # a few nodes in the near fields Omega_M and Y_M
+        t[:3] = [1e-12, 3e-13, 1e-11]
+        s[:3] = [1e-9, 2e-10, 5e-9]
+    t[t == 0] = 0.5
+    s[s == 0] = 1.0
+    return rng.standard_normal(N), t, s
+
+
+def _kernel_tol(kind, eps, prec, c, t, s, ref):
+    # E <= eps in exact arithmetic; rounding is relative to sum_k |c_k kappa|
+    # (the singular kernel reaches ~1e10 in the near fields)
+    absum = np.max(np.abs(S.smooth_kernel(kind, s, t)) @ np.abs(c))
+    u = 2.0 ** -53 if prec == "fp64" else U32
+    return eps * np.sum(np.abs(c)) + 64 * u * absum
+
+
+@pytest.mark.parametrize("kind", ["exp", "bessel_half"])
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp64", 1e-6), ("fp32", 1e-5)])
+@pytest.mark.parametrize("N,M", [(700, 400), (1 << 16, 1 << 16), (33, 5000)])
+def test_general_kernel_against_oracle(fl, kind, prec, eps, N, M):
+    c, t, s = _kernel_inputs(N, M, seed=N + M)
+    f, info = _run_kernel(fl, kind, c, t, s, eps, prec)
+    assert info["kernel"] == kind
+    P = S.general_params(kind, eps, s.max(), t.max(), N)
+    assert info["q"] == P.q and info["levels"] == P.M
+    idx = np.arange(M) if M <= 4096 else np.concatenate(
+        [np.arange(3), np.random.default_rng(1).choice(M, 2000, replace=False)])
+    ref = oracle.kernel_direct(kind, c, t, s[idx])
+    err = np.max(np.abs(f[idx] - ref))
+    assert err <= _kernel_tol(kind, eps, prec, c, t, s[idx], ref), err
+
+
+@pytest.mark.parametrize("kind", ["exp", "bessel_half"])
+def test_general_kernel_matches_structured(fl, kind):
+    c, t, s = _kernel_inputs(900, 600, seed=5)
+    eps = 1e-8
+    f, info = _run_kernel(fl, kind, c, t, s, eps, "fp64")
+    fs, P = S.laplace_alg1_general(kind, c, t, s, eps)
+    assert info["q"] == P.q
+    # the same f~ step by step: rounding only
+    absum = np.max(np.abs(S.smooth_kernel(kind, s, t)) @ np.abs(c))
+    assert np.max(np.abs(f - fs)) <= 1e-12 * np.sum(np.abs(c)) + 64 * 2.0 ** -53 * absum
+
+
+def test_general_kernel_invalid(fl):
+    dev = torch.device("cuda")
+    t = torch.tensor([0.0, 0.5], dtype=torch.float64, device=dev)
+    s = torch.tensor([1.0, 2.0], dtype=torch.float64, device=dev)
+    with pytest.raises(fl.FLError) as ei:
+        fl.LaplacePlan(t, s, 1e-6, kernel="bessel_half")     # singular at s t = 0
+    assert ei.value.status == fl.FL_EINVAL
+    p = fl.LaplacePlan(t, s, 1e-6, kernel="exp")              # t = 0 is fine for exp
+    f = p.execute(torch.tensor([1.0, 2.0], dtype=torch.float64, device=dev)).cpu().numpy()
+    assert np.allclose(f, oracle.kernel_direct("exp", np.array([1.0, 2.0]), t.cpu().numpy(),
+                                               s.cpu().numpy()), rtol=1e-12, atol=1e-12)
+    p.close()
