@@ -40,7 +40,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT};
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -253,6 +253,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
     FL_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
+    FL_CUDA(cudaMalloc((void**)&p.d_cheb32, 3 * kMaxQ * sizeof(float)), "cudaMalloc cheb32");
     FL_CUDA(cudaMalloc(&p.d_z0, 2 * sizeof(double)), "cudaMalloc z0");
 
     // classify and sort the nodes of every transform into its slice

@@ -44,14 +44,19 @@ __device__ __forceinline__ int band_of_freq(double k, double xi1, int levels) {
 }
 
 // Chebyshev points t_s = cos((2s+1) pi / (2q)) and barycentric weights
-// lambda_s = (-1)^s sin((2s+1) pi / (2q)) (Section 2).
-__global__ void k_cheb(int q, double* cheb) {
+// lambda_s = (-1)^s sin((2s+1) pi / (2q)) (Section 2); cheb32 holds t_s as a
+// float pair (hi, lo: t_s = hi + lo to ~2^-48) and lambda_s in float.
+__global__ void k_cheb(int q, double* cheb, float* cheb32) {
     const int s = threadIdx.x;
     if (s >= q) return;
     double sn, cs;
     sincospi((2.0 * s + 1.0) / (2.0 * q), &sn, &cs);
     cheb[s] = cs;
     cheb[q + s] = (s & 1) ? -sn : sn;
+    const float hi = (float)cs;
+    cheb32[s] = hi;
+    cheb32[q + s] = (float)(cs - (double)hi);
+    cheb32[2 * q + s] = (float)cheb[q + s];
 }
 
 // K^{Y_m,Omega_l}_{s r} = exp(-y_s^{Y_m} xi_r^{Omega_l}) for l = l_m..L_m
@@ -197,7 +202,7 @@ cudaError_t build_twiddles(Plan& p, cudaStream_t st) {
 }
 
 cudaError_t build_cheb(Plan& p, cudaStream_t st) {
-    k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb);
+    k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb, p.d_cheb32);
     return cudaGetLastError();
 }
 
@@ -266,6 +271,55 @@ __device__ __forceinline__ void bary_weights(double y, const BandDev& B, int q,
     for (int s = 0; s < q; ++s) Ls[s] = (hit >= 0) ? (s == hit ? (T)1 : (T)0) : Ls[s] * inv;
 }
 
+// FP32 form of the q-right-hand-side gather: sum_s L_s(y) sum_t phi_t g_s[lo + t].
+// The barycentric differences tau - t_s are formed from float pairs
+// (tau_hi + tau_lo) - (t_s,hi + t_s,lo): the high parts cancel exactly when
+// tau is near t_s (Sterbenz), so each difference keeps float relative accuracy
+// without FP64 arithmetic per s.  The weights are recomputed in the gather loop
+// instead of being stored, and two right-hand sides are gathered per step.
+template <int MW>
+__device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, const BandDev& B,
+                                                 int64_t lo, int64_t nmask, const float* phi,
+                                                 double y, int q, const float* __restrict__ cheb32) {
+    const double tau = (y - B.yc) * B.yh_inv;
+    const float th = (float)tau, tl = (float)(tau - (double)th);
+    float den = 0.f;
+    int hit = -1;
+    for (int s = 0; s < q; ++s) {
+        const float d = (th - cheb32[s]) + (tl - cheb32[q + s]);
+        if (d == 0.f) hit = s;
+        den += cheb32[2 * q + s] / d;
+    }
+    const float inv = 1.f / den;
+    float2 acc = {0.f, 0.f};
+    for (int s = 0; s < q; s += 2) {
+        const bool two = s + 1 < q;
+        const float2* g0 = g + (int64_t)s * B.n;
+        const float2* g1 = g0 + B.n;
+        float2 a0 = {0.f, 0.f}, a1 = {0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 2 * MW; ++t) {
+            const int64_t idx = (lo + t) & nmask;
+            const float2 v0 = g0[idx];
+            const float2 v1 = two ? g1[idx] : float2{0.f, 0.f};
+            a0.x += phi[t] * v0.x;
+            a0.y += phi[t] * v0.y;
+            a1.x += phi[t] * v1.x;
+            a1.y += phi[t] * v1.y;
+        }
+        const float d0 = (th - cheb32[s]) + (tl - cheb32[q + s]);
+        float L0 = hit >= 0 ? (s == hit ? 1.f : 0.f) : cheb32[2 * q + s] / d0 * inv;
+        float L1 = 0.f;
+        if (two) {
+            const float d1 = (th - cheb32[s + 1]) + (tl - cheb32[q + s + 1]);
+            L1 = hit >= 0 ? (s + 1 == hit ? 1.f : 0.f) : cheb32[2 * q + s + 1] / d1 * inv;
+        }
+        acc.x += L0 * a0.x + L1 * a1.x;
+        acc.y += L0 * a0.y + L1 * a1.y;
+    }
+    return acc;
+}
+
 // Gather + barycentric recombination + centring shift, one thread per node in
 // sorted order; writes f[perm[i]].  Z^0 nodes (band 0) receive c_0.
 template <typename T, int MW>
@@ -274,7 +328,8 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
                                                 const int32_t* __restrict__ bandid,
                                                 const BandDev* __restrict__ bands,
                                                 const C_t<T>* __restrict__ grid,
-                                                const double* __restrict__ cheb, int q, T kb_b,
+                                                const double* __restrict__ cheb,
+                                                const float* __restrict__ cheb32, int q, T kb_b,
                                                 const C_t<T>* __restrict__ c, int deriv,
                                                 const C_t<T>* __restrict__ rmul,
                                                 C_t<T>* __restrict__ f) {
@@ -302,14 +357,22 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     const int64_t nmask = B.n - 1;
     const C* g = grid + B.grid_off;
     C acc = {(T)0, (T)0};
-    if (B.nrhs == 1) {
+    bool done = false;
+    if constexpr (sizeof(T) == 4) {
+        if (B.nrhs > 1) {
+            acc = gather_rhs_f32<MW>(g, B, lo, nmask, phi, kTwoPiD * wv.y, q, cheb32);
+            done = true;
+        }
+    }
+    if (done) {
+    } else if (B.nrhs == 1) {
 #pragma unroll
         for (int t = 0; t < 2 * MW; ++t) {
             const C v = g[(lo + t) & nmask];
             acc.x += phi[t] * v.x;
             acc.y += phi[t] * v.y;
         }
-    } else {
+    } else if constexpr (sizeof(T) == 8) {
         T Ls[kMaxQ];
         bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
         for (int s = 0; s < q; ++s) {
@@ -622,8 +685,8 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
     int slot;
     timer_begin(p, "gather", bytes, st, &slot);
     k_gather<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
-        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.q,
-        (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, (C*)f);
+        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.d_cheb32,
+        p.q, (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, (C*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
