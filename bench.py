@@ -344,6 +344,12 @@ def secondary_workloads(dev, flush, rank):
     fwd = _time_cuda(lambda: op(c.detach(), w.detach()), 10, flush)
     out["gradients_2^18_fp32"] = {"ms_fwd_bwd": ms, "ms_fwd": fwd, "unit": "ms",
                                   "note": "forward + adjoint (grad c) + k-weighted transform (grad w)"}
+    # adjoint and transposed evaluation (C^T g, integer exponents) on the same plan
+    r = g.detach()
+    adj = _time_cuda(lambda: op._plan.adjoint(r), 10, flush)
+    tr = _time_cuda(lambda: op._plan.transposed(r), 10, flush)
+    out["adjoint_transposed_2^18_fp32"] = {"ms_adjoint": adj, "ms_transposed": tr,
+                                           "value_transposed": N * M / (tr * 1e-3), "unit": "ms"}
     return out
 
 

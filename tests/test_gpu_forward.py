@@ -241,3 +241,27 @@ def test_derivative_and_node_gradient_routes(fl, route):
     ref = oracle.flt_direct(cd, w)
     f, _ = _run(fl, c, w, 1e-10, "fp64", deriv=True, route=route)
     assert oracle.error_E(ref, f, cd) <= 1e-10
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_nodes_on_and_next_to_chebyshev_points(fl, prec, eps):
+    # y = 2 pi Im w on (or a few ulps from) a Chebyshev point of its band: the
+    # barycentric weights take their hit / near-hit branches (FP32 form: the
+    # differences tau - t_s from float pairs; FP64 form: in double).
+    N = 3000
+    c = W.coefficients(N, seed=21)
+    P = S.xflt_params(N, eps)
+    q = P.lap.q
+    ts = S.chebyshev_points(q)
+    rows = []
+    rng = np.random.default_rng(22)
+    for m in (2, 5, 9, 14):
+        a = P.y1 / 2.0 ** m
+        for s in (0, q // 2, q - 1):
+            y = 1.5 * a + 0.5 * a * ts[s]
+            for rel in (0.0, 1e-15, -3e-16, 1e-9):
+                rows.append([rng.uniform(), y * (1 + rel) / (2 * np.pi)])
+    w = np.array(rows)
+    f, _ = _run(fl, c, w, eps, prec)
+    ref = oracle.flt_direct(c, w)
+    assert oracle.error_E(ref, f, c) <= tol(eps, prec, ref, c)
