@@ -67,9 +67,11 @@ def _load():
             lib.oracle_flt_adjoint_at.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_laplace_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_kernel_direct.argtypes = [ci, i64, dp, dp, i64, dp, dp, ci]
+            lib.oracle_xi_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_flt_brute_ld.argtypes = [i64, dp, i64, dp, dp]
             for fn in (lib.oracle_flt_direct, lib.oracle_flt_adjoint, lib.oracle_flt_adjoint_at,
-                       lib.oracle_laplace_direct, lib.oracle_kernel_direct, lib.oracle_flt_brute_ld):
+                       lib.oracle_laplace_direct, lib.oracle_kernel_direct, lib.oracle_xi_direct,
+                       lib.oracle_flt_brute_ld):
                 fn.restype = ci
             lib.oracle_default_threads.restype = ci
             _lib = lib
@@ -136,6 +138,19 @@ def laplace_direct(c, t, s, threads: int = 0) -> np.ndarray:
                                        s.ctypes.data, f.ctypes.data, threads)
     if rc != 0:
         raise ValueError("oracle_laplace_direct: invalid arguments")
+    return f
+
+
+def xi_direct(c, xi, w, threads: int = 0) -> np.ndarray:
+    """f_j = sum_k c_k exp(2 pi i xi_k w_j) for real exponents xi_k >= 0 (eq. 4.1
+    with general xi_k), FP64 term by term."""
+    c, w = _c128(c), _nodes(w)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    f = np.empty(w.shape[0], dtype=np.complex128)
+    rc = _load().oracle_xi_direct(c.size, c.ctypes.data, xi.ctypes.data, w.shape[0], w.ctypes.data,
+                                  f.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle_xi_direct: invalid arguments")
     return f
 
 

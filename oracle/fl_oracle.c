@@ -23,6 +23,9 @@
  *                          generalised Algorithm 1 (Section 3, after Algorithm 1):
  *                          kind 1 exp(-s t), kind 2 the Bessel kernel of the
  *                          example there, K_{1/2}(s t) = sqrt(pi / (2 s t)) exp(-s t).
+ *   oracle_xi_direct       f_j = sum_k c_k exp(2 pi i xi_k w_j) for real exponents
+ *                          xi_k (the generalised polynomials of eq. (4.1) with
+ *                          xi_k in [1, N]): z_j^xi_k = exp(-y xi_k) exp(2 pi i xi_k x).
  *   oracle_flt_brute_ld    oracle_flt_direct in long double, for tiny N.
  *
  * Phase reduction: the phase k*x is split exactly into p + e with an FMA
@@ -160,6 +163,51 @@ int oracle_flt_direct(int64_t N, const double *c, int64_t M, const double *w,
         if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
     flt_ctx cx = {N, c, w, f};
     run_parallel(flt_range, &cx, M, nthreads);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Real exponents: f_j = sum_k c_k exp(2 pi i xi_k w_j).  The phase xi_k x is  */
+/* split exactly with an FMA as for integer k.                               */
+
+typedef struct {
+    int64_t N;
+    const double *c, *xi, *w;
+    double *f;
+} xi_ctx;
+
+static void xi_range(void *vctx, int64_t lo, int64_t hi)
+{
+    const xi_ctx *cx = (const xi_ctx *)vctx;
+    for (int64_t j = lo; j < hi; ++j) {
+        const double x = cx->w[2 * j];
+        const double y = ORACLE_TWO_PI * cx->w[2 * j + 1];
+        acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
+        for (int64_t k = 0; k < cx->N; ++k) {
+            const double xk = cx->xi[k];
+            const double mag = exp(-y * xk);
+            const double ang = ORACLE_TWO_PI * phase_frac(xk, x);
+            const double zr = mag * cos(ang), zi = mag * sin(ang);
+            const double cr = cx->c[2 * k], ci = cx->c[2 * k + 1];
+            acc_add(&re, cr * zr);
+            acc_add(&re, -(ci * zi));
+            acc_add(&im, cr * zi);
+            acc_add(&im, ci * zr);
+        }
+        cx->f[2 * j] = acc_get(&re);
+        cx->f[2 * j + 1] = acc_get(&im);
+    }
+}
+
+int oracle_xi_direct(int64_t N, const double *c, const double *xi, int64_t M,
+                     const double *w, double *f, int nthreads)
+{
+    if (N < 0 || M < 0 || (N > 0 && (!c || !xi)) || (M > 0 && (!w || !f))) return -1;
+    for (int64_t k = 0; k < N; ++k) if (!(xi[k] >= 0.0) || !isfinite(xi[k])) return -1;
+    for (int64_t j = 0; j < M; ++j)
+        if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
+    xi_ctx cx = {N, c, xi, w, f};
+    run_parallel(xi_range, &cx, M, nthreads);
     return 0;
 }
 

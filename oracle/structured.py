@@ -487,3 +487,67 @@ def laplace_alg1_general(kind: str, c, t, s, eps: float, q: int | None = None):
             fm = fm + smooth_kernel(kind, s[sel], t[near_t]) @ c[near_t]
         f[sel] = fm
     return f, p
+
+
+# --------------------------------------------------------------------------
+# Real exponents (eq. 4.1 with xi_k in [1, N]): Algorithm 2 with the Fourier
+# factor A = (exp(2 pi i xi_k x_j)) applied exactly (a dense NNDFT; the fast
+# path uses an NNFFT).  Readings: x = Re w is taken as given (principal branch
+# of z^xi: nodes with |Re w| <= 1/2, the negative real axis Re w = +-1/2 kept as
+# the limit from either side), so no reduction mod 1; Z^0 nodes give 0
+# (every term is below eps |c_k| there because xi_k >= 1); the frequency bands
+# Omega_l and the weights W_{k,s} are those of Algorithm 2 evaluated at the
+# values xi_k, with xi_1 = max xi_k.
+
+def nndft(coef, xi, x) -> np.ndarray:
+    """sum_k coef_k exp(2 pi i xi_k x_j) (dense); coef may be 2-D (k, s)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    E = np.exp(2j * np.pi * np.outer(x, xi))
+    return E @ coef
+
+
+def xflt_alg2_xi(c, xi, w, eps: float, q: int | None = None):
+    """Algorithm 2 for real exponents xi_k >= 1 with exact NNDFTs; returns (f~, params)."""
+    c = np.asarray(c, dtype=np.complex128)
+    xi = np.asarray(xi, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64).reshape(-1, 2)
+    x, yim = w[:, 0], w[:, 1]
+    N = c.size
+    eps_K = eps / 3.0
+    y1 = math.log(1.0 / eps)
+    xi1 = float(xi.max())
+    p = laplace_params(eps_K, y1, xi1, q)
+    P = XFLTParams(eps, eps_K, y1, xi1, p)
+    y = 2.0 * np.pi * yim
+    f = np.zeros(x.shape, dtype=np.complex128)
+    z0 = y > y1
+    bx = np.where(z0, 0, band_of(y, y1, p.M))
+    bk = band_of(xi, xi1, p.M)
+    sel = bx == p.M
+    if sel.any():
+        f[sel] = nndft(c, xi, x[sel])
+    Fhat = {}
+    for l in range(1, p.M):
+        kl = np.nonzero(bk == l)[0]
+        a, b = band_interval(xi1, l)
+        Fhat[l] = (c[kl][:, None] * lagrange_barycentric(xi[kl], a, b, p.q), kl)
+    for m in range(1, p.M):
+        sel = bx == m
+        if not sel.any():
+            continue
+        xm = x[sel]
+        kiv = np.nonzero(bk > p.L[m])[0]
+        fm = nndft(c[kiv], xi[kiv], xm) if kiv.size else np.zeros(xm.size, complex)
+        rows, ks = [], []
+        for l in range(p.ell[m], p.L[m] + 1):
+            Fl, kl = Fhat[l]
+            if kl.size:
+                rows.append(Fl @ kernel_block(p, m, l).T)
+                ks.append(kl)
+        if rows:
+            F = nndft(np.concatenate(rows, axis=0), xi[np.concatenate(ks)], xm)
+            ya, yb = band_interval(y1, m)
+            fm = fm + (lagrange_barycentric(y[sel], ya, yb, p.q) * F).sum(axis=1)
+        f[sel] = fm
+    return f, P

@@ -185,3 +185,29 @@ def test_kernel_direct_pins():
     assert np.max(np.abs(got - np.array([float(r) for r in ref]))) <= 1e-13 * np.sum(np.abs(c))
     with pytest.raises(ValueError):
         oracle.kernel_direct("bessel_half", c, np.zeros(50), s)   # singular at s t = 0
+
+
+def test_xi_direct_pins():
+    # real exponents: integer xi_k = k + 1 reduce to z * (the integer sum); single
+    # terms and a 40-digit brute force for fractional xi_k
+    mpmath = pytest.importorskip("mpmath")
+    rng = np.random.default_rng(11)
+    N, M = 60, 25
+    c = W.coefficients(N, seed=12)
+    w = W.nodes_disk_uniform(M, seed=13)
+    w[:, 0] -= 0.5                         # principal branch: Re w in [-1/2, 1/2)
+    z = np.exp(2j * np.pi * (w[:, 0] + 1j * w[:, 1]))
+    got = oracle.xi_direct(c, np.arange(N) + 1.0, w)
+    assert np.max(np.abs(got - z * oracle.flt_direct(c, w))) <= 1e-13 * np.sum(np.abs(c))
+    xi = np.sort(rng.uniform(1.0, N, N))
+    mpmath.mp.dps = 40
+    two_pi_i = 2j * mpmath.pi
+    ref = []
+    for j in range(M):
+        wj = mpmath.mpc(w[j, 0], w[j, 1])
+        ref.append(complex(sum(mpmath.mpc(c[k].real, c[k].imag) * mpmath.exp(two_pi_i * mpmath.mpf(xi[k]) * wj)
+                               for k in range(N))))
+    got = oracle.xi_direct(c, xi, w)
+    assert np.max(np.abs(got - np.array(ref))) <= 1e-14 * np.sum(np.abs(c))
+    with pytest.raises(ValueError):
+        oracle.xi_direct(c, -xi, w)

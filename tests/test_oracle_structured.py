@@ -324,3 +324,23 @@ def test_general_algorithm1_meets_eps(kind, eps):
     if kind == "exp":
         f1, _ = S.laplace_alg1(c, t, s, eps)
         assert np.max(np.abs(f - f1)) <= 2 * eps * np.sum(np.abs(c))
+
+
+# --------------------------------------------------------------------------
+# Real exponents (eq. 4.1 with xi_k in [1, N]) with exact NNDFTs
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
+@pytest.mark.parametrize("kind", ["disk", "clustered", "integer"])
+def test_algorithm2_real_exponents_meets_eps(eps, kind):
+    rng = np.random.default_rng(41)
+    N, M = 500, 300
+    c = W.coefficients(N, seed=42)
+    xi = np.arange(N) + 1.0 if kind == "integer" else np.sort(rng.uniform(1.0, N, N))
+    w = (W.nodes_circle_clustered(M, seed=43) if kind == "clustered"
+         else W.nodes_disk_uniform(M, seed=44)).copy()
+    w[:, 0] -= 0.5
+    w = np.concatenate([w, [[0.1, 4.0], [-0.5, 0.0], [0.5, 0.3]]])   # Z^0 node, branch edges
+    ref = oracle.xi_direct(c, xi, w)
+    f, P = S.xflt_alg2_xi(c, xi, w, eps)
+    assert oracle.error_E(ref, f, c) <= eps
+    assert f[M] == 0                                   # Z^0 -> 0 (xi_k >= 1)
