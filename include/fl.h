@@ -229,6 +229,29 @@ fl_status fl_adjoint(fl_plan_t p, const void *r_dev, void *c_out_dev, void *stre
 fl_status fl_transposed(fl_plan_t p, const void *g_dev, void *out_dev, void *stream);
 
 /*
+ * fl_plan_xi -- plan the generalised polynomial of eq. (4.1) with real
+ * exponents: f_j = sum_k c_k z_j^{xi_k} = sum_k c_k exp(2 pi i xi_k w_j),
+ * xi_k >= 1 (the paper's xi_k in [1, N]).  Algorithm 2 with the bands and
+ * weights evaluated at the exponent values (xi_1 = max xi_k) and every band's
+ * Fourier factor computed by an NNFFT (nonequispaced in time and frequency,
+ * as the proof of Theorem 4.3 notes): the exponents are spread onto a
+ * frequency grid of spacing 1/2 with a Kaiser-Bessel window, followed by an
+ * NFFT at x/2 and the division by the window's transform.
+ *   xi_dev    : device, N float64 exponents >= 1 (any order; read at planning).
+ *   nodes_dev : device, M x {Re w, Im w}; |Re w| <= 1/2 (principal branch of
+ *               z^xi, the negative real axis Re w = +-1/2 as a one-sided
+ *               limit), Im w >= 0.
+ *   q, eps, prec : as fl_plan (each NNFFT gets eps/3).
+ * Nodes with |z| < eps return 0 (every term is below eps |c_k| there).
+ * Forward only: fl_execute / fl_execute_host; the derivative, gradient,
+ * adjoint and transposed calls return FL_EUNSUPPORTED.  Returns FL_EINVAL for
+ * an exponent below 1 or not finite and for a node outside the range above,
+ * FL_EUNSUPPORTED for N > 2^22.
+ */
+fl_status fl_plan_xi(fl_plan_t *out, int64_t N, const double *xi_dev, int64_t M,
+                     const double *nodes_dev, int q, double eps, fl_precision prec, void *stream);
+
+/*
  * fl_plan_laplace -- plan Algorithm 1 (Section 3) for the real discrete Laplace
  * transform f_j = sum_k c_k exp(-s_j t_k).
  *   t_dev : device, N float64 frequencies t_k >= 0.

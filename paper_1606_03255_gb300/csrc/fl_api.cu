@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -40,7 +41,8 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32};
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32,
+                    d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -113,14 +115,69 @@ static fl_status select_common(Plan& p, int q_in) {
         p.q = (int)ceil(0.5 + log(1.0 / p.eps_K) / log(4.0));
     if (p.q > kMaxQ) return fail(FL_EUNSUPPORTED, "interpolation rank q above 40");
     p.y1 = log(1.0 / p.eps);            // Z^0 removed: y in [0, ln(1/eps)]
-    p.mw = window_width(p.eps_A, 2.0);
+    // real exponents: two windows (frequency spreading and the outer NFFT),
+    // the latter's error amplified by up to Phi(0)/Phi(1/4) < 8 in the division
+    // by Phi(x/2): each gets eps_A / 8
+    p.mw = window_width(p.xi_mode ? p.eps_A / 8.0 : p.eps_A, 2.0);
     p.kb_b = M_PI * (2.0 - 1.0 / 2.0);
+    return FL_OK;
+}
+
+// Real exponents: Definition 3.2 with xi_1 = max xi_k; band m keeps the sorted
+// exponents xi_k <= xi_1 / 2^(l_m - 1) (a prefix of length K).  Its NNFFT
+// spreads them, centred on xc (2 xc = floor of the cut, an integer), onto the
+// frequency grid of spacing 1/2 (grid frequency g <-> xi = xc + g/2; taps
+// g in (2(xi - xc) - m_w, 2(xi - xc) + m_w]); the occupied |g| <= gh, and the
+// outer NFFT has bandwidth Nm = 2^lg >= 2 gh + 2 on n = 2 Nm points.
+static fl_status select_bands_xi(Plan& p, Instance& in, int inst_index) {
+    const std::vector<double>& xs = p.h_xis;
+    in.xi1 = xs.empty() ? 0.0 : xs.back();
+    const double lv = ceil(log2(p.y1 * in.xi1 / p.eps_K)) + 1.0;
+    in.levels = (int)std::max(1.0, lv);
+    if (in.levels > 127) return fail(FL_EUNSUPPORTED, "more than 127 dyadic levels");
+    in.band_base = (int)p.bands.size();
+    for (int b = 0; b <= in.levels; ++b) {
+        BandHost bh;
+        bh.inst = inst_index;
+        bh.local = b;
+        bh.dev.c_off = in.noff;
+        if (b == 0) {
+            p.bands.push_back(bh);
+            continue;
+        }
+        double cut = in.xi1;
+        if (b < in.levels) {
+            const double lg = log2(p.y1 * in.xi1) - b - log2(log(1.0 / p.eps_K));
+            bh.ell = std::max(1, (int)floor(lg) + 1);
+            bh.Lm = in.levels - b;
+            cut = std::min(in.xi1, ldexp(in.xi1, 1 - bh.ell));
+            bh.dev.nrhs = p.q;
+            const double a = ldexp(p.y1, -b);
+            bh.dev.yc = 1.5 * a;
+            bh.dev.yh = 0.5 * a;
+            bh.dev.yh_inv = 1.0 / bh.dev.yh;
+        } else {
+            bh.dev.nrhs = 1;
+        }
+        const int64_t K = (int64_t)(std::upper_bound(xs.begin(), xs.end(), cut) - xs.begin());
+        const double two_xc = floor(cut);
+        bh.dev.xc = 0.5 * two_xc;
+        bh.dev.gh = (int64_t)std::max(two_xc, ceil(2.0 * cut - two_xc)) + p.mw + 1;
+        const int lg = std::max(4, ilog2_ceil(2 * bh.dev.gh + 2));
+        bh.dev.K = K;
+        bh.dev.Nm = (int64_t)1 << lg;
+        bh.dev.log2n = lg + 1;
+        bh.dev.n = (int64_t)1 << (lg + 1);
+        if (bh.dev.log2n > kMaxLog2n) return fail(FL_EUNSUPPORTED, "NNFFT grid above 2^24 points");
+        p.bands.push_back(bh);
+    }
     return FL_OK;
 }
 
 // The dyadic partition of one transform (Definition 3.2 with xi_1 = N - 1):
 // appends its bands 0..levels to p.bands.
 static fl_status select_bands(Plan& p, Instance& in, int inst_index) {
+    if (p.xi_mode) return select_bands_xi(p, in, inst_index);
     in.xi1 = (double)(in.N - 1);        // frequencies 0..N-1
     if (in.N == 1) {
         in.levels = 1;
@@ -296,7 +353,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             if (e == cudaSuccess) e = cudaStreamSynchronize(st);
             if (e == cudaSuccess && flag) {
                 cleanup();
-                return fail(FL_EINVAL, "fl_plan: a node has Im w < 0 or a non-finite part");
+                return fail(FL_EINVAL, p.xi_mode ? "fl_plan_xi: a node has Im w < 0, a non-finite part or |Re w| > 1/2"
+                                                 : "fl_plan: a node has Im w < 0 or a non-finite part");
             }
         }
         cleanup();
@@ -698,7 +756,8 @@ fl_status fl_execute(fl_plan_t h, const void* c_dev, void* f_dev, void* stream) 
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute: NULL buffer");
     if (h->p.batched) return fail(FL_EINVAL, "fl_execute: batched plan (use fl_execute_batched)");
-    cudaError_t e = forward_graphed(h->p, c_dev, f_dev, (cudaStream_t)stream);
+    cudaError_t e = h->p.xi_mode ? run_forward_xi(h->p, c_dev, f_dev, (cudaStream_t)stream)
+                                 : forward_graphed(h->p, c_dev, f_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute");
     return FL_OK;
 }
@@ -707,6 +766,7 @@ fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* st
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_deriv: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_deriv: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: batched plans are forward only");
+    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: real-exponent plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, f_dev, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute_deriv");
     return FL_OK;
@@ -716,6 +776,7 @@ fl_status fl_grad_w(fl_plan_t h, const void* c_dev, const void* r_dev, void* gw_
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_grad_w: not a Fourier-Laplace plan");
     if (h->p.M > 0 && (!c_dev || !r_dev || !gw_dev)) return fail(FL_EINVAL, "fl_grad_w: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_grad_w: batched plans are forward only");
+    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_grad_w: real-exponent plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, gw_dev, true, (cudaStream_t)stream, r_dev);
     if (e != cudaSuccess) return cuda_fail(e, "fl_grad_w");
     return FL_OK;
@@ -730,7 +791,9 @@ fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* s
     if (!p.d_stage_c) FL_CUDA(cudaMalloc(&p.d_stage_c, p.N * cs), "cudaMalloc staging");
     if (!p.d_stage_f && p.M > 0) FL_CUDA(cudaMalloc(&p.d_stage_f, p.M * cs), "cudaMalloc staging");
     FL_CUDA(cudaMemcpyAsync(p.d_stage_c, c_host, p.N * cs, cudaMemcpyHostToDevice, st), "copy c");
-    FL_CUDA(forward_graphed(p, p.d_stage_c, p.d_stage_f, st), "fl_execute_host");
+    FL_CUDA(p.xi_mode ? run_forward_xi(p, p.d_stage_c, p.d_stage_f, st)
+                      : forward_graphed(p, p.d_stage_c, p.d_stage_f, st),
+            "fl_execute_host");
     if (p.M > 0)
         FL_CUDA(cudaMemcpyAsync(f_host, p.d_stage_f, p.M * cs, cudaMemcpyDeviceToHost, st), "copy f");
     FL_CUDA(cudaStreamSynchronize(st), "fl_execute_host: synchronise");
@@ -741,6 +804,7 @@ fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stre
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_adjoint: not a Fourier-Laplace plan");
     if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
+    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_adjoint: real-exponent plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
     return FL_OK;
@@ -750,8 +814,68 @@ fl_status fl_transposed(fl_plan_t h, const void* g_dev, void* out_dev, void* str
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_transposed: not a Fourier-Laplace plan");
     if (!out_dev || (h->p.M > 0 && !g_dev)) return fail(FL_EINVAL, "fl_transposed: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_transposed: batched plans are forward only");
+    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_transposed: real-exponent plans are forward only");
     cudaError_t e = run_transposed(h->p, g_dev, out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_transposed");
+    return FL_OK;
+}
+
+fl_status fl_plan_xi(fl_plan_t* out, int64_t N, const double* xi_dev, int64_t M,
+                     const double* nodes_dev, int q, double eps, fl_precision prec, void* stream) {
+    g_err.clear();
+    if (!out) return fail(FL_EINVAL, "fl_plan_xi: out is NULL");
+    *out = nullptr;
+    if (N < 1 || M < 0) return fail(FL_EINVAL, "fl_plan_xi: need N >= 1 and M >= 0");
+    if (N > ((int64_t)1 << 22) || M > ((int64_t)1 << 31) - 1)
+        return fail(FL_EUNSUPPORTED, "fl_plan_xi: N above 2^22 or M above 2^31 - 1");
+    if (!(eps > 0.0 && eps < 1.0)) return fail(FL_EINVAL, "fl_plan_xi: eps must lie in (0, 1)");
+    if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan_xi: q must lie in [0, 40]");
+    if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan_xi: unknown precision");
+    if (!xi_dev || (M > 0 && !nodes_dev)) return fail(FL_EINVAL, "fl_plan_xi: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> xh(N);
+    FL_CUDA(cudaMemcpyAsync(xh.data(), xi_dev, N * sizeof(double), cudaMemcpyDeviceToHost, st), "copy xi");
+    FL_CUDA(cudaStreamSynchronize(st), "fl_plan_xi: synchronise");
+    std::vector<std::pair<double, int32_t>> order(N);
+    for (int64_t k = 0; k < N; ++k) {
+        if (!(xh[k] >= 1.0) || !std::isfinite(xh[k]))
+            return fail(FL_EINVAL, "fl_plan_xi: every exponent must be finite and >= 1");
+        order[k] = {xh[k], (int32_t)k};
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<double, int32_t>& a, const std::pair<double, int32_t>& b) {
+                         return a.first < b.first;
+                     });
+    fl_plan_s* h = new (std::nothrow) fl_plan_s();
+    if (!h) return fail(FL_ENOMEM, "fl_plan_xi: host allocation");
+    Plan& p = h->p;
+    p.kind = 0;
+    p.prec = prec;
+    p.eps = eps;
+    p.route_mode = 1;
+    p.xi_mode = true;
+    p.h_xis.resize(N);
+    std::vector<int32_t> perm(N);
+    for (int64_t k = 0; k < N; ++k) {
+        p.h_xis[k] = order[k].first;
+        perm[k] = order[k].second;
+    }
+    auto bail = [&](fl_status s) {
+        delete h;
+        return s;
+    };
+    cudaError_t e = cudaMalloc((void**)&p.d_xis, N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p.d_xperm, N * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p.d_xis, p.h_xis.data(), N * sizeof(double), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p.d_xperm, perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "fl_plan_xi: exponents"));
+    fl_status s = plan_multi(p, 1, &N, &M, nodes_dev, q, st);
+    if (s != FL_OK) return bail(s);
+    e = build_xi_tables(p, st);
+    if (e != cudaSuccess) return bail(cuda_fail(e, "fl_plan_xi: tables"));
+    *out = h;
     return FL_OK;
 }
 

@@ -65,6 +65,15 @@ __host__ __device__ constexpr int tw_region(int LOG2L, int FIRST) {
     return ((LOG2L - kTwMinLog) * 2 + (FIRST - 3)) * kTwRegion;
 }
 
+// Kaiser-Bessel window in grid units, phi(t) = sinh(b sqrt(m^2 - t^2)) / sqrt(m^2 - t^2),
+// |t| <= m (limit b at |t| = m).
+template <typename T> __device__ __forceinline__ T kb_window(T t, T m, T b) {
+    const T s2 = m * m - t * t;
+    if (!(s2 > (T)0)) return b;
+    const T r = sqrt(s2);
+    return sinh(b * r) / r;
+}
+
 // Per-band descriptor (bands 1..levels; band 0 is Z^0).  Built on the host at
 // plan time, read by every kernel of the forward and adjoint transforms.
 struct BandDev {
@@ -85,6 +94,12 @@ struct BandDev {
     int pad2;
     int64_t c_off;     // offset of the band's transform in the coefficient buffer (batches)
     int64_t nodes;     // nodes of the band (sorted positions node_off .. node_off + nodes)
+    // real exponents (NNFFT bands): 2 xc is the integer grid position of the
+    // band's centre frequency, gh the half-width of the occupied grid
+    // frequencies, phi_off the offset of the grid's 1/Phi table
+    double xc;
+    int64_t gh;
+    int64_t phi_off;
 };
 
 // ---------------------------------------------------------------------------

@@ -511,6 +511,7 @@ cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands
     extern template cudaError_t launch_pass1<T, 1, 0, false>(FL_P1_SIG(T)); \
     extern template cudaError_t launch_pass1<T, 1, 0, true>(FL_P1_SIG(T));  \
     extern template cudaError_t launch_pass1<T, -1, 1, false>(FL_P1_SIG(T)); \
+    extern template cudaError_t launch_pass1<T, 1, 1, false>(FL_P1_SIG(T));  \
     extern template cudaError_t launch_pass2<T, 1>(FL_P2_SIG(T));          \
     extern template cudaError_t launch_pass2<T, -1>(FL_P2_SIG(T));
 

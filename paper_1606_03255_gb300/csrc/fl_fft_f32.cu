@@ -7,6 +7,7 @@ namespace fl {
 template cudaError_t launch_pass1<float, 1, 0, false>(FL_P1_SIG(float));
 template cudaError_t launch_pass1<float, 1, 0, true>(FL_P1_SIG(float));
 template cudaError_t launch_pass1<float, -1, 1, false>(FL_P1_SIG(float));
+template cudaError_t launch_pass1<float, 1, 1, false>(FL_P1_SIG(float));
 template cudaError_t launch_pass2<float, 1>(FL_P2_SIG(float));
 template cudaError_t launch_pass2<float, -1>(FL_P2_SIG(float));
 

@@ -7,6 +7,7 @@ namespace fl {
 template cudaError_t launch_pass1<double, 1, 0, false>(FL_P1_SIG(double));
 template cudaError_t launch_pass1<double, 1, 0, true>(FL_P1_SIG(double));
 template cudaError_t launch_pass1<double, -1, 1, false>(FL_P1_SIG(double));
+template cudaError_t launch_pass1<double, 1, 1, false>(FL_P1_SIG(double));
 template cudaError_t launch_pass2<double, 1>(FL_P2_SIG(double));
 template cudaError_t launch_pass2<double, -1>(FL_P2_SIG(double));
 

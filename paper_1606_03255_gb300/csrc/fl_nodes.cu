@@ -23,9 +23,11 @@ __device__ __forceinline__ int band_of(double v, double v1, int levels) {
     return b;
 }
 
+// xhalf (real exponents): the grid coordinate is x/2 (the NNFFT's outer NFFT
+// runs at x/2) and |Re w| <= 1/2 is required (principal branch of z^xi).
 __global__ void k_classify(int64_t M, const double* __restrict__ w,
                            const BandDev* __restrict__ bands, int levels, double y1,
-                           int constant_only, uint32_t* __restrict__ keys,
+                           int constant_only, int xhalf, uint32_t* __restrict__ keys,
                            int32_t* __restrict__ vals, unsigned long long* __restrict__ counts,
                            int* __restrict__ flag) {
     __shared__ unsigned int cnt[FL_MAX_LEVELS + 1];
@@ -36,15 +38,16 @@ __global__ void k_classify(int64_t M, const double* __restrict__ w,
         const double x = w[2 * j], v = w[2 * j + 1];
         int band = 0;
         uint32_t cell = 0;
-        if (!(v >= 0.0) || !isfinite(x) || !isfinite(v)) {
+        if (!(v >= 0.0) || !isfinite(x) || !isfinite(v) || (xhalf && !(fabs(x) <= 0.5))) {
             atomicOr(flag, 1);
         } else if (!constant_only) {
             const double y = kTwoPi * v;          // the paper's radial variable
             band = (y > y1) ? 0 : band_of(y, y1, levels);
             const int64_t n = bands[band].n;
             if (band > 0 && n > 0) {
-                const double xr = x - floor(x);   // exact
-                cell = (uint32_t)floor(xr * (double)n);   // exact: n is a power of two
+                const double xs = xhalf ? 0.5 * x : x;   // exact
+                const double xr = xs - floor(xs);        // exact
+                cell = (uint32_t)floor(xr * (double)n);  // exact: n is a power of two
             }
         }
         keys[j] = ((uint32_t)band << 25) | cell;
@@ -62,7 +65,8 @@ cudaError_t launch_classify(const Plan& p, const Instance& in, const double* nod
     const int bs = 256;
     const int64_t grid = (in.M + bs - 1) / bs;
     k_classify<<<(unsigned)grid, bs, 0, st>>>(in.M, nodes + 2 * in.moff, p.d_bands + in.band_base,
-                                              in.levels, p.y1, in.N == 1 ? 1 : 0, keys, vals,
+                                              in.levels, p.y1, (in.N == 1 && !p.xi_mode) ? 1 : 0,
+                                              p.xi_mode ? 1 : 0, keys, vals,
                                               (unsigned long long*)(counts + in.band_base), flag);
     return cudaGetLastError();
 }

@@ -117,6 +117,16 @@ struct Plan {
     int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
     int variant = 0;               // 0 Algorithm 2 weights, 1 one-sided interpolation
+    // real exponents xi_k >= 1 (fl_plan_xi): the Fourier factor is an NNFFT
+    bool xi_mode = false;
+    std::vector<double> h_xis;     // exponents in ascending order (host)
+    double* d_xis = nullptr;       // the same on the device
+    int32_t* d_xperm = nullptr;    // sorted position -> coefficient index
+    int32_t* d_xbk = nullptr;      // floor(2 xi_k) per sorted position
+    int32_t* d_xstart = nullptr;   // first sorted position with floor(2 xi) >= B, B = 0 .. 2 xi_1 + 1
+    void* d_xwin = nullptr;        // frequency-window taps per sorted position (2 m_w, T)
+    void* d_xiphi = nullptr;       // 1 / Phi of every NNFFT grid size (T)
+    int64_t xiphi_elems = 0;
     double direct_bias = 1.0;
     double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)
     std::vector<DirectItem> direct_work;
@@ -213,6 +223,10 @@ cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_
                         const void* rmul = nullptr);
 cudaError_t run_adjoint(Plan& p, const void* r, void* c_out, cudaStream_t st);
 cudaError_t run_transposed(Plan& p, const void* g, void* out, cudaStream_t st);
+// Real exponents (fl_xi.cu): plan-time tables and the forward transform
+cudaError_t build_xi_tables(Plan& p, cudaStream_t st);
+cudaError_t launch_xi_spread(Plan& p, const void* c, cudaStream_t st);
+cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st);
 
 // Launchers (fl_direct.cu)
 cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,

@@ -77,15 +77,22 @@ __global__ void k_coupling(double y1, double xi1, int m, int ellm, int Lm, int q
 // transform Phi(nu) = pi I_0(m_w sqrt(b^2 - (2 pi nu)^2)) (window in grid units).
 // one_sided: W_{k,s} = exp(-y_s k) at the band's Chebyshev points y_s (the
 // interpolation in y alone, first term of the proof of Theorem 3.1).
+// xis (real exponents): frequency k is the sorted exponent xis[k] and no 1/Phi
+// is folded in (the NNFFT deconvolves per grid frequency instead).
 template <typename T>
 __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int levels,
                           const double* __restrict__ cheb, const double* __restrict__ Kt,
-                          int mw, double kb_b, int one_sided, T* __restrict__ D) {
+                          int mw, double kb_b, int one_sided, const double* __restrict__ xis,
+                          T* __restrict__ D) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= B.K) return;
-    const double nu = (double)(k - B.Nm / 2) / (double)B.n;
-    const double arg = kb_b * kb_b - (kTwoPiD * nu) * (kTwoPiD * nu);
-    const double inv_phi = 1.0 / (kPi * cyl_bessel_i0((double)mw * sqrt(fmax(arg, 0.0))));
+    const double xk = xis ? xis[k] : (double)k;
+    double inv_phi = 1.0;
+    if (!xis) {
+        const double nu = (double)(k - B.Nm / 2) / (double)B.n;
+        const double arg = kb_b * kb_b - (kTwoPiD * nu) * (kTwoPiD * nu);
+        inv_phi = 1.0 / (kPi * cyl_bessel_i0((double)mw * sqrt(fmax(arg, 0.0))));
+    }
     T* Dk = D + B.D_off;
     if (B.nrhs == 1) {
         Dk[k] = (T)inv_phi;
@@ -94,11 +101,11 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
     if (one_sided) {
         for (int s = 0; s < q; ++s) {
             const double ys = B.yc + B.yh * cheb[s];
-            Dk[(int64_t)s * B.K + k] = (T)(exp(-ys * (double)k) * inv_phi);
+            Dk[(int64_t)s * B.K + k] = (T)(exp(-ys * xk) * inv_phi);
         }
         return;
     }
-    const int l = band_of_freq((double)k, xi1, levels);
+    const int l = band_of_freq(xk, xi1, levels);
     if (l > Lm) {   // region (iv): kernel ~ 1
         for (int s = 0; s < q; ++s) Dk[(int64_t)s * B.K + k] = (T)inv_phi;
         return;
@@ -109,7 +116,7 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
     }
     // Lagrange weights L_r^{Omega_l}(k), barycentric form, tau in [-1, 1]
     const double ax = ldexp(xi1, -l);
-    const double tau = ((double)k - 1.5 * ax) / (0.5 * ax);
+    const double tau = (xk - 1.5 * ax) / (0.5 * ax);
     double Lr[kMaxQ];
     int hit = -1;
     double den = 0.0;
@@ -152,7 +159,7 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
         }
         k_weights<T><<<(unsigned)((bh.dev.K + 255) / 256), 256, 0, st>>>(
             bh.dev, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, p.variant,
-            (T*)p.d_D);
+            p.xi_mode ? p.d_xis : nullptr, (T*)p.d_D);
     }
     e = cudaGetLastError();
     if (Kt) {
@@ -244,14 +251,6 @@ __global__ void __launch_bounds__(512) k_small_fft(const SmallWork* __restrict__
 // ---------------------------------------------------------------------------
 // Window and barycentric weights of one node.
 
-// Kaiser-Bessel window in grid units, phi(t) = sinh(b sqrt(m^2 - t^2)) / sqrt(m^2 - t^2),
-// |t| <= m (limit b at |t| = m).
-template <typename T> __device__ __forceinline__ T kb_window(T t, T m, T b) {
-    const T s2 = m * m - t * t;
-    if (!(s2 > (T)0)) return b;
-    const T r = sqrt(s2);
-    return sinh(b * r) / r;
-}
 
 // Barycentric weights of y in Y_m = [yc - yh, yc + yh]: tau - t_s in double (the
 // cancellation-prone step), the rest in T.  Returns in Ls[0..q-1].
@@ -322,7 +321,10 @@ __device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, c
 
 // Gather + barycentric recombination + centring shift, one thread per node in
 // sorted order; writes f[perm[i]].  Z^0 nodes (band 0) receive c_0.
-template <typename T, int MW>
+// XI (real exponents): the outer NFFT of the band's NNFFT runs at x/2, Z^0
+// nodes receive 0, and the epilogue is exp(2 pi i xc x) / Phi(x/2) instead of
+// the centring shift.
+template <typename T, int MW, bool XI = false>
 __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __restrict__ ws,
                                                 const int32_t* __restrict__ perm,
                                                 const int32_t* __restrict__ bandid,
@@ -339,14 +341,15 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     const int b = bandid[i];
     const int32_t j = perm[i];
     const BandDev B = bands[b];
-    if (B.K == 0) {   // Z^0 (band 0 of its transform): c_0
-        f[j] = deriv ? C{(T)0, (T)0} : c[B.c_off];
+    if (B.K == 0 && B.n == 0) {   // Z^0 (band 0 of its transform): c_0 (0 for real exponents >= 1)
+        f[j] = (deriv || XI) ? C{(T)0, (T)0} : c[B.c_off];
         return;
     }
     // with rmul: f[j] = rmul[j] * conj(value) (node gradient, see fl_grad_w)
     if (B.route != 1) return;   // direct-route band: written by k_direct_reduce
     const double2 wv = ws[i];
-    const double x = wv.x - floor(wv.x);
+    const double xs = XI ? 0.5 * wv.x : wv.x;
+    const double x = xs - floor(xs);
     const double t0 = (double)B.n * x;
     const double u = floor(t0);
     const T fr = (T)(t0 - u);
@@ -388,11 +391,28 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
             acc.y += Ls[s] * a.y;
         }
     }
-    // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
-    double ph = (double)(B.Nm >> 1) * x;
-    ph -= floor(ph);
-    if (ph >= 0.5) ph -= 1.0;
-    const C val = cmul(acc, expipi<T>((T)(2.0 * ph)));
+    C val;
+    if constexpr (XI) {
+        // exp(2 pi i xc x) / Phi(x/2), x = Re w in [-1/2, 1/2]
+        double ph = B.xc * wv.x;
+        ph -= floor(ph);
+        if (ph >= 0.5) ph -= 1.0;
+        const T v = (T)(kTwoPiD * 0.5 * wv.x);
+        const T arg = kb_b * kb_b - v * v;
+        const T r = (T)MW * sqrt(arg > (T)0 ? arg : (T)0);
+        T i0;
+        if constexpr (sizeof(T) == 4) i0 = cyl_bessel_i0f(r);
+        else i0 = cyl_bessel_i0(r);
+        const T iphi = (T)1 / ((T)kPi * i0);
+        const C e = expipi<T>((T)(2.0 * ph));
+        val = cmul(acc, C{e.x * iphi, e.y * iphi});
+    } else {
+        // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
+        double ph = (double)(B.Nm >> 1) * x;
+        ph -= floor(ph);
+        if (ph >= 0.5) ph -= 1.0;
+        val = cmul(acc, expipi<T>((T)(2.0 * ph)));
+    }
     f[j] = rmul ? cmulc(rmul[j], val) : val;
 }
 
@@ -674,6 +694,16 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
 template <typename T, int MW>
 static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                             cudaStream_t st) {
+    if (p.xi_mode) {
+        int slot;
+        timer_begin(p, "gather", 0.0, st, &slot);
+        k_gather<T, MW, true><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+            p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C_t<T>*)p.d_grid, p.d_cheb,
+            p.d_cheb32, p.q, (T)p.kb_b, (const C_t<T>*)c, 0, nullptr, (C_t<T>*)f);
+        timer_end(p, slot, st);
+        ++p.launches;
+        return cudaGetLastError();
+    }
     using C = C_t<T>;
     double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(C));
     for (int b = 1; b <= p.levels; ++b) {
@@ -713,6 +743,22 @@ static cudaError_t forward_t(Plan& p, const void* c, void* f, bool deriv, const 
     if (e != cudaSuccess) return e;
     if ((e = run_direct_forward(p, c, f, deriv, rmul, st)) != cudaSuccess) return e;
     return gather_dispatch<T>(p, c, f, deriv, rmul, st);
+}
+
+// Real exponents: frequency spreading of every band, the FFTs of the grids
+// (inputs read from the grids, sign +), and the gather at x/2 with the NNFFT
+// epilogue.
+template <typename T>
+static cudaError_t forward_xi_t(Plan& p, const void* c, void* f, cudaStream_t st) {
+    cudaError_t e = launch_xi_spread(p, c, st);
+    if (e != cudaSuccess) return e;
+    e = fft_bands<T, 1, 1, false>(p, nullptr, st);
+    if (e != cudaSuccess) return e;
+    return gather_dispatch<T>(p, c, f, false, nullptr, st);
+}
+
+cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st) {
+    return p.prec == FL_FP64 ? forward_xi_t<double>(p, c, f, st) : forward_xi_t<float>(p, c, f, st);
 }
 
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,

@@ -1,0 +1,169 @@
+// fl_xi.cu -- real exponents: f_j = sum_k c_k z_j^{xi_k}, xi_k >= 1 (Kunis &
+// Melzer, Section 4, eq. (4.1) with general xi_k), where Algorithm 2's Fourier
+// factor A = (exp(2 pi i xi_k x_j)) becomes a transform nonequispaced in both
+// time and frequency (an NNFFT, as the proof of Theorem 4.3 notes).
+//
+// NNFFT of one band (frequencies xi_k <= cut, sorted; centre xc, 2 xc an
+// integer; |x| <= 1/2):
+//   sum_k u_k exp(2 pi i xi_k x)
+//     = exp(2 pi i xc x) sum_k u_k exp(2 pi i (xi_k - xc) x)
+//     ~ exp(2 pi i xc x) / Phi(x/2) * sum_g G_g exp(2 pi i g (x/2)),
+//   G_g = sum_k u_k phi(g - 2 (xi_k - xc)),
+// with phi the Kaiser-Bessel window (half-width m_w, grid spacing 1/2 in
+// frequency) and Phi its Fourier transform: by Poisson summation the sampled
+// integral of the spread function equals the continuous one up to aliases at
+// x/2 + n, n != 0, which the window suppresses exactly as in an NFFT with
+// oversampling 2 (|x/2| <= 1/4).  The sum over g is an ordinary NFFT at the
+// nodes x/2 (the grid, FFT and gather of the integer path), with its own
+// deconvolution 1/Phi(g / n) applied to G_g here.
+//
+// This file: the plan-time tables (window taps per exponent, the CSR of
+// floor(2 xi_k), the 1/Phi tables of the grid sizes) and the frequency
+// spreading, written deterministically: one thread per grid frequency sums
+// over its exponents in sorted order.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "fl_plan.cuh"
+
+namespace fl {
+
+// win[k 2m + t] = phi((bk_k - m + 1 + t) - 2 xi_k), bk_k = floor(2 xi_k), t < 2m.
+template <typename T>
+__global__ void k_xi_win(int64_t N, const double* __restrict__ xis, int m, double b,
+                         int32_t* __restrict__ bk, T* __restrict__ win) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const double x2 = 2.0 * xis[k];
+    const double fb = floor(x2);
+    bk[k] = (int32_t)fb;
+    for (int t = 0; t < 2 * m; ++t)
+        win[k * 2 * m + t] = (T)kb_window<double>(fb - m + 1 + t - x2, (double)m, b);
+}
+
+// iphi[g] = 1 / Phi(g / n), g = 0 .. n/4, Phi(nu) = pi I_0(m sqrt(b^2 - (2 pi nu)^2)).
+template <typename T>
+__global__ void k_xi_iphi(int64_t count, double n, int m, double b, T* __restrict__ iphi) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= count) return;
+    const double nu = 6.283185307179586476925286766559 * (double)g / n;
+    iphi[g] = (T)(1.0 / (3.141592653589793238462643383279 * cyl_bessel_i0((double)m * sqrt(fmax(b * b - nu * nu, 0.0)))));
+}
+
+// G of one band: thread per grid index i (all right-hand sides), written to the
+// band grid (zeros outside |g| <= gh).
+template <typename T>
+__global__ void k_xi_spread(BandDev B, const C_t<T>* __restrict__ c, const int32_t* __restrict__ xperm,
+                            const int32_t* __restrict__ xbk, const int32_t* __restrict__ xstart,
+                            int64_t nstart, const T* __restrict__ win, const T* __restrict__ D,
+                            const T* __restrict__ iphi, int m, C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B.n) return;
+    const int64_t g = i < (B.n >> 1) ? i : i - B.n;
+    C* out = grid + B.grid_off + i;
+    if (g > B.gh || g < -B.gh) {
+        for (int s = 0; s < B.nrhs; ++s) out[(int64_t)s * B.n] = C{(T)0, (T)0};
+        return;
+    }
+    const int64_t G = g + (int64_t)(2.0 * B.xc);
+    const int64_t b0 = std::min<int64_t>(std::max<int64_t>(G - m, 0), nstart - 1);
+    const int64_t b1 = std::min<int64_t>(std::max<int64_t>(G + m, 0), nstart - 1);
+    const int64_t k0 = xstart[b0];
+    const int64_t k1 = std::min<int64_t>(xstart[b1], B.K);
+    const T inv = iphi[B.phi_off + (g < 0 ? -g : g)];
+    for (int s = 0; s < B.nrhs; ++s) {
+        const T* Ds = D + B.D_off + (int64_t)s * B.K;
+        C acc = {(T)0, (T)0};
+        for (int64_t k = k0; k < k1; ++k) {
+            const int t = (int)(G + m - 1 - xbk[k]);      // in [0, 2m)
+            const T ph = win[k * 2 * m + t] * Ds[k];
+            const C v = c[xperm[k]];
+            acc.x += ph * v.x;
+            acc.y += ph * v.y;
+        }
+        out[(int64_t)s * B.n] = C{acc.x * inv, acc.y * inv};
+    }
+}
+
+template <typename T>
+static cudaError_t xi_tables_t(Plan& p, cudaStream_t st) {
+    const int64_t N = p.N;
+    const int m = p.mw;
+    cudaError_t e = cudaMalloc((void**)&p.d_xbk, std::max<int64_t>(N, 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_xwin, std::max<int64_t>(N, 1) * 2 * m * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (N > 0)
+        k_xi_win<T><<<(unsigned)((N + 255) / 256), 256, 0, st>>>(N, p.d_xis, m, p.kb_b, p.d_xbk,
+                                                                 (T*)p.d_xwin);
+    // CSR of floor(2 xi): xstart[B] = first sorted k with floor(2 xi_k) >= B
+    const int64_t bmax = N > 0 ? (int64_t)floor(2.0 * p.h_xis.back()) : 0;
+    std::vector<int32_t> start(bmax + 2);
+    int64_t k = 0;
+    for (int64_t B = 0; B <= bmax + 1; ++B) {
+        while (k < N && (int64_t)floor(2.0 * p.h_xis[k]) < B) ++k;
+        start[B] = (int32_t)k;
+    }
+    e = cudaMalloc((void**)&p.d_xstart, start.size() * sizeof(int32_t));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(p.d_xstart, start.data(), start.size() * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    // 1/Phi of every NNFFT grid size (g = 0 .. Nm/2)
+    std::vector<int64_t> off(kMaxLog2n + 1, -1);
+    int64_t tot = 0;
+    for (BandHost& bh : p.bands) {
+        BandDev& d = bh.dev;
+        if (d.route != 1 || d.n == 0) continue;
+        if (off[d.log2n] < 0) {
+            off[d.log2n] = tot;
+            tot += d.Nm / 2 + 1;
+        }
+        d.phi_off = off[d.log2n];
+    }
+    p.xiphi_elems = tot;
+    if (tot > 0) {
+        e = cudaMalloc(&p.d_xiphi, tot * sizeof(T));
+        if (e != cudaSuccess) return e;
+        for (int lg = 0; lg <= kMaxLog2n; ++lg) {
+            if (off[lg] < 0) continue;
+            const int64_t n = (int64_t)1 << lg, cnt = n / 4 + 1;
+            k_xi_iphi<T><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, (double)n, m, p.kb_b,
+                                                                        (T*)p.d_xiphi + off[lg]);
+        }
+    }
+    // the band table with phi_off
+    std::vector<BandDev> hb(p.bands.size());
+    for (size_t b = 0; b < p.bands.size(); ++b) hb[b] = p.bands[b].dev;
+    e = cudaMemcpyAsync(p.d_bands, hb.data(), hb.size() * sizeof(BandDev), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t build_xi_tables(Plan& p, cudaStream_t st) {
+    return p.prec == FL_FP64 ? xi_tables_t<double>(p, st) : xi_tables_t<float>(p, st);
+}
+
+template <typename T>
+static cudaError_t xi_spread_t(Plan& p, const void* c, cudaStream_t st) {
+    const int64_t nstart = p.N > 0 ? (int64_t)floor(2.0 * p.h_xis.back()) + 2 : 1;
+    for (const BandHost& bh : p.bands) {
+        const BandDev& d = bh.dev;
+        if (d.route != 1 || d.n == 0) continue;
+        k_xi_spread<T><<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(
+            d, (const C_t<T>*)c, p.d_xperm, p.d_xbk, p.d_xstart, nstart, (const T*)p.d_xwin,
+            (const T*)p.d_D, (const T*)p.d_xiphi, p.mw, (C_t<T>*)p.d_grid);
+        ++p.launches;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xi_spread(Plan& p, const void* c, cudaStream_t st) {
+    return p.prec == FL_FP64 ? xi_spread_t<double>(p, c, st) : xi_spread_t<float>(p, c, st);
+}
+
+}  // namespace fl

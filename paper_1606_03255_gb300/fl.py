@@ -31,7 +31,7 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
 
 # Every symbol include/fl.h declares.
 EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
-            "fl_adjoint", "fl_transposed",
+            "fl_adjoint", "fl_transposed", "fl_plan_xi",
             "fl_plan_laplace", "fl_plan_kernel", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
 
@@ -117,6 +117,7 @@ def load(path: str | None = None):
         "fl_execute_host": [vp, vp, vp, vp],
         "fl_adjoint": [vp, vp, vp, vp],
         "fl_transposed": [vp, vp, vp, vp],
+        "fl_plan_xi": [pp, i64, vp, i64, vp, ci, cd, ci, vp],
         "fl_plan_laplace": [pp, i64, i64, vp, vp, ci, cd, ci, vp],
         "fl_plan_kernel": [pp, ci, i64, i64, vp, vp, ci, cd, ci, vp],
         "fl_laplace_real": [vp, vp, vp, vp],
@@ -194,6 +195,13 @@ def fl_adjoint(plan, r_ptr, c_out_ptr, stream):
 
 def fl_transposed(plan, g_ptr, out_ptr, stream):
     return load().fl_transposed(plan, g_ptr, out_ptr, stream)
+
+
+def fl_plan_xi(N, xi_ptr, M, nodes_ptr, q, eps, prec, stream):
+    h = ctypes.c_void_p()
+    st = load().fl_plan_xi(ctypes.byref(h), int(N), xi_ptr, int(M), nodes_ptr, int(q), float(eps),
+                           int(prec), stream)
+    return st, h
 
 
 def fl_plan_laplace(N, M, t_ptr, s_ptr, q, eps, prec, stream):
@@ -476,6 +484,65 @@ class BatchedPlan:
         if self._handle is not None and self._handle.value:
             fl_destroy(self._handle)
         self._handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class XiPlan:
+    """Owner of a real-exponent plan: f_j = sum_k c_k exp(2 pi i xi_k w_j), xi_k >= 1.
+
+    xi: CUDA float64 tensor (N,); nodes: CUDA float64 (M, 2) with |Re w| <= 1/2.
+    """
+
+    def __init__(self, xi, nodes, eps: float, precision: str = "fp32", q: int = 0, stream=None):
+        torch = _torch()
+        xi = xi.to(torch.float64).contiguous()
+        nodes = nodes.to(torch.float64).contiguous()
+        self.N = int(xi.numel())
+        self.M = int(nodes.shape[0]) if nodes.dim() else 0
+        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
+        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self._handle = None
+        st, h = fl_plan_xi(self.N, _ptr(xi), self.M, _ptr(nodes) if self.M else None, q, eps,
+                           self.prec, _stream_handle(stream))
+        check(st, "fl_plan_xi")
+        self._handle = h
+
+    @property
+    def handle(self):
+        return self._handle
+
+    def execute(self, c, out=None, stream=None):
+        torch = _torch()
+        _require(c, self.cdtype, self.N, "c")
+        if out is None:
+            out = torch.empty(self.M, dtype=self.cdtype, device=c.device)
+        _require(out, self.cdtype, self.M, "out")
+        check(fl_execute(self._handle, _ptr(c), _ptr(out) if self.M else None,
+                         _stream_handle(stream)), "fl_execute")
+        return out
+
+    def info(self) -> dict:
+        st, inf = fl_get_info(self._handle)
+        check(st, "fl_get_info")
+        return info_dict(inf)
+
+    def set_timing(self, enable: bool):
+        check(fl_set_timing(self._handle, enable), "fl_set_timing")
+
+    def timing(self) -> dict:
+        st, t = fl_get_timing(self._handle)
+        check(st, "fl_get_timing")
+        return timing_dict(t)
+
+    def close(self):
+        if self._handle is not None:
+            fl_destroy(self._handle)
+            self._handle = None
 
     def __del__(self):
         try:
