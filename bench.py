@@ -344,6 +344,23 @@ def secondary_workloads(dev, flush, rank):
     fwd = _time_cuda(lambda: op(c.detach(), w.detach()), 10, flush)
     out["gradients_2^18_fp32"] = {"ms_fwd_bwd": ms, "ms_fwd": fwd, "unit": "ms",
                                   "note": "forward + adjoint (grad c) + k-weighted transform (grad w)"}
+    # real exponents: N = M = 2^18, xi_k ~ U[1, N], nodes as the headline
+    # workload shifted to Re w in [-1/2, 1/2), FP32, eps = 1e-6
+    N = M = 1 << 18
+    rng = np.random.default_rng(500 + rank)
+    xi = torch.from_numpy(rng.uniform(1.0, N, N)).to(dev)
+    wx = W.nodes_circle_clustered(M, seed=600 + rank).copy()
+    wx[:, 0] -= 0.5
+    cx = torch.from_numpy(W.coefficients(N, seed=700 + rank)).to(torch.complex64).to(dev)
+    px = fl.XiPlan(xi, torch.from_numpy(wx).to(dev), 1e-6, precision="fp32")
+    fx = torch.empty(M, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        px.execute(cx, out=fx)
+    msx = _time_cuda(lambda: px.execute(cx, out=fx), 10, flush)
+    out["real_exponents_2^18_fp32"] = {"ms": msx, "value": N * M / (msx * 1e-3), "unit": "evals/s",
+                                       "q": px.info()["q"], "m_w": px.info()["m_w"]}
+    px.close()
+    N = M = 1 << 18
     # adjoint and transposed evaluation (C^T g, integer exponents) on the same plan
     r = g.detach()
     adj = _time_cuda(lambda: op._plan.adjoint(r), 10, flush)
