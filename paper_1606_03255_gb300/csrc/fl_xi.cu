@@ -74,17 +74,31 @@ __global__ void k_xi_spread(BandDev B, const C_t<T>* __restrict__ c, const int32
     const int64_t k0 = xstart[b0];
     const int64_t k1 = std::min<int64_t>(xstart[b1], B.K);
     const T inv = iphi[B.phi_off + (g < 0 ? -g : g)];
-    for (int s = 0; s < B.nrhs; ++s) {
-        const T* Ds = D + B.D_off + (int64_t)s * B.K;
-        C acc = {(T)0, (T)0};
+    // right-hand sides in chunks of SC: each exponent's tap, window value and
+    // coefficient are loaded once per chunk and used for all SC weights
+    constexpr int SC = 8;
+    const T* D0 = D + B.D_off;
+    for (int s0 = 0; s0 < B.nrhs; s0 += SC) {
+        C acc[SC];
+#pragma unroll
+        for (int u = 0; u < SC; ++u) acc[u] = C{(T)0, (T)0};
         for (int64_t k = k0; k < k1; ++k) {
             const int t = (int)(G + m - 1 - xbk[k]);      // in [0, 2m)
-            const T ph = win[k * 2 * m + t] * Ds[k];
+            const T wk = win[k * 2 * m + t];
             const C v = c[xperm[k]];
-            acc.x += ph * v.x;
-            acc.y += ph * v.y;
+            const C wv = C{wk * v.x, wk * v.y};
+#pragma unroll
+            for (int u = 0; u < SC; ++u) {
+                if (s0 + u < B.nrhs) {
+                    const T d = D0[(int64_t)(s0 + u) * B.K + k];
+                    acc[u].x += d * wv.x;
+                    acc[u].y += d * wv.y;
+                }
+            }
         }
-        out[(int64_t)s * B.n] = C{acc.x * inv, acc.y * inv};
+#pragma unroll
+        for (int u = 0; u < SC; ++u)
+            if (s0 + u < B.nrhs) out[(int64_t)(s0 + u) * B.n] = C{acc[u].x * inv, acc[u].y * inv};
     }
 }
 
@@ -151,6 +165,8 @@ cudaError_t build_xi_tables(Plan& p, cudaStream_t st) {
 template <typename T>
 static cudaError_t xi_spread_t(Plan& p, const void* c, cudaStream_t st) {
     const int64_t nstart = p.N > 0 ? (int64_t)floor(2.0 * p.h_xis.back()) + 2 : 1;
+    int slot;
+    timer_begin(p, "xi_spread", 0.0, st, &slot);
     for (const BandHost& bh : p.bands) {
         const BandDev& d = bh.dev;
         if (d.route != 1 || d.n == 0) continue;
@@ -159,6 +175,7 @@ static cudaError_t xi_spread_t(Plan& p, const void* c, cudaStream_t st) {
             (const T*)p.d_D, (const T*)p.d_xiphi, p.mw, (C_t<T>*)p.d_grid);
         ++p.launches;
     }
+    timer_end(p, slot, st);
     return cudaGetLastError();
 }
 
