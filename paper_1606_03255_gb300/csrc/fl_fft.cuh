@@ -69,6 +69,20 @@ template <typename T> __device__ __forceinline__ int swz(int e) {
     return e ^ ((e >> 4) & (P - 1));
 }
 
+// swz(b0 + r D) from bs = swz(b0) for a stride D that is a multiple of 16 and a
+// base b0 whose bits below log2(D) hold everything b0 has below the top part
+// (the load pattern jj + r L/R with jj < L/R, and the store pattern
+// (jj - k) R + k + r NS with k < NS): the mask (e >> 4) & (P - 1) of
+// e = b0 + r D is then mask(b0) ^ ((r D >> 4) & (P - 1)) with disjoint bits,
+// and the XOR touches only bits below 4, so
+//   swz(b0 + r D) = (swz(b0) ^ ((r D >> 4) & (P - 1))) + r D,
+// a compile-time XOR constant and offset per unrolled r.
+template <typename T, int D> __device__ __forceinline__ int swz_step(int bs, int r) {
+    constexpr int P = (int)(128 / sizeof(C_t<T>));
+    static_assert(D % 16 == 0, "stride of the swizzle shortcut");
+    return (bs ^ (((r * D) >> 4) & (P - 1))) + r * D;
+}
+
 // 16-point DFT in registers (4 x 4 with internal twiddles), sign SIGN.
 template <int SIGN, typename T> __device__ __forceinline__ void dft16(C_t<T>* a) {
     using C = C_t<T>;
@@ -169,7 +183,14 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __
         const int jj = t + jb * NTHR;
         const int k = jj & (NS - 1);
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
+        if constexpr ((L / R) % 16 == 0) {
+            const int bs = swz<T>(jj);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz_step<T, L / R>(bs, r)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
+        }
         if constexpr (NS > 1) apply_stage_twiddles<R, NS, SIGN>(v + jb * R, tws, k);
     }
     __syncthreads();
@@ -184,7 +205,14 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __
         const int k = jj & (NS - 1);
         const int base = (jj - k) * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) buf[swz<T>(base + r * NS)] = a[r];
+        if constexpr (NS % 16 == 0) {
+            const int bs = swz<T>(base);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[swz_step<T, NS>(bs, r)] = a[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[swz<T>(base + r * NS)] = a[r];
+        }
     }
     __syncthreads();
 }
@@ -205,8 +233,10 @@ template <int LOG2L, int FIRST = 4> struct StagePlan {
 template <int LOG2L, int SIGN, typename T>
 __device__ __forceinline__ void fft_first_from_regs(C_t<T>* v, C_t<T>* buf, int t) {
     dft16<SIGN, T>(v);
+    // swz(16 t + r) = (16 t + mask) ^ r, mask = t & (P - 1) < 16
+    const int bs = swz<T>(t * 16);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf[swz<T>(t * 16 + r)] = v[r];
+    for (int r = 0; r < 16; ++r) buf[bs ^ r] = v[r];
     __syncthreads();
 }
 
@@ -218,8 +248,9 @@ template <int LOG2L, int SIGN, typename T>
 __device__ __forceinline__ void fft_first8x2_from_regs(C_t<T>* v, C_t<T>* buf, int t) {
     dft8<SIGN, T>(v);
     dft8<SIGN, T>(v + 8);
+    const int bs = swz<T>(t * 16);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) buf[swz<T>(t * 16 + r)] = v[r];
+    for (int r = 0; r < 16; ++r) buf[bs ^ r] = v[r];
     __syncthreads();
 }
 
@@ -247,7 +278,14 @@ __device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T
     for (int jb = 0; jb < J; ++jb) {
         const int jj = t + jb * NTHR;   // < LAST_NS, so k = jj
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
+        if constexpr ((L / R) % 16 == 0) {
+            const int bs = swz<T>(jj);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz_step<T, L / R>(bs, r)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[jb * R + r] = buf[swz<T>(jj + r * (L / R))];
+        }
         apply_stage_twiddles<R, NS, SIGN>(v + jb * R, tws, jj);
         C* a = v + jb * R;
         if constexpr (R == 16) dft16<SIGN, T>(a);
