@@ -18,8 +18,9 @@
  *     *_host pointers are host memory (pinned memory gives overlapped copies).
  *     The caller owns every buffer it passes; the plan owns its own scratch.
  *   - Complex arrays are interleaved (re, im).  The element type follows the
- *     plan's precision: FL_FP32 -> float pairs (complex64),
- *     FL_FP64 -> double pairs (complex128).  Nodes are always float64.
+ *     plan's precision: FL_FP32 -> (float, float) (complex64),
+ *     FL_FP64 and FL_FP64_FF -> (double, double) (complex128).  Nodes are
+ *     always float64.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  fl_execute / fl_adjoint / fl_laplace_real are asynchronous on
  *     it; planning synchronises it.
@@ -48,7 +49,16 @@ typedef enum {
     FL_EUNSUPPORTED = 5   /* size or parameter outside what is implemented    */
 } fl_status;
 
-typedef enum { FL_FP32 = 0, FL_FP64 = 1 } fl_precision;
+/* FL_FP64_FF: the FP64-accuracy form with complex128 c and f whose band-grid
+ * FFTs run in float pairs (hi + lo, about 48 significant bits from FP32
+ * arithmetic, which this part issues at 64 times its FP64 rate); the
+ * coefficient weights and twiddles are rounded once from FP64 to pairs, and
+ * the window gather, barycentric recombination, phases and direct bands run
+ * in double.  Forward only: fl_plan, fl_plan_ex and fl_plan_batched accept
+ * it, with fl_execute, fl_execute_host and fl_execute_batched; fl_adjoint,
+ * fl_transposed, fl_execute_deriv and fl_grad_w return FL_EUNSUPPORTED on
+ * such a plan, and the other plan calls reject it with FL_EINVAL. */
+typedef enum { FL_FP32 = 0, FL_FP64 = 1, FL_FP64_FF = 2 } fl_precision;
 
 #define FL_MAX_LEVELS 128
 
@@ -104,7 +114,8 @@ typedef struct {
  *               max_j |f_j - f~_j| <= eps * sum_k |c_k| (Theorem 4.3) up to
  *               the rounding of the chosen precision.
  *   prec      : FL_FP32 (grids, FFT and recombination in float; phases and
- *               barycentric differences in double) or FL_FP64.
+ *               barycentric differences in double), FL_FP64, or FL_FP64_FF
+ *               (FFTs in float pairs, the rest in double; see fl_precision).
  * Returns FL_EINVAL for N < 1, M < 0, eps outside (0, 1), q outside [0, 40] or
  * a node with Im w < 0 or a non-finite part; FL_EUNSUPPORTED for N > 2^23.
  * On failure *out is NULL.

@@ -41,7 +41,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32,
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff,
                     d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi};
     for (void* q : ptrs)
         if (q) cudaFree(q);
@@ -235,7 +235,7 @@ static int route_of(const Plan& p, const BandHost& bh) {
     if (p.route_mode == 1) return 1;
     if (p.route_mode == 2) return 2;
     const BandDev& d = bh.dev;
-    const bool dbl = p.prec == FL_FP64;
+    const bool dbl = p.prec != FL_FP32;   // float pairs: gather and direct bands in double
     const double fft_pt = dbl ? 2.0 : 1.0, win = dbl ? 150.0 : 20.0, div = dbl ? 40.0 : 4.0;
     const double per_node = (double)d.nrhs * 2 * p.mw * 2 + 2.0 * p.mw * win + (d.nrhs > 1 ? p.q * div : 0.0);
     const double fft = (double)d.nrhs * d.n * (d.log2n + 8) * fft_pt + (double)bh.nodes * per_node + 2.0e5;
@@ -430,7 +430,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
-    const size_t cs = p.prec == FL_FP64 ? 16 : 8, rs = cs / 2;
+    // complex128 I/O for FP64 and float pairs; real tables double or float pairs
+    const size_t cs = p.prec != FL_FP32 ? 16 : 8, rs = cs / 2;
     if (!p.small_work.empty()) {
         FL_CUDA(cudaMalloc((void**)&p.d_small, p.small_work.size() * sizeof(SmallWork)), "cudaMalloc work");
         FL_CUDA(cudaMemcpyAsync(p.d_small, p.small_work.data(), p.small_work.size() * sizeof(SmallWork),
@@ -455,8 +456,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                                 p.direct_ranges.size() * sizeof(DirectRange), cudaMemcpyHostToDevice, st),
                 "copy direct ranges");
         FL_CUDA(cudaMalloc(&p.d_dpart, p.dpart_elems * cs), "cudaMalloc direct partials");
-        std::vector<DirectAdjItem>& adj = p.prec == FL_FP64 ? p.dadj_work64 : p.dadj_work32;
-        DirectAdjItem*& d_adj = p.prec == FL_FP64 ? p.d_dadj64 : p.d_dadj32;
+        std::vector<DirectAdjItem>& adj = p.prec != FL_FP32 ? p.dadj_work64 : p.dadj_work32;
+        DirectAdjItem*& d_adj = p.prec != FL_FP32 ? p.d_dadj64 : p.d_dadj32;
         if (!adj.empty()) {
             FL_CUDA(cudaMalloc((void**)&d_adj, adj.size() * sizeof(DirectAdjItem)), "cudaMalloc adjoint work");
             FL_CUDA(cudaMemcpyAsync(d_adj, adj.data(), adj.size() * sizeof(DirectAdjItem),
@@ -500,9 +501,12 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
     if (p.Y_elems) {
         FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
-        FL_CUDA(cudaMalloc(&p.d_tw, (size_t)kTwEntries * cs), "cudaMalloc twiddles");
+        FL_CUDA(cudaMalloc(&p.d_tw, (size_t)(kTwEntries + (p.prec == FL_FP64_FF ? 8192 : 0)) * cs),
+                "cudaMalloc twiddles");
         FL_CUDA(build_twiddles(p, st), "fl_plan: twiddles");
     }
+    if (p.prec == FL_FP64_FF)
+        FL_CUDA(cudaMalloc(&p.d_cff, (size_t)p.N * sizeof(ffc)), "cudaMalloc float-pair coefficients");
     FL_CUDA(build_cheb(p, st), "fl_plan: tables");
     for (int i = 0; i < B; ++i) FL_CUDA(build_tables(p, p.inst[i], st), "fl_plan: tables");
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
@@ -588,7 +592,7 @@ static uint64_t plan_signature(const Plan& p) {
 }
 
 static fl_status time_plan(Plan& p, cudaStream_t st, double* ms) {
-    const size_t cs = p.prec == FL_FP64 ? 16 : 8;
+    const size_t cs = p.prec != FL_FP32 ? 16 : 8;
     void *c = nullptr, *f = nullptr;
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaMalloc(&c, std::max<int64_t>(1, p.N) * cs);
@@ -739,7 +743,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (M > ((int64_t)1 << 31) - 1) return fail(FL_EUNSUPPORTED, "fl_plan: M above 2^31 - 1");
     if (!(eps > 0.0 && eps < 1.0)) return fail(FL_EINVAL, "fl_plan: eps must lie in (0, 1)");
     if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan: q must lie in [0, 40]");
-    if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan: unknown precision");
+    if (prec != FL_FP32 && prec != FL_FP64 && prec != FL_FP64_FF)
+        return fail(FL_EINVAL, "fl_plan: unknown precision");
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
     PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
                  opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false,
@@ -767,6 +772,7 @@ fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* st
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_deriv: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: real-exponent plans are forward only");
+    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: float-pair plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, f_dev, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute_deriv");
     return FL_OK;
@@ -777,6 +783,7 @@ fl_status fl_grad_w(fl_plan_t h, const void* c_dev, const void* r_dev, void* gw_
     if (h->p.M > 0 && (!c_dev || !r_dev || !gw_dev)) return fail(FL_EINVAL, "fl_grad_w: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_grad_w: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_grad_w: real-exponent plans are forward only");
+    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_grad_w: float-pair plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, gw_dev, true, (cudaStream_t)stream, r_dev);
     if (e != cudaSuccess) return cuda_fail(e, "fl_grad_w");
     return FL_OK;
@@ -786,7 +793,7 @@ fl_status fl_execute_host(fl_plan_t h, const void* c_host, void* f_host, void* s
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_execute_host: not a Fourier-Laplace plan");
     Plan& p = h->p;
     if (!c_host || (p.M > 0 && !f_host)) return fail(FL_EINVAL, "fl_execute_host: NULL buffer");
-    const size_t cs = p.prec == FL_FP64 ? 16 : 8;
+    const size_t cs = p.prec != FL_FP32 ? 16 : 8;
     cudaStream_t st = (cudaStream_t)stream;
     if (!p.d_stage_c) FL_CUDA(cudaMalloc(&p.d_stage_c, p.N * cs), "cudaMalloc staging");
     if (!p.d_stage_f && p.M > 0) FL_CUDA(cudaMalloc(&p.d_stage_f, p.M * cs), "cudaMalloc staging");
@@ -805,6 +812,7 @@ fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stre
     if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_adjoint: real-exponent plans are forward only");
+    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_adjoint: float-pair plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
     return FL_OK;
@@ -815,6 +823,7 @@ fl_status fl_transposed(fl_plan_t h, const void* g_dev, void* out_dev, void* str
     if (!out_dev || (h->p.M > 0 && !g_dev)) return fail(FL_EINVAL, "fl_transposed: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_transposed: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_transposed: real-exponent plans are forward only");
+    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_transposed: float-pair plans are forward only");
     cudaError_t e = run_transposed(h->p, g_dev, out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_transposed");
     return FL_OK;
@@ -898,7 +907,8 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
         return fail(FL_EUNSUPPORTED, "fl_plan_batched: sum of M_i above 2^31 - 1");
     if (!(eps > 0.0 && eps < 1.0)) return fail(FL_EINVAL, "fl_plan_batched: eps must lie in (0, 1)");
     if (q < 0 || q > kMaxQ) return fail(FL_EINVAL, "fl_plan_batched: q must lie in [0, 40]");
-    if (prec != FL_FP32 && prec != FL_FP64) return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
+    if (prec != FL_FP32 && prec != FL_FP64 && prec != FL_FP64_FF)
+        return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
     if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
                 opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1))

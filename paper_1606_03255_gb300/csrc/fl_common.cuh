@@ -10,9 +10,54 @@
 
 namespace fl {
 
+// Float pairs (the FP64-accuracy form FL_FP64_FF): a value hi + lo, about 48
+// significant bits from FP32 arithmetic alone (double-length arithmetic after
+// Dekker, 1971: Knuth's error-free sum and the FMA error-free product).  The
+// pairs are kept unnormalised: a sum or product returns the exact rounded
+// leading part and the collected low-order terms without the final fast
+// two-sum, so |lo| may grow to a few ulp(hi), or exceed |hi| after
+// cancellation.  The value is always hi + lo, and the error of each operation
+// stays a few 2^-48 of the operands' magnitudes (|a| + |b|, |a| |b|), the
+// norm-wise bound an FFT needs.  Values enter as pairs rounded from FP64 and
+// leave through double(hi) + double(lo).
+struct __align__(8) ff {
+    float hi, lo;
+    ff() = default;
+    __host__ __device__ constexpr ff(float h, float l) : hi(h), lo(l) {}
+    __host__ __device__ constexpr ff(float v) : hi(v), lo(0.f) {}
+    // exact for |v| <= 2^24 (the integers used here are transform indices)
+    __host__ __device__ constexpr ff(int v) : hi((float)v), lo(0.f) {}
+    __host__ __device__ constexpr ff(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+    __host__ __device__ explicit constexpr operator double() const { return (double)hi + (double)lo; }
+};
+struct __align__(16) ffc {
+    ff x, y;
+};
+
+__device__ __forceinline__ ff operator-(ff a) { return ff(-a.hi, -a.lo); }
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+    const float s = a.hi + b.hi;                      // Knuth: s + err == a.hi + b.hi
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    return ff(s, err + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);             // the rounding error of p, exactly
+    return ff(p, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e)));
+}
+// s * a for s = +-1 or a power of two (the sign factors of the butterflies):
+// exact
+__device__ __forceinline__ ff operator*(int s, ff a) { return ff((float)s * a.hi, (float)s * a.lo); }
+// through double: used only for set-up values (1 / power of two)
+__device__ __forceinline__ ff operator/(ff a, ff b) { return ff((double)a / (double)b); }
+__device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
+
 template <typename T> struct cplx;
 template <> struct cplx<float> { using type = float2; };
 template <> struct cplx<double> { using type = double2; };
+template <> struct cplx<ff> { using type = ffc; };
 template <typename T> using C_t = typename cplx<T>::type;
 
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
@@ -28,6 +73,13 @@ template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
 
 __device__ __forceinline__ void sincospi_t(float x, float* s, float* c) { sincospif(x, s, c); }
 __device__ __forceinline__ void sincospi_t(double x, double* s, double* c) { sincospi(x, s, c); }
+// float pairs: through double sincospi, rounded to a pair (relative error ~2^-48)
+__device__ __forceinline__ void sincospi_t(ff x, ff* s, ff* c) {
+    double sd, cd;
+    sincospi((double)x, &sd, &cd);
+    *s = ff(sd);
+    *c = ff(cd);
+}
 
 // exp(i * pi * x)
 template <typename T> __device__ __forceinline__ C_t<T> expipi(T x) {

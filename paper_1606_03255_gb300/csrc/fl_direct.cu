@@ -211,7 +211,8 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
 
 cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                                cudaStream_t st) {
-    return p.prec == FL_FP64 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
+    // the FP64-accuracy form in float pairs sums its direct bands in double
+    return p.prec != FL_FP32 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
                              : direct_forward_t<float>(p, c, f, deriv, rmul, st);
 }
 

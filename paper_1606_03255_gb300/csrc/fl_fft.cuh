@@ -11,6 +11,8 @@
 //   n = n1 n2 for grids above one CTA (n > 4096).
 #pragma once
 
+#include <type_traits>
+
 #include "fl_plan.cuh"
 
 namespace fl {
@@ -159,6 +161,23 @@ template <int SIGN> __device__ __forceinline__ void tw_load2(const double2* p, d
     }
 }
 
+template <int SIGN> __device__ __forceinline__ void tw_load2(const ffc* p, ffc& a, ffc& b) {
+    const float4 qa = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 qb = __ldg(reinterpret_cast<const float4*>(p + 1));
+    a = ffc{ff(qa.x, qa.y), SIGN < 0 ? ff(-qa.z, -qa.w) : ff(qa.z, qa.w)};
+    b = ffc{ff(qb.x, qb.y), SIGN < 0 ? ff(-qb.z, -qb.w) : ff(qb.z, qb.w)};
+}
+
+// Float pairs: exp(SIGN 2 pi i e / 2^24), 0 <= e < 2^24, as the product of two
+// plan-time table entries (each rounded once from FP64): tab[a] = exp(2 pi i
+// a / 2^12) and tab[4096 + b] = exp(2 pi i b / 2^24), e = 2^12 a + b.
+template <int SIGN> __device__ __forceinline__ ffc ff_twiddle24(const ffc* __restrict__ tab, int e) {
+    const float4 qa = __ldg(reinterpret_cast<const float4*>(tab + (e >> 12)));
+    const float4 qb = __ldg(reinterpret_cast<const float4*>(tab + 4096 + (e & 4095)));
+    const ffc w = cmul(ffc{ff(qa.x, qa.y), ff(qa.z, qa.w)}, ffc{ff(qb.x, qb.y), ff(qb.z, qb.w)});
+    return SIGN < 0 ? ffc{w.x, -w.y} : w;
+}
+
 // v[1 .. R-1] *= w^(r k) from the stage table tws (pairs, see fl_common.cuh).
 template <int R, int NS, int SIGN, typename C>
 __device__ __forceinline__ void apply_stage_twiddles(C* v, const C* __restrict__ tws, int k) {
@@ -182,7 +201,6 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __
     for (int jb = 0; jb < J; ++jb) {
         const int jj = t + jb * NTHR;
         const int k = jj & (NS - 1);
-#pragma unroll
         if constexpr ((L / R) % 16 == 0) {
             const int bs = swz<T>(jj);
 #pragma unroll
@@ -204,7 +222,6 @@ __device__ __forceinline__ void fft16_stage(C_t<T>* buf, int t, const C_t<T>* __
         const int jj = t + jb * NTHR;
         const int k = jj & (NS - 1);
         const int base = (jj - k) * R + k;
-#pragma unroll
         if constexpr (NS % 16 == 0) {
             const int bs = swz<T>(base);
 #pragma unroll
@@ -277,7 +294,6 @@ __device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T
 #pragma unroll
     for (int jb = 0; jb < J; ++jb) {
         const int jj = t + jb * NTHR;   // < LAST_NS, so k = jj
-#pragma unroll
         if constexpr ((L / R) % 16 == 0) {
             const int bs = swz<T>(jj);
 #pragma unroll
@@ -389,29 +405,45 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
     // = w0 rho^jb step^r with w0 = exp(.. i1 t), rho = exp(.. i1 L/16) and
     // step = exp(.. i1 NS): three sincospi values and short products
     constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
-    const T inv_n = (T)1 / (T)n;                  // a power of two
-    int es = (i1 * NS) & (n - 1);                 // i1 NS < n
-    if (es >= n / 2) es -= n;
-    C step[R];
-    twiddle_powers<R, T>((T)(2 * SIGN) * (T)es * inv_n, step);
-    int e0 = i1 * t;                              // < n
-    if (e0 >= n / 2) e0 -= n;
-    C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
-    C rho = C{(T)1, (T)0};
-    if constexpr (J > 1) {
-        int er = i1 * (L / 16);                   // < n / 16
-        if (er >= n / 2) er -= n;
-        rho = expipi<T>((T)(2 * SIGN) * (T)er * inv_n);
-    }
     C* out = Y + item.y_off;
+    if constexpr (std::is_same<T, ff>::value) {
+        // float pairs: every factor from the two plan-time tables after the
+        // stage table (i1 l2 < n <= 2^24, scaled to units of 2^-24 turns)
+        const C* tab = tw + kTwEntries;
+        const int sh = 24 - (log2n1 + LOG2L);
 #pragma unroll
-    for (int jb = 0; jb < J; ++jb) {
-        const int jj = t + jb * (L / 16);
-        if (jb > 0) w0 = cmul(w0, rho);
+        for (int jb = 0; jb < J; ++jb) {
+            const int jj = t + jb * (L / 16);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int l2 = jj + r * NS;
-            out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], cmul(w0, step[r]));
+            for (int r = 0; r < R; ++r) {
+                const int l2 = jj + r * NS;
+                out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], ff_twiddle24<SIGN>(tab, (i1 * l2) << sh));
+            }
+        }
+    } else {
+        const T inv_n = (T)1 / (T)n;                  // a power of two
+        int es = (i1 * NS) & (n - 1);                 // i1 NS < n
+        if (es >= n / 2) es -= n;
+        C step[R];
+        twiddle_powers<R, T>((T)(2 * SIGN) * (T)es * inv_n, step);
+        int e0 = i1 * t;                              // < n
+        if (e0 >= n / 2) e0 -= n;
+        C w0 = expipi<T>((T)(2 * SIGN) * (T)e0 * inv_n);
+        C rho = C{(T)1, (T)0};
+        if constexpr (J > 1) {
+            int er = i1 * (L / 16);                   // < n / 16
+            if (er >= n / 2) er -= n;
+            rho = expipi<T>((T)(2 * SIGN) * (T)er * inv_n);
+        }
+#pragma unroll
+        for (int jb = 0; jb < J; ++jb) {
+            const int jj = t + jb * (L / 16);
+            if (jb > 0) w0 = cmul(w0, rho);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int l2 = jj + r * NS;
+                out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], cmul(w0, step[r]));
+            }
         }
     }
 }
@@ -552,5 +584,9 @@ cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands
     extern template cudaError_t launch_pass1<T, 1, 1, false>(FL_P1_SIG(T));  \
     extern template cudaError_t launch_pass2<T, 1>(FL_P2_SIG(T));          \
     extern template cudaError_t launch_pass2<T, -1>(FL_P2_SIG(T));
+// float pairs: the forward transform only
+#define FL_FFT_EXTERN_FF                                                      \
+    extern template cudaError_t launch_pass1<ff, 1, 0, false>(FL_P1_SIG(ff)); \
+    extern template cudaError_t launch_pass2<ff, 1>(FL_P2_SIG(ff));
 
 }  // namespace fl

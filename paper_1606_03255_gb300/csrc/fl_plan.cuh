@@ -160,10 +160,12 @@ struct Plan {
     void* d_D = nullptr;           // weight tables (T)
     void* d_grid = nullptr;        // band grids (complex T)
     void* d_Y = nullptr;           // four-step intermediate (complex T)
-    void* d_tw = nullptr;          // four-step stage twiddles (complex T, kTwEntries)
+    void* d_tw = nullptr;          // four-step stage twiddles (complex T, kTwEntries;
+                                   // float pairs: + 8192 pass-1 output twiddles)
     void* d_stage_c = nullptr;     // staging for fl_execute_host
     void* d_stage_f = nullptr;
     void* d_stage_r = nullptr;     // fl_transposed: conj of the node values
+    void* d_cff = nullptr;         // FL_FP64_FF: the coefficients as float pairs (N)
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)
     DirectItem* d_direct = nullptr;
     DirectRange* d_dranges = nullptr;

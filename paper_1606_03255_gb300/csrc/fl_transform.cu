@@ -22,6 +22,7 @@
 namespace fl {
 FL_FFT_EXTERN(float)
 FL_FFT_EXTERN(double)
+FL_FFT_EXTERN_FF
 }  // namespace fl
 
 namespace fl {
@@ -199,12 +200,28 @@ __global__ void k_twiddles(C_t<T>* __restrict__ tw) {
     tw[i] = v;
 }
 
+// Float pairs: the pass-1 output twiddles as products of two tables,
+// tab[a] = exp(2 pi i a / 2^12) and tab[4096 + b] = exp(2 pi i b / 2^24),
+// a, b < 4096, each computed in FP64 (exact arguments) and rounded once.
+__global__ void k_ff_tables(ffc* __restrict__ tab) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 8192) return;
+    const double x = i < 4096 ? ldexp((double)i, -11) : ldexp((double)(i - 4096), -23);
+    double sn, cs;
+    sincospi(x, &sn, &cs);
+    tab[i] = ffc{ff(cs), ff(sn)};
+}
+
 cudaError_t build_twiddles(Plan& p, cudaStream_t st) {
     const unsigned blocks = (unsigned)((kTwEntries + 255) / 256);
-    if (p.prec == FL_FP64)
+    if (p.prec == FL_FP64_FF) {
+        k_twiddles<ff><<<blocks, 256, 0, st>>>((ffc*)p.d_tw);
+        k_ff_tables<<<8192 / 256, 256, 0, st>>>((ffc*)p.d_tw + kTwEntries);
+    } else if (p.prec == FL_FP64) {
         k_twiddles<double><<<blocks, 256, 0, st>>>((C_t<double>*)p.d_tw);
-    else
+    } else {
         k_twiddles<float><<<blocks, 256, 0, st>>>((C_t<float>*)p.d_tw);
+    }
     return cudaGetLastError();
 }
 
@@ -214,6 +231,7 @@ cudaError_t build_cheb(Plan& p, cudaStream_t st) {
 }
 
 cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st) {
+    if (p.prec == FL_FP64_FF) return build_tables_t<ff>(p, in, st);
     return p.prec == FL_FP64 ? build_tables_t<double>(p, in, st) : build_tables_t<float>(p, in, st);
 }
 
@@ -319,17 +337,45 @@ __device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, c
     return acc;
 }
 
+// sum_t phi_t g[(lo + t) mod n] over the 2 m_w taps of one right-hand side.
+template <int MW, typename T, typename C>
+__device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_t nmask, const T* phi) {
+    C a = {(T)0, (T)0};
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) {
+        const C v = g[(lo + t) & nmask];
+        a.x += phi[t] * v.x;
+        a.y += phi[t] * v.y;
+    }
+    return a;
+}
+// Float-pair grids: the taps summed in float pairs (window values rounded
+// once from double), the sum handed back in double.
+template <int MW>
+__device__ __forceinline__ double2 tap_sum(const ffc* __restrict__ g, int64_t lo, int64_t nmask,
+                                           const ff* phi) {
+    ffc a = {ff(0), ff(0)};
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) {
+        const ffc v = g[(lo + t) & nmask];
+        a.x += phi[t] * v.x;
+        a.y += phi[t] * v.y;
+    }
+    return double2{(double)a.x, (double)a.y};
+}
+
 // Gather + barycentric recombination + centring shift, one thread per node in
 // sorted order; writes f[perm[i]].  Z^0 nodes (band 0) receive c_0.
 // XI (real exponents): the outer NFFT of the band's NNFFT runs at x/2, Z^0
 // nodes receive 0, and the epilogue is exp(2 pi i xc x) / Phi(x/2) instead of
-// the centring shift.
-template <typename T, int MW, bool XI = false>
+// the centring shift.  G: the grid's element type (float pairs for the
+// FP64-accuracy form, whose gather runs in double).
+template <typename T, int MW, bool XI = false, typename G = C_t<T>>
 __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __restrict__ ws,
                                                 const int32_t* __restrict__ perm,
                                                 const int32_t* __restrict__ bandid,
                                                 const BandDev* __restrict__ bands,
-                                                const C_t<T>* __restrict__ grid,
+                                                const G* __restrict__ grid,
                                                 const double* __restrict__ cheb,
                                                 const float* __restrict__ cheb32, int q, T kb_b,
                                                 const C_t<T>* __restrict__ c, int deriv,
@@ -358,7 +404,12 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 #pragma unroll
     for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
     const int64_t nmask = B.n - 1;
-    const C* g = grid + B.grid_off;
+    const G* g = grid + B.grid_off;
+    constexpr bool kPairs = std::is_same<G, ffc>::value;
+    using PhiT = typename std::conditional<kPairs, ff, T>::type;
+    PhiT phg[2 * MW];
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) phg[t] = (PhiT)phi[t];
     C acc = {(T)0, (T)0};
     bool done = false;
     if constexpr (sizeof(T) == 4) {
@@ -369,24 +420,12 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     }
     if (done) {
     } else if (B.nrhs == 1) {
-#pragma unroll
-        for (int t = 0; t < 2 * MW; ++t) {
-            const C v = g[(lo + t) & nmask];
-            acc.x += phi[t] * v.x;
-            acc.y += phi[t] * v.y;
-        }
+        acc = tap_sum<MW>(g, lo, nmask, phg);
     } else if constexpr (sizeof(T) == 8) {
         T Ls[kMaxQ];
         bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
         for (int s = 0; s < q; ++s) {
-            const C* gs = g + (int64_t)s * B.n;
-            C a = {(T)0, (T)0};
-#pragma unroll
-            for (int t = 0; t < 2 * MW; ++t) {
-                const C v = gs[(lo + t) & nmask];
-                a.x += phi[t] * v.x;
-                a.y += phi[t] * v.y;
-            }
+            const C a = tap_sum<MW>(g + (int64_t)s * B.n, lo, nmask, phg);
             acc.x += Ls[s] * a.x;
             acc.y += Ls[s] * a.y;
         }
@@ -761,8 +800,54 @@ cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st) {
     return p.prec == FL_FP64 ? forward_xi_t<double>(p, c, f, st) : forward_xi_t<float>(p, c, f, st);
 }
 
+// FP64-accuracy form in float pairs: c converted once to pairs, the FFTs of
+// the band grids in float pairs, the direct bands and the gather (window,
+// barycentric weights, shift) in double.
+__global__ void k_to_ff(int64_t n, const double2* __restrict__ in, ffc* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = ffc{ff(in[i].x), ff(in[i].y)};
+}
+
+template <int MW>
+static cudaError_t gather_ff_t(Plan& p, const void* c, void* f, cudaStream_t st) {
+    double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(double2));
+    for (int b = 1; b <= p.levels; ++b) {
+        const BandDev& B = p.bands[b].dev;
+        if (B.route != 1) continue;
+        bytes += std::min<double>((double)B.nrhs * B.n * sizeof(ffc),
+                                  (double)p.bands[b].nodes * B.nrhs * 2 * MW * sizeof(ffc));
+    }
+    int slot;
+    timer_begin(p, "gather", bytes, st, &slot);
+    k_gather<double, MW, false, ffc><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const ffc*)p.d_grid, p.d_cheb, p.d_cheb32,
+        p.q, p.kb_b, (const double2*)c, 0, nullptr, (double2*)f);
+    timer_end(p, slot, st);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+static cudaError_t forward_ff(Plan& p, const void* c, void* f, cudaStream_t st) {
+    if (p.M == 0) return cudaSuccess;
+    k_to_ff<<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, (const double2*)c, (ffc*)p.d_cff);
+    ++p.launches;
+    cudaError_t e = fft_bands<ff, +1, 0, false>(p, p.d_cff, st);
+    if (e != cudaSuccess) return e;
+    if ((e = run_direct_forward(p, c, f, false, nullptr, st)) != cudaSuccess) return e;
+    switch (p.mw) {
+#define FL_MW_CASE(W) \
+    case W: return gather_ff_t<W>(p, c, f, st);
+        FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
+        FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
+#undef FL_MW_CASE
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul) {
+    if (p.prec == FL_FP64_FF)
+        return deriv || rmul ? cudaErrorNotSupported : forward_ff(p, c, f, st);
     return p.prec == FL_FP64 ? forward_t<double>(p, c, f, deriv, rmul, st)
                              : forward_t<float>(p, c, f, deriv, rmul, st);
 }

@@ -21,7 +21,9 @@ import os
 from . import build as _build
 
 FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT, FL_EUNSUPPORTED = range(6)
-FL_FP32, FL_FP64 = 0, 1
+FL_FP32, FL_FP64, FL_FP64_FF = 0, 1, 2
+# "fp64ff": complex128 in and out, band-grid FFTs in float pairs (forward only)
+PRECISIONS = {"fp32": FL_FP32, "fp64": FL_FP64, "fp64ff": FL_FP64_FF}
 FL_MAX_LEVELS = 128
 FL_MAX_TIMED_KERNELS = 16
 
@@ -268,6 +270,12 @@ def check(status: int, what: str = "") -> None:
 # ---------------------------------------------------------------------------
 # Tensor-level helpers.
 
+def _precision(name: str) -> int:
+    if name not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}, not {name!r}")
+    return PRECISIONS[name]
+
+
 def _torch():
     import torch
     return torch
@@ -324,7 +332,8 @@ class Plan:
     """Owner of an Algorithm-2 plan: f = sum_k c_k exp(2 pi i k w_j).
 
     nodes: CUDA float64 tensor (M, 2) of (Re w, Im w), or complex128 (M,).
-    precision: "fp32" (complex64 c/f) or "fp64" (complex128 c/f).
+    precision: "fp32" (complex64 c/f), "fp64" (complex128 c/f) or "fp64ff"
+    (complex128 c/f, band-grid FFTs in float pairs; forward only).
     """
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
@@ -337,8 +346,8 @@ class Plan:
         nodes = nodes.to(torch.float64).contiguous()
         self.N = int(N)
         self.M = int(nodes.shape[0]) if nodes.dim() else 0
-        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
-        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self.prec = _precision(precision)
+        self.cdtype = torch.complex64 if self.prec == FL_FP32 else torch.complex128
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)),
                          int(bool(autotune)), VARIANTS[variant])
@@ -443,8 +452,8 @@ class BatchedPlan:
         self.Ns = [int(x) for x in Ns]
         self.Ms = [int(x) for x in Ms]
         self.N, self.M = sum(self.Ns), sum(self.Ms)
-        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
-        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self.prec = _precision(precision)
+        self.cdtype = torch.complex64 if self.prec == FL_FP32 else torch.complex128
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
                          1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant])
@@ -504,8 +513,8 @@ class XiPlan:
         nodes = nodes.to(torch.float64).contiguous()
         self.N = int(xi.numel())
         self.M = int(nodes.shape[0]) if nodes.dim() else 0
-        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
-        self.cdtype = torch.complex128 if self.prec == FL_FP64 else torch.complex64
+        self.prec = _precision(precision)
+        self.cdtype = torch.complex64 if self.prec == FL_FP32 else torch.complex128
         self._handle = None
         st, h = fl_plan_xi(self.N, _ptr(xi), self.M, _ptr(nodes) if self.M else None, q, eps,
                            self.prec, _stream_handle(stream))
@@ -565,8 +574,8 @@ class LaplacePlan:
         t = t.to(torch.float64).contiguous()
         s = s.to(torch.float64).contiguous()
         self.N, self.M = int(t.numel()), int(s.numel())
-        self.prec = FL_FP64 if precision == "fp64" else FL_FP32
-        self.rdtype = torch.float64 if self.prec == FL_FP64 else torch.float32
+        self.prec = _precision(precision)
+        self.rdtype = torch.float32 if self.prec == FL_FP32 else torch.float64
         self._handle = None
         if kernel == "laplace":
             st, h = fl_plan_laplace(self.N, self.M, _ptr(t), _ptr(s), q, eps, self.prec,
