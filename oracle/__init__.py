@@ -68,10 +68,11 @@ def _load():
             lib.oracle_laplace_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_kernel_direct.argtypes = [ci, i64, dp, dp, i64, dp, dp, ci]
             lib.oracle_xi_direct.argtypes = [i64, dp, dp, i64, dp, dp, ci]
+            lib.oracle_xi_transposed.argtypes = [i64, dp, i64, dp, dp, dp, ci]
             lib.oracle_flt_brute_ld.argtypes = [i64, dp, i64, dp, dp]
             for fn in (lib.oracle_flt_direct, lib.oracle_flt_adjoint, lib.oracle_flt_adjoint_at,
                        lib.oracle_laplace_direct, lib.oracle_kernel_direct, lib.oracle_xi_direct,
-                       lib.oracle_flt_brute_ld):
+                       lib.oracle_xi_transposed, lib.oracle_flt_brute_ld):
                 fn.restype = ci
             lib.oracle_default_threads.restype = ci
             _lib = lib
@@ -152,6 +153,21 @@ def xi_direct(c, xi, w, threads: int = 0) -> np.ndarray:
     if rc != 0:
         raise ValueError("oracle_xi_direct: invalid arguments")
     return f
+
+
+def xi_transposed(h, xi, w, threads: int = 0) -> np.ndarray:
+    """g_k = sum_j h_j exp(2 pi i xi_k w_j): the transposed evaluation at real
+    exponents (remark after Algorithm 2), FP64 term by term."""
+    h, w = _c128(h), _nodes(w)
+    xi = np.ascontiguousarray(xi, dtype=np.float64)
+    if h.size != w.shape[0]:
+        raise ValueError("xi_transposed: one value per node")
+    g = np.empty(xi.size, dtype=np.complex128)
+    rc = _load().oracle_xi_transposed(xi.size, xi.ctypes.data, w.shape[0], w.ctypes.data,
+                                      h.ctypes.data, g.ctypes.data, threads)
+    if rc != 0:
+        raise ValueError("oracle_xi_transposed: invalid arguments")
+    return g
 
 
 KERNELS = {"exp": 1, "bessel_half": 2}

@@ -26,6 +26,9 @@
  *   oracle_xi_direct       f_j = sum_k c_k exp(2 pi i xi_k w_j) for real exponents
  *                          xi_k (the generalised polynomials of eq. (4.1) with
  *                          xi_k in [1, N]): z_j^xi_k = exp(-y xi_k) exp(2 pi i xi_k x).
+ *   oracle_xi_transposed   g_k = sum_j h_j exp(2 pi i xi_k w_j): the transposed
+ *                          evaluation at real exponents (Section 4, remark
+ *                          after Algorithm 2: the sum over nodes at given xi).
  *   oracle_flt_brute_ld    oracle_flt_direct in long double, for tiny N.
  *
  * Phase reduction: the phase k*x is split exactly into p + e with an FMA
@@ -208,6 +211,51 @@ int oracle_xi_direct(int64_t N, const double *c, const double *xi, int64_t M,
         if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
     xi_ctx cx = {N, c, xi, w, f};
     run_parallel(xi_range, &cx, M, nthreads);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Transposed evaluation at real exponents: g_k = sum_j h_j exp(2 pi i xi_k w_j), */
+/* the same terms as xi_range summed over nodes instead of exponents.        */
+
+typedef struct {
+    int64_t M;
+    const double *h, *xi, *w;
+    double *g;
+} xit_ctx;
+
+static void xit_range(void *vctx, int64_t lo, int64_t hi)
+{
+    const xit_ctx *cx = (const xit_ctx *)vctx;
+    for (int64_t k = lo; k < hi; ++k) {
+        const double xk = cx->xi[k];
+        acc_t re = {0.0, 0.0}, im = {0.0, 0.0};
+        for (int64_t j = 0; j < cx->M; ++j) {
+            const double x = cx->w[2 * j];
+            const double y = ORACLE_TWO_PI * cx->w[2 * j + 1];
+            const double mag = exp(-y * xk);
+            const double ang = ORACLE_TWO_PI * phase_frac(xk, x);
+            const double zr = mag * cos(ang), zi = mag * sin(ang);
+            const double hr = cx->h[2 * j], hi_ = cx->h[2 * j + 1];
+            acc_add(&re, hr * zr);
+            acc_add(&re, -(hi_ * zi));
+            acc_add(&im, hr * zi);
+            acc_add(&im, hi_ * zr);
+        }
+        cx->g[2 * k] = acc_get(&re);
+        cx->g[2 * k + 1] = acc_get(&im);
+    }
+}
+
+int oracle_xi_transposed(int64_t N, const double *xi, int64_t M, const double *w,
+                         const double *h, double *g, int nthreads)
+{
+    if (N < 0 || M < 0 || (N > 0 && (!xi || !g)) || (M > 0 && (!w || !h))) return -1;
+    for (int64_t k = 0; k < N; ++k) if (!(xi[k] >= 0.0) || !isfinite(xi[k])) return -1;
+    for (int64_t j = 0; j < M; ++j)
+        if (!(w[2 * j + 1] >= 0.0) || !isfinite(w[2 * j])) return -1;
+    xit_ctx cx = {M, h, xi, w, g};
+    run_parallel(xit_range, &cx, N, nthreads);
     return 0;
 }
 

@@ -211,3 +211,36 @@ def test_xi_direct_pins():
     assert np.max(np.abs(got - np.array(ref))) <= 1e-14 * np.sum(np.abs(c))
     with pytest.raises(ValueError):
         oracle.xi_direct(c, -xi, w)
+
+
+def test_xi_transposed_pins():
+    # the transposed real-exponent sum g_k = sum_j h_j z_j^{xi_k}:
+    # (1) integer exponents xi_k = k give conj(C^* conj h), the independently
+    #     written adjoint; (2) the bilinear identity h . (C c) = (C^T h) . c with
+    #     the pinned forward sum; (3) a 40-digit brute force at fractional xi_k
+    rng = np.random.default_rng(21)
+    N, M = 50, 30
+    h = W.targets(M, seed=22)
+    w = W.nodes_disk_uniform(M, seed=23)
+    w[:, 0] -= 0.5
+    got = oracle.xi_transposed(h, np.arange(N, dtype=np.float64), w)
+    ref = np.conj(oracle.flt_adjoint(np.conj(h), w, N))
+    assert np.max(np.abs(got - ref)) <= 1e-14 * np.sum(np.abs(h))
+    xi = np.sort(rng.uniform(1.0, N, N))
+    c = W.coefficients(N, seed=24)
+    lhs = np.dot(h, oracle.xi_direct(c, xi, w))
+    rhs = np.dot(oracle.xi_transposed(h, xi, w), c)
+    assert abs(lhs - rhs) <= 1e-13 * np.sum(np.abs(h)) * np.sum(np.abs(c))
+    mpmath.mp.dps = 40
+    two_pi_i = 2j * mpmath.pi
+    brute = []
+    for k in range(N):
+        brute.append(complex(sum(mpmath.mpc(h[j].real, h[j].imag) *
+                                 mpmath.exp(two_pi_i * mpmath.mpf(xi[k]) * mpmath.mpc(w[j, 0], w[j, 1]))
+                                 for j in range(M))))
+    got = oracle.xi_transposed(h, xi, w)
+    assert np.max(np.abs(got - np.array(brute))) <= 1e-14 * np.sum(np.abs(h))
+    with pytest.raises(ValueError):
+        oracle.xi_transposed(h, -xi, w)
+    with pytest.raises(ValueError):
+        oracle.xi_transposed(h[:-1], xi, w)
