@@ -357,8 +357,14 @@ def secondary_workloads(dev, flush, rank):
     for _ in range(3):
         px.execute(cx, out=fx)
     msx = _time_cuda(lambda: px.execute(cx, out=fx), 10, flush)
+    gx = fx.clone()                       # node values to transpose back
+    tx = torch.empty(N, dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        px.transposed(gx, out=tx)
+    mst = _time_cuda(lambda: px.transposed(gx, out=tx), 10, flush)
     out["real_exponents_2^18_fp32"] = {"ms": msx, "value": N * M / (msx * 1e-3), "unit": "evals/s",
-                                       "q": px.info()["q"], "m_w": px.info()["m_w"]}
+                                       "q": px.info()["q"], "m_w": px.info()["m_w"],
+                                       "ms_transposed": mst}
     px.close()
     N = M = 1 << 18
     # adjoint and transposed evaluation (C^T g, integer exponents) on the same plan

@@ -231,7 +231,9 @@ fl_status fl_adjoint(fl_plan_t p, const void *r_dev, void *c_out_dev, void *stre
  * fl_transposed -- g_k = sum_j ghat_j z_j^k for k = 0 .. N-1, i.e. C^T ghat:
  * the evaluation of g(xi) = sum_j ghat_j z_j^xi at the integer exponents
  * xi = k that the remark after Algorithm 2 (Section 4) obtains from the
- * adjoint algorithms; computed as conj(C^* conj(ghat)).
+ * adjoint algorithms; computed as conj(C^* conj(ghat)).  On a plan of
+ * fl_plan_xi: g_k = sum_j ghat_j z_j^{xi_k} at the plan's real exponents, in
+ * their original order (fl_adjoint likewise returns sum_j conj(z_j^{xi_k}) r_j).
  *   g_dev   : device, M complex (plan precision).
  *   out_dev : device, N complex, overwritten.
  * Accuracy as fl_adjoint.  The plan keeps an M-element staging buffer
@@ -254,8 +256,11 @@ fl_status fl_transposed(fl_plan_t p, const void *g_dev, void *out_dev, void *str
  *               limit), Im w >= 0.
  *   q, eps, prec : as fl_plan (each NNFFT gets eps/3).
  * Nodes with |z| < eps return 0 (every term is below eps |c_k| there).
- * Forward only: fl_execute / fl_execute_host; the derivative, gradient,
- * adjoint and transposed calls return FL_EUNSUPPORTED.  Returns FL_EINVAL for
+ * Calls: fl_execute / fl_execute_host (forward), fl_adjoint and fl_transposed
+ * (every step transposed: spreading at x/2 with the conjugate epilogue, FFTs
+ * of sign -, the outer deconvolution and the frequency window gathered back to
+ * each exponent); the derivative and gradient calls return FL_EUNSUPPORTED.
+ * Returns FL_EINVAL for
  * an exponent below 1 or not finite and for a node outside the range above,
  * FL_EUNSUPPORTED for N > 2^22.
  */

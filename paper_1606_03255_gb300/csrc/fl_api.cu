@@ -811,7 +811,6 @@ fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stre
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_adjoint: not a Fourier-Laplace plan");
     if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
-    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_adjoint: real-exponent plans are forward only");
     if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_adjoint: float-pair plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
@@ -822,7 +821,6 @@ fl_status fl_transposed(fl_plan_t h, const void* g_dev, void* out_dev, void* str
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_transposed: not a Fourier-Laplace plan");
     if (!out_dev || (h->p.M > 0 && !g_dev)) return fail(FL_EINVAL, "fl_transposed: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_transposed: batched plans are forward only");
-    if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_transposed: real-exponent plans are forward only");
     if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_transposed: float-pair plans are forward only");
     cudaError_t e = run_transposed(h->p, g_dev, out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_transposed");

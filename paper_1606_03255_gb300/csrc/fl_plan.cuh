@@ -228,6 +228,7 @@ cudaError_t run_transposed(Plan& p, const void* g, void* out, cudaStream_t st);
 // Real exponents (fl_xi.cu): plan-time tables and the forward transform
 cudaError_t build_xi_tables(Plan& p, cudaStream_t st);
 cudaError_t launch_xi_spread(Plan& p, const void* c, cudaStream_t st);
+cudaError_t launch_xi_combine(Plan& p, void* out, cudaStream_t st);   // adjoint: grids -> c
 cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st);
 
 // Launchers (fl_direct.cu)

@@ -461,7 +461,9 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 // Adjoint spreading, the transpose of the gather, without atomics in two
 // steps.  k_spread_prep: for every sorted node of an NFFT band its 2 m_w window
 // taps, its barycentric weights L_s(y_j) and rv_j = r_j exp(-2 pi i (N_m/2) x_j).
-template <typename T, int MW>
+// XI (real exponents): taps at x_j/2 and rv_j = r_j exp(-2 pi i xc x_j) /
+// Phi(x_j/2), the conjugate of the forward epilogue.
+template <typename T, int MW, bool XI = false>
 __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* __restrict__ ws,
                                                      const int32_t* __restrict__ perm,
                                                      const int32_t* __restrict__ bandid,
@@ -476,13 +478,28 @@ __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* _
     const BandDev B = bands[bandid[i]];
     if (B.route != 1) return;
     const double2 wv = ws[i];
-    const double x = wv.x - floor(wv.x);
+    const double xs = XI ? 0.5 * wv.x : wv.x;
+    const double x = xs - floor(xs);
     const double t0 = (double)B.n * x;
     const T fr = (T)(t0 - floor(t0));
-    double ph = (double)(B.Nm >> 1) * x;
-    ph -= floor(ph);
-    if (ph >= 0.5) ph -= 1.0;
-    sp_rv[i] = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
+    if constexpr (XI) {
+        double ph = B.xc * wv.x;
+        ph -= floor(ph);
+        if (ph >= 0.5) ph -= 1.0;
+        const T v = (T)(kTwoPiD * 0.5 * wv.x);
+        const T arg = kb_b * kb_b - v * v;
+        const T rr = (T)MW * sqrt(arg > (T)0 ? arg : (T)0);
+        T i0;
+        if constexpr (sizeof(T) == 4) i0 = cyl_bessel_i0f(rr);
+        else i0 = cyl_bessel_i0(rr);
+        const C rv = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
+        sp_rv[i] = cscale(rv, (T)1 / ((T)kPi * i0));
+    } else {
+        double ph = (double)(B.Nm >> 1) * x;
+        ph -= floor(ph);
+        if (ph >= 0.5) ph -= 1.0;
+        sp_rv[i] = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
+    }
 #pragma unroll
     for (int t = 0; t < 2 * MW; ++t)
         sp_phi[i * (2 * MW) + t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
@@ -858,7 +875,8 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     if (p.cell_bands.empty()) return cudaSuccess;
     int slot;
     timer_begin(p, "spread", 0.0, st, &slot);
-    k_spread_prep<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+    auto prep = p.xi_mode ? k_spread_prep<T, MW, true> : k_spread_prep<T, MW, false>;
+    prep<<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q, (T)p.kb_b,
         (T*)p.d_sp_phi, (T*)p.d_sp_L, (C*)p.d_sp_rv);
     if (p.cells_total > 0)
@@ -889,6 +907,7 @@ static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st
     }
     if (e != cudaSuccess) return e;
     if ((e = fft_bands<T, -1, 1, false>(p, nullptr, st)) != cudaSuccess) return e;
+    if (p.xi_mode) return launch_xi_combine(p, cout, st);   // no direct bands, Z^0 adds 0
     if ((e = run_direct_adjoint(p, r, st)) != cudaSuccess) return e;
     C* z0sum = (C*)p.d_z0;
     k_z0_sum<T><<<1, 256, 0, st>>>(p.z0_nodes, p.d_perm, (const C*)r, z0sum);

@@ -102,6 +102,47 @@ __global__ void k_xi_spread(BandDev B, const C_t<T>* __restrict__ c, const int32
     }
 }
 
+// Adjoint of the frequency spreading and of the outer deconvolution, summed
+// over the bands (the transpose of k_xi_spread): thread per sorted exponent k,
+//   out[xperm[k]] = sum_bands sum_s D[s][k] sum_t phi_t,k / Phi(g_t / n) b_s[g_t mod n],
+// g_t = floor(2 xi_k) - m + 1 + t - 2 xc, t < 2m, |g_t| <= gh: exactly the
+// (exponent, grid frequency) pairs the forward spreading couples.
+template <typename T>
+__global__ void k_xi_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
+                             const int32_t* __restrict__ xperm, const int32_t* __restrict__ xbk,
+                             const T* __restrict__ win, const T* __restrict__ D,
+                             const T* __restrict__ iphi, int m, const C_t<T>* __restrict__ grid,
+                             C_t<T>* __restrict__ out) {
+    using C = C_t<T>;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    const int64_t bk = xbk[k];
+    const T* wk = win + k * 2 * m;
+    C acc = {(T)0, (T)0};
+    for (int b = 1; b <= levels; ++b) {
+        const BandDev B = bands[b];
+        if (B.route != 1 || B.n == 0 || k >= B.K) continue;
+        const int64_t c2 = (int64_t)(2.0 * B.xc);
+        for (int t = 0; t < 2 * m; ++t) {
+            const int64_t g = bk - m + 1 + t - c2;
+            if (g > B.gh || g < -B.gh) continue;
+            const T wt = wk[t] * iphi[B.phi_off + (g < 0 ? -g : g)];
+            const C* gs = grid + B.grid_off + (g & (B.n - 1));
+            const T* Dk = D + B.D_off + k;
+            C a = {(T)0, (T)0};
+            for (int s = 0; s < B.nrhs; ++s) {
+                const T d = Dk[(int64_t)s * B.K];
+                const C v = gs[(int64_t)s * B.n];
+                a.x += d * v.x;
+                a.y += d * v.y;
+            }
+            acc.x += wt * a.x;
+            acc.y += wt * a.y;
+        }
+    }
+    out[xperm[k]] = acc;
+}
+
 template <typename T>
 static cudaError_t xi_tables_t(Plan& p, cudaStream_t st) {
     const int64_t N = p.N;
@@ -181,6 +222,22 @@ static cudaError_t xi_spread_t(Plan& p, const void* c, cudaStream_t st) {
 
 cudaError_t launch_xi_spread(Plan& p, const void* c, cudaStream_t st) {
     return p.prec == FL_FP64 ? xi_spread_t<double>(p, c, st) : xi_spread_t<float>(p, c, st);
+}
+
+template <typename T>
+static cudaError_t xi_combine_t(Plan& p, void* out, cudaStream_t st) {
+    int slot;
+    timer_begin(p, "combine", 0.0, st, &slot);
+    k_xi_combine<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
+        p.N, p.levels, p.d_bands, p.d_xperm, p.d_xbk, (const T*)p.d_xwin, (const T*)p.d_D,
+        (const T*)p.d_xiphi, p.mw, (const C_t<T>*)p.d_grid, (C_t<T>*)out);
+    timer_end(p, slot, st);
+    ++p.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_xi_combine(Plan& p, void* out, cudaStream_t st) {
+    return p.prec == FL_FP64 ? xi_combine_t<double>(p, out, st) : xi_combine_t<float>(p, out, st);
 }
 
 }  // namespace fl

@@ -535,6 +535,28 @@ class XiPlan:
                          _stream_handle(stream)), "fl_execute")
         return out
 
+    def adjoint(self, r, out=None, stream=None):
+        """out_k = sum_j conj(z_j^{xi_k}) r_j (C^* r), in the order of xi."""
+        torch = _torch()
+        _require(r, self.cdtype, self.M, "r")
+        if out is None:
+            out = torch.empty(self.N, dtype=self.cdtype, device=r.device)
+        _require(out, self.cdtype, self.N, "out")
+        check(fl_adjoint(self._handle, _ptr(r) if self.M else None, _ptr(out),
+                         _stream_handle(stream)), "fl_adjoint")
+        return out
+
+    def transposed(self, g, out=None, stream=None):
+        """out_k = sum_j g_j z_j^{xi_k} (C^T g), in the order of xi."""
+        torch = _torch()
+        _require(g, self.cdtype, self.M, "g")
+        if out is None:
+            out = torch.empty(self.N, dtype=self.cdtype, device=g.device)
+        _require(out, self.cdtype, self.N, "out")
+        check(fl_transposed(self._handle, _ptr(g) if self.M else None, _ptr(out),
+                            _stream_handle(stream)), "fl_transposed")
+        return out
+
     def info(self) -> dict:
         st, inf = fl_get_info(self._handle)
         check(st, "fl_get_info")

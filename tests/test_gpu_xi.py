@@ -9,6 +9,10 @@ window's transform), through the C ABI:
 * integer exponents xi_k = k + 1 agree with z times the integer transform;
 * the GPU result differs from the structured reference (exact NNDFTs) by at
   most the NNFFT share eps/3;
+* the adjoint and the transposed evaluation g_k = sum_j ghat_j z_j^{xi_k}
+  (remark after Algorithm 2 at real exponents) against the plain oracle sum
+  over nodes, max_k |g_k - g~_k| <= eps sum_j |ghat_j| (FP64; the FP32 bound
+  adds the same rounding term), and the inner-product identity;
 * invalid exponents and nodes are rejected.
 """
 import numpy as np
@@ -115,7 +119,65 @@ def test_xi_invalid(fl):
                   torch.tensor([[0.7, 0.2]], dtype=torch.float64, device="cuda"), 1e-6)
     assert ei.value.status == fl.FL_EINVAL
     p = fl.XiPlan(torch.tensor([1.5, 2.0], dtype=torch.float64, device="cuda"), w, 1e-6)
-    r = torch.zeros(1, dtype=torch.complex64, device="cuda")
-    out = torch.zeros(2, dtype=torch.complex64, device="cuda")
-    assert fl.fl_adjoint(p.handle, r.data_ptr(), out.data_ptr(), None) == fl.FL_EUNSUPPORTED
+    c = torch.zeros(2, dtype=torch.complex64, device="cuda")
+    out = torch.zeros(1, dtype=torch.complex64, device="cuda")
+    assert fl.fl_execute_deriv(p.handle, c.data_ptr(), out.data_ptr(), None) == fl.FL_EUNSUPPORTED
     p.close()
+
+
+def _tol_t(eps, prec, ref, g):
+    if prec == "fp64":
+        return eps
+    return eps + 32 * U32 * np.max(np.abs(ref)) / np.sum(np.abs(g))
+
+
+@pytest.mark.parametrize("prec,eps", [("fp64", 1e-10), ("fp64", 1e-6), ("fp32", 1e-6)])
+@pytest.mark.parametrize("kind", ["disk", "clustered"])
+@pytest.mark.parametrize("N,M,xikind", [(500, 300, "uniform"), (3000, 1000, "uniform"),
+                                        (20000, 1500, "uniform"), (4096, 700, "integer")])
+def test_xi_transposed_against_oracle(fl, prec, eps, kind, N, M, xikind):
+    rng = np.random.default_rng(N + 7 * M)
+    xi = np.arange(N) + 1.0 if xikind == "integer" else rng.uniform(1.0, N, N)
+    w = _nodes(kind, M, seed=M + 1)
+    g = W.targets(w.shape[0], seed=M + 2)
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    p = fl.XiPlan(torch.from_numpy(xi).cuda(), torch.from_numpy(w).cuda(), eps, precision=prec)
+    gd = torch.from_numpy(g).to(cdt).cuda()
+    out = p.transposed(gd).cpu().numpy().astype(np.complex128)
+    adj = p.adjoint(gd).cpu().numpy().astype(np.complex128)
+    p.close()
+    ref = oracle.xi_transposed(g, xi, w)
+    assert oracle.error_E(ref, out, g) <= _tol_t(eps, prec, ref, g)
+    ref_adj = np.conj(oracle.xi_transposed(np.conj(g), xi, w))
+    assert oracle.error_E(ref_adj, adj, g) <= _tol_t(eps, prec, ref_adj, g)
+
+
+def test_xi_adjoint_inner_product(fl):
+    # <C c, r> = <c, C^* r> with both sides from the GPU plan
+    rng = np.random.default_rng(31)
+    N, M, eps = 6000, 2000, 1e-10
+    xi = rng.uniform(1.0, N, N)
+    w = _nodes("clustered", M, seed=32)
+    c = W.coefficients(N, seed=33)
+    r = W.targets(w.shape[0], seed=34)
+    p = fl.XiPlan(torch.from_numpy(xi).cuda(), torch.from_numpy(w).cuda(), eps, precision="fp64")
+    f = p.execute(torch.from_numpy(c).cuda()).cpu().numpy()
+    a = p.adjoint(torch.from_numpy(r).cuda()).cpu().numpy()
+    p.close()
+    lhs = np.vdot(r, f)
+    rhs = np.vdot(a, c)
+    assert abs(lhs - rhs) <= 4 * eps * np.sum(np.abs(c)) * np.sum(np.abs(r))
+
+
+def test_xi_transposed_full_size_sampled(fl):
+    N = M = 1 << 18
+    rng = np.random.default_rng(41)
+    xi = rng.uniform(1.0, N, N)
+    w = _nodes("clustered", M, seed=42)
+    g = W.targets(w.shape[0], seed=43)
+    p = fl.XiPlan(torch.from_numpy(xi).cuda(), torch.from_numpy(w).cuda(), 1e-6, precision="fp32")
+    out = p.transposed(torch.from_numpy(g).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+    p.close()
+    idx = np.random.default_rng(44).choice(N, 256, replace=False)
+    ref = oracle.xi_transposed(g, xi[idx], w)
+    assert oracle.error_E(ref, out[idx], g) <= _tol_t(1e-6, "fp32", ref, g)
