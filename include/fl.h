@@ -53,8 +53,9 @@ typedef enum {
  * FFTs run in float pairs (hi + lo, about 48 significant bits from FP32
  * arithmetic, which this part issues at 64 times its FP64 rate); the
  * coefficient weights and twiddles are rounded once from FP64 to pairs, and
- * the window gather, barycentric recombination, phases and direct bands run
- * in double.  Forward only: fl_plan, fl_plan_ex and fl_plan_batched accept
+ * the window gather, barycentric recombination and direct bands also run in
+ * pairs (exponential, sincospi, square root and division written for pairs),
+ * with the phases n x mod 1 reduced exactly in double.  Forward only: fl_plan, fl_plan_ex and fl_plan_batched accept
  * it, with fl_execute, fl_execute_host and fl_execute_batched; fl_adjoint,
  * fl_transposed, fl_execute_deriv and fl_grad_w return FL_EUNSUPPORTED on
  * such a plan, and the other plan calls reject it with FL_EINVAL. */

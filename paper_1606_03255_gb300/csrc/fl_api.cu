@@ -310,7 +310,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
     FL_CUDA(cudaMalloc((void**)&p.d_cheb, 2 * kMaxQ * sizeof(double)), "cudaMalloc cheb");
-    FL_CUDA(cudaMalloc((void**)&p.d_cheb32, 3 * kMaxQ * sizeof(float)), "cudaMalloc cheb32");
+    FL_CUDA(cudaMalloc((void**)&p.d_cheb32, 4 * kMaxQ * sizeof(float)), "cudaMalloc cheb32");
     FL_CUDA(cudaMalloc(&p.d_z0, 2 * sizeof(double)), "cudaMalloc z0");
 
     // classify and sort the nodes of every transform into its slice

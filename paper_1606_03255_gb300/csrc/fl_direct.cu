@@ -9,6 +9,7 @@
 // is a Horner polynomial in z_j, and z_j^{k_b} at the block start is formed
 // from an exactly reduced phase (k_b x_j mod 1) and exp(-y_j k_b), so the error
 // does not grow with k.
+#include "fl_ffmath.cuh"
 #include "fl_plan.cuh"
 
 namespace fl {
@@ -188,6 +189,101 @@ __global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restri
     }
 }
 
+// The float-pair form (FL_FP64_FF): k_direct with the Horner steps, the
+// block-start powers z_j^kb = exp(-y kb) e^(2 pi i frac(kb x)) and the sums in
+// float pairs (fl_ffmath.cuh); the phases kb x are still reduced exactly in
+// double.  c: the coefficients already converted to pairs.
+__global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict__ items,
+                                                   const BandDev* __restrict__ bands,
+                                                   const double2* __restrict__ ws,
+                                                   const ffc* __restrict__ c,
+                                                   ffc* __restrict__ part) {
+    extern __shared__ unsigned char smem_raw[];
+    ffc* tile = reinterpret_cast<ffc*>(smem_raw);
+    const DirectItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int64_t k0 = (int64_t)it.chunk * kDirChunk;
+    const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
+    for (int i = threadIdx.x; i < kDirChunk; i += blockDim.x) {
+        const int64_t k = k0 + i;
+        tile[i] = k < kend ? c[B.c_off + k] : ffc{ff(0), ff(0)};
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (w >= it.nnodes) return;
+    const int64_t i = it.node0 + w;
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double y = kTwoPiDir * wv.y;
+    double xr = x;
+    if (xr >= 0.5) xr -= 1.0;
+    ffc z;
+    ff_sincospi(ff(2.0 * xr), &z.y, &z.x);
+    const ff mag = ff_exp(ff(-y));
+    z = ffc{z.x * mag, z.y * mag};
+    ffc acc = {ff(0), ff(0)};
+#pragma unroll 1
+    for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
+        const int b = bb * 32 + lane;
+        const int64_t kb = k0 + (int64_t)b * kDirBlock;
+        if (kb >= kend) break;
+        const double ykb = y * (double)kb;
+        if (ykb > 104.0) break;     // below 2^-150 |c|: so are the later blocks
+        const ffc* cb = tile + b * kDirBlock;
+        ffc P = cb[kDirBlock - 1];
+#pragma unroll
+        for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
+        ffc zk;
+        ff_sincospi(ff(2.0 * dir_phase<double>((double)kb, x)), &zk.y, &zk.x);
+        const ff mk = ff_exp(ff(-ykb));
+        acc = cadd(acc, cmul(ffc{zk.x * mk, zk.y * mk}, P));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const ffc o = {ff(__shfl_xor_sync(0xffffffffu, acc.x.hi, off),
+                          __shfl_xor_sync(0xffffffffu, acc.x.lo, off)),
+                       ff(__shfl_xor_sync(0xffffffffu, acc.y.hi, off),
+                          __shfl_xor_sync(0xffffffffu, acc.y.lo, off))};
+        acc = cadd(acc, o);
+    }
+    if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
+}
+
+// f[perm[i]] = sum over the node's chunks (in chunk order), rounded to double.
+__global__ void k_direct_reduce_ff(int nranges, const DirectRange* __restrict__ ranges,
+                                   int64_t total, const BandDev* __restrict__ bands,
+                                   const int32_t* __restrict__ perm, const ffc* __restrict__ part,
+                                   double2* __restrict__ f) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    int r = 0;
+    while (r + 1 < nranges && ranges[r + 1].prefix <= t) ++r;
+    const DirectRange R = ranges[r];
+    const BandDev B = bands[R.band];
+    const int64_t local = t - R.prefix;
+    const ffc* p = part + B.dslot + local * B.nchunk;
+    ffc acc = {ff(0), ff(0)};
+    for (int ch = 0; ch < B.nchunk; ++ch) acc = cadd(acc, p[ch]);
+    f[perm[B.node_off + local]] = double2{(double)acc.x, (double)acc.y};
+}
+
+static cudaError_t direct_forward_ff(Plan& p, void* f, cudaStream_t st) {
+    if (p.direct_work.empty()) return cudaSuccess;
+    const size_t smem = (size_t)kDirChunk * sizeof(ffc);
+    cudaError_t e = cudaFuncSetAttribute(k_direct_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int slot;
+    timer_begin(p, "direct", (double)p.direct_terms * sizeof(ffc) / 32.0, st, &slot);
+    k_direct_ff<<<(unsigned)p.direct_work.size(), 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws,
+                                                                  (const ffc*)p.d_cff, (ffc*)p.d_dpart);
+    timer_end(p, slot, st);
+    k_direct_reduce_ff<<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
+        (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
+        (const ffc*)p.d_dpart, (double2*)f);
+    p.launches += 2;
+    return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                                     cudaStream_t st) {
@@ -211,8 +307,9 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
 
 cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                                cudaStream_t st) {
-    // the FP64-accuracy form in float pairs sums its direct bands in double
-    return p.prec != FL_FP32 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
+    if (p.prec == FL_FP64_FF)   // reads the coefficients as pairs (converted by the caller)
+        return deriv || rmul ? cudaErrorNotSupported : direct_forward_ff(p, f, st);
+    return p.prec == FL_FP64 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
                              : direct_forward_t<float>(p, c, f, deriv, rmul, st);
 }
 

@@ -156,7 +156,8 @@ struct Plan {
     SmallWork* d_small = nullptr;
     PassItem* d_pass = nullptr;
     double* d_cheb = nullptr;      // t_s (q), lambda_s (q)
-    float* d_cheb32 = nullptr;     // t_s as (hi, lo) float pairs, lambda_s in float (3 q)
+    float* d_cheb32 = nullptr;     // t_s as (hi, lo) float pairs, lambda_s in float, and the
+                                   // low part of lambda_s (4 q)
     void* d_D = nullptr;           // weight tables (T)
     void* d_grid = nullptr;        // band grids (complex T)
     void* d_Y = nullptr;           // four-step intermediate (complex T)

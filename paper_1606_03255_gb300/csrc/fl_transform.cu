@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include "fl_fft.cuh"
+#include "fl_ffmath.cuh"
 
 namespace fl {
 FL_FFT_EXTERN(float)
@@ -46,7 +47,8 @@ __device__ __forceinline__ int band_of_freq(double k, double xi1, int levels) {
 
 // Chebyshev points t_s = cos((2s+1) pi / (2q)) and barycentric weights
 // lambda_s = (-1)^s sin((2s+1) pi / (2q)) (Section 2); cheb32 holds t_s as a
-// float pair (hi, lo: t_s = hi + lo to ~2^-48) and lambda_s in float.
+// float pair (hi, lo: t_s = hi + lo to ~2^-48), lambda_s in float, and the
+// low part of lambda_s (lambda_s = cheb32[2q + s] + cheb32[3q + s] to ~2^-48).
 __global__ void k_cheb(int q, double* cheb, float* cheb32) {
     const int s = threadIdx.x;
     if (s >= q) return;
@@ -58,6 +60,7 @@ __global__ void k_cheb(int q, double* cheb, float* cheb32) {
     cheb32[s] = hi;
     cheb32[q + s] = (float)(cs - (double)hi);
     cheb32[2 * q + s] = (float)cheb[q + s];
+    cheb32[3 * q + s] = (float)(cheb[q + s] - (double)cheb32[2 * q + s]);
 }
 
 // K^{Y_m,Omega_l}_{s r} = exp(-y_s^{Y_m} xi_r^{Omega_l}) for l = l_m..L_m
@@ -349,33 +352,18 @@ __device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_
     }
     return a;
 }
-// Float-pair grids: the taps summed in float pairs (window values rounded
-// once from double), the sum handed back in double.
-template <int MW>
-__device__ __forceinline__ double2 tap_sum(const ffc* __restrict__ g, int64_t lo, int64_t nmask,
-                                           const ff* phi) {
-    ffc a = {ff(0), ff(0)};
-#pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) {
-        const ffc v = g[(lo + t) & nmask];
-        a.x += phi[t] * v.x;
-        a.y += phi[t] * v.y;
-    }
-    return double2{(double)a.x, (double)a.y};
-}
 
 // Gather + barycentric recombination + centring shift, one thread per node in
 // sorted order; writes f[perm[i]].  Z^0 nodes (band 0) receive c_0.
 // XI (real exponents): the outer NFFT of the band's NNFFT runs at x/2, Z^0
 // nodes receive 0, and the epilogue is exp(2 pi i xc x) / Phi(x/2) instead of
-// the centring shift.  G: the grid's element type (float pairs for the
-// FP64-accuracy form, whose gather runs in double).
-template <typename T, int MW, bool XI = false, typename G = C_t<T>>
+// the centring shift.
+template <typename T, int MW, bool XI = false>
 __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __restrict__ ws,
                                                 const int32_t* __restrict__ perm,
                                                 const int32_t* __restrict__ bandid,
                                                 const BandDev* __restrict__ bands,
-                                                const G* __restrict__ grid,
+                                                const C_t<T>* __restrict__ grid,
                                                 const double* __restrict__ cheb,
                                                 const float* __restrict__ cheb32, int q, T kb_b,
                                                 const C_t<T>* __restrict__ c, int deriv,
@@ -404,12 +392,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 #pragma unroll
     for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
     const int64_t nmask = B.n - 1;
-    const G* g = grid + B.grid_off;
-    constexpr bool kPairs = std::is_same<G, ffc>::value;
-    using PhiT = typename std::conditional<kPairs, ff, T>::type;
-    PhiT phg[2 * MW];
-#pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) phg[t] = (PhiT)phi[t];
+    const C* g = grid + B.grid_off;
     C acc = {(T)0, (T)0};
     bool done = false;
     if constexpr (sizeof(T) == 4) {
@@ -420,12 +403,12 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     }
     if (done) {
     } else if (B.nrhs == 1) {
-        acc = tap_sum<MW>(g, lo, nmask, phg);
+        acc = tap_sum<MW>(g, lo, nmask, phi);
     } else if constexpr (sizeof(T) == 8) {
         T Ls[kMaxQ];
         bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
         for (int s = 0; s < q; ++s) {
-            const C a = tap_sum<MW>(g + (int64_t)s * B.n, lo, nmask, phg);
+            const C a = tap_sum<MW>(g + (int64_t)s * B.n, lo, nmask, phi);
             acc.x += Ls[s] * a.x;
             acc.y += Ls[s] * a.y;
         }
@@ -817,12 +800,82 @@ cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st) {
     return p.prec == FL_FP64 ? forward_xi_t<double>(p, c, f, st) : forward_xi_t<float>(p, c, f, st);
 }
 
-// FP64-accuracy form in float pairs: c converted once to pairs, the FFTs of
-// the band grids in float pairs, the direct bands and the gather (window,
-// barycentric weights, shift) in double.
+// FP64-accuracy form in float pairs: c converted once to pairs; the FFTs of
+// the band grids, the direct bands and the gather (window, barycentric
+// weights, shift) in float pairs, with the phases reduced exactly in double.
 __global__ void k_to_ff(int64_t n, const double2* __restrict__ in, ffc* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = ffc{ff(in[i].x), ff(in[i].y)};
+}
+
+// The gather of the float-pair form: k_gather's steps with the window values,
+// tap sums, barycentric weights and recombination in float pairs (fl_ffmath.cuh)
+// instead of double; the phases n x mod 1 and (N_m/2) x mod 1 and tau are
+// still reduced exactly in double (once per node).  The barycentric sum is
+// accumulated in one pass, sum_s L_s a_s / sum_s L_s with L_s = lambda_s /
+// (tau - t_s); an exact hit tau = t_s returns a_s.
+template <int MW>
+__global__ void __launch_bounds__(256) k_gather_ff(int64_t M, const double2* __restrict__ ws,
+                                                   const int32_t* __restrict__ perm,
+                                                   const int32_t* __restrict__ bandid,
+                                                   const BandDev* __restrict__ bands,
+                                                   const ffc* __restrict__ grid,
+                                                   const float* __restrict__ cheb32, int q,
+                                                   double kb_b, const double2* __restrict__ c,
+                                                   double2* __restrict__ f) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int b = bandid[i];
+    const int32_t j = perm[i];
+    const BandDev B = bands[b];
+    if (B.K == 0 && B.n == 0) {   // Z^0: c_0
+        f[j] = c[B.c_off];
+        return;
+    }
+    if (B.route != 1) return;     // direct-route band: written by the direct kernels
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double t0 = (double)B.n * x;
+    const double u = floor(t0);
+    const ff fr = ff(t0 - u);
+    const int64_t lo = (int64_t)u - (MW - 1);
+    const ff bb = ff(kb_b);
+    ff phi[2 * MW];
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) phi[t] = ff_kb_window(fr + ff(MW - 1 - t), (float)MW, bb);
+    const int64_t nmask = B.n - 1;
+    const ffc* g = grid + B.grid_off;
+    ffc acc;
+    if (B.nrhs == 1) {
+        acc = tap_sum<MW>(g, lo, nmask, phi);
+    } else {
+        const ff tf = ff((kTwoPiD * wv.y - B.yc) * B.yh_inv);
+        ff den = ff(0);
+        ffc num = {ff(0), ff(0)}, ahit = {ff(0), ff(0)};
+        bool hit = false;
+        for (int s = 0; s < q; ++s) {
+            const ffc a = tap_sum<MW>(g + (int64_t)s * B.n, lo, nmask, phi);
+            const ff d = tf - ff(cheb32[s], cheb32[q + s]);
+            if (d.hi == 0.f && d.lo == 0.f) {
+                hit = true;
+                ahit = a;
+                continue;
+            }
+            const ff L = ff_div(ff(cheb32[2 * q + s], cheb32[3 * q + s]), d);
+            den += L;
+            num.x += L * a.x;
+            num.y += L * a.y;
+        }
+        acc = hit ? ahit : ffc{ff_div(num.x, den), ff_div(num.y, den)};
+    }
+    // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
+    double ph = (double)(B.Nm >> 1) * x;
+    ph -= floor(ph);
+    if (ph >= 0.5) ph -= 1.0;
+    ffc e;
+    ff_sincospi(ff(2.0 * ph), &e.y, &e.x);
+    const ffc v = cmul(acc, e);
+    f[j] = double2{(double)v.x, (double)v.y};
 }
 
 template <int MW>
@@ -836,9 +889,9 @@ static cudaError_t gather_ff_t(Plan& p, const void* c, void* f, cudaStream_t st)
     }
     int slot;
     timer_begin(p, "gather", bytes, st, &slot);
-    k_gather<double, MW, false, ffc><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
-        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const ffc*)p.d_grid, p.d_cheb, p.d_cheb32,
-        p.q, p.kb_b, (const double2*)c, 0, nullptr, (double2*)f);
+    k_gather_ff<MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const ffc*)p.d_grid, p.d_cheb32, p.q,
+        p.kb_b, (const double2*)c, (double2*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
