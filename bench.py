@@ -118,15 +118,15 @@ def source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, N: int):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    captured from the current sources (else None)."""
+    captured from the current sources on the same workload size (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as fh:
         d = json.load(fh)
-    if d.get("source_hash") != source_hash():
+    if d.get("source_hash") != source_hash() or int(d.get("N", -1)) != int(N):
         return None
     k = d.get("kernels", {}).get(kernel)
     return None if k is None else float(k["dram_bytes_per_launch"])
@@ -486,7 +486,7 @@ def run_ours(args):
         kt = kernel_table[top]
         roof = {"kernel": top, "bound": "hbm", "achieved": kt["GBps"], "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": kt["GBps"] / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(top), "peak_source": peaks["source"],
+                "traffic": ncu_traffic(top, N), "peak_source": peaks["source"],
                 "algorithmic_bytes_per_launch": kt["bytes_per_launch"]}
 
     # end-to-end through the host-buffer C call (copies inside the timed region)
