@@ -125,10 +125,16 @@ static fl_status select_common(Plan& p, int q_in) {
 
 // Real exponents: Definition 3.2 with xi_1 = max xi_k; band m keeps the sorted
 // exponents xi_k <= xi_1 / 2^(l_m - 1) (a prefix of length K).  Its NNFFT
-// spreads them, centred on xc (2 xc = floor of the cut, an integer), onto the
+// spreads them, centred on xc (2 xc = floor(xi_min + cut), an integer), onto the
 // frequency grid of spacing 1/2 (grid frequency g <-> xi = xc + g/2; taps
 // g in (2(xi - xc) - m_w, 2(xi - xc) + m_w]); the occupied |g| <= gh, and the
-// outer NFFT has bandwidth Nm = 2^lg >= 2 gh + 2 on n = 2 Nm points.
+// outer NFFT has bandwidth Nm = 2^lg >= 2 gh + 2 on n = 2 Nm points.  The
+// dyadic cuts lie just below powers of two, so the window margin m_w + 1 alone
+// would double Nm; the half-size Nm is kept when it misses at most m_w + 3
+// occupied frequencies, e = gh - (Nm/2 - 1), and these raise the
+// Kaiser-Bessel aliasing term by at most 1 %: the nearest alias of frequency
+// Nm/2 - 1 + e sits at |nu| = 3/4 - e/n, where Phi = pi I_0(m_w pi sqrt(6 e / n))
+// (b = 3 pi / 2), so the condition is m_w pi sqrt(6 e / n) <= 0.2 (I_0(0.2) = 1.01).
 static fl_status select_bands_xi(Plan& p, Instance& in, int inst_index) {
     const std::vector<double>& xs = p.h_xis;
     in.xi1 = xs.empty() ? 0.0 : xs.back();
@@ -160,10 +166,15 @@ static fl_status select_bands_xi(Plan& p, Instance& in, int inst_index) {
             bh.dev.nrhs = 1;
         }
         const int64_t K = (int64_t)(std::upper_bound(xs.begin(), xs.end(), cut) - xs.begin());
-        const double two_xc = floor(cut);
+        const double lo = K > 0 ? xs[0] : cut;
+        const double two_xc = floor(lo + cut);
         bh.dev.xc = 0.5 * two_xc;
-        bh.dev.gh = (int64_t)std::max(two_xc, ceil(2.0 * cut - two_xc)) + p.mw + 1;
-        const int lg = std::max(4, ilog2_ceil(2 * bh.dev.gh + 2));
+        bh.dev.gh = (int64_t)std::max(ceil(two_xc - 2.0 * lo), ceil(2.0 * cut - two_xc)) + p.mw + 1;
+        int lg = std::max(4, ilog2_ceil(2 * bh.dev.gh + 2));
+        if (lg > 4) {
+            const int64_t e = bh.dev.gh - (((int64_t)1 << (lg - 1)) / 2 - 1);
+            if (e <= p.mw + 3 && p.mw * M_PI * sqrt(6.0 * (double)e / ldexp(1.0, lg)) <= 0.2) --lg;
+        }
         bh.dev.K = K;
         bh.dev.Nm = (int64_t)1 << lg;
         bh.dev.log2n = lg + 1;

@@ -43,7 +43,8 @@ __global__ void k_xi_win(int64_t N, const double* __restrict__ xis, int m, doubl
         win[k * 2 * m + t] = (T)kb_window<double>(fb - m + 1 + t - x2, (double)m, b);
 }
 
-// iphi[g] = 1 / Phi(g / n), g = 0 .. n/4, Phi(nu) = pi I_0(m sqrt(b^2 - (2 pi nu)^2)).
+// iphi[g] = 1 / Phi(g / n), g = 0 .. count - 1 (count - 1 = the largest occupied
+// |g| of the grids of this size, n/4 or a few beyond), Phi(nu) = pi I_0(m sqrt(b^2 - (2 pi nu)^2)).
 template <typename T>
 __global__ void k_xi_iphi(int64_t count, double n, int m, double b, T* __restrict__ iphi) {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,16 +167,22 @@ static cudaError_t xi_tables_t(Plan& p, cudaStream_t st) {
         e = cudaMemcpyAsync(p.d_xstart, start.data(), start.size() * sizeof(int32_t),
                             cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return e;
-    // 1/Phi of every NNFFT grid size (g = 0 .. Nm/2)
-    std::vector<int64_t> off(kMaxLog2n + 1, -1);
+    // 1/Phi of every NNFFT grid size (g = 0 .. max(Nm/2, largest gh of the size))
+    std::vector<int64_t> off(kMaxLog2n + 1, -1), cnt(kMaxLog2n + 1, 0);
+    for (const BandHost& bh : p.bands) {
+        const BandDev& d = bh.dev;
+        if (d.route != 1 || d.n == 0) continue;
+        cnt[d.log2n] = std::max(cnt[d.log2n], std::max(d.Nm / 2, d.gh) + 1);
+    }
     int64_t tot = 0;
+    for (int lg = 0; lg <= kMaxLog2n; ++lg) {
+        if (cnt[lg] == 0) continue;
+        off[lg] = tot;
+        tot += cnt[lg];
+    }
     for (BandHost& bh : p.bands) {
         BandDev& d = bh.dev;
         if (d.route != 1 || d.n == 0) continue;
-        if (off[d.log2n] < 0) {
-            off[d.log2n] = tot;
-            tot += d.Nm / 2 + 1;
-        }
         d.phi_off = off[d.log2n];
     }
     p.xiphi_elems = tot;
@@ -184,9 +191,9 @@ static cudaError_t xi_tables_t(Plan& p, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         for (int lg = 0; lg <= kMaxLog2n; ++lg) {
             if (off[lg] < 0) continue;
-            const int64_t n = (int64_t)1 << lg, cnt = n / 4 + 1;
-            k_xi_iphi<T><<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(cnt, (double)n, m, p.kb_b,
-                                                                        (T*)p.d_xiphi + off[lg]);
+            const int64_t n = (int64_t)1 << lg;
+            k_xi_iphi<T><<<(unsigned)((cnt[lg] + 255) / 256), 256, 0, st>>>(cnt[lg], (double)n, m, p.kb_b,
+                                                                            (T*)p.d_xiphi + off[lg]);
         }
     }
     // the band table with phi_off
