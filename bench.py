@@ -225,27 +225,29 @@ def secondary_workloads(dev, flush, rank):
     from paper_1606_03255_gb300.autograd import FourierLaplace
     out = {}
     # N = M = 1024, disk-uniform, FP64, eps = 1e-10 (latency-bound; CUDA-graph replay)
+    # (and the same in the float-pair FP64-accuracy form)
     N = M = 1024
     c = torch.from_numpy(W.coefficients(N, seed=rank)).to(dev)
     w = torch.from_numpy(W.nodes_disk_uniform(M, seed=100 + rank)).to(dev)
-    p = fl.Plan(N, w, 1e-10, precision="fp64", use_graph=True)
-    f = torch.empty(M, dtype=torch.complex128, device=dev)
     s = torch.cuda.Stream()
-    with torch.cuda.stream(s):
-        for _ in range(5):
-            p.execute(c, out=f)
+    for prec in ("fp64", "fp64ff"):
+        p = fl.Plan(N, w, 1e-10, precision=prec, use_graph=True)
+        f = torch.empty(M, dtype=torch.complex128, device=dev)
+        with torch.cuda.stream(s):
+            for _ in range(5):
+                p.execute(c, out=f)
+            s.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            for _ in range(200):
+                p.execute(c, out=f)
+            b.record(s)
         s.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(s)
-        for _ in range(200):
-            p.execute(c, out=f)
-        b.record(s)
-    s.synchronize()
-    us = a.elapsed_time(b) * 1e3 / 200
-    out["disk_1024_fp64_eps1e-10"] = {"us_per_call": us, "value": N * M / (us * 1e-6),
-                                       "unit": "evals/s", "graph": True}
-    p.close()
+        us = a.elapsed_time(b) * 1e3 / 200
+        out[f"disk_1024_{prec}_eps1e-10"] = {"us_per_call": us, "value": N * M / (us * 1e-6),
+                                            "unit": "evals/s", "graph": True}
+        p.close()
     # Laplace, N = M = 2^16, FP64 and FP32 forms, eps = 1e-6
     N = M = 1 << 16
     cl, t, sv = W.laplace_inputs(N, M, seed=rank)
