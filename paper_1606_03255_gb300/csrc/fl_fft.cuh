@@ -37,21 +37,25 @@ __device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
     return C_t<T>{v.x * d, v.y * d};
 }
 
-// Same with 32-bit grid indices and the band's c/D base pointers resolved.
+// Same with 32-bit grid indices and the band's c/D base pointers resolved,
+// branch-free: the index is clamped into [0, K) so the loads are always in
+// bounds and a thread's loads can all be in flight together; frequencies
+// outside [0, K) are then replaced by zero.
 template <typename T, bool DERIV>
 __device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K,
                                                const C_t<T>* __restrict__ c,
                                                const T* __restrict__ Ds) {
     const int kp = (i < (n >> 1)) ? i : i - n;
     const int k = kp + half_Nm;
-    if (k < 0 || k >= K) return C_t<T>{(T)0, (T)0};
-    const T d = Ds[k];
-    C_t<T> v = c[k];
+    const bool in = k >= 0 && k < K;
+    const int kk = min(max(k, 0), K - 1);
+    const T d = Ds[kk];
+    C_t<T> v = c[kk];
     if (DERIV) {
-        const T w = (T)(kTwoPiFFT * (double)k);
+        const T w = (T)(kTwoPiFFT * (double)kk);
         v = C_t<T>{-v.y * w, v.x * w};
     }
-    return C_t<T>{v.x * d, v.y * d};
+    return in ? C_t<T>{v.x * d, v.y * d} : C_t<T>{(T)0, (T)0};
 }
 
 // ---------------------------------------------------------------------------
