@@ -411,17 +411,41 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
     constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
     C* out = Y + item.y_off;
     if constexpr (std::is_same<T, ff>::value) {
-        // float pairs: every factor from the two plan-time tables after the
-        // stage table (i1 l2 < n <= 2^24, scaled to units of 2^-24 turns)
+        // float pairs: the same factorisation w0 rho^jb step^r as below, with
+        // the base factors from the two plan-time tables after the stage table
+        // (exponents i1 l2 < n <= 2^24, scaled to units of 2^-24 turns) and the
+        // powers of step formed by products at most three deep
         const C* tab = tw + kTwEntries;
         const int sh = 24 - (log2n1 + LOG2L);
+        C step[R];
+        step[0] = C{ff(1), ff(0)};
+        if constexpr (R >= 2) step[1] = ff_twiddle24<SIGN>(tab, ((i1 * NS) & (n - 1)) << sh);
+        if constexpr (R >= 4) {
+            step[2] = cmul(step[1], step[1]);
+            step[3] = cmul(step[2], step[1]);
+        }
+        if constexpr (R >= 8) {
+            step[4] = ff_twiddle24<SIGN>(tab, ((i1 * 4 * NS) & (n - 1)) << sh);
+#pragma unroll
+            for (int b = 1; b < 4; ++b) step[4 + b] = cmul(step[4], step[b]);
+        }
+        if constexpr (R == 16) {
+            step[8] = ff_twiddle24<SIGN>(tab, ((i1 * 8 * NS) & (n - 1)) << sh);
+            step[12] = ff_twiddle24<SIGN>(tab, ((i1 * 12 * NS) & (n - 1)) << sh);
+#pragma unroll
+            for (int b = 1; b < 4; ++b) {
+                step[8 + b] = cmul(step[8], step[b]);
+                step[12 + b] = cmul(step[12], step[b]);
+            }
+        }
 #pragma unroll
         for (int jb = 0; jb < J; ++jb) {
             const int jj = t + jb * (L / 16);
+            const C wj = ff_twiddle24<SIGN>(tab, (i1 * jj) << sh);   // i1 jj < n
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int l2 = jj + r * NS;
-                out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], ff_twiddle24<SIGN>(tab, (i1 * l2) << sh));
+                out[(int64_t)l2 * n1 + i1] = cmul(v[jb * R + r], cmul(wj, step[r]));
             }
         }
     } else {
