@@ -324,7 +324,8 @@ fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *str
  * or a device that is already full.
  *   t_dev, s_dev, c_dev, f_dev, q, eps, prec : as fl_plan_laplace and
  *               fl_laplace_real (c and f real, float64 for FL_FP64, float32
- *               for FL_FP32); the result equals theirs.
+ *               for FL_FP32); the result is theirs up to rounding (the
+ *               planned call sums the moments in band order).
  * Scratch: a fixed static device array of 2 MiB, held by every GPU that loads
  * libfl.so until the process exits.  Its use depends on the number of levels
  * and on q only (not on N or M); a problem that needs more returns

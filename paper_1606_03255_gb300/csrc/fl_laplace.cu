@@ -135,15 +135,116 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
     }
 }
 
-// vS[i] = sum over blocks (in block order) of partial[b][i].
+// Barycentric weights w_r = lambda_r / (tau - t_r), r < q, with one division:
+// Montgomery's batch inversion (prefix products of d_r = tau - t_r, one
+// reciprocal, a backward sweep), about 3q ulps instead of 1/2 ulp per weight.
+// Returns false and leaves hit = r when some d_r is exactly zero.
+__device__ __forceinline__ bool bary_batch(double tau, int q, const double* __restrict__ cheb,
+                                           double* w, int* hit) {
+    double pre = 1.0;
+    for (int r = 0; r < q; ++r) {
+        const double d = tau - cheb[r];
+        if (d == 0.0) {
+            *hit = r;
+            return false;
+        }
+        w[r] = pre;                      // product of d_0 .. d_{r-1}
+        pre *= d;
+    }
+    double inv = 1.0 / pre;              // 1 / (d_0 ... d_{q-1})
+    for (int r = q - 1; r >= 0; --r) {
+        const double d = tau - cheb[r];
+        const double ir = inv * w[r];    // 1 / d_r
+        inv *= d;
+        w[r] = cheb[q + r] * ir;
+    }
+    return true;
+}
+
+// The moments of k_lap_moments for t_k in band order (plan time, a stable
+// sort by band): t, tband sorted, c read through tperm.  A warp's 32 elements
+// then form runs of equal band, so each moment is summed per run by a
+// segmented shuffle scan (5 steps instead of 32) whose last lane adds it to
+// the warp's table; the runs of one chunk have distinct bands, so no two lanes
+// add to one entry and the order stays fixed.  Each weight lambda_r / (tau - t_r)
+// is formed once.
+template <typename T>
+__global__ void k_lap_moments_sorted(int64_t N, const double* __restrict__ t,
+                                     const uint8_t* __restrict__ tband,
+                                     const int32_t* __restrict__ tperm, const T* __restrict__ c,
+                                     int levels, int q, double xi1, const double* __restrict__ cheb,
+                                     T* __restrict__ partial) {
+    extern __shared__ unsigned char smem_raw[];
+    T* tab = reinterpret_cast<T*>(smem_raw);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int row = q + 1;
+    const int entries = (levels + 1) * row;
+    for (int i = threadIdx.x; i < nw * entries; i += blockDim.x) tab[i] = (T)0;
+    __syncthreads();
+    T* mytab = tab + w * entries;
+    const int64_t nchunk = (N + 31) / 32;
+    for (int64_t ch = (int64_t)blockIdx.x * nw + w; ch < nchunk; ch += (int64_t)gridDim.x * nw) {
+        const int64_t k = ch * 32 + lane;
+        const bool valid = k < N;
+        const int l = valid ? tband[k] : 255;       // invalid lanes: a run of their own at the end
+        const double cv = valid ? (double)c[tperm[k]] : 0.0;
+        double tau = 0.0, inv_den = 1.0;
+        double wr[kMaxQ];
+        int hit = -1;
+        const bool interp = valid && l < levels;
+        if (interp) {
+            const double a = ldexp(xi1, -l);
+            tau = (t[k] - 1.5 * a) / (0.5 * a);
+            if (bary_batch(tau, q, cheb, wr, &hit)) {
+                double den = 0.0;
+                for (int r = 0; r < q; ++r) den += wr[r];
+                inv_den = 1.0 / den;
+            }
+        }
+        // runs of equal band: s0 = first lane of my run, tail = last lane of it
+        const int lprev = __shfl_up_sync(0xffffffffu, l, 1);
+        const bool head = lane == 0 || lprev != l;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const int s0 = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u);
+        for (int r = 0; r <= q; ++r) {
+            T val = (T)0;
+            if (r == q) {
+                val = (T)cv;
+            } else if (interp) {
+                const double Lr = (hit >= 0) ? (r == hit ? 1.0 : 0.0) : wr[r] * inv_den;
+                val = (T)(Lr * cv);
+            }
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const T x = __shfl_up_sync(0xffffffffu, val, off);
+                if (lane - off >= s0) val += x;
+            }
+            if (valid && tail) mytab[l * row + r] += val;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < entries; i += blockDim.x) {
+        T s = (T)0;
+        for (int ww = 0; ww < nw; ++ww) s += tab[ww * entries + i];
+        partial[(int64_t)blockIdx.x * entries + i] = s;
+    }
+}
+
+// vS[i] = sum over blocks of partial[b][i]: one warp per entry, lane l summing
+// the blocks l, l + 32, ... and a fixed shuffle tree combining the lanes.
 template <typename T>
 __global__ void k_lap_reduce(int nblocks, int entries, const T* __restrict__ partial,
                              double* __restrict__ vS) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= entries) return;
+    const int i = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= entries) return;                    // uniform across the warp
     double s = 0.0;
-    for (int b = 0; b < nblocks; ++b) s += (double)partial[(int64_t)b * entries + i];
-    vS[i] = s;
+    for (int b = lane; b < nblocks; b += 32) s += (double)partial[(int64_t)b * entries + i];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) vS[i] = s;
 }
 
 // h^{Y_m}_s for m = blockIdx.x + 1 (threads over s) with
@@ -206,15 +307,22 @@ __global__ void k_lap_couple_tab(int levels, int q, const int* __restrict__ ell,
         for (int l = levels; l >= 1; --l) g[l] = g[l + 1] + vS[l * row + q];
     }
     if (m >= levels) return;
-    const int s = threadIdx.x;
-    if (s >= q) return;
-    double acc = 0.0;
+    // one warp per s: lanes stride over the (l, r) terms, a fixed shuffle tree
+    // combines them
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int l0 = ell[m];
+    const int tot = max(levels - m - l0 + 1, 0) * q;
     const double* K = Kt + koff[m];
-    for (int l = ell[m]; l <= levels - m; ++l) {
-        const double* Kb = K + ((int64_t)(l - ell[m]) * q + s) * q;
-        for (int r = 0; r < q; ++r) acc += Kb[r] * vS[l * row + r];
+    for (int s = warp; s < q; s += nw) {
+        double acc = 0.0;
+        for (int i = lane; i < tot; i += 32) {
+            const int li = i / q, r = i - li * q;
+            acc += K[((int64_t)li * q + s) * q + r] * vS[(l0 + li) * row + r];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) h[m * q + s] = acc;
     }
-    h[m * q + s] = acc;
 }
 
 // f~_j: barycentric weights of s_j on Y_m (double), then sum_s L_s h_s + g_{L_m + 1}.
@@ -232,16 +340,19 @@ __global__ void k_lap_eval(int64_t M, const double* __restrict__ sv,
     }
     const double a = ldexp(y1, -m);
     const double tau = (sv[j] - 1.5 * a) / (0.5 * a);
-    double den = 0.0, num = 0.0;
+    double w[kMaxQ];
     int hit = -1;
-    for (int s = 0; s < q; ++s) {
-        const double d = tau - cheb[s];
-        if (d == 0.0) hit = s;
-        const double wgt = cheb[q + s] / d;
-        den += wgt;
-        num += wgt * h[m * q + s];
+    double interp;
+    if (bary_batch(tau, q, cheb, w, &hit)) {
+        double den = 0.0, num = 0.0;
+        for (int s = 0; s < q; ++s) {
+            den += w[s];
+            num += w[s] * h[m * q + s];
+        }
+        interp = num / den;
+    } else {
+        interp = h[m * q + hit];
     }
-    const double interp = (hit >= 0) ? h[m * q + hit] : num / den;
     f[j] = (T)(interp + g[levels - m + 1]);
 }
 
@@ -404,7 +515,8 @@ static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* 
                            const uint8_t* tband, const uint8_t* sband, const LapParams& P,
                            const double* cheb, const T* c, T* f, unsigned char* scratch,
                            int nblocks, cudaStream_t st, Plan* timed,
-                           const double* Kt = nullptr, const int64_t* koff = nullptr) {
+                           const double* Kt = nullptr, const int64_t* koff = nullptr,
+                           const int32_t* tperm = nullptr) {
     const LapLayout L = lap_layout(P.levels, P.q, nblocks, sizeof(T));
     const int entries = (P.levels + 1) * (P.q + 1);
     T* partial = (T*)(scratch + L.partial);
@@ -415,20 +527,27 @@ static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* 
     const size_t smem = (size_t)kLapWarps * entries * sizeof(T);
     int slot = -1;
     if (N > 0) {
-        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T, BANDS_FROM_VALUES>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        auto kern = k_lap_moments<T, BANDS_FROM_VALUES>;
+        cudaError_t e = tperm ? cudaFuncSetAttribute(k_lap_moments_sorted<T>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                              : cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)smem);
         if (e != cudaSuccess) return e;
-        if (timed) timer_begin(*timed, "lap_moments", (double)N * (8 + 1 + sizeof(T)), st, &slot);
-        k_lap_moments<T, BANDS_FROM_VALUES><<<nblocks, kLapWarps * 32, smem, st>>>(
-            N, t, tband, c, P.levels, P.q, P.xi1, cheb, partial);
+        if (timed) timer_begin(*timed, "lap_moments", (double)N * (8 + 1 + 4 + sizeof(T)), st, &slot);
+        if (tperm)   // t in band order (plans of fl_plan_laplace)
+            k_lap_moments_sorted<T><<<nblocks, kLapWarps * 32, smem, st>>>(
+                N, t, tband, tperm, c, P.levels, P.q, P.xi1, cheb, partial);
+        else
+            kern<<<nblocks, kLapWarps * 32, smem, st>>>(N, t, tband, c, P.levels, P.q, P.xi1, cheb,
+                                                        partial);
         if (timed) timer_end(*timed, slot, st);
-        k_lap_reduce<T><<<(entries + 255) / 256, 256, 0, st>>>(nblocks, entries, partial, vS);
+        k_lap_reduce<T><<<(entries * 32 + 255) / 256, 256, 0, st>>>(nblocks, entries, partial, vS);
     } else {
         cudaError_t e = cudaMemsetAsync(vS, 0, entries * sizeof(double), st);
         if (e != cudaSuccess) return e;
     }
     if (Kt)
-        k_lap_couple_tab<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
+        k_lap_couple_tab<<<std::max(1, P.levels - 1), 32 * std::min(P.q, 32), 0, st>>>(
             P.levels, P.q, ell, koff, Kt, vS, h, g);
     else
         k_lap_couple<<<std::max(1, P.levels - 1), std::max(32, ((P.q + 31) / 32) * 32), 0, st>>>(
@@ -477,7 +596,7 @@ static cudaError_t gen_run(Plan& p, const T* c, T* f, cudaStream_t st) {
         k_lap_moments<T, false><<<p.lap_blocks, nw * 32, smem, st>>>(
             p.N, p.d_t, p.d_tband, c, p.levels, p.q, p.xi1, p.d_cheb, partial);
         timer_end(p, slot, st);
-        k_lap_reduce<T><<<(entries + 255) / 256, 256, 0, st>>>(p.lap_blocks, entries, partial, vS);
+        k_lap_reduce<T><<<(entries * 32 + 255) / 256, 256, 0, st>>>(p.lap_blocks, entries, partial, vS);
         k_gen_couple<<<p.levels - 1, ((p.q + 31) / 32) * 32, 0, st>>>(p.levels, p.q, p.d_lapK, vS, h);
         p.launches += 3;
     }
@@ -512,10 +631,10 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
     if (p.prec == FL_FP64)
         return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb,
                                (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
-                               st, &p, p.d_lapK, p.d_lapKoff);
+                               st, &p, p.d_lapK, p.d_lapKoff, p.d_tperm);
     return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb, (const float*)c,
                           (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p, p.d_lapK,
-                          p.d_lapKoff);
+                          p.d_lapKoff, p.d_tperm);
 }
 
 }  // namespace fl
@@ -527,6 +646,65 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
             return lap_fail(e_ == cudaErrorMemoryAllocation ? FL_ENOMEM : FL_ECUDA, \
                             std::string(where) + ": " + cudaGetErrorString(e_));   \
     } while (0)
+
+__global__ void k_lap_sortprep(int64_t n, const uint8_t* __restrict__ band, uint32_t* __restrict__ keys,
+                               int32_t* __restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        keys[i] = band[i];
+        vals[i] = (int32_t)i;
+    }
+}
+
+__global__ void k_lap_sorted(int64_t n, const double* __restrict__ t, const uint32_t* __restrict__ keys,
+                             const int32_t* __restrict__ vals, double* __restrict__ ts,
+                             uint8_t* __restrict__ bs, int32_t* __restrict__ perm) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        ts[i] = t[vals[i]];
+        bs[i] = (uint8_t)keys[i];
+        perm[i] = vals[i];
+    }
+}
+
+// Plan time: t_k and their bands in band order (stable: equal bands keep the
+// input order), with tperm the original index of each.
+static cudaError_t sort_t_by_band(Plan& p, cudaStream_t st) {
+    const int64_t n = p.N;
+    uint32_t *keys = nullptr, *ktmp = nullptr, *hist = nullptr;
+    int32_t *vals = nullptr, *vtmp = nullptr;
+    double* ts = nullptr;
+    uint8_t* bs = nullptr;
+    const int64_t nblocks = (n + 2047) / 2048;        // radix-sort tiles of 256 x 8
+    cudaError_t e = cudaMalloc((void**)&keys, n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ktmp, n * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&vals, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&vtmp, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&hist, 256 * nblocks * sizeof(uint32_t));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ts, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&bs, n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p.d_tperm, n * sizeof(int32_t));
+    if (e == cudaSuccess) {
+        k_lap_sortprep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, p.d_tband, keys, vals);
+        e = radix_sort_pairs(keys, vals, ktmp, vtmp, hist, n, 8, st);
+    }
+    if (e == cudaSuccess) {
+        k_lap_sorted<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, p.d_t, keys, vals, ts, bs, p.d_tperm);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    for (void* ptr : {(void*)keys, (void*)ktmp, (void*)vals, (void*)vtmp, (void*)hist}) cudaFree(ptr);
+    if (e == cudaSuccess) {
+        cudaFree(p.d_t);
+        cudaFree(p.d_tband);
+        p.d_t = ts;
+        p.d_tband = bs;
+    } else {
+        cudaFree(ts);
+        cudaFree(bs);
+    }
+    return e;
+}
 
 static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, int q,
                                    cudaStream_t st) {
@@ -573,6 +751,7 @@ static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, in
         LAP_CUDA(cudaMemcpyAsync(p.d_t, t, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy t");
         LAP_CUDA(cudaMalloc((void**)&p.d_tband, N), "cudaMalloc t bands");
         k_lap_band<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(p.N, p.d_t, xi1, P.levels, p.d_tband);
+        LAP_CUDA(sort_t_by_band(p, st), "fl_plan_laplace: band order");
     }
     if (M) {
         LAP_CUDA(cudaMalloc((void**)&p.d_s, M * sizeof(double)), "cudaMalloc s");
