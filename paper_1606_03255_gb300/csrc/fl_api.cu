@@ -41,7 +41,7 @@ Plan::~Plan() {
     void* ptrs[] = {d_ws, d_perm, d_bandid, d_bands, d_small, d_pass, d_cheb, d_D, d_grid, d_Y,
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
-                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm,
+                    d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm, d_ts, d_tbs,
                     d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi};
     for (void* q : ptrs)
         if (q) cudaFree(q);

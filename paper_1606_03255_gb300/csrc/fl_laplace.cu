@@ -135,6 +135,10 @@ __global__ void k_lap_moments(int64_t N, const double* __restrict__ t,
     }
 }
 
+// Largest rank any Laplace plan uses (Algorithm 1: kMaxQ; the generalised
+// algorithm: kGenMaxQ below): the size of the per-element weight arrays.
+constexpr int kLapMaxRank = 64;
+
 // Barycentric weights w_r = lambda_r / (tau - t_r), r < q, with one division:
 // Montgomery's batch inversion (prefix products of d_r = tau - t_r, one
 // reciprocal, a backward sweep), about 3q ulps instead of 1/2 ulp per weight.
@@ -190,7 +194,7 @@ __global__ void k_lap_moments_sorted(int64_t N, const double* __restrict__ t,
         const int l = valid ? tband[k] : 255;       // invalid lanes: a run of their own at the end
         const double cv = valid ? (double)c[tperm[k]] : 0.0;
         double tau = 0.0, inv_den = 1.0;
-        double wr[kMaxQ];
+        double wr[kLapMaxRank];
         int hit = -1;
         const bool interp = valid && l < levels;
         if (interp) {
@@ -376,6 +380,7 @@ __global__ void k_lap_cheb(int q, double* cheb) {
 // (the example there, y, xi > 0).
 
 constexpr int kGenMaxQ = 64;
+static_assert(kGenMaxQ <= kLapMaxRank && kMaxQ <= kLapMaxRank, "weight arrays of the moments kernel");
 
 __device__ __forceinline__ double gen_kappa(int kind, double y, double xi) {
     const double x = y * xi;
@@ -398,16 +403,24 @@ __global__ void k_gen_ktable(int kind, int levels, int q, double y1, double xi1,
 }
 
 // h^{Y_m}_s = sum_{l = 1}^{M - 1} sum_r Kt(m, l)_{s r} v^{Omega_l}_r, m = blockIdx.x + 1.
+// One warp per s: lanes stride over the (l, r) terms, a fixed shuffle tree
+// combines them.
 __global__ void k_gen_couple(int levels, int q, const double* __restrict__ Kt,
                              const double* __restrict__ vS, double* __restrict__ h) {
-    const int m = blockIdx.x + 1, s = threadIdx.x, row = q + 1, nb = levels - 1;
-    if (m >= levels || s >= q) return;
-    double acc = 0.0;
-    for (int l = 1; l < levels; ++l) {
-        const double* Kb = Kt + (((int64_t)(m - 1) * nb + (l - 1)) * q + s) * q;
-        for (int r = 0; r < q; ++r) acc += Kb[r] * vS[l * row + r];
+    const int m = blockIdx.x + 1, row = q + 1, nb = levels - 1;
+    if (m >= levels) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int tot = nb * q;
+    for (int s = warp; s < q; s += nw) {
+        double acc = 0.0;
+        for (int i = lane; i < tot; i += 32) {
+            const int li = i / q, r = i - li * q;      // l = li + 1
+            acc += Kt[(((int64_t)(m - 1) * nb + li) * q + s) * q + r] * vS[(li + 1) * row + r];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) h[m * q + s] = acc;
     }
-    h[m * q + s] = acc;
 }
 
 // f~_j: s_j in Y_m (m < M): sum_s L_s^{Y_m}(s_j) h^{Y_m}_s plus the Omega_M near
@@ -589,15 +602,15 @@ static cudaError_t gen_run(Plan& p, const T* c, T* f, cudaStream_t st) {
     const size_t smem = (size_t)nw * entries * sizeof(T);
     int slot = -1;
     if (p.N > 0 && p.levels > 1) {
-        cudaError_t e = cudaFuncSetAttribute(k_lap_moments<T, false>,
+        cudaError_t e = cudaFuncSetAttribute(k_lap_moments_sorted<T>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        timer_begin(p, "lap_moments", (double)p.N * (8 + 1 + sizeof(T)), st, &slot);
-        k_lap_moments<T, false><<<p.lap_blocks, nw * 32, smem, st>>>(
-            p.N, p.d_t, p.d_tband, c, p.levels, p.q, p.xi1, p.d_cheb, partial);
+        timer_begin(p, "lap_moments", (double)p.N * (8 + 1 + 4 + sizeof(T)), st, &slot);
+        k_lap_moments_sorted<T><<<p.lap_blocks, nw * 32, smem, st>>>(
+            p.N, p.d_ts, p.d_tbs, p.d_tperm, c, p.levels, p.q, p.xi1, p.d_cheb, partial);
         timer_end(p, slot, st);
         k_lap_reduce<T><<<(entries * 32 + 255) / 256, 256, 0, st>>>(p.lap_blocks, entries, partial, vS);
-        k_gen_couple<<<p.levels - 1, ((p.q + 31) / 32) * 32, 0, st>>>(p.levels, p.q, p.d_lapK, vS, h);
+        k_gen_couple<<<p.levels - 1, 32 * std::min(p.q, 32), 0, st>>>(p.levels, p.q, p.d_lapK, vS, h);
         p.launches += 3;
     }
     if (p.M > 0) {
@@ -629,10 +642,10 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
     for (int m = 1; m < p.levels && m < (int)p.bands.size(); ++m) P.ell[m] = p.bands[m].ell;
     const uint8_t* tband = p.d_tband;
     if (p.prec == FL_FP64)
-        return lap_run<double>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb,
+        return lap_run<double>(p.N, p.M, p.d_ts, p.d_s, p.d_tbs, p.d_sband, P, p.d_cheb,
                                (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
                                st, &p, p.d_lapK, p.d_lapKoff, p.d_tperm);
-    return lap_run<float>(p.N, p.M, p.d_t, p.d_s, tband, p.d_sband, P, p.d_cheb, (const float*)c,
+    return lap_run<float>(p.N, p.M, p.d_ts, p.d_s, p.d_tbs, p.d_sband, P, p.d_cheb, (const float*)c,
                           (float*)f, (unsigned char*)p.d_lap, p.lap_blocks, st, &p, p.d_lapK,
                           p.d_lapKoff, p.d_tperm);
 }
@@ -667,8 +680,8 @@ __global__ void k_lap_sorted(int64_t n, const double* __restrict__ t, const uint
     }
 }
 
-// Plan time: t_k and their bands in band order (stable: equal bands keep the
-// input order), with tperm the original index of each.
+// Plan time: copies of the t_k and their bands in band order (stable: equal
+// bands keep the input order), with tperm the original index of each.
 static cudaError_t sort_t_by_band(Plan& p, cudaStream_t st) {
     const int64_t n = p.N;
     uint32_t *keys = nullptr, *ktmp = nullptr, *hist = nullptr;
@@ -681,9 +694,11 @@ static cudaError_t sort_t_by_band(Plan& p, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaMalloc((void**)&vals, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&vtmp, n * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc((void**)&hist, 256 * nblocks * sizeof(uint32_t));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ts, n * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&bs, n);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p.d_ts, n * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p.d_tbs, n);
     if (e == cudaSuccess) e = cudaMalloc((void**)&p.d_tperm, n * sizeof(int32_t));
+    ts = p.d_ts;
+    bs = p.d_tbs;
     if (e == cudaSuccess) {
         k_lap_sortprep<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, p.d_tband, keys, vals);
         e = radix_sort_pairs(keys, vals, ktmp, vtmp, hist, n, 8, st);
@@ -694,16 +709,7 @@ static cudaError_t sort_t_by_band(Plan& p, cudaStream_t st) {
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     for (void* ptr : {(void*)keys, (void*)ktmp, (void*)vals, (void*)vtmp, (void*)hist}) cudaFree(ptr);
-    if (e == cudaSuccess) {
-        cudaFree(p.d_t);
-        cudaFree(p.d_tband);
-        p.d_t = ts;
-        p.d_tband = bs;
-    } else {
-        cudaFree(ts);
-        cudaFree(bs);
-    }
-    return e;
+    return e;   // on failure the plan's destructor frees what was allocated
 }
 
 static fl_status plan_laplace_impl(Plan& p, const double* t, const double* s, int q,
@@ -858,6 +864,7 @@ static fl_status plan_general_impl(Plan& p, int kind, const double* t, const dou
         LAP_CUDA(cudaMemcpyAsync(p.d_t, t, N * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy t");
         LAP_CUDA(cudaMalloc((void**)&p.d_tband, N), "cudaMalloc t bands");
         k_lap_band<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(p.N, p.d_t, xi1, levels, p.d_tband);
+        LAP_CUDA(sort_t_by_band(p, st), "fl_plan_kernel: band order");
     }
     if (M) {
         LAP_CUDA(cudaMalloc((void**)&p.d_s, M * sizeof(double)), "cudaMalloc s");

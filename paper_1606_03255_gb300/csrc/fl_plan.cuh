@@ -179,8 +179,10 @@ struct Plan {
     // Laplace (Algorithm 1)
     double* d_t = nullptr;
     double* d_s = nullptr;
-    uint8_t* d_tband = nullptr;    // band of every t_k (Algorithm 1: in band order, see d_tperm)
-    int32_t* d_tperm = nullptr;    // Algorithm 1: original index of the k-th t in band order
+    uint8_t* d_tband = nullptr;    // band of every t_k
+    double* d_ts = nullptr;        // the t_k in band order (stable), for the moments
+    uint8_t* d_tbs = nullptr;      // their bands
+    int32_t* d_tperm = nullptr;    // original index of the k-th t in band order
     uint8_t* d_sband = nullptr;    // band of every s_j
     void* d_lap = nullptr;         // moments and partial sums
     double* d_lapK = nullptr;      // coupling blocks K^{Y_m, Omega_l} (plan-time table)
