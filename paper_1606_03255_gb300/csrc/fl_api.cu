@@ -381,7 +381,9 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.dadj_work32.clear();
     p.dadj_work64.clear();
     p.direct_nodes = p.direct_terms = p.dpart_elems = 0;
+    p.n_direct_small = 0;
     p.z0_nodes = 0;
+    std::vector<DirectItem> small_items;
     for (int i = 0; i < B; ++i) {
         Instance& in = p.inst[i];
         in.z0_nodes = counts[in.band_base];
@@ -407,10 +409,16 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                 p.direct_ranges.push_back({b, 0, bh.nodes, p.direct_nodes});
                 p.direct_nodes += bh.nodes;
                 p.direct_terms += bh.nodes * d.K;
-                for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirNodes)
-                    for (int ch = 0; ch < d.nchunk; ++ch)
-                        p.direct_work.push_back({b, ch, bh.node_off + n0,
-                                                 (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
+                if (d.K <= kDirSmallK && p.prec != FL_FP64_FF) {
+                    for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirSmallNodes)
+                        small_items.push_back({b, 0, bh.node_off + n0,
+                                               (int)std::min<int64_t>(kDirSmallNodes, bh.nodes - n0), 0});
+                } else {
+                    for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirNodes)
+                        for (int ch = 0; ch < d.nchunk; ++ch)
+                            p.direct_work.push_back({b, ch, bh.node_off + n0,
+                                                     (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
+                }
                 if (!p.batched) {
                     for (int kl : {32, 16}) {
                         std::vector<DirectAdjItem>& v = kl == 32 ? p.dadj_work32 : p.dadj_work64;
@@ -437,6 +445,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             }
         }
     }
+    p.n_direct_small = (int64_t)small_items.size();
+    p.direct_work.insert(p.direct_work.end(), small_items.begin(), small_items.end());
     build_pass_groups(p);
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),

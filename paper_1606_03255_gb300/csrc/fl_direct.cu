@@ -37,6 +37,37 @@ template <typename T> __device__ __forceinline__ T dir_exp(T a);
 template <> __device__ __forceinline__ float dir_exp<float>(float a) { return expf(a); }
 template <> __device__ __forceinline__ double dir_exp<double>(double a) { return exp(a); }
 
+// FP32 form without FP64 arithmetic per block: x in [0, 1) held as the 64-bit
+// fixed-point X = x 2^64 (exact for the 53-bit x), so frac(k x) is the
+// wrapped product k X, rounded to 24 bits and read as a signed value in
+// [-1/2, 1/2); y as a float pair (hi + lo), so y k = p + e with p = fl(hi k)
+// and e its error plus lo k, and exp(-y k) = exp(-p) (1 - e) (|e| < 2^-20 p).
+struct DirF32Node {
+    uint64_t X;
+    float yh, yl;
+};
+__device__ __forceinline__ DirF32Node dir_f32_node(double x, double y) {
+    DirF32Node d;
+    d.X = (uint64_t)ldexp(x, 64);
+    d.yh = (float)y;
+    d.yl = (float)(y - (double)d.yh);
+    return d;
+}
+// z^k = exp(-y k) e^(2 pi i frac(k x)) for 0 <= k < 2^24 (SIGN = -1: the conjugate
+// phase); false when y k > lim (the power underflows: so do all later ones).
+template <int SIGN>
+__device__ __forceinline__ bool dir_f32_power(const DirF32Node& d, int64_t k, float lim, float2* zk) {
+    const float kf = (float)k;                 // exact: k < 2^24
+    const float p = d.yh * kf;
+    if (p > lim) return false;
+    const float e = fmaf(d.yh, kf, -p) + d.yl * kf;
+    const float mag = expf(-p) * (1.f - e);
+    const uint64_t ph = (uint64_t)k * d.X + (1ull << 39);
+    const float phase = (float)((int64_t)ph >> 40) * 0x1p-24f;   // frac(k x) in [-1/2, 1/2)
+    *zk = cscale(expipi<float>((float)(2 * SIGN) * phase), mag);
+    return true;
+}
+
 // One CTA per work item: up to kDirNodes consecutive sorted nodes of one band
 // against one chunk of kDirChunk coefficients staged in shared memory.  Warp w
 // takes node w; lane l takes the Horner blocks l, l + 32, ... of the chunk.
@@ -59,7 +90,9 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
         if (k < kend) {
             v = c[B.c_off + k];
             if (DERIV) {
-                const T wgt = (T)(kTwoPiDir * (double)k);
+                T wgt;
+                if constexpr (sizeof(T) == 4) wgt = (float)k * 6.28318530717958647692f;   // k < 2^24: one rounding
+                else wgt = kTwoPiDir * (double)k;
                 v = C{-v.y * wgt, v.x * wgt};
             }
         }
@@ -76,19 +109,26 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
     double xr = x;
     if (xr >= 0.5) xr -= 1.0;
     const C z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    DirF32Node nd;
+    if constexpr (sizeof(T) == 4) nd = dir_f32_node(x, y);
     C acc = C{(T)0, (T)0};
 #pragma unroll 1
     for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
         const int b = bb * 32 + lane;
         const int64_t kb = k0 + (int64_t)b * kDirBlock;
         if (kb >= kend) break;
-        const double ykb = y * (double)kb;
-        if (ykb > (sizeof(T) == 4 ? 104.0 : 745.0)) break;   // z^kb underflows: so do later blocks
+        C zk;
+        if constexpr (sizeof(T) == 4) {
+            if (!dir_f32_power<1>(nd, kb, 104.f, &zk)) break;   // z^kb underflows: so do later blocks
+        } else {
+            const double ykb = y * (double)kb;
+            if (ykb > 745.0) break;
+            zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)kb, x))), dir_exp<T>((T)(-ykb)));
+        }
         const C* cb = tile + b * kDirBlock;
         C P = cb[kDirBlock - 1];
 #pragma unroll
         for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
-        const C zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)kb, x))), dir_exp<T>((T)(-ykb)));
         acc = cadd(acc, cmul(zk, P));
     }
 #pragma unroll
@@ -97,6 +137,65 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
     if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
+}
+
+// Bands with K <= kDirSmallK: one thread per node (up to kDirSmallNodes per
+// CTA), the band's K coefficients staged once, all K terms per thread in the
+// same blocked Horner form (blocks of kDirBlock terms from an exactly reduced
+// power z^kb); the partial of chunk 0 as for k_direct.
+template <typename T, bool DERIV>
+__global__ void __launch_bounds__(kDirSmallNodes) k_direct_small(const DirectItem* __restrict__ items,
+                                                                 const BandDev* __restrict__ bands,
+                                                                 const double2* __restrict__ ws,
+                                                                 const C_t<T>* __restrict__ c,
+                                                                 C_t<T>* __restrict__ part) {
+    using C = C_t<T>;
+    __shared__ C tile[kDirSmallK];
+    const DirectItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int K = (int)B.K;                              // <= kDirSmallK
+    const int Kr = (K + kDirBlock - 1) / kDirBlock * kDirBlock;
+    for (int k = threadIdx.x; k < Kr; k += blockDim.x) {
+        C v = C{(T)0, (T)0};
+        if (k < K) {
+            v = c[B.c_off + k];
+            if (DERIV) {
+                T wgt;
+                if constexpr (sizeof(T) == 4) wgt = (float)k * 6.28318530717958647692f;
+                else wgt = kTwoPiDir * (double)k;
+                v = C{-v.y * wgt, v.x * wgt};
+            }
+        }
+        tile[k] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= it.nnodes) return;
+    const int64_t i = it.node0 + threadIdx.x;
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double y = kTwoPiDir * wv.y;
+    double xr = x;
+    if (xr >= 0.5) xr -= 1.0;
+    const C z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    DirF32Node nd;
+    if constexpr (sizeof(T) == 4) nd = dir_f32_node(x, y);
+    C acc = C{(T)0, (T)0};
+    for (int kb = 0; kb < K; kb += kDirBlock) {
+        C zk;
+        if constexpr (sizeof(T) == 4) {
+            if (!dir_f32_power<1>(nd, kb, 104.f, &zk)) break;
+        } else {
+            const double ykb = y * (double)kb;
+            if (ykb > 745.0) break;
+            zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)kb, x))), dir_exp<T>((T)(-ykb)));
+        }
+        const C* cb = tile + kb;
+        C P = cb[kDirBlock - 1];
+#pragma unroll
+        for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
+        acc = cadd(acc, cmul(zk, P));
+    }
+    part[B.dslot + (i - B.node_off) * B.nchunk] = acc;
 }
 
 // f[perm[i]] = sum over the node's chunks (in chunk order); with rmul,
@@ -151,6 +250,7 @@ __global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restri
         // lane loads node nb + lane: x, y, r_j and conj(z_j) in T
         double xl = 0.0, yl = 0.0;
         C rl = C{(T)0, (T)0}, zl = C{(T)0, (T)0};
+        DirF32Node nl = {0ull, 0.f, 0.f};
         if (nb + lane < it.nnodes) {
             const int64_t i = it.node0 + nb + lane;
             const double2 wv = ws[i];
@@ -159,17 +259,29 @@ __global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restri
             rl = r[perm[i]];
             double xr = xl >= 0.5 ? xl - 1.0 : xl;
             zl = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-yl)));
+            if constexpr (sizeof(T) == 4) nl = dir_f32_node(xl, yl);
         }
         const int cnt = min(32, it.nnodes - nb);
         for (int q = 0; q < cnt; ++q) {
-            const double x = __shfl_sync(0xffffffffu, xl, q);
-            const double y = __shfl_sync(0xffffffffu, yl, q);
             const C rq = C{__shfl_sync(0xffffffffu, rl.x, q), __shfl_sync(0xffffffffu, rl.y, q)};
             const C zq = C{__shfl_sync(0xffffffffu, zl.x, q), __shfl_sync(0xffffffffu, zl.y, q)};
-            if (!active) continue;
-            const double yk = y * (double)k0;
-            if (yk > (sizeof(T) == 4 ? 104.0 : 745.0)) continue;
-            const C w0 = cscale(expipi<T>((T)(-2.0 * dir_phase<T>((double)k0, x))), dir_exp<T>((T)(-yk)));
+            C w0;
+            if constexpr (sizeof(T) == 4) {
+                DirF32Node nq;
+                nq.X = ((uint64_t)__shfl_sync(0xffffffffu, (unsigned)(nl.X >> 32), q) << 32) |
+                       (uint64_t)__shfl_sync(0xffffffffu, (unsigned)nl.X, q);
+                nq.yh = __shfl_sync(0xffffffffu, nl.yh, q);
+                nq.yl = __shfl_sync(0xffffffffu, nl.yl, q);
+                if (!active) continue;
+                if (!dir_f32_power<-1>(nq, k0, 104.f, &w0)) continue;
+            } else {
+                const double x = __shfl_sync(0xffffffffu, xl, q);
+                const double y = __shfl_sync(0xffffffffu, yl, q);
+                if (!active) continue;
+                const double yk = y * (double)k0;
+                if (yk > 745.0) continue;
+                w0 = cscale(expipi<T>((T)(-2.0 * dir_phase<T>((double)k0, x))), dir_exp<T>((T)(-yk)));
+            }
             C rw = cmul(rq, w0);
 #pragma unroll
             for (int t = 0; t < KL; ++t) {
@@ -295,13 +407,20 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
     if (e != cudaSuccess) return e;
     int slot;
     timer_begin(p, "direct", (double)p.direct_terms * sizeof(C) / 32.0, st, &slot);
-    kern<<<(unsigned)p.direct_work.size(), 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws,
-                                                           (const C*)c, (C*)p.d_dpart);
+    const int64_t nbig = (int64_t)p.direct_work.size() - p.n_direct_small;
+    if (nbig > 0)
+        kern<<<(unsigned)nbig, 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws, (const C*)c, (C*)p.d_dpart);
+    if (p.n_direct_small > 0) {
+        auto ks = deriv ? k_direct_small<T, true> : k_direct_small<T, false>;
+        ks<<<(unsigned)p.n_direct_small, kDirSmallNodes, 0, st>>>(p.d_direct + nbig, p.d_bands, p.d_ws,
+                                                                  (const C*)c, (C*)p.d_dpart);
+        ++p.launches;
+    }
     timer_end(p, slot, st);
     k_direct_reduce<T><<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
         (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
         (const C*)p.d_dpart, (const C*)rmul, (C*)f);
-    p.launches += 2;
+    p.launches += 1 + (nbig > 0);
     return cudaGetLastError();
 }
 

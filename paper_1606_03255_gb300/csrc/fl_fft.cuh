@@ -19,6 +19,13 @@ namespace fl {
 
 constexpr double kTwoPiFFT = 6.283185307179586476925286766559;
 
+// 2 pi k in T: float from the exact float k (k < 2^24), with one rounding and
+// no FP64 arithmetic; double (and float pairs) through double.
+template <typename T> __device__ __forceinline__ T deriv_weight(int64_t k) {
+    if constexpr (sizeof(T) == 4) return (float)k * 6.28318530717958647692f;
+    else return (T)(kTwoPiFFT * (double)k);
+}
+
 // Forward input: grid index i in [0, n) holds frequency k' = i (i < n/2) or
 // i - n, i.e. k = k' + N_m/2; value c_k D[s][k] for 0 <= k < K, else 0.
 template <typename T, bool DERIV>
@@ -30,8 +37,8 @@ __device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
     if (k < 0 || k >= B.K) return C_t<T>{(T)0, (T)0};
     const T d = D[B.D_off + (int64_t)s * B.K + k];
     C_t<T> v = c[k];
-    if (DERIV) {   // (2 pi i k) c_k
-        const T w = (T)(kTwoPiFFT * (double)k);
+    if (DERIV) {   // (2 pi i k) c_k; float: k < 2^24 exact, one rounding
+        const T w = deriv_weight<T>(k);
         v = C_t<T>{-v.y * w, v.x * w};
     }
     return C_t<T>{v.x * d, v.y * d};
@@ -52,7 +59,7 @@ __device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K,
     const T d = Ds[kk];
     C_t<T> v = c[kk];
     if (DERIV) {
-        const T w = (T)(kTwoPiFFT * (double)kk);
+        const T w = deriv_weight<T>(kk);
         v = C_t<T>{-v.y * w, v.x * w};
     }
     return in ? C_t<T>{v.x * d, v.y * d} : C_t<T>{(T)0, (T)0};

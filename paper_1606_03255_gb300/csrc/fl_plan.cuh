@@ -46,6 +46,9 @@ struct PassGroup {
 constexpr int kDirBlock = 32;
 constexpr int kDirChunk = 4096;
 constexpr int kDirNodes = 8;
+// Bands with K <= kDirSmallK (FP32 and FP64 forms): one thread per node, up to
+// kDirSmallNodes nodes per CTA, all K terms per thread (see k_direct_small).
+constexpr int kDirSmallK = 256, kDirSmallNodes = 256;
 
 struct DirectItem {
     int band;
@@ -129,7 +132,8 @@ struct Plan {
     int64_t xiphi_elems = 0;
     double direct_bias = 1.0;
     double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)
-    std::vector<DirectItem> direct_work;
+    std::vector<DirectItem> direct_work;   // items of the larger-K bands, then n_direct_small
+    int64_t n_direct_small = 0;            // items of the bands with K <= kDirSmallK (at the end)
     std::vector<DirectRange> direct_ranges;
     std::vector<DirectAdjItem> dadj_work32, dadj_work64;   // adjoint items for KL = 32 / 16
     int64_t direct_nodes = 0, direct_terms = 0, dpart_elems = 0;
