@@ -382,8 +382,10 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.dadj_work64.clear();
     p.direct_nodes = p.direct_terms = p.dpart_elems = 0;
     p.n_direct_small = 0;
+    p.n_dadj_small = 0;
     p.z0_nodes = 0;
     std::vector<DirectItem> small_items;
+    std::vector<DirectAdjItem> small_adj;
     for (int i = 0; i < B; ++i) {
         Instance& in = p.inst[i];
         in.z0_nodes = counts[in.band_base];
@@ -419,7 +421,11 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                             p.direct_work.push_back({b, ch, bh.node_off + n0,
                                                      (int)std::min<int64_t>(kDirNodes, bh.nodes - n0), 0});
                 }
-                if (!p.batched) {
+                if (!p.batched && d.K <= kDirSmallK) {
+                    for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirAdjNodes)
+                        small_adj.push_back({b, 0, bh.node_off + n0,
+                                             (int)std::min<int64_t>(kDirAdjNodes, bh.nodes - n0), 0});
+                } else if (!p.batched) {
                     for (int kl : {32, 16}) {
                         std::vector<DirectAdjItem>& v = kl == 32 ? p.dadj_work32 : p.dadj_work64;
                         const int64_t kc = (d.K + 32 * kl - 1) / (32 * kl);
@@ -447,6 +453,9 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     }
     p.n_direct_small = (int64_t)small_items.size();
     p.direct_work.insert(p.direct_work.end(), small_items.begin(), small_items.end());
+    p.n_dadj_small = (int64_t)small_adj.size();
+    p.dadj_work32.insert(p.dadj_work32.end(), small_adj.begin(), small_adj.end());
+    p.dadj_work64.insert(p.dadj_work64.end(), small_adj.begin(), small_adj.end());
     build_pass_groups(p);
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),

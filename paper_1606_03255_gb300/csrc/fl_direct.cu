@@ -396,6 +396,72 @@ static cudaError_t direct_forward_ff(Plan& p, void* f, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Adjoint of the bands with K <= kDirSmallK: one warp per (band, group of up
+// to kDirAdjNodes nodes).  The lanes split into KB blocks of KL frequencies
+// (KB the smallest power of two with KB KL >= K) and G = 32 / KB node
+// subgroups; each lane sums its subgroup's nodes (every G-th) over its KL
+// frequencies, a fixed shuffle tree adds the subgroups, and the first
+// subgroup adds the result to cdir (atomics across node groups, as k_direct_adj).
+template <typename T>
+__global__ void __launch_bounds__(32) k_direct_adj_small(const DirectAdjItem* __restrict__ items,
+                                                         const BandDev* __restrict__ bands,
+                                                         const double2* __restrict__ ws,
+                                                         const int32_t* __restrict__ perm,
+                                                         const C_t<T>* __restrict__ r,
+                                                         C_t<T>* __restrict__ cdir) {
+    using C = C_t<T>;
+    constexpr int KL = AdjKL<T>::KL;
+    const DirectAdjItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int K = (int)B.K;
+    int lkb = 0;
+    while ((KL << lkb) < K) ++lkb;                 // KB = 2^lkb <= 32 (K <= kDirSmallK)
+    const int lane = threadIdx.x, g = lane >> lkb, G = 32 >> lkb;
+    const int64_t k0 = (int64_t)(lane & ((1 << lkb) - 1)) * KL;
+    const bool active = k0 < K;
+    C acc[KL];
+#pragma unroll
+    for (int t = 0; t < KL; ++t) acc[t] = C{(T)0, (T)0};
+    for (int jn = g; active && jn < it.nnodes; jn += G) {
+        const int64_t i = it.node0 + jn;
+        const double2 wv = ws[i];
+        const double x = wv.x - floor(wv.x);
+        const double y = kTwoPiDir * wv.y;
+        const double xr = x >= 0.5 ? x - 1.0 : x;
+        const C zq = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-y)));
+        C w0;
+        if constexpr (sizeof(T) == 4) {
+            if (!dir_f32_power<-1>(dir_f32_node(x, y), k0, 104.f, &w0)) continue;
+        } else {
+            const double yk = y * (double)k0;
+            if (yk > 745.0) continue;
+            w0 = cscale(expipi<T>((T)(-2.0 * dir_phase<T>((double)k0, x))), dir_exp<T>((T)(-yk)));
+        }
+        C rw = cmul(r[perm[i]], w0);
+#pragma unroll
+        for (int t = 0; t < KL; ++t) {
+            acc[t] = cadd(acc[t], rw);
+            rw = cmul(rw, zq);
+        }
+    }
+    for (int off = 1 << lkb; off < 32; off <<= 1) {
+#pragma unroll
+        for (int t = 0; t < KL; ++t) {
+            acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, off);
+            acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, off);
+        }
+    }
+    if (g != 0 || !active) return;
+#pragma unroll
+    for (int t = 0; t < KL; ++t) {
+        const int64_t k = k0 + t;
+        if (k < K) {
+            atomicAdd(&cdir[k].x, acc[t].x);
+            atomicAdd(&cdir[k].y, acc[t].y);
+        }
+    }
+}
+
 template <typename T>
 static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                                     cudaStream_t st) {
@@ -443,10 +509,18 @@ static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
     const DirectAdjItem* d_items = dbl ? p.d_dadj64 : p.d_dadj32;
     int slot;
     timer_begin(p, "direct_adj", 0.0, st, &slot);
-    k_direct_adj<T><<<(unsigned)items.size(), 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
-                                                         (const C*)r, (C*)p.d_cdir);
+    const int64_t nbig = (int64_t)items.size() - p.n_dadj_small;
+    if (nbig > 0) {
+        k_direct_adj<T><<<(unsigned)nbig, 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
+                                                       (const C*)r, (C*)p.d_cdir);
+        ++p.launches;
+    }
+    if (p.n_dadj_small > 0) {
+        k_direct_adj_small<T><<<(unsigned)p.n_dadj_small, 32, 0, st>>>(
+            d_items + nbig, p.d_bands, p.d_ws, p.d_perm, (const C*)r, (C*)p.d_cdir);
+        ++p.launches;
+    }
     timer_end(p, slot, st);
-    ++p.launches;
     return cudaGetLastError();
 }
 

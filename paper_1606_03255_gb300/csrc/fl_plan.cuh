@@ -135,7 +135,8 @@ struct Plan {
     std::vector<DirectItem> direct_work;   // items of the larger-K bands, then n_direct_small
     int64_t n_direct_small = 0;            // items of the bands with K <= kDirSmallK (at the end)
     std::vector<DirectRange> direct_ranges;
-    std::vector<DirectAdjItem> dadj_work32, dadj_work64;   // adjoint items for KL = 32 / 16
+    std::vector<DirectAdjItem> dadj_work32, dadj_work64;   // adjoint items for KL = 32 / 16, then
+    int64_t n_dadj_small = 0;                              // the items of K <= kDirSmallK bands
     int64_t direct_nodes = 0, direct_terms = 0, dpart_elems = 0;
 
     // device memory
