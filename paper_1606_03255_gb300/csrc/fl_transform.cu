@@ -588,28 +588,31 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
     for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = acc[s];
 }
 
-// Dense NFFT bands (many nodes per cell): one warp per cell, lanes strided
-// over the covering nodes, lane sums combined in a fixed shuffle order.
+// Dense NFFT bands (many nodes per cell): one CTA of kSpreadDense threads per
+// cell, threads strided over the covering nodes; the thread sums are combined
+// in a fixed order (a shuffle tree per warp, then the warps in order).
+constexpr int kSpreadDense = 256;
+
 template <typename T, int MW>
-__global__ void __launch_bounds__(256) k_spread_cells_warp(int ncb, const Plan::CellBand* __restrict__ cbs,
-                                                           int64_t total,
-                                                           const BandDev* __restrict__ bands,
-                                                           const int32_t* __restrict__ cell,
-                                                           const T* __restrict__ sp_phi,
-                                                           const T* __restrict__ sp_L,
-                                                           const C_t<T>* __restrict__ sp_rv, int q,
-                                                           C_t<T>* __restrict__ grid) {
+__global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, const Plan::CellBand* __restrict__ cbs,
+                                                                    int64_t total,
+                                                                    const BandDev* __restrict__ bands,
+                                                                    const int32_t* __restrict__ cell,
+                                                                    const T* __restrict__ sp_phi,
+                                                                    const T* __restrict__ sp_L,
+                                                                    const C_t<T>* __restrict__ sp_rv, int q,
+                                                                    C_t<T>* __restrict__ grid) {
     using C = C_t<T>;
-    const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
+    __shared__ C red[kSpreadDense / 32][kMaxQ];
+    const int64_t g = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (g >= total) return;
     const int cb = find_cell_band(cbs, ncb, g);
     const BandDev B = bands[cbs[cb].band];
     const int64_t l = g - cbs[cb].prefix;
     C acc[kMaxQ];
     for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
-    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, lane, 32, acc);
-    C* gb = grid + B.grid_off + l;
+    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, threadIdx.x, kSpreadDense, acc);
     for (int s = 0; s < B.nrhs; ++s) {
         T x = acc[s].x, y = acc[s].y;
 #pragma unroll
@@ -617,7 +620,14 @@ __global__ void __launch_bounds__(256) k_spread_cells_warp(int ncb, const Plan::
             x += __shfl_xor_sync(0xffffffffu, x, off);
             y += __shfl_xor_sync(0xffffffffu, y, off);
         }
-        if (lane == 0) gb[(int64_t)s * B.n] = C{x, y};
+        if (lane == 0) red[w][s] = C{x, y};
+    }
+    __syncthreads();
+    const int s = threadIdx.x;
+    if (s < B.nrhs) {
+        C sum = red[0][s];
+        for (int ww = 1; ww < kSpreadDense / 32; ++ww) sum = cadd(sum, red[ww][s]);
+        grid[B.grid_off + l + (int64_t)s * B.n] = sum;
     }
 }
 
@@ -937,7 +947,7 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
             (int)p.n_sparse_cb, p.d_cell_bands, p.cells_total, p.d_bands, p.d_cell,
             (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
     if (p.cells_dense > 0)
-        k_spread_cells_warp<T, MW><<<(unsigned)((p.cells_dense * 32 + 255) / 256), 256, 0, st>>>(
+        k_spread_cells_warp<T, MW><<<(unsigned)p.cells_dense, kSpreadDense, 0, st>>>(
             (int)(p.cell_bands.size() - p.n_sparse_cb), p.d_cell_bands + p.n_sparse_cb,
             p.cells_dense, p.d_bands, p.d_cell, (const T*)p.d_sp_phi, (const T*)p.d_sp_L,
             (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
