@@ -411,7 +411,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                 p.direct_ranges.push_back({b, 0, bh.nodes, p.direct_nodes});
                 p.direct_nodes += bh.nodes;
                 p.direct_terms += bh.nodes * d.K;
-                if (d.K <= kDirSmallK && p.prec != FL_FP64_FF) {
+                if (d.K <= kDirSmallK && bh.nodes >= kDirSmallMinNodes && p.prec == FL_FP32) {
                     for (int64_t n0 = 0; n0 < bh.nodes; n0 += kDirSmallNodes)
                         small_items.push_back({b, 0, bh.node_off + n0,
                                                (int)std::min<int64_t>(kDirSmallNodes, bh.nodes - n0), 0});

@@ -46,9 +46,11 @@ struct PassGroup {
 constexpr int kDirBlock = 32;
 constexpr int kDirChunk = 4096;
 constexpr int kDirNodes = 8;
-// Bands with K <= kDirSmallK (FP32 and FP64 forms): one thread per node, up to
-// kDirSmallNodes nodes per CTA, all K terms per thread (see k_direct_small).
-constexpr int kDirSmallK = 256, kDirSmallNodes = 256;
+// FP32 bands with K <= kDirSmallK and at least kDirSmallMinNodes nodes: one
+// thread per node, up to kDirSmallNodes nodes per CTA, all K terms per thread
+// (see k_direct_small).  Fewer nodes, or FP64 (whose serial chains are long),
+// keep a warp per node.
+constexpr int kDirSmallK = 256, kDirSmallNodes = 256, kDirSmallMinNodes = 128;
 
 struct DirectItem {
     int band;
