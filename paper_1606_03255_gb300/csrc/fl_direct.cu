@@ -84,7 +84,9 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
     const BandDev B = bands[it.band];
     const int64_t k0 = (int64_t)it.chunk * kDirChunk;
     const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
-    for (int i = threadIdx.x; i < kDirChunk; i += blockDim.x) {
+    // the chunk's terms rounded up to whole Horner blocks (zeros past kend)
+    const int nst = (int)((kend - k0 + kDirBlock - 1) / kDirBlock) * kDirBlock;
+    for (int i = threadIdx.x; i < nst; i += blockDim.x) {
         const int64_t k = k0 + i;
         C v = C{(T)0, (T)0};
         if (k < kend) {
@@ -316,7 +318,8 @@ __global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict_
     const BandDev B = bands[it.band];
     const int64_t k0 = (int64_t)it.chunk * kDirChunk;
     const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
-    for (int i = threadIdx.x; i < kDirChunk; i += blockDim.x) {
+    const int nst = (int)((kend - k0 + kDirBlock - 1) / kDirBlock) * kDirBlock;
+    for (int i = threadIdx.x; i < nst; i += blockDim.x) {
         const int64_t k = k0 + i;
         tile[i] = k < kend ? c[B.c_off + k] : ffc{ff(0), ff(0)};
     }

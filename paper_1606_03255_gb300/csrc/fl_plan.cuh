@@ -50,7 +50,10 @@ constexpr int kDirNodes = 8;
 // thread per node, up to kDirSmallNodes nodes per CTA, all K terms per thread
 // (see k_direct_small).  Fewer nodes, or FP64 (whose serial chains are long),
 // keep a warp per node.
-constexpr int kDirSmallK = 256, kDirSmallNodes = 256, kDirSmallMinNodes = 128;
+#ifndef FL_DIR_SMALL_MIN_NODES
+#define FL_DIR_SMALL_MIN_NODES 2048
+#endif
+constexpr int kDirSmallK = 256, kDirSmallNodes = 256, kDirSmallMinNodes = FL_DIR_SMALL_MIN_NODES;
 
 struct DirectItem {
     int band;

@@ -265,3 +265,19 @@ def test_nodes_on_and_next_to_chebyshev_points(fl, prec, eps):
     f, _ = _run(fl, c, w, eps, prec)
     ref = oracle.flt_direct(c, w)
     assert oracle.error_E(ref, f, c) <= tol(eps, prec, ref, c)
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_direct_bands_with_many_nodes(fl, prec, eps):
+    # every band summed directly; on 2^16 disk nodes the low bands hold
+    # thousands of nodes each with K <= 256 (the thread-per-node kernel in FP32)
+    N, M = 1 << 12, 1 << 16
+    c = W.coefficients(N, seed=31)
+    w = W.nodes_disk_uniform(M, seed=32)
+    f, info = _run(fl, c, w, eps, prec, route="direct")
+    many = [b for b in range(1, info["levels"] + 1)
+            if info["band_route"][b] == 2 and info["band_K"][b] <= 256 and info["band_nodes"][b] >= 2048]
+    assert many, "expected direct bands with K <= 256 and >= 2048 nodes"
+    idx = np.random.default_rng(33).choice(M, 2048, replace=False)
+    ref = oracle.flt_direct(c, w[idx])
+    assert oracle.error_E(ref, f[idx], c) <= tol(eps, prec, ref, c)
