@@ -51,9 +51,13 @@ constexpr int kDirNodes = 8;
 // (see k_direct_small).  Fewer nodes, or FP64 (whose serial chains are long),
 // keep a warp per node.
 #ifndef FL_DIR_SMALL_MIN_NODES
-#define FL_DIR_SMALL_MIN_NODES 2048
+#define FL_DIR_SMALL_MIN_NODES 128
 #endif
-constexpr int kDirSmallK = 256, kDirSmallNodes = 256, kDirSmallMinNodes = FL_DIR_SMALL_MIN_NODES;
+#ifndef FL_DIR_SMALL_NODES
+#define FL_DIR_SMALL_NODES 256
+#endif
+constexpr int kDirSmallK = 256, kDirSmallNodes = FL_DIR_SMALL_NODES,
+              kDirSmallMinNodes = FL_DIR_SMALL_MIN_NODES;
 
 struct DirectItem {
     int band;
