@@ -16,13 +16,9 @@ namespace fl {
 
 constexpr double kTwoPiDir = 6.283185307179586476925286766559;
 
-// frac(k x) in [-1/2, 1/2).  double: k x = p + e exactly (FMA), one rounding.
-// float: the double product's error (2^-53 k |x|) is far below float resolution.
+// frac(k x) in [-1/2, 1/2) for the FP64 form and the float pairs: k x = p + e
+// exactly (FMA), one rounding.  (The FP32 form uses dir_f32_power below.)
 template <typename T> __device__ __forceinline__ double dir_phase(double k, double x);
-template <> __device__ __forceinline__ double dir_phase<float>(double k, double x) {
-    const double p = k * x;
-    return p - rint(p);
-}
 template <> __device__ __forceinline__ double dir_phase<double>(double k, double x) {
     const double p = k * x;
     const double e = fma(k, x, -p);

@@ -640,7 +640,6 @@ cudaError_t run_laplace(Plan& p, const void* c, void* f, cudaStream_t st) {
     P.y1 = p.y1;
     P.xi1 = p.xi1;
     for (int m = 1; m < p.levels && m < (int)p.bands.size(); ++m) P.ell[m] = p.bands[m].ell;
-    const uint8_t* tband = p.d_tband;
     if (p.prec == FL_FP64)
         return lap_run<double>(p.N, p.M, p.d_ts, p.d_s, p.d_tbs, p.d_sband, P, p.d_cheb,
                                (const double*)c, (double*)f, (unsigned char*)p.d_lap, p.lap_blocks,
