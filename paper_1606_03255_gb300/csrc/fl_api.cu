@@ -443,7 +443,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             p.grid_elems += (int64_t)d.nrhs * d.n;
             p.D_elems += (int64_t)d.nrhs * d.K;
             if (d.log2n <= kSmallMaxLog2) {
-                const int per = std::max(1, (int)((1 << kSmallMaxLog2) / d.n));
+                // 4096 points per CTA (256 threads x 16); n = 32 at 8 points per thread
+                const int per = std::max(1, (int)((d.log2n >= 6 ? 4096 : 2048) / d.n));
                 for (int s0 = 0; s0 < d.nrhs; s0 += per)
                     p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
             } else {
@@ -529,8 +530,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     }
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
-    if (p.Y_elems) {
-        FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
+    if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
+    if (p.Y_elems || !p.small_work.empty()) {   // stage twiddles of the passes and the small FFTs
         FL_CUDA(cudaMalloc(&p.d_tw, (size_t)(kTwEntries + (p.prec == FL_FP64_FF ? 8192 : 0)) * cs),
                 "cudaMalloc twiddles");
         FL_CUDA(build_twiddles(p, st), "fl_plan: twiddles");

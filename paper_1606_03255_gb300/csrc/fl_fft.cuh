@@ -608,6 +608,100 @@ cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands
     }
 }
 
+// ---------------------------------------------------------------------------
+// FFTs of the grids of at most 4096 points: one CTA of 256 threads per work
+// item (nfft FFTs of one band, nfft n <= 4096).  n >= 64: the compile-time
+// radix-16 transform above with 16 points per thread and the plan-time stage
+// twiddles; n = 32: the generic radix-8 transform of fl_common.cuh (8 points
+// per thread).  MODE 0: input generated from c and D (forward), written to the
+// band grid; MODE 1: the grid read and transformed in place.
+constexpr int kSmallThreads = 256;
+
+template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
+__device__ __forceinline__ void small_fft_ct(const SmallWork& wk, const BandDev& B,
+                                             const C_t<T>* __restrict__ c, const T* __restrict__ D,
+                                             C_t<T>* __restrict__ grid, const C_t<T>* __restrict__ tw,
+                                             C_t<T>* sm) {
+    using C = C_t<T>;
+    using SP = StagePlan<LOG2L>;
+    constexpr int L = 1 << LOG2L, NT = L / 16;
+    const int f = threadIdx.x / NT, t = threadIdx.x % NT;   // f < 4096 / L: own smem region
+    const bool active = f < wk.nfft;
+    const int s = wk.s0 + f;
+    C* g = grid + B.grid_off + (int64_t)s * L;
+    C v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+        const int e = t + r * (L / 16);
+        v[r] = !active ? C{(T)0, (T)0}
+                       : (MODE == 0 ? prep_value<T, DERIV>(e, B, s, c + B.c_off, D) : g[e]);
+    }
+    C* buf = sm + f * L;
+    const C* twr = tw + tw_region(LOG2L, 4);
+    fft_first_from_regs<LOG2L, SIGN, T>(v, buf, t);
+    fft_middle<LOG2L, 4, SIGN, T>(buf, t, twr);
+    fft_last_to_regs<LOG2L, 4, SIGN, T>(buf, t, v, twr);
+    if (!active) return;
+    constexpr int R = SP::LAST_R, NS = SP::LAST_NS, J = 16 / R;
+#pragma unroll
+    for (int jb = 0; jb < J; ++jb) {
+        const int jj = t + jb * (L / 16);
+#pragma unroll
+        for (int r = 0; r < R; ++r) g[jj + r * NS] = v[jb * R + r];
+    }
+}
+
+template <typename T, int SIGN, int MODE, bool DERIV>
+__global__ void __launch_bounds__(kSmallThreads) k_small_fft(const SmallWork* __restrict__ work,
+                                                             const BandDev* __restrict__ bands,
+                                                             const C_t<T>* __restrict__ c,
+                                                             const T* __restrict__ D,
+                                                             C_t<T>* __restrict__ grid,
+                                                             const C_t<T>* __restrict__ tw) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const SmallWork wk = work[blockIdx.x];
+    const BandDev B = bands[wk.band];
+    switch (wk.log2n) {
+#define FL_SMALL(LG) \
+    case LG: small_fft_ct<T, SIGN, MODE, DERIV, LG>(wk, B, c, D, grid, tw, sm); return;
+        FL_SMALL(6) FL_SMALL(7) FL_SMALL(8) FL_SMALL(9) FL_SMALL(10) FL_SMALL(11) FL_SMALL(12)
+#undef FL_SMALL
+        default: break;
+    }
+    // n = 32 (at most 64 FFTs per item): radix 8 with per-stage twiddles
+    const int L = 1 << wk.log2n;
+    const int nthr = L >> 3;
+    const int f = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const bool active = f < wk.nfft;
+    const int s = wk.s0 + f;
+    C* buf = sm + (int64_t)f * padded_len(L);
+    C* g = grid + B.grid_off + (int64_t)s * L;
+    if (active) {
+        for (int e = t; e < L; e += nthr)
+            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c + B.c_off, D) : g[e];
+    }
+    __syncthreads();
+    fft_smem<SIGN, T>(buf, wk.log2n, t, active);
+    if (active)
+        for (int e = t; e < L; e += nthr) g[e] = buf[pad8(e)];
+}
+
+template <typename T, int SIGN, int MODE, bool DERIV>
+cudaError_t launch_small_fft(const SmallWork* work, int nwork, const BandDev* bands, const C_t<T>* c,
+                             const T* D, C_t<T>* grid, const C_t<T>* tw, cudaStream_t st) {
+    const size_t smem = (size_t)4096 * sizeof(C_t<T>);
+    auto k = k_small_fft<T, SIGN, MODE, DERIV>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<(unsigned)nwork, kSmallThreads, smem, st>>>(work, bands, c, D, grid, tw);
+    return cudaGetLastError();
+}
+
+#define FL_SMALL_SIG(T) const SmallWork*, int, const BandDev*, const C_t<T>*, const T*, C_t<T>*, \
+                        const C_t<T>*, cudaStream_t
+
 #define FL_P1_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, const T*, \
                      const C_t<T>*, C_t<T>*, const C_t<T>*, cudaStream_t
 #define FL_P2_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, C_t<T>*, \
@@ -618,10 +712,15 @@ cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands
     extern template cudaError_t launch_pass1<T, -1, 1, false>(FL_P1_SIG(T)); \
     extern template cudaError_t launch_pass1<T, 1, 1, false>(FL_P1_SIG(T));  \
     extern template cudaError_t launch_pass2<T, 1>(FL_P2_SIG(T));          \
-    extern template cudaError_t launch_pass2<T, -1>(FL_P2_SIG(T));
+    extern template cudaError_t launch_pass2<T, -1>(FL_P2_SIG(T));          \
+    extern template cudaError_t launch_small_fft<T, 1, 0, false>(FL_SMALL_SIG(T)); \
+    extern template cudaError_t launch_small_fft<T, 1, 0, true>(FL_SMALL_SIG(T));  \
+    extern template cudaError_t launch_small_fft<T, -1, 1, false>(FL_SMALL_SIG(T)); \
+    extern template cudaError_t launch_small_fft<T, 1, 1, false>(FL_SMALL_SIG(T));
 // float pairs: the forward transform only
 #define FL_FFT_EXTERN_FF                                                      \
     extern template cudaError_t launch_pass1<ff, 1, 0, false>(FL_P1_SIG(ff)); \
-    extern template cudaError_t launch_pass2<ff, 1>(FL_P2_SIG(ff));
+    extern template cudaError_t launch_pass2<ff, 1>(FL_P2_SIG(ff));           \
+    extern template cudaError_t launch_small_fft<ff, 1, 0, false>(FL_SMALL_SIG(ff));
 
 }  // namespace fl

@@ -238,37 +238,6 @@ cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st) {
     return p.prec == FL_FP64 ? build_tables_t<double>(p, in, st) : build_tables_t<float>(p, in, st);
 }
 
-// One CTA per work item: nfft FFTs of one band (one per right-hand side).
-// MODE 0: input generated from c and D (forward), written to the band grid.
-// MODE 1: input read from the band grid and transformed in place (adjoint).
-template <typename T, int SIGN, int MODE, bool DERIV>
-__global__ void __launch_bounds__(512) k_small_fft(const SmallWork* __restrict__ work,
-                                                   const BandDev* __restrict__ bands,
-                                                   const C_t<T>* __restrict__ c,
-                                                   const T* __restrict__ D,
-                                                   C_t<T>* __restrict__ grid) {
-    using C = C_t<T>;
-    extern __shared__ unsigned char smem_raw[];
-    C* sm = reinterpret_cast<C*>(smem_raw);
-    const SmallWork wk = work[blockIdx.x];
-    const BandDev B = bands[wk.band];
-    const int L = 1 << wk.log2n;
-    const int nthr = L >> 3;
-    const int f = threadIdx.x / nthr, t = threadIdx.x % nthr;
-    const bool active = f < wk.nfft;
-    const int s = wk.s0 + f;
-    C* buf = sm + (int64_t)f * padded_len(L);
-    C* g = grid + B.grid_off + (int64_t)s * L;
-    if (active) {
-        for (int e = t; e < L; e += nthr)
-            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c + B.c_off, D) : g[e];
-    }
-    __syncthreads();
-    fft_smem<SIGN, T>(buf, wk.log2n, t, active);
-    if (active)
-        for (int e = t; e < L; e += nthr) g[e] = buf[pad8(e)];
-}
-
 // ---------------------------------------------------------------------------
 // Window and barycentric weights of one node.
 
@@ -696,10 +665,6 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
     C* grid = (C*)p.d_grid;
     cudaError_t e = cudaSuccess;
     if (!p.small_work.empty()) {
-        const size_t smem = (size_t)padded_len(1 << kSmallMaxLog2) * sizeof(C);
-        auto kern = k_small_fft<T, SIGN, MODE, DERIV>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
         double bytes = 0;
         for (const SmallWork& w : p.small_work) {
             const BandDev& B = p.bands[w.band].dev;
@@ -708,11 +673,12 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         }
         int slot;
         timer_begin(p, "small_fft", bytes, st, &slot);
-        kern<<<(unsigned)p.small_work.size(), 512, smem, st>>>(p.d_small, p.d_bands, (const C*)c,
-                                                             (const T*)p.d_D, grid);
+        e = launch_small_fft<T, SIGN, MODE, DERIV>(p.d_small, (int)p.small_work.size(), p.d_bands,
+                                                   (const C*)c, (const T*)p.d_D, grid,
+                                                   (const C*)p.d_tw, st);
         timer_end(p, slot, st);
         ++p.launches;
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (e != cudaSuccess) return e;
     }
     for (const PassGroup& g : p.pass_groups) {
         int l1, l2;
