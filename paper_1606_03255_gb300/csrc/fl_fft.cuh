@@ -688,14 +688,57 @@ __global__ void __launch_bounds__(kSmallThreads) k_small_fft(const SmallWork* __
         for (int e = t; e < L; e += nthr) g[e] = buf[pad8(e)];
 }
 
+// The same work items with 512 threads, 8 points per thread and the generic
+// radix-8 transform for every n: shorter per-thread chains, the faster choice
+// when there are too few items to fill the GPU.
+template <typename T, int SIGN, int MODE, bool DERIV>
+__global__ void __launch_bounds__(2 * kSmallThreads) k_small_fft_r8(const SmallWork* __restrict__ work,
+                                                                    const BandDev* __restrict__ bands,
+                                                                    const C_t<T>* __restrict__ c,
+                                                                    const T* __restrict__ D,
+                                                                    C_t<T>* __restrict__ grid) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const SmallWork wk = work[blockIdx.x];
+    const BandDev B = bands[wk.band];
+    const int L = 1 << wk.log2n;
+    const int nthr = L >> 3;
+    const int f = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const bool active = f < wk.nfft;
+    const int s = wk.s0 + f;
+    C* buf = sm + (int64_t)f * padded_len(L);
+    C* g = grid + B.grid_off + (int64_t)s * L;
+    if (active) {
+        for (int e = t; e < L; e += nthr)
+            buf[pad8(e)] = (MODE == 0) ? prep_value<T, DERIV>(e, B, s, c + B.c_off, D) : g[e];
+    }
+    __syncthreads();
+    fft_smem<SIGN, T>(buf, wk.log2n, t, active);
+    if (active)
+        for (int e = t; e < L; e += nthr) g[e] = buf[pad8(e)];
+}
+
 template <typename T, int SIGN, int MODE, bool DERIV>
 cudaError_t launch_small_fft(const SmallWork* work, int nwork, const BandDev* bands, const C_t<T>* c,
                              const T* D, C_t<T>* grid, const C_t<T>* tw, cudaStream_t st) {
-    const size_t smem = (size_t)4096 * sizeof(C_t<T>);
-    auto k = k_small_fft<T, SIGN, MODE, DERIV>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)nwork, kSmallThreads, smem, st>>>(work, bands, c, D, grid, tw);
+    if (nwork >= 2 * sms) {   // enough items: the radix-16 kernel
+        const size_t smem = (size_t)4096 * sizeof(C_t<T>);
+        auto k = k_small_fft<T, SIGN, MODE, DERIV>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)nwork, kSmallThreads, smem, st>>>(work, bands, c, D, grid, tw);
+    } else {
+        const size_t smem = (size_t)padded_len(4096) * sizeof(C_t<T>);
+        auto k = k_small_fft_r8<T, SIGN, MODE, DERIV>;
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k<<<(unsigned)nwork, 2 * kSmallThreads, smem, st>>>(work, bands, c, D, grid);
+    }
     return cudaGetLastError();
 }
 
