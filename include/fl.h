@@ -55,8 +55,9 @@ typedef enum {
  * coefficient weights and twiddles are rounded once from FP64 to pairs, and
  * the window gather, barycentric recombination and direct bands also run in
  * pairs (exponential, sincospi, square root and division written for pairs),
- * with the phases n x mod 1 reduced exactly in double.  Forward only: fl_plan, fl_plan_ex and fl_plan_batched accept
- * it, with fl_execute, fl_execute_host and fl_execute_batched; fl_adjoint,
+ * with the phases n x mod 1 reduced exactly in double.  Forward only:
+ * fl_plan, fl_plan_ex and fl_plan_batched accept it, with fl_execute,
+ * fl_execute_host and fl_execute_batched; fl_adjoint,
  * fl_transposed, fl_execute_deriv and fl_grad_w return FL_EUNSUPPORTED on
  * such a plan, and the other plan calls reject it with FL_EINVAL. */
 typedef enum { FL_FP32 = 0, FL_FP64 = 1, FL_FP64_FF = 2 } fl_precision;
@@ -250,7 +251,10 @@ fl_status fl_transposed(fl_plan_t p, const void *g_dev, void *out_dev, void *str
  * Fourier factor computed by an NNFFT (nonequispaced in time and frequency,
  * as the proof of Theorem 4.3 notes): the exponents are spread onto a
  * frequency grid of spacing 1/2 with a Kaiser-Bessel window, followed by an
- * NFFT at x/2 and the division by the window's transform.
+ * NFFT at x/2 and the division by the window's transform.  Each band is
+ * centred on its exponent range; its NFFT keeps the half-size bandwidth when
+ * only the window margin (at most m_w + 3 frequencies) overflows it and the
+ * Kaiser-Bessel aliasing term grows by at most 1 %.
  *   xi_dev    : device, N float64 exponents >= 1 (any order; read at planning).
  *   nodes_dev : device, M x {Re w, Im w}; |Re w| <= 1/2 (principal branch of
  *               z^xi, the negative real axis Re w = +-1/2 as a one-sided
@@ -261,9 +265,8 @@ fl_status fl_transposed(fl_plan_t p, const void *g_dev, void *out_dev, void *str
  * (every step transposed: spreading at x/2 with the conjugate epilogue, FFTs
  * of sign -, the outer deconvolution and the frequency window gathered back to
  * each exponent); the derivative and gradient calls return FL_EUNSUPPORTED.
- * Returns FL_EINVAL for
- * an exponent below 1 or not finite and for a node outside the range above,
- * FL_EUNSUPPORTED for N > 2^22.
+ * Returns FL_EINVAL for an exponent below 1 or not finite and for a node
+ * outside the range above, FL_EUNSUPPORTED for N > 2^22.
  */
 fl_status fl_plan_xi(fl_plan_t *out, int64_t N, const double *xi_dev, int64_t M,
                      const double *nodes_dev, int q, double eps, fl_precision prec, void *stream);
