@@ -88,6 +88,19 @@ template <typename T> __device__ __forceinline__ C_t<T> expipi(T x) {
     return {c, s};
 }
 
+// k x mod 1 in [-1/2, 1/2) (turns).  The product is split exactly by one FMA
+// (k x = p + e, Dekker's two-product), so the reduced phase is correct to
+// about 2^-53 however large k x is; a rounded k x alone would lose
+// ulp(k x) / 2, 2^-31 turns at k x = 2^22.
+__device__ __forceinline__ double frac_turns(double k, double x) {
+    const double p = k * x;
+    const double e = fma(k, x, -p);
+    double f = (p - rint(p)) + e;
+    if (f >= 0.5) f -= 1.0;
+    if (f < -0.5) f += 1.0;
+    return f;
+}
+
 // Stage twiddle tables.  In a length-L transform whose first stage has radix
 // 2^FIRST, every later stage (radix R, span NS = 2^d) multiplies input r of job
 // jj by w^(r k), w = exp(SIGN 2 pi i / (NS R)), k = jj mod NS.  Those values are

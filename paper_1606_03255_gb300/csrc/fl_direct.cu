@@ -20,13 +20,7 @@ constexpr double kTwoPiDir = 6.283185307179586476925286766559;
 // exactly (FMA), one rounding.  (The FP32 form uses dir_f32_power below.)
 template <typename T> __device__ __forceinline__ double dir_phase(double k, double x);
 template <> __device__ __forceinline__ double dir_phase<double>(double k, double x) {
-    const double p = k * x;
-    const double e = fma(k, x, -p);
-    double f = p - rint(p);
-    f += e;
-    if (f >= 0.5) f -= 1.0;
-    if (f < -0.5) f += 1.0;
-    return f;
+    return frac_turns(k, x);
 }
 
 template <typename T> __device__ __forceinline__ T dir_exp(T a);

@@ -385,9 +385,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     C val;
     if constexpr (XI) {
         // exp(2 pi i xc x) / Phi(x/2), x = Re w in [-1/2, 1/2]
-        double ph = B.xc * wv.x;
-        ph -= floor(ph);
-        if (ph >= 0.5) ph -= 1.0;
+        const double ph = frac_turns(B.xc, wv.x);
         const T v = (T)(kTwoPiD * 0.5 * wv.x);
         const T arg = kb_b * kb_b - v * v;
         const T r = (T)MW * sqrt(arg > (T)0 ? arg : (T)0);
@@ -398,8 +396,8 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
         const C e = expipi<T>((T)(2.0 * ph));
         val = cmul(acc, C{e.x * iphi, e.y * iphi});
     } else {
-        // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
-        double ph = (double)(B.Nm >> 1) * x;
+        // centring shift exp(2 pi i (N_m/2) x)
+        double ph = (double)(B.Nm >> 1) * x;   // N_m a power of two: exact
         ph -= floor(ph);
         if (ph >= 0.5) ph -= 1.0;
         val = cmul(acc, expipi<T>((T)(2.0 * ph)));
@@ -435,9 +433,7 @@ __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* _
     const double t0 = (double)B.n * x;
     const T fr = (T)(t0 - floor(t0));
     if constexpr (XI) {
-        double ph = B.xc * wv.x;
-        ph -= floor(ph);
-        if (ph >= 0.5) ph -= 1.0;
+        const double ph = frac_turns(B.xc, wv.x);
         const T v = (T)(kTwoPiD * 0.5 * wv.x);
         const T arg = kb_b * kb_b - v * v;
         const T rr = (T)MW * sqrt(arg > (T)0 ? arg : (T)0);
@@ -447,7 +443,7 @@ __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* _
         const C rv = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
         sp_rv[i] = cscale(rv, (T)1 / ((T)kPi * i0));
     } else {
-        double ph = (double)(B.Nm >> 1) * x;
+        double ph = (double)(B.Nm >> 1) * x;   // N_m a power of two: exact
         ph -= floor(ph);
         if (ph >= 0.5) ph -= 1.0;
         sp_rv[i] = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
@@ -844,7 +840,8 @@ __global__ void __launch_bounds__(256) k_gather_ff(int64_t M, const double2* __r
         }
         acc = hit ? ahit : ffc{ff_div(num.x, den), ff_div(num.y, den)};
     }
-    // centring shift exp(2 pi i (N_m/2) x), the product reduced exactly in double
+    // centring shift exp(2 pi i (N_m/2) x); N_m is a power of two, so the
+    // product is exact in double
     double ph = (double)(B.Nm >> 1) * x;
     ph -= floor(ph);
     if (ph >= 0.5) ph -= 1.0;

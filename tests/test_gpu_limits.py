@@ -4,7 +4,9 @@
   grids, 2^24 points, i.e. both four-step passes at 2^12; FP32 at eps = 1e-6
   and the float-pair FP64-accuracy form at eps = 1e-12, on clustered nodes;
 * fl_plan_xi at N = 2^22 (its limit), FP32;
-* Laplace at N = M = 2^22.
+* Laplace at N = M = 2^22;
+* real exponents in FP64 at N = 2^22 with data coherent at one node, where
+  the band-centre phase must keep the full double precision.
 Every result is checked against the oracle on a seeded sample of outputs
 (the oracle sums all N terms for each sampled node), with the same bounds as
 the smaller parity tests.
@@ -73,3 +75,45 @@ def test_laplace_large(fl):
     idx = np.random.default_rng(9).choice(M, 256, replace=False)
     ref = oracle.laplace_direct(c, t, s[idx])
     assert np.max(np.abs(ref - f[idx])) <= 1e-10 * np.sum(np.abs(c))
+
+
+def _phase_sensitive_node(xi, rng):
+    """Re w in [1/4, 1/2) whose product with the last band's centre xc
+    (2 xc = floor(min xi + max xi)) loses nearly half an ulp when rounded to
+    double, so an epilogue exp(2 pi i xc x) formed from the rounded product is
+    off by almost 2 pi ulp / 2 radians."""
+    from fractions import Fraction
+    xc = 0.5 * np.floor(xi.min() + xi.max())
+    best, dbest = 0.0, 0.0
+    for x in rng.uniform(0.25, 0.5, 400):
+        d = abs(float(Fraction(xc) * Fraction(float(x)) - Fraction(xc * float(x))))
+        if d > dbest:
+            best, dbest = float(x), d
+    return best, dbest
+
+
+def test_xi_fp64_epilogue_phase_at_max_N(fl):
+    # Real exponents in FP64 at N = 2^22, eps = 1e-10, with the data made
+    # coherent at one node on |z| = 1: c_k = exp(-2 pi i xi_k x0) gives
+    # |f(z0)| = ||c||_1 and, transposed, h = e_0 gives |g_k| = ||h||_1, so the
+    # centre phase xc x0 (xc ~ 2^21) must carry the full double precision.
+    N, M, eps = 1 << 22, 64, 1e-10
+    rng = np.random.default_rng(51)
+    xi = rng.uniform(1.0, N, N)
+    x0, dphase = _phase_sensitive_node(xi, rng)
+    assert 2 * np.pi * dphase >= 3 * eps        # a rounded product would fail
+    w = np.zeros((M, 2))
+    w[:, 0] = rng.uniform(-0.5, 0.5, M)
+    w[0, 0] = x0
+    c = np.exp(-2j * np.pi * np.mod(xi * x0, 1.0))
+    h = np.zeros(M, dtype=np.complex128)
+    h[0] = 1.0
+    p = fl.XiPlan(torch.from_numpy(xi).cuda(), torch.from_numpy(w).cuda(), eps, precision="fp64")
+    f = p.execute(torch.from_numpy(c).cuda()).cpu().numpy()
+    g = p.transposed(torch.from_numpy(h).cuda()).cpu().numpy()
+    p.close()
+    ref = oracle.xi_direct(c, xi, w)
+    assert abs(ref[0]) >= 0.999 * N
+    assert oracle.error_E(ref, f, c) <= eps
+    gref = oracle.xi_transposed(h, xi, w)
+    assert np.max(np.abs(gref - g)) <= eps * np.sum(np.abs(h))
