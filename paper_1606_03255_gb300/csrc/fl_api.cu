@@ -42,7 +42,7 @@ Plan::~Plan() {
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
                     d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm, d_ts, d_tbs,
-                    d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi};
+                    d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi, d_xcs, d_xsb};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -183,6 +183,23 @@ static fl_status select_bands_xi(Plan& p, Instance& in, int inst_index) {
         p.bands.push_back(bh);
     }
     return FL_OK;
+}
+
+// Right-hand sides per chunk of the real-exponent spreading, QC in {4, 8, 12,
+// 16}: each chunk passes over a grid frequency's exponents once, at about
+// 10 + QC/4 + 2 QC instructions per exponent (index, window and coefficient;
+// the 16-byte weight loads; the complex multiply-adds), the last chunk padded
+// with zero weights.  The QC of least total cost for q.
+static int xi_chunk(int q) {
+    int best = 4, best_cost = 1 << 30;
+    for (int qc : {16, 12, 8, 4}) {
+        const int cost = (q + qc - 1) / qc * (10 + qc / 4 + 2 * qc);
+        if (cost < best_cost) {
+            best = qc;
+            best_cost = cost;
+        }
+    }
+    return best;
 }
 
 // The dyadic partition of one transform (Definition 3.2 with xi_1 = N - 1):
@@ -374,6 +391,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
 
     // routes, offsets and work lists
     p.grid_elems = p.D_elems = p.Y_elems = 0;
+    p.xqc = p.xi_mode ? xi_chunk(p.q) : 0;
     p.small_work.clear();
     p.large_bands.clear();
     p.direct_work.clear();
@@ -439,9 +457,17 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             }
             if (d.route != 1) continue;
             d.grid_off = p.grid_elems;
-            d.D_off = p.D_elems;
             p.grid_elems += (int64_t)d.nrhs * d.n;
-            p.D_elems += (int64_t)d.nrhs * d.K;
+            if (p.xi_mode) {
+                // exponent-major rows of whole spreading chunks, 16-byte aligned
+                d.dld = d.nrhs == 1 ? 1 : (d.nrhs + p.xqc - 1) / p.xqc * p.xqc;
+                p.D_elems = (p.D_elems + 3) & ~(int64_t)3;
+                d.D_off = p.D_elems;
+                p.D_elems += (int64_t)d.dld * d.K;
+            } else {
+                d.D_off = p.D_elems;
+                p.D_elems += (int64_t)d.nrhs * d.K;
+            }
             if (d.log2n <= kSmallMaxLog2) {
                 // 4096 points per CTA (256 threads x 16); n = 32 at 8 points per thread
                 const int per = std::max(1, (int)((d.log2n >= 6 ? 4096 : 2048) / d.n));
@@ -530,6 +556,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     }
     if (p.grid_elems) FL_CUDA(cudaMalloc(&p.d_grid, p.grid_elems * cs), "cudaMalloc grids");
     if (p.D_elems) FL_CUDA(cudaMalloc(&p.d_D, p.D_elems * rs), "cudaMalloc weights");
+    if (p.D_elems && p.xi_mode)   // the padding of the exponent-major rows
+        FL_CUDA(cudaMemsetAsync(p.d_D, 0, p.D_elems * rs, st), "clear weights");
     if (p.Y_elems) FL_CUDA(cudaMalloc(&p.d_Y, p.Y_elems * cs), "cudaMalloc intermediate");
     if (p.Y_elems || !p.small_work.empty()) {   // stage twiddles of the passes and the small FFTs
         FL_CUDA(cudaMalloc(&p.d_tw, (size_t)(kTwEntries + (p.prec == FL_FP64_FF ? 8192 : 0)) * cs),

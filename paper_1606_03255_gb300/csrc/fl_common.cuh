@@ -150,7 +150,8 @@ struct BandDev {
     int nrhs;          // right-hand sides: q for interpolated bands, 1 for Y_M
     int log2n;
     int route;         // 0 empty, 1 NFFT, 2 direct sum
-    int pad;
+    int dld;           // 0: weights D[s K + k]; > 0 (real exponents): one row of
+                       // dld >= nrhs entries per exponent, D[k dld + s], zero-padded
     double yc, yh;     // band Y_m = [yc - yh, yc + yh] (paper's y), for barycentric weights
     double yh_inv;     // 1 / yh (a power of two times 1/y_1)
     int64_t node_off;  // first node of the band in sorted order

@@ -138,6 +138,11 @@ struct Plan {
     int32_t* d_xstart = nullptr;   // first sorted position with floor(2 xi) >= B, B = 0 .. 2 xi_1 + 1
     void* d_xwin = nullptr;        // frequency-window taps per sorted position (2 m_w, T)
     void* d_xiphi = nullptr;       // 1 / Phi of every NNFFT grid size (T)
+    void* d_xcs = nullptr;         // coefficients in sorted exponent order (complex T, per execute)
+    int2* d_xsb = nullptr;         // NNFFT bands of the spreading launch: {first block, band}
+    int xsb_n = 0;                 // entries of d_xsb
+    int64_t xsb_blocks = 0;        // blocks of the spreading launch
+    int xqc = 0;                   // right-hand sides per spreading chunk (4, 8, 12 or 16)
     int64_t xiphi_elems = 0;
     double direct_bias = 1.0;
     double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)

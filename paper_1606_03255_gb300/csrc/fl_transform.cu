@@ -81,8 +81,9 @@ __global__ void k_coupling(double y1, double xi1, int m, int ellm, int Lm, int q
 // transform Phi(nu) = pi I_0(m_w sqrt(b^2 - (2 pi nu)^2)) (window in grid units).
 // one_sided: W_{k,s} = exp(-y_s k) at the band's Chebyshev points y_s (the
 // interpolation in y alone, first term of the proof of Theorem 3.1).
-// xis (real exponents): frequency k is the sorted exponent xis[k] and no 1/Phi
-// is folded in (the NNFFT deconvolves per grid frequency instead).
+// xis (real exponents): frequency k is the sorted exponent xis[k], no 1/Phi
+// is folded in (the NNFFT deconvolves per grid frequency instead), and the
+// table is exponent-major, D[k dld + s] (B.dld > 0).
 template <typename T>
 __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int levels,
                           const double* __restrict__ cheb, const double* __restrict__ Kt,
@@ -97,25 +98,27 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
         const double arg = kb_b * kb_b - (kTwoPiD * nu) * (kTwoPiD * nu);
         inv_phi = 1.0 / (kPi * cyl_bessel_i0((double)mw * sqrt(fmax(arg, 0.0))));
     }
-    T* Dk = D + B.D_off;
+    // entry s of frequency k at Dk[s * ds]
+    T* Dk = D + B.D_off + (B.dld ? k * B.dld : k);
+    const int64_t ds = B.dld ? 1 : B.K;
     if (B.nrhs == 1) {
-        Dk[k] = (T)inv_phi;
+        Dk[0] = (T)inv_phi;
         return;
     }
     if (one_sided) {
         for (int s = 0; s < q; ++s) {
             const double ys = B.yc + B.yh * cheb[s];
-            Dk[(int64_t)s * B.K + k] = (T)(exp(-ys * xk) * inv_phi);
+            Dk[s * ds] = (T)(exp(-ys * xk) * inv_phi);
         }
         return;
     }
     const int l = band_of_freq(xk, xi1, levels);
     if (l > Lm) {   // region (iv): kernel ~ 1
-        for (int s = 0; s < q; ++s) Dk[(int64_t)s * B.K + k] = (T)inv_phi;
+        for (int s = 0; s < q; ++s) Dk[s * ds] = (T)inv_phi;
         return;
     }
     if (l < ellm) {   // region (ii): kernel ~ 0 (not reached: k < K)
-        for (int s = 0; s < q; ++s) Dk[(int64_t)s * B.K + k] = (T)0;
+        for (int s = 0; s < q; ++s) Dk[s * ds] = (T)0;
         return;
     }
     // Lagrange weights L_r^{Omega_l}(k), barycentric form, tau in [-1, 1]
@@ -135,7 +138,7 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
     for (int s = 0; s < q; ++s) {
         double W = 0.0;
         for (int r = 0; r < q; ++r) W += Kb[s * q + r] * Lr[r];
-        Dk[(int64_t)s * B.K + k] = (T)(W * inv_phi);
+        Dk[s * ds] = (T)(W * inv_phi);
     }
 }
 

@@ -53,20 +53,71 @@ __global__ void k_xi_iphi(int64_t count, double n, int m, double b, T* __restric
     iphi[g] = (T)(1.0 / (3.141592653589793238462643383279 * cyl_bessel_i0((double)m * sqrt(fmax(b * b - nu * nu, 0.0)))));
 }
 
-// G of one band: thread per grid index i (all right-hand sides), written to the
-// band grid (zeros outside |g| <= gh).
+// The coefficients in sorted exponent order, once per execute: cs[k] = c[xperm[k]].
 template <typename T>
-__global__ void k_xi_spread(BandDev B, const C_t<T>* __restrict__ c, const int32_t* __restrict__ xperm,
-                            const int32_t* __restrict__ xbk, const int32_t* __restrict__ xstart,
-                            int64_t nstart, const T* __restrict__ win, const T* __restrict__ D,
-                            const T* __restrict__ iphi, int m, C_t<T>* __restrict__ grid) {
+__global__ void k_xi_sortc(int64_t N, const int32_t* __restrict__ xperm, const C_t<T>* __restrict__ c,
+                           C_t<T>* __restrict__ cs) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) cs[k] = c[xperm[k]];
+}
+
+// QC consecutive weights of one exponent-major row, 16-byte loads (the row
+// start is 16-byte aligned: D_off, dld and s0 are multiples of 4).
+template <typename T, int QC>
+__device__ __forceinline__ void load_row(const T* __restrict__ p, T* d) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int v = 0; v < QC / 4; ++v) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(p) + v);
+            d[4 * v] = x.x;
+            d[4 * v + 1] = x.y;
+            d[4 * v + 2] = x.z;
+            d[4 * v + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int v = 0; v < QC / 2; ++v) {
+            const double2 x = __ldg(reinterpret_cast<const double2*>(p) + v);
+            d[2 * v] = x.x;
+            d[2 * v + 1] = x.y;
+        }
+    }
+}
+
+// G of every NNFFT band in one launch: the blocks first_j .. first_{j+1} - 1
+// belong to band xsb[j].y (found by binary search over the nsb entries), one
+// thread per grid index i of the band, all right-hand sides, written to the
+// band grid (zeros outside |g| <= gh):
+//   G_s[g] = (1 / Phi(g / n)) sum_k cs_k D[k][s] phi(g - 2 (xi_k - xc)),
+// over the sorted exponents whose taps cover g (floor(2 xi_k) in [G - m, G + m),
+// G = g + 2 xc, tap t = G + m - 1 - floor(2 xi_k)), in ascending k.  The
+// right-hand sides go in chunks of QC: per exponent one window value, one
+// coefficient and QC/4 (float) or QC/2 (double) 16-byte weight loads feed
+// 2 QC multiply-adds.
+template <typename T, int QC>
+__global__ void __launch_bounds__(256)
+    k_xi_spread(const int2* __restrict__ xsb, int nsb, const BandDev* __restrict__ bands,
+                const C_t<T>* __restrict__ cs, const int32_t* __restrict__ xbk,
+                const int32_t* __restrict__ xstart, int64_t nstart, const T* __restrict__ win,
+                const T* __restrict__ D, const T* __restrict__ iphi, int m, C_t<T>* __restrict__ grid) {
     using C = C_t<T>;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= B.n) return;
-    const int64_t g = i < (B.n >> 1) ? i : i - B.n;
+    const int blk = (int)blockIdx.x;
+    int lo = 0, hi = nsb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (xsb[mid].x <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    const int2 sb = xsb[lo];
+    const BandDev& B = bands[sb.y];
+    const int64_t n = B.n;
+    const int64_t i = (int64_t)(blk - sb.x) * 256 + threadIdx.x;
+    if (i >= n) return;
+    const int nrhs = B.nrhs;
+    const int64_t g = i < (n >> 1) ? i : i - n;
     C* out = grid + B.grid_off + i;
     if (g > B.gh || g < -B.gh) {
-        for (int s = 0; s < B.nrhs; ++s) out[(int64_t)s * B.n] = C{(T)0, (T)0};
+        for (int s = 0; s < nrhs; ++s) out[(int64_t)s * n] = C{(T)0, (T)0};
         return;
     }
     const int64_t G = g + (int64_t)(2.0 * B.xc);
@@ -75,37 +126,46 @@ __global__ void k_xi_spread(BandDev B, const C_t<T>* __restrict__ c, const int32
     const int64_t k0 = xstart[b0];
     const int64_t k1 = std::min<int64_t>(xstart[b1], B.K);
     const T inv = iphi[B.phi_off + (g < 0 ? -g : g)];
-    // right-hand sides in chunks of SC: each exponent's tap, window value and
-    // coefficient are loaded once per chunk and used for all SC weights
-    constexpr int SC = 8;
-    const T* D0 = D + B.D_off;
-    for (int s0 = 0; s0 < B.nrhs; s0 += SC) {
-        C acc[SC];
-#pragma unroll
-        for (int u = 0; u < SC; ++u) acc[u] = C{(T)0, (T)0};
+    const T* Db = D + B.D_off;
+    if (nrhs == 1) {   // one right-hand side, dld = 1
+        C acc = {(T)0, (T)0};
         for (int64_t k = k0; k < k1; ++k) {
             const int t = (int)(G + m - 1 - xbk[k]);      // in [0, 2m)
-            const T wk = win[k * 2 * m + t];
-            const C v = c[xperm[k]];
-            const C wv = C{wk * v.x, wk * v.y};
+            const T wd = win[k * 2 * m + t] * Db[k];
+            const C v = cs[k];
+            acc.x += wd * v.x;
+            acc.y += wd * v.y;
+        }
+        out[0] = C{acc.x * inv, acc.y * inv};
+        return;
+    }
+    const int64_t ld = B.dld;   // a multiple of QC
+    for (int s0 = 0; s0 < nrhs; s0 += QC) {
+        C acc[QC];
 #pragma unroll
-            for (int u = 0; u < SC; ++u) {
-                if (s0 + u < B.nrhs) {
-                    const T d = D0[(int64_t)(s0 + u) * B.K + k];
-                    acc[u].x += d * wv.x;
-                    acc[u].y += d * wv.y;
-                }
+        for (int u = 0; u < QC; ++u) acc[u] = C{(T)0, (T)0};
+        for (int64_t k = k0; k < k1; ++k) {
+            const int t = (int)(G + m - 1 - xbk[k]);
+            const T wk = win[k * 2 * m + t];
+            const C v = cs[k];
+            const C wv = C{wk * v.x, wk * v.y};
+            T d[QC];
+            load_row<T, QC>(Db + k * ld + s0, d);
+#pragma unroll
+            for (int u = 0; u < QC; ++u) {
+                acc[u].x += d[u] * wv.x;
+                acc[u].y += d[u] * wv.y;
             }
         }
 #pragma unroll
-        for (int u = 0; u < SC; ++u)
-            if (s0 + u < B.nrhs) out[(int64_t)(s0 + u) * B.n] = C{acc[u].x * inv, acc[u].y * inv};
+        for (int u = 0; u < QC; ++u)
+            if (s0 + u < nrhs) out[(int64_t)(s0 + u) * n] = C{acc[u].x * inv, acc[u].y * inv};
     }
 }
 
 // Adjoint of the frequency spreading and of the outer deconvolution, summed
 // over the bands (the transpose of k_xi_spread): thread per sorted exponent k,
-//   out[xperm[k]] = sum_bands sum_s D[s][k] sum_t phi_t,k / Phi(g_t / n) b_s[g_t mod n],
+//   out[xperm[k]] = sum_bands sum_s D[k][s] sum_t phi_t,k / Phi(g_t / n) b_s[g_t mod n],
 // g_t = floor(2 xi_k) - m + 1 + t - 2 xc, t < 2m, |g_t| <= gh: exactly the
 // (exponent, grid frequency) pairs the forward spreading couples.
 template <typename T>
@@ -129,10 +189,10 @@ __global__ void k_xi_combine(int64_t N, int levels, const BandDev* __restrict__ 
             if (g > B.gh || g < -B.gh) continue;
             const T wt = wk[t] * iphi[B.phi_off + (g < 0 ? -g : g)];
             const C* gs = grid + B.grid_off + (g & (B.n - 1));
-            const T* Dk = D + B.D_off + k;
+            const T* Dk = D + B.D_off + k * B.dld;
             C a = {(T)0, (T)0};
             for (int s = 0; s < B.nrhs; ++s) {
-                const T d = Dk[(int64_t)s * B.K];
+                const T d = Dk[s];
                 const C v = gs[(int64_t)s * B.n];
                 a.x += d * v.x;
                 a.y += d * v.y;
@@ -196,6 +256,26 @@ static cudaError_t xi_tables_t(Plan& p, cudaStream_t st) {
                                                                             (T*)p.d_xiphi + off[lg]);
         }
     }
+    // the spreading launch: its NNFFT bands in order with their first blocks
+    std::vector<int2> sb;
+    int64_t blocks = 0;
+    for (size_t b = 0; b < p.bands.size(); ++b) {
+        const BandDev& d = p.bands[b].dev;
+        if (d.route != 1 || d.n == 0) continue;
+        sb.push_back(make_int2((int)blocks, (int)b));
+        blocks += (d.n + 255) / 256;
+    }
+    if (blocks > INT32_MAX) return cudaErrorInvalidValue;
+    p.xsb_n = (int)sb.size();
+    p.xsb_blocks = blocks;
+    if (!sb.empty()) {
+        e = cudaMalloc((void**)&p.d_xsb, sb.size() * sizeof(int2));
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p.d_xsb, sb.data(), sb.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaMalloc(&p.d_xcs, std::max<int64_t>(N, 1) * sizeof(C_t<T>));
+    if (e != cudaSuccess) return e;
     // the band table with phi_off
     std::vector<BandDev> hb(p.bands.size());
     for (size_t b = 0; b < p.bands.size(); ++b) hb[b] = p.bands[b].dev;
@@ -210,17 +290,40 @@ cudaError_t build_xi_tables(Plan& p, cudaStream_t st) {
     return p.prec == FL_FP64 ? xi_tables_t<double>(p, st) : xi_tables_t<float>(p, st);
 }
 
+template <typename T, int QC>
+static void xi_spread_launch(Plan& p, int64_t nstart, cudaStream_t st) {
+    k_xi_spread<T, QC><<<(unsigned)p.xsb_blocks, 256, 0, st>>>(
+        p.d_xsb, p.xsb_n, p.d_bands, (const C_t<T>*)p.d_xcs, p.d_xbk, p.d_xstart, nstart,
+        (const T*)p.d_xwin, (const T*)p.d_D, (const T*)p.d_xiphi, p.mw, (C_t<T>*)p.d_grid);
+}
+
 template <typename T>
 static cudaError_t xi_spread_t(Plan& p, const void* c, cudaStream_t st) {
+    using C = C_t<T>;
     const int64_t nstart = p.N > 0 ? (int64_t)floor(2.0 * p.h_xis.back()) + 2 : 1;
-    int slot;
-    timer_begin(p, "xi_spread", 0.0, st, &slot);
+    // algorithmic bytes: the sorted coefficients (gather + write + read), each
+    // exponent's taps and weight row once per band, the grids written
+    double bytes = (double)p.N * (3 * sizeof(C) + 4);
     for (const BandHost& bh : p.bands) {
         const BandDev& d = bh.dev;
         if (d.route != 1 || d.n == 0) continue;
-        k_xi_spread<T><<<(unsigned)((d.n + 255) / 256), 256, 0, st>>>(
-            d, (const C_t<T>*)c, p.d_xperm, p.d_xbk, p.d_xstart, nstart, (const T*)p.d_xwin,
-            (const T*)p.d_D, (const T*)p.d_xiphi, p.mw, (C_t<T>*)p.d_grid);
+        bytes += (double)d.K * (4 + 2 * p.mw * sizeof(T) + d.dld * sizeof(T)) +
+                 (double)d.nrhs * d.n * sizeof(C);
+    }
+    int slot;
+    timer_begin(p, "xi_spread", bytes, st, &slot);
+    if (p.N > 0) {
+        k_xi_sortc<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, p.d_xperm, (const C*)c,
+                                                                      (C*)p.d_xcs);
+        ++p.launches;
+    }
+    if (p.xsb_blocks > 0) {
+        switch (p.xqc) {
+        case 4: xi_spread_launch<T, 4>(p, nstart, st); break;
+        case 8: xi_spread_launch<T, 8>(p, nstart, st); break;
+        case 12: xi_spread_launch<T, 12>(p, nstart, st); break;
+        default: xi_spread_launch<T, 16>(p, nstart, st); break;
+        }
         ++p.launches;
     }
     timer_end(p, slot, st);
