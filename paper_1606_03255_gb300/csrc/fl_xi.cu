@@ -167,13 +167,15 @@ __global__ void __launch_bounds__(256)
 // over the bands (the transpose of k_xi_spread): thread per sorted exponent k,
 //   out[xperm[k]] = sum_bands sum_s D[k][s] sum_t phi_t,k / Phi(g_t / n) b_s[g_t mod n],
 // g_t = floor(2 xi_k) - m + 1 + t - 2 xc, t < 2m, |g_t| <= gh: exactly the
-// (exponent, grid frequency) pairs the forward spreading couples.
-template <typename T>
-__global__ void k_xi_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
-                             const int32_t* __restrict__ xperm, const int32_t* __restrict__ xbk,
-                             const T* __restrict__ win, const T* __restrict__ D,
-                             const T* __restrict__ iphi, int m, const C_t<T>* __restrict__ grid,
-                             C_t<T>* __restrict__ out) {
+// (exponent, grid frequency) pairs the forward spreading couples.  The
+// exponent's weight row is read in chunks of QC by 16-byte loads, once per
+// band and chunk, and kept in registers over the 2m taps.
+template <typename T, int QC>
+__global__ void __launch_bounds__(256)
+    k_xi_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
+                 const int32_t* __restrict__ xperm, const int32_t* __restrict__ xbk,
+                 const T* __restrict__ win, const T* __restrict__ D, const T* __restrict__ iphi,
+                 int m, const C_t<T>* __restrict__ grid, C_t<T>* __restrict__ out) {
     using C = C_t<T>;
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
@@ -184,21 +186,39 @@ __global__ void k_xi_combine(int64_t N, int levels, const BandDev* __restrict__ 
         const BandDev B = bands[b];
         if (B.route != 1 || B.n == 0 || k >= B.K) continue;
         const int64_t c2 = (int64_t)(2.0 * B.xc);
-        for (int t = 0; t < 2 * m; ++t) {
-            const int64_t g = bk - m + 1 + t - c2;
-            if (g > B.gh || g < -B.gh) continue;
-            const T wt = wk[t] * iphi[B.phi_off + (g < 0 ? -g : g)];
-            const C* gs = grid + B.grid_off + (g & (B.n - 1));
-            const T* Dk = D + B.D_off + k * B.dld;
-            C a = {(T)0, (T)0};
-            for (int s = 0; s < B.nrhs; ++s) {
-                const T d = Dk[s];
-                const C v = gs[(int64_t)s * B.n];
-                a.x += d * v.x;
-                a.y += d * v.y;
+        const T* Dk = D + B.D_off + k * B.dld;
+        if (B.nrhs == 1) {   // dld = 1
+            const T d = Dk[0];
+            for (int t = 0; t < 2 * m; ++t) {
+                const int64_t g = bk - m + 1 + t - c2;
+                if (g > B.gh || g < -B.gh) continue;
+                const T wt = wk[t] * iphi[B.phi_off + (g < 0 ? -g : g)] * d;
+                const C v = grid[B.grid_off + (g & (B.n - 1))];
+                acc.x += wt * v.x;
+                acc.y += wt * v.y;
             }
-            acc.x += wt * a.x;
-            acc.y += wt * a.y;
+            continue;
+        }
+        for (int s0 = 0; s0 < B.nrhs; s0 += QC) {   // dld is a multiple of QC
+            T d[QC];
+            load_row<T, QC>(Dk + s0, d);
+            for (int t = 0; t < 2 * m; ++t) {
+                const int64_t g = bk - m + 1 + t - c2;
+                if (g > B.gh || g < -B.gh) continue;
+                const T wt = wk[t] * iphi[B.phi_off + (g < 0 ? -g : g)];
+                const C* gs = grid + B.grid_off + (g & (B.n - 1)) + (int64_t)s0 * B.n;
+                C a = {(T)0, (T)0};
+#pragma unroll
+                for (int u = 0; u < QC; ++u) {
+                    if (s0 + u < B.nrhs) {
+                        const C v = gs[(int64_t)u * B.n];
+                        a.x += d[u] * v.x;
+                        a.y += d[u] * v.y;
+                    }
+                }
+                acc.x += wt * a.x;
+                acc.y += wt * a.y;
+            }
         }
     }
     out[xperm[k]] = acc;
@@ -334,13 +354,23 @@ cudaError_t launch_xi_spread(Plan& p, const void* c, cudaStream_t st) {
     return p.prec == FL_FP64 ? xi_spread_t<double>(p, c, st) : xi_spread_t<float>(p, c, st);
 }
 
+template <typename T, int QC>
+static void xi_combine_launch(Plan& p, void* out, cudaStream_t st) {
+    k_xi_combine<T, QC><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
+        p.N, p.levels, p.d_bands, p.d_xperm, p.d_xbk, (const T*)p.d_xwin, (const T*)p.d_D,
+        (const T*)p.d_xiphi, p.mw, (const C_t<T>*)p.d_grid, (C_t<T>*)out);
+}
+
 template <typename T>
 static cudaError_t xi_combine_t(Plan& p, void* out, cudaStream_t st) {
     int slot;
     timer_begin(p, "combine", 0.0, st, &slot);
-    k_xi_combine<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
-        p.N, p.levels, p.d_bands, p.d_xperm, p.d_xbk, (const T*)p.d_xwin, (const T*)p.d_D,
-        (const T*)p.d_xiphi, p.mw, (const C_t<T>*)p.d_grid, (C_t<T>*)out);
+    switch (p.xqc) {
+    case 4: xi_combine_launch<T, 4>(p, out, st); break;
+    case 8: xi_combine_launch<T, 8>(p, out, st); break;
+    case 12: xi_combine_launch<T, 12>(p, out, st); break;
+    default: xi_combine_launch<T, 16>(p, out, st); break;
+    }
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
