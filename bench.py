@@ -58,7 +58,13 @@ def parse():
     ap.add_argument("--sample", type=int, default=2048, help="oracle sample size (nodes)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the secondary workloads (Laplace, batched, gradients, N=1024)")
-    return ap.parse_args()
+    ap.add_argument("--workloads", default=",".join(SECONDARY),
+                    help="comma-separated secondary workloads to run: " + ", ".join(SECONDARY))
+    args = ap.parse_args()
+    bad = set(args.workloads.split(",")) - set(SECONDARY)
+    if bad:
+        ap.error("unknown workloads: " + ", ".join(sorted(bad)))
+    return args
 
 
 def dist_env():
@@ -218,163 +224,175 @@ def _time_cuda(fn, reps, flush=None):
     return float(np.mean(ts))
 
 
-def secondary_workloads(dev, flush, rank):
-    """The other workloads of the method, each timed on its own (not the headline)."""
+SECONDARY = ("disk_1024", "laplace", "batched", "gradients", "real_exponents")
+
+
+def secondary_workloads(dev, flush, rank, names=SECONDARY):
+    """The other workloads of the method, each timed on its own (not the headline);
+    `names` selects among SECONDARY."""
     import torch
     from paper_1606_03255_gb300 import fl
     from paper_1606_03255_gb300.autograd import FourierLaplace
+
+    def want(name):
+        return name in names
     out = {}
-    # N = M = 1024, disk-uniform, FP64, eps = 1e-10 (latency-bound; CUDA-graph replay)
-    # (and the same in the float-pair FP64-accuracy form)
-    N = M = 1024
-    c = torch.from_numpy(W.coefficients(N, seed=rank)).to(dev)
-    w = torch.from_numpy(W.nodes_disk_uniform(M, seed=100 + rank)).to(dev)
     s = torch.cuda.Stream()
-    for prec in ("fp64", "fp64ff"):
-        p = fl.Plan(N, w, 1e-10, precision=prec, use_graph=True)
-        f = torch.empty(M, dtype=torch.complex128, device=dev)
+    if want("disk_1024"):
+        # N = M = 1024, disk-uniform, FP64, eps = 1e-10 (latency-bound; CUDA-graph replay)
+        # (and the same in the float-pair FP64-accuracy form)
+        N = M = 1024
+        c = torch.from_numpy(W.coefficients(N, seed=rank)).to(dev)
+        w = torch.from_numpy(W.nodes_disk_uniform(M, seed=100 + rank)).to(dev)
+        for prec in ("fp64", "fp64ff"):
+            p = fl.Plan(N, w, 1e-10, precision=prec, use_graph=True)
+            f = torch.empty(M, dtype=torch.complex128, device=dev)
+            with torch.cuda.stream(s):
+                for _ in range(5):
+                    p.execute(c, out=f)
+                s.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                for _ in range(200):
+                    p.execute(c, out=f)
+                b.record(s)
+            s.synchronize()
+            us = a.elapsed_time(b) * 1e3 / 200
+            out[f"disk_1024_{prec}_eps1e-10"] = {"us_per_call": us, "value": N * M / (us * 1e-6),
+                                                "unit": "evals/s", "graph": True}
+            p.close()
+    if want("laplace"):
+        # Laplace, N = M = 2^16, FP64 and FP32 forms, eps = 1e-6
+        N = M = 1 << 16
+        cl, t, sv = W.laplace_inputs(N, M, seed=rank)
+        for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
+            lp = fl.LaplacePlan(torch.from_numpy(t).to(dev), torch.from_numpy(sv).to(dev), 1e-6,
+                                precision=prec)
+            cc = torch.from_numpy(cl).to(dt).to(dev)
+            ff = torch.empty(M, dtype=dt, device=dev)
+            for _ in range(3):
+                lp.execute(cc, out=ff)
+            ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
+            out[f"laplace_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s"}
+            lp.close()
+        # generalised Algorithm 1 on the same inputs (t, s > 0): the K_1/2 Bessel kernel
+        tp, sp = np.where(t > 0, t, 0.5), np.where(sv > 0, sv, 1.0)
+        for prec, dt in (("fp64", torch.float64),):
+            lp = fl.LaplacePlan(torch.from_numpy(tp).to(dev), torch.from_numpy(sp).to(dev), 1e-6,
+                                precision=prec, kernel="bessel_half")
+            cc = torch.from_numpy(cl).to(dt).to(dev)
+            ff = torch.empty(M, dtype=dt, device=dev)
+            for _ in range(3):
+                lp.execute(cc, out=ff)
+            ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
+            inf = lp.info()
+            out[f"bessel_half_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s",
+                                               "q": inf["q"], "levels": inf["levels"]}
+            lp.close()
+    if want("batched"):
+        # batched: 512 transforms, N_i = floor(2^U), U ~ U[8,16], M_i = N_i, FP32, eps = 1e-6:
+        # one plan + CUDA graph vs 512 separate plans with plain launches
+        Ns = W.batched_degrees(512, seed=rank)
+        cs = np.concatenate([W.coefficients(int(n), seed=7 + i).astype(np.complex64)
+                             for i, n in enumerate(Ns)])
+        ws = [W.nodes_disk_uniform(int(n), seed=9000 + i) for i, n in enumerate(Ns)]
+        evals = float(np.sum(Ns.astype(np.float64) ** 2))
+        t0 = time.perf_counter()
+        bp = fl.BatchedPlan(Ns, Ns, torch.from_numpy(np.concatenate(ws)).to(dev), 1e-6, autotune=True)
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        cb = torch.from_numpy(cs).to(dev)
+        fb = torch.empty(int(Ns.sum()), dtype=torch.complex64, device=dev)
         with torch.cuda.stream(s):
-            for _ in range(5):
-                p.execute(c, out=f)
+            for _ in range(3):
+                bp.execute(cb, out=fb)
             s.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            for _ in range(200):
-                p.execute(c, out=f)
-            b.record(s)
-        s.synchronize()
-        us = a.elapsed_time(b) * 1e3 / 200
-        out[f"disk_1024_{prec}_eps1e-10"] = {"us_per_call": us, "value": N * M / (us * 1e-6),
-                                            "unit": "evals/s", "graph": True}
-        p.close()
-    # Laplace, N = M = 2^16, FP64 and FP32 forms, eps = 1e-6
-    N = M = 1 << 16
-    cl, t, sv = W.laplace_inputs(N, M, seed=rank)
-    for prec, dt in (("fp64", torch.float64), ("fp32", torch.float32)):
-        lp = fl.LaplacePlan(torch.from_numpy(t).to(dev), torch.from_numpy(sv).to(dev), 1e-6,
-                            precision=prec)
-        cc = torch.from_numpy(cl).to(dt).to(dev)
-        ff = torch.empty(M, dtype=dt, device=dev)
-        for _ in range(3):
-            lp.execute(cc, out=ff)
-        ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
-        out[f"laplace_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s"}
-        lp.close()
-    # generalised Algorithm 1 on the same inputs (t, s > 0): the K_1/2 Bessel kernel
-    tp, sp = np.where(t > 0, t, 0.5), np.where(sv > 0, sv, 1.0)
-    for prec, dt in (("fp64", torch.float64),):
-        lp = fl.LaplacePlan(torch.from_numpy(tp).to(dev), torch.from_numpy(sp).to(dev), 1e-6,
-                            precision=prec, kernel="bessel_half")
-        cc = torch.from_numpy(cl).to(dt).to(dev)
-        ff = torch.empty(M, dtype=dt, device=dev)
-        for _ in range(3):
-            lp.execute(cc, out=ff)
-        ms = _time_cuda(lambda: lp.execute(cc, out=ff), 20)
-        inf = lp.info()
-        out[f"bessel_half_2^16_{prec}"] = {"ms": ms, "value": N * M / (ms * 1e-3), "unit": "evals/s",
-                                           "q": inf["q"], "levels": inf["levels"]}
-        lp.close()
-    # batched: 512 transforms, N_i = floor(2^U), U ~ U[8,16], M_i = N_i, FP32, eps = 1e-6:
-    # one plan + CUDA graph vs 512 separate plans with plain launches
-    Ns = W.batched_degrees(512, seed=rank)
-    cs = np.concatenate([W.coefficients(int(n), seed=7 + i).astype(np.complex64)
-                         for i, n in enumerate(Ns)])
-    ws = [W.nodes_disk_uniform(int(n), seed=9000 + i) for i, n in enumerate(Ns)]
-    evals = float(np.sum(Ns.astype(np.float64) ** 2))
-    t0 = time.perf_counter()
-    bp = fl.BatchedPlan(Ns, Ns, torch.from_numpy(np.concatenate(ws)).to(dev), 1e-6, autotune=True)
-    torch.cuda.synchronize()
-    plan_s = time.perf_counter() - t0
-    cb = torch.from_numpy(cs).to(dev)
-    fb = torch.empty(int(Ns.sum()), dtype=torch.complex64, device=dev)
-    with torch.cuda.stream(s):
-        for _ in range(3):
-            bp.execute(cb, out=fb)
-        s.synchronize()
-        ms_b = []
-        for _ in range(10):
-            flush.zero_()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(s)
-            bp.execute(cb, out=fb)
-            b.record(s)
-            s.synchronize()
-            ms_b.append(a.elapsed_time(b))
-    ms_b = float(np.mean(ms_b))
-    info_b = bp.info()
-    bp.close()
-    plans = []
-    off = 0
-    for i, n in enumerate(Ns):
-        plans.append((fl.Plan(int(n), torch.from_numpy(ws[i]).to(dev), 1e-6), off, int(n)))
-        off += int(n)
+            ms_b = []
+            for _ in range(10):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(s)
+                bp.execute(cb, out=fb)
+                b.record(s)
+                s.synchronize()
+                ms_b.append(a.elapsed_time(b))
+        ms_b = float(np.mean(ms_b))
+        info_b = bp.info()
+        bp.close()
+        plans = []
+        off = 0
+        for i, n in enumerate(Ns):
+            plans.append((fl.Plan(int(n), torch.from_numpy(ws[i]).to(dev), 1e-6), off, int(n)))
+            off += int(n)
 
-    def run_separate():
-        for pl, o, n in plans:
-            pl.execute(cb[o:o + n], out=fb[o:o + n])
-    for _ in range(2):
-        run_separate()
-    ms_s = _time_cuda(run_separate, 5, flush)
-    for pl, _, _ in plans:
-        pl.close()
-    out["batched_512"] = {"ms": ms_b, "value": evals / (ms_b * 1e-3), "unit": "evals/s",
-                          "separate_plans_ms": ms_s,
-                          "separate_plans_value": evals / (ms_s * 1e-3),
-                          "speedup_vs_separate": ms_s / ms_b, "plan_s": plan_s,
-                          "sum_N_i": int(Ns.sum()), "sum_NiMi": evals,
-                          "bands_fft": info_b["n_bands_fft"], "bands_direct": info_b["n_bands_direct"],
-                          "autotuned_direct_bias": info_b["direct_bias"],
-                          "separate_plans": "512 fl_plan + fl_execute, plain launches, default routes"}
-    # gradients: N = M = 2^18, disk-uniform, FP32 (eps 1e-7), loss sum |f - g|^2
-    N = M = 1 << 18
-    c = torch.from_numpy(W.coefficients(N, seed=rank)).to(torch.complex64).to(dev).requires_grad_(True)
-    w = torch.from_numpy(W.nodes_disk_uniform(M, seed=200 + rank)).to(dev).requires_grad_(True)
-    g = torch.from_numpy(W.targets(M, seed=300 + rank)).to(torch.complex64).to(dev)
-    op = FourierLaplace(N, eps=1e-7, precision="fp32")
-    op.plan_for(w)
+        def run_separate():
+            for pl, o, n in plans:
+                pl.execute(cb[o:o + n], out=fb[o:o + n])
+        for _ in range(2):
+            run_separate()
+        ms_s = _time_cuda(run_separate, 5, flush)
+        for pl, _, _ in plans:
+            pl.close()
+        out["batched_512"] = {"ms": ms_b, "value": evals / (ms_b * 1e-3), "unit": "evals/s",
+                              "separate_plans_ms": ms_s,
+                              "separate_plans_value": evals / (ms_s * 1e-3),
+                              "speedup_vs_separate": ms_s / ms_b, "plan_s": plan_s,
+                              "sum_N_i": int(Ns.sum()), "sum_NiMi": evals,
+                              "bands_fft": info_b["n_bands_fft"], "bands_direct": info_b["n_bands_direct"],
+                              "autotuned_direct_bias": info_b["direct_bias"],
+                              "separate_plans": "512 fl_plan + fl_execute, plain launches, default routes"}
+    if want("gradients"):
+        # gradients: N = M = 2^18, disk-uniform, FP32 (eps 1e-7), loss sum |f - g|^2
+        N = M = 1 << 18
+        c = torch.from_numpy(W.coefficients(N, seed=rank)).to(torch.complex64).to(dev).requires_grad_(True)
+        w = torch.from_numpy(W.nodes_disk_uniform(M, seed=200 + rank)).to(dev).requires_grad_(True)
+        g = torch.from_numpy(W.targets(M, seed=300 + rank)).to(torch.complex64).to(dev)
+        op = FourierLaplace(N, eps=1e-7, precision="fp32")
+        op.plan_for(w)
 
-    def fwd_bwd():
-        c.grad = None
-        w.grad = None
-        loss = torch.sum(torch.abs(op(c, w) - g) ** 2)
-        loss.backward()
-    for _ in range(3):
-        fwd_bwd()
-    ms = _time_cuda(fwd_bwd, 10, flush)
-    fwd = _time_cuda(lambda: op(c.detach(), w.detach()), 10, flush)
-    out["gradients_2^18_fp32"] = {"ms_fwd_bwd": ms, "ms_fwd": fwd, "unit": "ms",
-                                  "note": "forward + adjoint (grad c) + k-weighted transform (grad w)"}
-    # real exponents: N = M = 2^18, xi_k ~ U[1, N], nodes as the headline
-    # workload shifted to Re w in [-1/2, 1/2), FP32, eps = 1e-6
-    N = M = 1 << 18
-    rng = np.random.default_rng(500 + rank)
-    xi = torch.from_numpy(rng.uniform(1.0, N, N)).to(dev)
-    wx = W.nodes_circle_clustered(M, seed=600 + rank).copy()
-    wx[:, 0] -= 0.5
-    cx = torch.from_numpy(W.coefficients(N, seed=700 + rank)).to(torch.complex64).to(dev)
-    px = fl.XiPlan(xi, torch.from_numpy(wx).to(dev), 1e-6, precision="fp32")
-    fx = torch.empty(M, dtype=torch.complex64, device=dev)
-    for _ in range(3):
-        px.execute(cx, out=fx)
-    msx = _time_cuda(lambda: px.execute(cx, out=fx), 10, flush)
-    gx = fx.clone()                       # node values to transpose back
-    tx = torch.empty(N, dtype=torch.complex64, device=dev)
-    for _ in range(3):
-        px.transposed(gx, out=tx)
-    mst = _time_cuda(lambda: px.transposed(gx, out=tx), 10, flush)
-    out["real_exponents_2^18_fp32"] = {"ms": msx, "value": N * M / (msx * 1e-3), "unit": "evals/s",
-                                       "q": px.info()["q"], "m_w": px.info()["m_w"],
-                                       "ms_transposed": mst}
-    px.close()
-    N = M = 1 << 18
-    # adjoint and transposed evaluation (C^T g, integer exponents) on the same plan
-    r = g.detach()
-    adj = _time_cuda(lambda: op._plan.adjoint(r), 10, flush)
-    tr = _time_cuda(lambda: op._plan.transposed(r), 10, flush)
-    out["adjoint_transposed_2^18_fp32"] = {"ms_adjoint": adj, "ms_transposed": tr,
-                                           "value_transposed": N * M / (tr * 1e-3), "unit": "ms"}
+        def fwd_bwd():
+            c.grad = None
+            w.grad = None
+            loss = torch.sum(torch.abs(op(c, w) - g) ** 2)
+            loss.backward()
+        for _ in range(3):
+            fwd_bwd()
+        ms = _time_cuda(fwd_bwd, 10, flush)
+        fwd = _time_cuda(lambda: op(c.detach(), w.detach()), 10, flush)
+        out["gradients_2^18_fp32"] = {"ms_fwd_bwd": ms, "ms_fwd": fwd, "unit": "ms",
+                                      "note": "forward + adjoint (grad c) + k-weighted transform (grad w)"}
+        N = M = 1 << 18
+        # adjoint and transposed evaluation (C^T g, integer exponents) on the same plan
+        r = g.detach()
+        adj = _time_cuda(lambda: op._plan.adjoint(r), 10, flush)
+        tr = _time_cuda(lambda: op._plan.transposed(r), 10, flush)
+        out["adjoint_transposed_2^18_fp32"] = {"ms_adjoint": adj, "ms_transposed": tr,
+                                               "value_transposed": N * M / (tr * 1e-3), "unit": "ms"}
+    if want("real_exponents"):
+        # real exponents: N = M = 2^18, xi_k ~ U[1, N], nodes as the headline
+        # workload shifted to Re w in [-1/2, 1/2), FP32, eps = 1e-6
+        N = M = 1 << 18
+        rng = np.random.default_rng(500 + rank)
+        xi = torch.from_numpy(rng.uniform(1.0, N, N)).to(dev)
+        wx = W.nodes_circle_clustered(M, seed=600 + rank).copy()
+        wx[:, 0] -= 0.5
+        cx = torch.from_numpy(W.coefficients(N, seed=700 + rank)).to(torch.complex64).to(dev)
+        px = fl.XiPlan(xi, torch.from_numpy(wx).to(dev), 1e-6, precision="fp32")
+        fx = torch.empty(M, dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            px.execute(cx, out=fx)
+        msx = _time_cuda(lambda: px.execute(cx, out=fx), 10, flush)
+        gx = fx.clone()                       # node values to transpose back
+        tx = torch.empty(N, dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            px.transposed(gx, out=tx)
+        mst = _time_cuda(lambda: px.transposed(gx, out=tx), 10, flush)
+        out["real_exponents_2^18_fp32"] = {"ms": msx, "value": N * M / (msx * 1e-3), "unit": "evals/s",
+                                           "q": px.info()["q"], "m_w": px.info()["m_w"],
+                                           "ms_transposed": mst}
+        px.close()
     return out
 
 
@@ -565,7 +583,7 @@ def run_ours(args):
 
     configs = None
     if not args.no_configs:
-        configs = secondary_workloads(dev, flush, rank)
+        configs = secondary_workloads(dev, flush, rank, tuple(args.workloads.split(",")))
 
     # cpu_baseline leg: the oracle on a seeded sample; the same sample gives E
     cpu = None
