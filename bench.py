@@ -42,7 +42,12 @@ N_DEFAULT = 1 << 20
 EPS32 = 1e-6
 EPS64 = 1e-12
 METRIC = "Fourier–Laplace evals/s (N·M/time) at N=M=2^20, FP32 vs FP64 form at stated E"
-WORKLOAD = ("N=M=2^20 Fourier-Laplace transform: c complex64 N(0,1); nodes half on |z|=1, "
+
+
+def workload(N: int) -> str:
+    """The headline workload's description at N = M (2^20 by default)."""
+    size = f"2^{N.bit_length() - 1}" if N > 0 and N & (N - 1) == 0 else str(N)
+    return (f"N=M={size} Fourier-Laplace transform: c complex64 N(0,1); nodes half on |z|=1, "
             "half with 1-|z|=10^(-6U); eps=1e-6 FP32 form (FP64 phase reduction)")
 
 
@@ -423,7 +428,7 @@ def run_reference(args):
         "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "M": N, "per_step_sample_nodes": S,
+        "config": {"workload": workload(N), "N": N, "M": N, "per_step_sample_nodes": S,
                    "note": "CPU oracle: term-by-term FP64 direct sum, all host cores"},
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": cores, "kind": "oracle",
                          "sample": f"{S} seeded nodes x N={N} terms per step"},
@@ -611,7 +616,7 @@ def run_ours(args):
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "N": N, "M": M, "eps": EPS32, "q": info["q"],
+        "config": {"workload": workload(N), "N": N, "M": M, "eps": EPS32, "q": info["q"],
                    "levels": info["levels"], "m_w": info["m_w"], "sigma": info["sigma"],
                    "bands_fft": info["n_bands_fft"],
                    "l2": "flushed between steps (256 MiB write); working set > L2",
