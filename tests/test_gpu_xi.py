@@ -85,14 +85,17 @@ def test_xi_integer_exponents_match_integer_transform(fl):
     assert np.max(np.abs(f - z * fi)) <= 2 * eps * np.sum(np.abs(c))
 
 
-def test_xi_matches_structured(fl):
+@pytest.mark.parametrize("q", [0, 3, 7])
+def test_xi_matches_structured(fl, q):
+    # q = 0: the rank from eps (15, right-hand sides in one chunk of 16); q = 3
+    # and 7: chunks of 4 and 8 (the ranks of eps around 1e-1 and 1e-3)
     rng = np.random.default_rng(8)
     N, M, eps = 400, 250, 1e-8
     xi = rng.uniform(1.0, N, N)
     c = W.coefficients(N, seed=9)
     w = _nodes("clustered", M, seed=10)
-    f, info = _run(fl, c, xi, w, eps, "fp64")
-    fs, P = S.xflt_alg2_xi(c, xi, w, eps)
+    f, info = _run(fl, c, xi, w, eps, "fp64", q=q)
+    fs, P = S.xflt_alg2_xi(c, xi, w, eps, q=q or None)
     assert info["q"] == P.lap.q and info["levels"] == P.lap.M
     assert oracle.error_E(fs, f, c) <= eps / 3
 
