@@ -10,9 +10,11 @@ Two layers:
   in FP64 with compensated summation -- the forward sum of eq. (4.1) with
   xi_k = k, its adjoint, the real Laplace sum of eq. (3.2), and a long-double
   brute force for tiny N.
-* ``structured.py``: Algorithms 1 and 2 of the paper step by step in numpy, with
-  the exact nonequispaced DFT in place of the NFFT, for tiny N.  It isolates
-  the error of the hierarchical Laplace factorisation from that of the NFFT.
+* ``structured.py``: the matrices Algorithms 1 and 2 of the paper apply,
+  assembled block by block from Definition 3.2 and eq. (A.1) in numpy (the
+  Hadamard product A o K~ of Lemma 4.1 for Algorithm 2, with the Fourier
+  matrix A formed exactly in place of the NFFT), for tiny N.  It isolates the
+  error of the hierarchical Laplace factorisation from that of the NFFT.
 
 Index convention: the paper sums k = 1..N; this library sums k = 0..N-1, so
 xi_k = k and xi_1 (the largest frequency) is N - 1.

@@ -1,9 +1,19 @@
-"""Structured reference: Algorithms 1 and 2 of Kunis & Melzer step by step (numpy).
+"""Structured reference: the matrices that Algorithms 1 and 2 of Kunis & Melzer apply (numpy).
 
-TEST INFRASTRUCTURE ONLY (see the package docstring).  Tiny N only: every
-block is formed as a dense matrix and the nonequispaced Fourier matrix A is
-applied exactly (a dense NDFT), so what remains is the error of the
-hierarchical Laplace factorisation alone.
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Tiny N only.  Nothing
+here follows the listings of the paper: each function assembles, block by
+block, the dense matrix that the paper proves its algorithm applies and
+multiplies it with the coefficient vector.
+
+* Algorithm 1 applies K~ of eq. (A.1): for a node in Y_m and a frequency in
+  Omega_l the entry is 1 (l > L_m), the rank-q interpolant
+  L^{Y_m} K^{Y_m,Omega_l} (L^{Omega_l})^T of Definition 3.2 (l_m <= l <= L_m)
+  or 0 (l < l_m); rows of Y_M are all ones.
+* Algorithm 2 applies the Hadamard product A o K~ (Lemma 4.1, Lemma 4.2,
+  Theorem 4.3): A = (exp(2 pi i xi_k x_j)) the Fourier matrix, here formed
+  exactly (a dense NDFT), and K~ the matrix above for the kernel exp(-y xi)
+  with y = 2 pi Im w.  So what remains is the error of the hierarchical
+  Laplace factorisation alone.
 
 Readings of the paper taken here (each is restated where it is used):
 
@@ -140,80 +150,70 @@ def kernel_block(params: LaplaceParams, m: int, l: int) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
-# Algorithm 1: the fast discrete Laplace transform, and the dense K~ of (A.1).
+# Algorithm 1 (Section 3): the matrix K~ of eq. (A.1), assembled block by block.
 
-def laplace_alg1(c, t, s, eps: float, q: int | None = None):
-    """Algorithm 1 step by step: returns (f~, params).  Real or complex c."""
-    c = np.asarray(c)
-    t = np.asarray(t, dtype=np.float64)
-    s = np.asarray(s, dtype=np.float64)
-    xi1 = float(t.max()) if t.size else 0.0
-    y1 = float(s.max()) if s.size else 0.0
-    p = laplace_params(eps, y1, xi1, q)
-    f = np.zeros(s.shape, dtype=np.result_type(c.dtype, np.float64))
+def tilde_kernel(yv, xv, p: LaplaceParams, y1: float, xi1: float) -> np.ndarray:
+    """Dense K~ (len(yv), len(xv)) of eq. (A.1) for the kernel exp(-y xi).
+
+    Node y in Y_m (m < M) and frequency xi in Omega_l (Definition 3.2):
+      l > L_m:          1                                     (Lemma A.2 (iv))
+      l_m <= l <= L_m:  L^{Y_m}(y) K^{Y_m,Omega_l} L^{Omega_l}(xi)^T  (Lemma A.1)
+      l < l_m:          0                                     (Lemma A.2 (ii))
+    and every row of Y_M is 1 (Lemma A.2 (i)); with a single level (M = 1)
+    every entry is 1.  Each block is one product of the three factors.
+    """
+    yv = np.atleast_1d(np.asarray(yv, dtype=np.float64))
+    xv = np.atleast_1d(np.asarray(xv, dtype=np.float64))
+    K = np.zeros((yv.size, xv.size))
     if p.M == 1:
-        f[:] = c.sum()
-        return f, p
-    bt = band_of(t, xi1, p.M)
-    bs = band_of(s, y1, p.M)
-    # cumulative sums g_M .. g_1 over the frequency bands
-    g = {p.M: c[bt == p.M].sum()}
-    for m in range(p.M - 1, 0, -1):
-        g[m] = g[m + 1] + c[bt == m].sum()
-    f[bs == p.M] = g[1]
-    # moments v^{Omega_l} = (L^{Omega_l})^T c^{Omega_l}
-    v = {}
+        K[:] = 1.0
+        return K
+    by = band_of(yv, y1, p.M)
+    bx = band_of(xv, xi1, p.M)
+    K[by == p.M, :] = 1.0
+    cols = {l: np.nonzero(bx == l)[0] for l in range(1, p.M + 1)}
+    Lx = {}
     for l in range(1, p.M):
-        sel = bt == l
-        a, b = band_interval(xi1, l)
-        v[l] = lagrange_barycentric(t[sel], a, b, p.q).T @ c[sel]
+        if cols[l].size:
+            Lx[l] = lagrange_barycentric(xv[cols[l]], *band_interval(xi1, l), p.q)
     for m in range(1, p.M):
-        sel = bs == m
-        if not sel.any():
+        rows = np.nonzero(by == m)[0]
+        if not rows.size:
             continue
-        h = np.zeros(p.q, dtype=f.dtype)
-        for l in range(p.ell[m], p.L[m] + 1):
-            h = h + kernel_block(p, m, l) @ v[l]
-        a, b = band_interval(y1, m)
-        f[sel] = lagrange_barycentric(s[sel], a, b, p.q) @ h + g[p.L[m] + 1]
-    return f, p
+        Ly = lagrange_barycentric(yv[rows], *band_interval(y1, m), p.q)
+        for l in range(1, p.M + 1):
+            if not cols[l].size:
+                continue
+            if l > p.L[m]:
+                K[np.ix_(rows, cols[l])] = 1.0
+            elif l >= p.ell[m]:
+                K[np.ix_(rows, cols[l])] = Ly @ kernel_block(p, m, l) @ Lx[l].T
+    return K
 
 
 def laplace_tilde_matrix(t, s, eps: float, q: int | None = None,
                          y1: float | None = None, xi1: float | None = None):
-    """Dense K~ with entries defined by eq. (A.1): 1, interpolated, or 0 per block.
+    """Dense K~ of eq. (A.1) for nodes s and frequencies t; returns (K~, params).
 
-    Entry (j, k) approximates exp(-s_j t_k).  Rows with s_j in Y_M are all ones;
-    for s_j in Y_m: columns with t_k in Omega_l, l_m <= l <= L_m, hold
-    I_q^{Y_m x Omega_l} kappa; l > L_m hold 1; l < l_m hold 0.
+    Entry (j, k) approximates exp(-s_j t_k); y_1 = max s_j and xi_1 = max t_k
+    unless given (Algorithm 1 takes the largest node and frequency).
     """
     t = np.asarray(t, dtype=np.float64)
     s = np.asarray(s, dtype=np.float64)
-    xi1 = float(t.max()) if xi1 is None else float(xi1)
-    y1 = float(s.max()) if y1 is None else float(y1)
+    xi1 = (float(t.max()) if t.size else 0.0) if xi1 is None else float(xi1)
+    y1 = (float(s.max()) if s.size else 0.0) if y1 is None else float(y1)
     p = laplace_params(eps, y1, xi1, q)
-    K = np.zeros((s.size, t.size))
-    if p.M == 1:
-        K[:] = 1.0
-        return K, p
-    bt = band_of(t, xi1, p.M)
-    bs = band_of(s, y1, p.M)
-    for j in range(s.size):
-        m = bs[j]
-        if m == p.M:
-            K[j, :] = 1.0
-            continue
-        ya, yb = band_interval(y1, m)
-        Ly = lagrange_barycentric(s[j], ya, yb, p.q)[0]
-        for k in range(t.size):
-            l = bt[k]
-            if l > p.L[m]:
-                K[j, k] = 1.0
-            elif l >= p.ell[m]:
-                xa, xb = band_interval(xi1, l)
-                Lx = lagrange_barycentric(t[k], xa, xb, p.q)[0]
-                K[j, k] = Ly @ kernel_block(p, m, l) @ Lx
-    return K, p
+    return tilde_kernel(s, t, p, y1, xi1), p
+
+
+def laplace_alg1(c, t, s, eps: float, q: int | None = None):
+    """What Algorithm 1 returns, f~ = K~ c (eq. (A.1), Theorem A.3); (f~, params).
+
+    Real or complex c.  K~ is formed densely (tiny N only).
+    """
+    c = np.asarray(c)
+    K, p = laplace_tilde_matrix(t, s, eps, q)
+    return K @ c, p
 
 
 # --------------------------------------------------------------------------
@@ -255,63 +255,51 @@ def xflt_params(N: int, eps: float, q: int | None = None) -> XFLTParams:
     return XFLTParams(eps, eps_K, y1, xi1, laplace_params(eps_K, y1, xi1, q))
 
 
-def xflt_alg2(c, w, eps: float, q: int | None = None):
-    """Algorithm 2 step by step with exact NDFTs; returns (f~, params).
-
-    w: complex nodes in the closed upper half plane (z = exp(2 pi i w)) or an
-    (M, 2) array of (Re w, Im w).
-    """
-    c = np.asarray(c, dtype=np.complex128)
+def _split_nodes(w):
+    """(x, Im w) of complex nodes or of an (M, 2) array of (Re w, Im w)."""
     w = np.asarray(w)
     if not np.iscomplexobj(w):
         w = np.asarray(w, dtype=np.float64).reshape(-1, 2)
-        x, yim = w[:, 0], w[:, 1]
-    else:
-        x, yim = w.real, w.imag
-    N = c.size
+        return w[:, 0], w[:, 1]
+    return w.real, w.imag
+
+
+def fourier_matrix(k, x) -> np.ndarray:
+    """A = (exp(2 pi i k x_j)) for integer k, formed exactly (phases reduced mod 1)."""
+    return np.exp(2j * np.pi * _frac_phase(x, np.asarray(k, dtype=np.int64)))
+
+
+def xflt_matrix(N: int, w, eps: float, q: int | None = None):
+    """The matrix Algorithm 2 applies to c, with the NFFT replaced by A itself.
+
+    Row j: Z^0 node (y_j > ln(1/eps), |z_j| < eps) -> e_0 (f~ = c_0, the index
+    shift reading); else A_j o K~_j with A_jk = exp(2 pi i k x_j) and K~ of
+    eq. (A.1) for exp(-y xi) at y = 2 pi Im w_j, xi = k, y_1 = ln(1/eps),
+    xi_1 = N - 1, built at eps/3 (Lemma 4.1: C ~ A o K~, Theorem 4.3).
+    Returns (matrix, XFLTParams).
+    """
+    x, yim = _split_nodes(w)
     P = xflt_params(N, eps, q)
-    p = P.lap
     y = 2.0 * np.pi * yim                 # the paper's y: |z| = exp(-y)
-    f = np.zeros(x.shape, dtype=np.complex128)
     kall = np.arange(N)
-    if N == 1:
-        f[:] = c[0]
-        return f, P
-    z0 = y > P.y1                         # Z^0: |z| < eps  -> c_0 (index-shift reading)
-    f[z0] = c[0]
-    bx = np.where(z0, 0, band_of(y, P.y1, p.M))
-    bk = band_of(kall.astype(np.float64), P.xi1, p.M)
-    sel = bx == p.M                       # Z_M: kernel ~ 1 -> plain Fourier sum
-    if sel.any():
-        f[sel] = ndft(c, kall, x[sel])
-    # F^_l = diag(c^l) L^{Omega_l}
-    Fhat = {}
-    for l in range(1, p.M):
-        kl = kall[bk == l]
-        a, b = band_interval(P.xi1, l)
-        Fhat[l] = (c[kl][:, None] * lagrange_barycentric(kl.astype(np.float64), a, b, p.q), kl)
-    for m in range(1, p.M):
-        sel = bx == m
-        if not sel.any():
-            continue
-        xm = x[sel]
-        # region (iv): Omega = union of l > L_m, kernel ~ 1
-        kiv = kall[bk > p.L[m]]
-        fm = ndft(c[kiv], kiv, xm) if kiv.size else np.zeros(xm.size, complex)
-        # interpolated blocks l_m..L_m stacked: one NDFT with q right-hand sides
-        rows, ks = [], []
-        for l in range(p.ell[m], p.L[m] + 1):
-            Fl, kl = Fhat[l]
-            if kl.size:
-                rows.append(Fl @ kernel_block(p, m, l).T)
-                ks.append(kl)
-        if rows:
-            F = ndft(np.concatenate(rows, axis=0), np.concatenate(ks), xm)
-            ya, yb = band_interval(P.y1, m)
-            Ly = lagrange_barycentric(y[sel], ya, yb, p.q)
-            fm = fm + (Ly * F).sum(axis=1)
-        f[sel] = fm
-    return f, P
+    z0 = y > P.y1
+    C = np.zeros((x.size, N), dtype=np.complex128)
+    C[z0, 0] = 1.0
+    keep = ~z0
+    if keep.any():
+        C[keep] = fourier_matrix(kall, x[keep]) * tilde_kernel(y[keep], kall, P.lap, P.y1, P.xi1)
+    return C, P
+
+
+def xflt_alg2(c, w, eps: float, q: int | None = None):
+    """What Algorithm 2 returns with exact NDFTs, f~ = (A o K~) c; (f~, params).
+
+    w: complex nodes in the closed upper half plane (z = exp(2 pi i w)) or an
+    (M, 2) array of (Re w, Im w).  The matrix is formed densely (tiny N only).
+    """
+    c = np.asarray(c, dtype=np.complex128)
+    C, P = xflt_matrix(c.size, w, eps, q)
+    return C @ c, P
 
 
 # --------------------------------------------------------------------------
@@ -342,48 +330,41 @@ def rank_q_onesided(eps: float, qmax: int = 64) -> int:
 
 
 def xflt_alg2_onesided(c, w, eps: float, q: int | None = None):
-    """The one-sided variant step by step with exact NDFTs; returns (f~, q).
+    """The one-sided variant with exact NDFTs, f~ = (A o K~1) c; returns (f~, q).
 
-    Bands, Z^0 and the Y_M band as in xflt_alg2; band m < M keeps the
-    frequencies of Omega_l, l >= l_m, and weights frequency k of right-hand
-    side s by exp(-y_s k) at the Chebyshev points y_s of Y_m.
+    Z^0 rows and the Y_M band as in xflt_matrix.  For a node in Y_m, m < M,
+    K~1(y, k) = sum_s L_s^{Y_m}(y) exp(-y_s k) (y_s the Chebyshev points of Y_m)
+    for frequencies in Omega_l with l >= l_m, and 0 for l < l_m.
     """
     c = np.asarray(c, dtype=np.complex128)
-    w = np.asarray(w)
-    if not np.iscomplexobj(w):
-        w = np.asarray(w, dtype=np.float64).reshape(-1, 2)
-        x, yim = w[:, 0], w[:, 1]
-    else:
-        x, yim = w.real, w.imag
+    x, yim = _split_nodes(w)
     N = c.size
     P = xflt_params(N, eps)
     p = P.lap
     qq = rank_q_onesided(P.eps_K) if q is None else int(q)
     y = 2.0 * np.pi * yim
-    f = np.zeros(x.shape, dtype=np.complex128)
     kall = np.arange(N)
-    if N == 1:
-        f[:] = c[0]
-        return f, qq
     z0 = y > P.y1
-    f[z0] = c[0]
-    bx = np.where(z0, 0, band_of(y, P.y1, p.M))
-    bk = band_of(kall.astype(np.float64), P.xi1, p.M)
-    sel = bx == p.M
-    if sel.any():
-        f[sel] = ndft(c, kall, x[sel])
-    for m in range(1, p.M):
-        sel = bx == m
-        if not sel.any():
-            continue
-        ya, yb = band_interval(P.y1, m)
-        ys = interval_points(ya, yb, qq)
-        kk = kall[bk >= p.ell[m]]
-        W = np.exp(-np.outer(kk.astype(np.float64), ys))          # (K, q)
-        F = ndft(c[kk][:, None] * W, kk, x[sel])                   # (M_m, q)
-        Ly = lagrange_barycentric(y[sel], ya, yb, qq)
-        f[sel] = (Ly * F).sum(axis=1)
-    return f, qq
+    K1 = np.zeros((x.size, N))
+    if p.M == 1:
+        K1[:] = 1.0
+    else:
+        by = band_of(y, P.y1, p.M)
+        bk = band_of(kall.astype(np.float64), P.xi1, p.M)
+        K1[by == p.M, :] = 1.0
+        for m in range(1, p.M):
+            rows = np.nonzero((by == m) & ~z0)[0]
+            if not rows.size:
+                continue
+            ya, yb = band_interval(P.y1, m)
+            ys = interval_points(ya, yb, qq)
+            kk = np.nonzero(bk >= p.ell[m])[0]
+            Ly = lagrange_barycentric(y[rows], ya, yb, qq)
+            K1[np.ix_(rows, kk)] = Ly @ np.exp(-np.outer(ys, kk.astype(np.float64)))
+    Cm = fourier_matrix(kall, x) * K1
+    Cm[z0] = 0.0
+    Cm[z0, 0] = 1.0
+    return Cm @ c, qq
 
 
 # --------------------------------------------------------------------------
@@ -446,47 +427,47 @@ def general_params(kind: str, eps: float, y1: float, xi1: float, N: int,
     return GeneralParams(kind, eps, y1, xi1, int(q), M)
 
 
+def general_tilde_kernel(kind: str, p: GeneralParams, t, s) -> np.ndarray:
+    """Dense matrix of the generalised Algorithm 1 for kappa(s_j, t_k).
+
+    Rows of Y_M (the near field in y) and columns of Omega_M (the near field
+    in xi) hold kappa itself; every other block Y_m x Omega_l, 1 <= m, l <= M-1,
+    holds its interpolant L^{Y_m} kappa(y_s, xi_r) L^{Omega_l}(xi)^T.
+    """
+    t = np.asarray(t, dtype=np.float64)
+    s = np.asarray(s, dtype=np.float64)
+    K = smooth_kernel(kind, s, t) if t.size and s.size else np.zeros((s.size, t.size))
+    if p.M == 1 or t.size == 0:
+        return K
+    bt = band_of(t, p.xi1, p.M)
+    bs = band_of(s, p.y1, p.M)
+    cols = {l: np.nonzero(bt == l)[0] for l in range(1, p.M)}
+    Lx = {l: lagrange_barycentric(t[cols[l]], *band_interval(p.xi1, l), p.q)
+          for l in cols if cols[l].size}
+    for m in range(1, p.M):
+        rows = np.nonzero(bs == m)[0]
+        if not rows.size:
+            continue
+        ya, yb = band_interval(p.y1, m)
+        ys = interval_points(ya, yb, p.q)
+        Ly = lagrange_barycentric(s[rows], ya, yb, p.q)
+        for l in Lx:
+            xr = interval_points(*band_interval(p.xi1, l), p.q)
+            K[np.ix_(rows, cols[l])] = Ly @ smooth_kernel(kind, ys, xr) @ Lx[l].T
+    return K
+
+
 def laplace_alg1_general(kind: str, c, t, s, eps: float, q: int | None = None):
-    """The generalised Algorithm 1 step by step; returns (f~, params)."""
+    """What the generalised Algorithm 1 returns, f~ = K~ c; returns (f~, params)."""
     c = np.asarray(c)
     t = np.asarray(t, dtype=np.float64)
     s = np.asarray(s, dtype=np.float64)
     xi1 = float(t.max()) if t.size else 0.0
     y1 = float(s.max()) if s.size else 0.0
     p = general_params(kind, eps, y1, xi1, t.size, q)
-    f = np.zeros(s.shape, dtype=np.result_type(c.dtype, np.float64))
-    if p.M == 1 or t.size == 0:
-        if t.size:
-            f[:] = smooth_kernel(kind, s, t) @ c
-        return f, p
-    bt = band_of(t, xi1, p.M)
-    bs = band_of(s, y1, p.M)
-    # near field in y: every frequency directly
-    near_y = bs == p.M
-    if near_y.any():
-        f[near_y] = smooth_kernel(kind, s[near_y], t) @ c
-    # moments v^{Omega_l} = (L^{Omega_l})^T c^{Omega_l}, l = 1 .. M-1
-    v = {}
-    for l in range(1, p.M):
-        sel = bt == l
-        a, b = band_interval(xi1, l)
-        v[l] = lagrange_barycentric(t[sel], a, b, p.q).T @ c[sel]
-    near_t = bt == p.M
-    for m in range(1, p.M):
-        sel = bs == m
-        if not sel.any():
-            continue
-        ya, yb = band_interval(y1, m)
-        ys = interval_points(ya, yb, p.q)
-        h = np.zeros(p.q, dtype=f.dtype)
-        for l in range(1, p.M):
-            xa, xb = band_interval(xi1, l)
-            h = h + smooth_kernel(kind, ys, interval_points(xa, xb, p.q)) @ v[l]
-        fm = lagrange_barycentric(s[sel], ya, yb, p.q) @ h
-        if near_t.any():   # near field in xi: directly for every node
-            fm = fm + smooth_kernel(kind, s[sel], t[near_t]) @ c[near_t]
-        f[sel] = fm
-    return f, p
+    if t.size == 0:
+        return np.zeros(s.shape, dtype=np.result_type(c.dtype, np.float64)), p
+    return general_tilde_kernel(kind, p, t, s) @ c, p
 
 
 # --------------------------------------------------------------------------
@@ -508,46 +489,24 @@ def nndft(coef, xi, x) -> np.ndarray:
 
 
 def xflt_alg2_xi(c, xi, w, eps: float, q: int | None = None):
-    """Algorithm 2 for real exponents xi_k >= 1 with exact NNDFTs; returns (f~, params)."""
+    """Algorithm 2 for real exponents xi_k >= 1 with exact NNDFTs; returns (f~, params).
+
+    f~ = (A o K~) c with A_jk = exp(2 pi i xi_k x_j) and K~ of eq. (A.1) at
+    y = 2 pi Im w_j and the values xi_k (xi_1 = max xi_k); Z^0 rows are 0.
+    """
     c = np.asarray(c, dtype=np.complex128)
     xi = np.asarray(xi, dtype=np.float64)
     w = np.asarray(w, dtype=np.float64).reshape(-1, 2)
     x, yim = w[:, 0], w[:, 1]
-    N = c.size
     eps_K = eps / 3.0
     y1 = math.log(1.0 / eps)
     xi1 = float(xi.max())
     p = laplace_params(eps_K, y1, xi1, q)
     P = XFLTParams(eps, eps_K, y1, xi1, p)
     y = 2.0 * np.pi * yim
-    f = np.zeros(x.shape, dtype=np.complex128)
     z0 = y > y1
-    bx = np.where(z0, 0, band_of(y, y1, p.M))
-    bk = band_of(xi, xi1, p.M)
-    sel = bx == p.M
-    if sel.any():
-        f[sel] = nndft(c, xi, x[sel])
-    Fhat = {}
-    for l in range(1, p.M):
-        kl = np.nonzero(bk == l)[0]
-        a, b = band_interval(xi1, l)
-        Fhat[l] = (c[kl][:, None] * lagrange_barycentric(xi[kl], a, b, p.q), kl)
-    for m in range(1, p.M):
-        sel = bx == m
-        if not sel.any():
-            continue
-        xm = x[sel]
-        kiv = np.nonzero(bk > p.L[m])[0]
-        fm = nndft(c[kiv], xi[kiv], xm) if kiv.size else np.zeros(xm.size, complex)
-        rows, ks = [], []
-        for l in range(p.ell[m], p.L[m] + 1):
-            Fl, kl = Fhat[l]
-            if kl.size:
-                rows.append(Fl @ kernel_block(p, m, l).T)
-                ks.append(kl)
-        if rows:
-            F = nndft(np.concatenate(rows, axis=0), xi[np.concatenate(ks)], xm)
-            ya, yb = band_interval(y1, m)
-            fm = fm + (lagrange_barycentric(y[sel], ya, yb, p.q) * F).sum(axis=1)
-        f[sel] = fm
-    return f, P
+    Cm = np.zeros((x.size, xi.size), dtype=np.complex128)
+    keep = ~z0
+    if keep.any():
+        Cm[keep] = np.exp(2j * np.pi * np.outer(x[keep], xi)) * tilde_kernel(y[keep], xi, p, y1, xi1)
+    return Cm @ c, P

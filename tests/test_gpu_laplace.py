@@ -3,8 +3,8 @@
 Two references:
 * the plain oracle (direct FP64 sum): E <= eps (Theorem A.3), plus the float
   rounding term for the FP32 form;
-* the structured reference (Algorithm 1 step by step in numpy): the GPU
-  computes the same f~ of eq. (A.1), so the two agree to rounding.
+* the structured reference (K~ c with K~ of eq. (A.1) assembled block by
+  block in numpy): the GPU computes the same f~, so the two agree to rounding.
 """
 import numpy as np
 import pytest
@@ -196,7 +196,7 @@ def test_general_kernel_matches_structured(fl, kind):
     f, info = _run_kernel(fl, kind, c, t, s, eps, "fp64")
     fs, P = S.laplace_alg1_general(kind, c, t, s, eps)
     assert info["q"] == P.q
-    # the same f~ step by step: rounding only
+    # the same f~ = K~ c: rounding only
     absum = np.max(np.abs(S.smooth_kernel(kind, s, t)) @ np.abs(c))
     assert np.max(np.abs(f - fs)) <= 1e-12 * np.sum(np.abs(c)) + 64 * 2.0 ** -53 * absum
 

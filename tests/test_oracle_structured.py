@@ -6,8 +6,10 @@ What the paper fixes and is checked here:
   unity; L_r(y_s) = delta_rs; exact interpolation of polynomials of degree < q.
 * Lemma A.1: every interpolated kernel entry is within 2^(1-2q) of exp(-y xi);
   Lemma A.2 (i), (ii), (iv): the entries set to 1 or 0 are within eps.
-* Algorithm 1 returns exactly K~ c with K~ from eq. (A.1), and Theorem A.3:
-  ||f - f~||_inf <= eps ||c||_1 against the plain oracle.
+* K~ of eq. (A.1) reproduces exp(-y xi) exactly where both y and xi are
+  Chebyshev points of their bands (the Kronecker property through
+  Definition 3.2's blocks; a transposed coupling block fails it), and
+  Theorem A.3: ||f - f~||_inf <= eps ||c||_1 against the plain oracle.
 * Section 5 experiment shape: E(q) decays faster than 4^(-q).
 * Lemma 4.2 (Hadamard identity) on random dense matrices, to roundoff.
 * Theorem 4.3 / Algorithm 2 (exact NDFT): E <= eps against the plain oracle;
@@ -103,13 +105,35 @@ def test_kernel_entries_meet_lemma_bounds(eps):
 
 
 @pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-10])
-def test_algorithm1_equals_dense_tilde_and_meets_theorem(eps):
+def test_algorithm1_meets_theorem(eps):
     c, t, s = W.laplace_inputs(400, 300, seed=4)
     f_alg, p = S.laplace_alg1(c, t, s, eps)
-    K, _ = S.laplace_tilde_matrix(t, s, eps)
-    assert np.max(np.abs(f_alg - K @ c)) <= 1e-12 * np.sum(np.abs(c))
     f = oracle.laplace_direct(c, t, s)
     assert oracle.error_E(f, f_alg, c) <= eps                          # Theorem A.3
+
+
+def test_tilde_blocks_interpolate_at_chebyshev_points():
+    # nodes and frequencies placed on the Chebyshev points of their bands: every
+    # interpolated entry of K~ is then exp(-y_s xi_r) itself (L_r(y_s) = delta_rs)
+    eps, y1, xi1 = 1e-6, 400.0, 3.0
+    p = S.laplace_params(eps, y1, xi1)
+    ys, xs = [y1], [xi1]
+    for m in (2, 5, 9):
+        ys += list(S.interval_points(*S.band_interval(y1, m), p.q)[[0, 3, p.q - 1]])
+    for l in range(1, p.M):
+        xs += list(S.interval_points(*S.band_interval(xi1, l), p.q)[[1, p.q - 2]])
+    ys, xs = np.array(ys), np.array(xs)
+    K, _ = S.laplace_tilde_matrix(xs, ys, eps, y1=y1, xi1=xi1)
+    by, bx = S.band_of(ys, y1, p.M), S.band_of(xs, xi1, p.M)
+    exact = np.exp(-np.outer(ys, xs))
+    n = 0
+    for j in range(ys.size):
+        for k in range(xs.size):
+            m, l = by[j], bx[k]
+            if m < p.M and p.ell[m] <= l <= p.L[m] and j > 0 and k > 0:
+                assert abs(K[j, k] - exact[j, k]) <= 1e-15 * exact[j, k] + 1e-300, (m, l)
+                n += 1
+    assert n >= 20
 
 
 def test_algorithm1_error_decays_faster_than_4_to_minus_q():
