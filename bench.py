@@ -65,6 +65,8 @@ def parse():
                     help="skip the secondary workloads (Laplace, batched, gradients, N=1024)")
     ap.add_argument("--workloads", default=",".join(SECONDARY),
                     help="comma-separated secondary workloads to run: " + ", ".join(SECONDARY))
+    ap.add_argument("--case", default=None, choices=sorted(CASES),
+                    help="run one small case only (for kernel profiling): " + ", ".join(sorted(CASES)))
     args = ap.parse_args()
     bad = set(args.workloads.split(",")) - set(SECONDARY)
     if bad:
@@ -119,6 +121,40 @@ def measured_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
+def pipe_peaks() -> dict:
+    """FP32 and FP64 FMA issue rates of this GPU (TFLOP/s, 2 per FMA), measured by
+    the libflpeaks.so microbenchmark with CUDA events: the denominators of the
+    pipe fractions of the arithmetic-bound kernels.  No clock is changed."""
+    import ctypes
+    from paper_1606_03255_gb300 import build as libbuild
+    lib = ctypes.CDLL(libbuild.PEAKS_LIB)
+    lib.fl_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.POINTER(ctypes.c_double)]
+    out = {}
+    for name, prec, iters in (("fp32", 0, 20000), ("fp64", 1, 400)):
+        v = ctypes.c_double(0.0)
+        rc = lib.fl_peak_fma(prec, 4, iters, 5, ctypes.byref(v))
+        out[name + "_tflops"] = v.value / 1e12 if rc == 0 else None
+    if out.get("fp32_tflops") and out.get("fp64_tflops"):
+        out["fp32_to_fp64"] = out["fp32_tflops"] / out["fp64_tflops"]
+    out["how"] = "8 independent FMA chains per thread, 4 x 256-thread CTAs per SM, best of 5, CUDA events"
+    return out
+
+
+def method_bytes(info: dict, q: int, cs: int = 8, n_min: int = 0) -> float:
+    """Bytes the method moves through the band grids per execute (the survey's
+    per-unit figure): one grid write and one read per right-hand side of every
+    NFFT band, 2 cs n_m each (cs = bytes per complex); only grids above n_min."""
+    total = 0.0
+    L = info["levels"]
+    for b in range(1, L + 1):
+        if info["band_route"][b] != 1 or info["band_n"][b] <= n_min:
+            continue
+        nrhs = 1 if b == L else q
+        total += nrhs * 2.0 * cs * info["band_n"][b]
+    return total
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_1606_03255_gb300", "csrc")
@@ -130,8 +166,9 @@ def source_hash() -> str:
 
 
 def ncu_traffic(kernel: str, N: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
-    captured from the current sources on the same workload size (else None)."""
+    """DRAM bytes per launch of `kernel` (or the sum over a list of kernels, one
+    launch of each) from the committed ncu summary, if it was captured from the
+    current sources on the same workload size (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -139,8 +176,11 @@ def ncu_traffic(kernel: str, N: int):
         d = json.load(fh)
     if d.get("source_hash") != source_hash() or int(d.get("N", -1)) != int(N):
         return None
-    k = d.get("kernels", {}).get(kernel)
-    return None if k is None else float(k["dram_bytes_per_launch"])
+    names = [kernel] if isinstance(kernel, str) else list(kernel)
+    ks = [d.get("kernels", {}).get(k) for k in names]
+    if any(k is None for k in ks):
+        return None
+    return float(sum(k["dram_bytes_per_launch"] for k in ks))
 
 
 class ClockSampler:
@@ -401,6 +441,56 @@ def secondary_workloads(dev, flush, rank, names=SECONDARY):
     return out
 
 
+CASES = ("disk_2e18_fp32", "disk_2e18_fp64", "adjoint_2e18_fp32", "laplace_2e16_fp64",
+         "laplace_2e16_fp32", "flt_2e20_fp32", "flt_2e18_fp32")
+
+
+def run_case(args):
+    """One small case on cuda:0, `--warmup` untimed and `--steps` timed calls,
+    for profiling single kernels: the disk-uniform forward at 2^18 (its bands
+    are mostly summed directly), its adjoint, the Laplace transform at 2^16, and
+    the headline workload at 2^20 or 2^18."""
+    import torch
+    from paper_1606_03255_gb300 import fl
+    dev = torch.device("cuda", 0)
+    name = args.case
+    if name.startswith("laplace"):
+        N = M = 1 << 16
+        prec = name.rsplit("_", 1)[1]
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        cl, t, sv = W.laplace_inputs(N, M, seed=0)
+        p = fl.LaplacePlan(torch.from_numpy(t).to(dev), torch.from_numpy(sv).to(dev), 1e-6,
+                           precision=prec)
+        cc = torch.from_numpy(cl).to(dt).to(dev)
+        out = torch.empty(M, dtype=dt, device=dev)
+        run = lambda: p.execute(cc, out=out)   # noqa: E731
+    else:
+        N = M = 1 << (20 if "2e20" in name else 18)
+        prec = name.rsplit("_", 1)[1]
+        cdt = torch.complex64 if prec == "fp32" else torch.complex128
+        if name.startswith("flt"):
+            c_np, w_np = rank_workload(N, 0)
+        else:
+            c_np, w_np = W.coefficients(N, seed=0), W.nodes_disk_uniform(M, seed=200)
+        p = fl.Plan(N, torch.from_numpy(w_np).to(dev), 1e-6 if prec == "fp32" else 1e-12,
+                    precision=prec)
+        c = torch.from_numpy(c_np).to(cdt).to(dev)
+        if name.startswith("adjoint"):
+            r = torch.from_numpy(W.targets(M, seed=300)).to(cdt).to(dev)
+            out = torch.empty(N, dtype=cdt, device=dev)
+            run = lambda: p.adjoint(r, out=out)   # noqa: E731
+        else:
+            out = torch.empty(M, dtype=cdt, device=dev)
+            run = lambda: p.execute(c, out=out)   # noqa: E731
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    ms = _time_cuda(run, args.steps)
+    p.close()
+    print(json.dumps({"case": name, "ms": ms, "steps": args.steps, "warmup": args.warmup}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle (plain FP64 direct sum) on the host cores."""
     rank, world, _ = dist_env()
@@ -505,14 +595,30 @@ def run_ours(args):
         kernel_table[name] = {"launches": kd["launches"], "ms_per_step": kd["total_ms"] / args.steps,
                               "avg_launch_ms": per, "bytes_per_launch": kd["bytes"] / max(kd["launches"], 1),
                               "GBps": gbs, "share": kd["total_ms"] / max(sum(v["total_ms"] for v in kern.values()), 1e-12)}
-    top = max(kernel_table, key=lambda k: kernel_table[k]["ms_per_step"]) if kernel_table else None
+    # Roofline of the dominant work, the four-step FFTs of the band grids (pass
+    # 1 and pass 2 together: the survey's per-unit figure, one grid write and
+    # one read per right-hand side, cannot be credited to either pass alone),
+    # and of the whole step on the method's bytes.
+    passes = sorted(k for k in kernel_table if k.startswith("fft_pass"))
     roof = None
-    if top:
-        kt = kernel_table[top]
-        roof = {"kernel": top, "bound": "hbm", "achieved": kt["GBps"], "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": kt["GBps"] / peaks["hbm_gbs"],
-                "traffic": ncu_traffic(top, N), "peak_source": peaks["source"],
-                "algorithmic_bytes_per_launch": kt["bytes_per_launch"]}
+    if passes:
+        pair_ms = sum(kernel_table[k]["ms_per_step"] for k in passes)
+        pair_launches = kernel_table[passes[0]]["launches"] / args.steps
+        mb_large = method_bytes(info, info["q"], 8, n_min=4096)
+        mb_all = method_bytes(info, info["q"], 8)
+        compulsory = 8.0 * N + 8.0 * M + 16.0 * M      # c, f and the nodes (Re w, Im w)
+        achieved = mb_large / (pair_ms * 1e-3) / 1e9
+        roof = {"kernel": "+".join(passes) + " (four-step FFT of the band grids, one pair per grid size)",
+                "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"],
+                "traffic": ncu_traffic(passes, N), "peak_source": peaks["source"],
+                "algorithmic_bytes_per_launch": mb_large / max(pair_launches, 1),
+                "bytes_rule": "16 n_m per right-hand side (one grid write + one read, complex64)",
+                "limiter_ncu": "issue / latency (see profiles/); HBM is the roofline it is measured against",
+                "step": {"method_bytes": mb_all + compulsory,
+                         "achieved": (mb_all + compulsory) / (ms * 1e-3) / 1e9,
+                         "frac": (mb_all + compulsory) / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "rule": "16 n_m per right-hand side of every NFFT band + c, f and the nodes"}}
 
     # end-to-end through the host-buffer C call (copies inside the timed region)
     c_host = torch.from_numpy(c_np).pin_memory()
@@ -611,6 +717,18 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
     launches_total = timing["total_launches"]
+    try:
+        pipes = pipe_peaks()
+    except OSError:
+        pipes = None
+    if roof is not None:
+        roof["pipe_peaks"] = pipes
+    accuracy = None
+    if errors:
+        accuracy = dict(errors)
+        accuracy["sample"] = f"max over {args.sample} seeded nodes, oracle FP64 direct sum"
+        if fp64:
+            accuracy["fp64_ms"] = {k: v["ms_per_step"] for k, v in fp64.items() if isinstance(v, dict)}
     line = {
         "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
@@ -621,7 +739,8 @@ def run_ours(args):
                    "bands_fft": info["n_bands_fft"],
                    "l2": "flushed between steps (256 MiB write); working set > L2",
                    "plan": "built once before the timed region (route bias autotuned)",
-                   "direct_bias": info["direct_bias"]},
+                   "direct_bias": info["direct_bias"],
+                   "E": accuracy},
         "plan_ms": plan_ms,
         "E": errors or None,
         "fp64": fp64 or None,
@@ -646,6 +765,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.case:
+        return run_case(args)
     return run_ours(args)
 
 

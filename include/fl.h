@@ -92,6 +92,8 @@ typedef struct {
     double scratch_bytes;     /* device memory owned by the plan */
     int variant;              /* fl_options.variant in use */
     int kernel;               /* Laplace plans: the fl_kernel */
+    int n_bands_fused;        /* bands whose window gather runs inside pass 2 (fuse_gather) */
+    int64_t fused_entries;    /* their (node, pass-2 row block) entries */
 } fl_info;
 
 /* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
@@ -156,6 +158,16 @@ typedef struct {
                                  q = 0 then means the smallest q with
                                  2 q^q e^-q / (4^q q!) <= eps/3, the
                                  per-entry bound of that interpolation.       */
+    int fuse_gather;      /* FL_FP32 forward transforms (fl_execute, the
+                             derivative and gradient calls, batches): the
+                             window gather of a band computed inside the second
+                             pass of its grid's FFT, so that the grid is never
+                             written to memory -- each node's taps are summed
+                             per pass-2 tile into partial sums that the gather
+                             recombines (the plan keeps the node/tile lists):
+                             0 = for grids above 4096 points whose nodes are
+                                 few for the grid (by estimated bytes; default);
+                             1 = never; 2 = for every grid above 4096 points. */
 } fl_options;
 
 /*
@@ -331,8 +343,10 @@ fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *str
  *               planned call sums the moments in band order).
  * Scratch: a fixed static device array of 2 MiB, held by every GPU that loads
  * libfl.so until the process exits.  Its use depends on the number of levels
- * and on q only (not on N or M); a problem that needs more returns
- * FL_EUNSUPPORTED with the bytes needed in fl_last_error().
+ * and on q only, not on N or M (the partial moment sums of the largest block
+ * count are reserved whatever N is): about 1 KiB (FP64) or 0.5 KiB (FP32) per
+ * entry of the (levels + 1) x (q + 1) moment table.  A problem that needs more
+ * returns FL_EUNSUPPORTED with the bytes needed in fl_last_error().
  * The first call on each device does a one-time set-up (it looks up the
  * array's device address); make that first call before any stream capture.
  * The call synchronises `stream` once (it reads max t and max s back to choose

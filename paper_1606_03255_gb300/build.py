@@ -2,7 +2,9 @@
 
 Each translation unit under csrc/ is compiled by nvcc in parallel and the
 objects are linked into ``_build/libfl.so``.  No torch extension machinery is
-involved: the library exposes a plain C ABI.
+involved: the library exposes a plain C ABI.  ``peaks/fl_peaks.cu`` becomes
+``_build/libflpeaks.so``, the FMA-rate microbenchmark the benchmark reads its
+FP32/FP64 pipe peaks from (measurement only, not part of the C ABI).
 """
 from __future__ import annotations
 
@@ -18,6 +20,8 @@ SRC = os.path.join(HERE, "csrc")
 INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfl.so")
+PEAKS_SRC = os.path.join(HERE, "peaks", "fl_peaks.cu")
+PEAKS_LIB = os.path.join(BUILD, "libflpeaks.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
@@ -61,6 +65,11 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         tmp = LIB + f".{os.getpid()}.tmp"
         subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
         os.replace(tmp, LIB)
+    if force or _stale(PEAKS_LIB, [PEAKS_SRC]):
+        tmp = PEAKS_LIB + f".{os.getpid()}.tmp"
+        subprocess.run([cc, *ARCH, "-O3", "-Xcompiler", "-fPIC", "-shared", PEAKS_SRC, "-o", tmp],
+                       check=True)
+        os.replace(tmp, PEAKS_LIB)
     return LIB
 
 

@@ -42,7 +42,8 @@ Plan::~Plan() {
                     d_stage_c, d_stage_f, d_stage_r, d_z0, d_t, d_s, d_tband, d_sband, d_lap, d_direct,
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
                     d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm, d_ts, d_tbs,
-                    d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi, d_xcs, d_xsb};
+                    d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi, d_xcs, d_xsb,
+                    d_frbs, d_fent, d_fphi, d_fpp};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -305,6 +306,135 @@ static void build_pass_groups(Plan& p) {
     }
 }
 
+// Window gather fused into pass 2 (FP32 forward, four-step grids).  A band
+// qualifies when its nodes are few for its grid: per right-hand side the
+// unfused path writes the grid (8 n bytes) and gathers about three 32-byte
+// sectors per node, the fused one reads its entries (8 + 16 NQ bytes: slot,
+// column, window values) and writes and later reads one partial sum per entry.
+// Each node's window of 2 m_w taps at grid indices lo .. lo + 2 m_w - 1
+// (lo = floor(n x) - m_w + 1, mod n) is cut into entries, one per pass-2 row
+// block its taps fall in (tile rows TR of the length-n1 pass, rows l2 = g mod
+// n2, column l1 = g / n2); the window values are those of the gather kernel,
+// phi_t = kb(frac(n x) + m_w - 1 - t), in FP64 rounded once.
+static double kb_window_host(double t, double m, double b) {
+    const double s2 = m * m - t * t;
+    if (!(s2 > 0.0)) return b;
+    const double r = sqrt(s2);
+    return sinh(b * r) / r;
+}
+
+static fl_status build_fused(Plan& p, cudaStream_t st) {
+    p.fused_bands = p.fused_entries = 0;
+    if (p.prec != FL_FP32 || p.xi_mode || p.fuse_mode == 1 || p.M == 0) return FL_OK;
+    struct Cand {
+        int b, l1, l2, TR, P;
+    };
+    std::vector<Cand> cands;
+    const int taps = 2 * p.mw;
+    for (int b = 0; b < (int)p.bands.size(); ++b) {
+        BandHost& bh = p.bands[b];
+        BandDev& d = bh.dev;
+        d.fused = 0;
+        if (d.route != 1 || d.log2n <= kSmallMaxLog2 || bh.nodes == 0) continue;
+        const int l2 = d.log2n / 2, l1 = (d.log2n + 1) / 2;
+        const int TR = pass_tiles(8, l1, FL_P2_THREADS_F32);
+        const int P = (taps - 1 + TR - 1) / TR + 1;
+        const int NQ = (TR + 3) / 4;
+        const double parts = (double)(TR + taps - 1) / TR;
+        const double unfused = 8.0 * d.n + std::min<double>(8.0 * d.n, 96.0 * bh.nodes);
+        const double fused = bh.nodes * parts * (8.0 + 16.0 * NQ + 8.0) + 8.0 * P * bh.nodes;
+        if (p.fuse_mode == 2 || fused <= 0.5 * unfused) cands.push_back({b, l1, l2, TR, P});
+    }
+    if (cands.empty()) return FL_OK;
+    std::vector<double2> hw(p.M);
+    FL_CUDA(cudaMemcpyAsync(hw.data(), p.d_ws, p.M * sizeof(double2), cudaMemcpyDeviceToHost, st),
+            "fl_plan: copy nodes");
+    FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
+    std::vector<int32_t> rbs;
+    std::vector<int2> ent;
+    std::vector<float4> phi;
+    int64_t pp = 0;
+    for (const Cand& cd : cands) {
+        BandHost& bh = p.bands[cd.b];
+        BandDev& d = bh.dev;
+        const int64_t n = d.n, n2 = (int64_t)1 << cd.l2, nrb = n2 / cd.TR;
+        const int NQ = (cd.TR + 3) / 4;
+        struct E {
+            int64_t rb;
+            int slot, l1;
+            float w[8];
+        };
+        std::vector<E> es;
+        es.reserve((size_t)(bh.nodes * ((cd.TR + taps - 1) / cd.TR + 1)));
+        for (int64_t jl = 0; jl < bh.nodes; ++jl) {
+            const double x = hw[bh.node_off + jl].x;
+            const double xr = x - floor(x);
+            const double t0 = (double)n * xr;
+            const double u = floor(t0);
+            const double fr = t0 - u;
+            const int64_t lo = (int64_t)u - (p.mw - 1);
+            int part = 0;
+            int64_t cur = -1;
+            for (int t = 0; t < taps; ++t) {
+                const int64_t g = ((lo + t) % n + n) % n;
+                const int64_t rho = g & (n2 - 1);
+                const int64_t rb = rho / cd.TR;
+                if (rb != cur) {
+                    if (part == cd.P)   // a window spans at most P row blocks (n2 >= 8 TR)
+                        return fail(FL_ECUDA, "fl_plan: fused gather entry count out of range");
+                    E e{};
+                    e.rb = rb;
+                    e.slot = (int)(jl * cd.P + part++);
+                    e.l1 = (int)(g >> cd.l2);
+                    es.push_back(e);
+                    cur = rb;
+                }
+                es.back().w[rho % cd.TR] = (float)kb_window_host(fr + (double)(p.mw - 1 - t), (double)p.mw, p.kb_b);
+            }
+        }
+        // bucket by row block (stable: node order within a block)
+        std::vector<int32_t> cnt(nrb + 1, 0);
+        for (const E& e : es) ++cnt[e.rb + 1];
+        for (int64_t r = 0; r < nrb; ++r) cnt[r + 1] += cnt[r];
+        d.fused = 1;
+        d.pparts = cd.P;
+        d.ent_off = (int64_t)ent.size();
+        d.rbs_off = (int64_t)rbs.size();
+        d.ph_off = (int64_t)phi.size();
+        d.pp_off = pp;
+        bh.fentries = (int64_t)es.size();
+        rbs.insert(rbs.end(), cnt.begin(), cnt.end());
+        std::vector<int32_t> pos(cnt.begin(), cnt.end() - 1);
+        const size_t e0 = ent.size(), q0 = phi.size();
+        ent.resize(e0 + es.size());
+        phi.resize(q0 + es.size() * NQ);
+        for (const E& e : es) {
+            const int64_t k = pos[e.rb]++;
+            ent[e0 + k] = make_int2(e.slot, e.l1);
+            for (int qd = 0; qd < NQ; ++qd)
+                phi[q0 + k * NQ + qd] = make_float4(e.w[4 * qd], e.w[4 * qd + 1], e.w[4 * qd + 2], e.w[4 * qd + 3]);
+        }
+        pp += (int64_t)d.nrhs * bh.nodes * cd.P;
+        ++p.fused_bands;
+    }
+    p.fused_entries = (int64_t)ent.size();
+    FL_CUDA(cudaMalloc((void**)&p.d_frbs, rbs.size() * sizeof(int32_t)), "cudaMalloc fused starts");
+    FL_CUDA(cudaMalloc((void**)&p.d_fent, ent.size() * sizeof(int2)), "cudaMalloc fused entries");
+    FL_CUDA(cudaMalloc((void**)&p.d_fphi, phi.size() * sizeof(float4)), "cudaMalloc fused windows");
+    FL_CUDA(cudaMalloc((void**)&p.d_fpp, pp * sizeof(float2)), "cudaMalloc fused partials");
+    FL_CUDA(cudaMemcpyAsync(p.d_frbs, rbs.data(), rbs.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st),
+            "copy fused starts");
+    FL_CUDA(cudaMemcpyAsync(p.d_fent, ent.data(), ent.size() * sizeof(int2), cudaMemcpyHostToDevice, st),
+            "copy fused entries");
+    FL_CUDA(cudaMemcpyAsync(p.d_fphi, phi.data(), phi.size() * sizeof(float4), cudaMemcpyHostToDevice, st),
+            "copy fused windows");
+    // slots beyond a node's parts are never written and must read as zero
+    FL_CUDA(cudaMemsetAsync(p.d_fpp, 0, pp * sizeof(float2), st), "clear fused partials");
+    // the host vectors are released on return: finish the copies first
+    FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
+    return FL_OK;
+}
+
 // Plans the transforms Ns[i] x Ms[i], i < B, whose nodes are consecutive in
 // `nodes` (a single plan is B = 1).  Every band of every transform gets an
 // entry of one global band table, and each kernel launch of fl_execute covers
@@ -484,6 +614,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.dadj_work32.insert(p.dadj_work32.end(), small_adj.begin(), small_adj.end());
     p.dadj_work64.insert(p.dadj_work64.end(), small_adj.begin(), small_adj.end());
     build_pass_groups(p);
+    if ((s = build_fused(p, st)) != FL_OK) return s;
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
@@ -579,6 +710,12 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
         const BandDev& d = p.bands[b].dev;
         if (d.route != 1) continue;
         const double g = (double)d.nrhs * d.n * cs;
+        if (d.fused) {   // Y write + read; entries read, partials written and gathered
+            const int NQ = (d.pparts > 0) ? (pass_tiles(8, (d.log2n + 1) / 2, FL_P2_THREADS_F32) + 3) / 4 : 1;
+            mb += 2.0 * g + (double)d.nrhs * p.bands[b].fentries * (8.0 + 16.0 * NQ + 8.0) +
+                  (double)d.nrhs * p.bands[b].nodes * d.pparts * cs;
+            continue;
+        }
         mb += (d.log2n <= kSmallMaxLog2) ? g : 3.0 * g;   // small: write; large: Y write+read, grid write
         mb += std::min<double>(g, (double)p.bands[b].nodes * d.nrhs * 2 * p.mw * cs);   // gather
     }
@@ -602,6 +739,7 @@ struct PlanSpec {
     int rhs_per_launch;
     bool use_graph;
     int variant;
+    int fuse_mode;
 };
 
 static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cudaStream_t st) {
@@ -616,6 +754,7 @@ static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cu
     h->p.rhs_per_launch = sp.rhs_per_launch;
     h->p.use_graph = sp.use_graph;
     h->p.variant = sp.variant;
+    h->p.fuse_mode = sp.fuse_mode;
     fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, st);
     if (s != FL_OK) {
         delete h;
@@ -793,7 +932,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
                      double eps, fl_precision prec, const fl_options* opt, void* stream) {
     g_err.clear();
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1))
+                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
+                opt->fuse_gather < 0 || opt->fuse_gather > 2))
         return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
@@ -807,7 +947,7 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
     PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
                  opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false,
-                 opt ? opt->variant : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -968,11 +1108,12 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
         return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
     if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1))
+                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
+                opt->fuse_gather < 0 || opt->fuse_gather > 2))
         return fail(FL_EINVAL, "fl_plan_batched: invalid options");
     PlanSpec sp{B, N_host, M_host, nodes_dev, q, eps, prec, true, opt ? opt->route : 0,
                  opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true,
-                 opt ? opt->variant : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -1030,6 +1171,8 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->scratch_bytes = p.scratch_bytes;
     info->variant = p.variant;
     info->kernel = p.kind == 1 ? p.lap_kernel : 0;
+    info->n_bands_fused = (int)p.fused_bands;
+    info->fused_entries = p.fused_entries;
     return FL_OK;
 }
 

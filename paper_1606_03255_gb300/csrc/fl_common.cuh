@@ -166,6 +166,15 @@ struct BandDev {
     double xc;
     int64_t gh;
     int64_t phi_off;
+    // window gather fused into the FFT's second pass (FP32 forward, four-step
+    // grids whose nodes are few for the grid): the grid is never written;
+    // pass 2 leaves per-node partial tap sums instead (see k_pass2)
+    int fused;         // 1: this band's gather is fused into pass 2
+    int pparts;        // partial sums per node and right-hand side (row blocks a window spans)
+    int64_t ent_off;   // first entry of the band's (node, row block) entry list
+    int64_t rbs_off;   // offset of the band's row-block starts (n2 / rows-per-CTA + 1 of them)
+    int64_t pp_off;    // offset of the band's partial sums (nrhs x nodes x pparts complex)
+    int64_t ph_off;    // offset (in float4) of the band's entry window values
 };
 
 // ---------------------------------------------------------------------------

@@ -322,34 +322,17 @@ __device__ __forceinline__ void fft_last_to_regs(const C_t<T>* buf, int t, C_t<T
     }
 }
 
-// Thread budgets per CTA of the two passes (float / double).  Pass 2 runs two
-// CTAs per SM so that one CTA's loads overlap the other's shared-memory stages.
-#ifndef FL_P1_THREADS_F32
-#define FL_P1_THREADS_F32 1024
-#endif
-#ifndef FL_P2_THREADS_F32
-#define FL_P2_THREADS_F32 512
-#endif
-#ifndef FL_P1_THREADS_F64
-#define FL_P1_THREADS_F64 512
-#endif
-#ifndef FL_P2_THREADS_F64
-#define FL_P2_THREADS_F64 512
-#endif
 template <typename T> struct PassBudget {
     static constexpr int P1 = sizeof(T) == 4 ? FL_P1_THREADS_F32 : FL_P1_THREADS_F64;
     static constexpr int P2 = sizeof(T) == 4 ? FL_P2_THREADS_F32 : FL_P2_THREADS_F64;
 };
 
-// Columns (pass 1) or rows (pass 2) per CTA: up to 64 contiguous bytes per
-// global row segment within the thread budget TMAX (L/16 threads per FFT).
+// Columns (pass 1) or rows (pass 2) per CTA: pass_tiles (fl_plan.cuh).
 template <typename T, int LOG2L, int TMAX>
 struct PassTile {
     static constexpr int L = 1 << LOG2L;
     static constexpr int EPT = 16;                       // elements per thread
-    static constexpr int W0 = (int)(64 / sizeof(C_t<T>));
-    static constexpr int WMIN = 32 / (L / EPT) > W0 ? 32 / (L / EPT) : W0;   // >= one warp
-    static constexpr int TILES = (WMIN * (L / EPT) <= TMAX) ? WMIN : (TMAX / (L / EPT));
+    static constexpr int TILES = pass_tiles((int)sizeof(C_t<T>), LOG2L, TMAX);
     static constexpr int LOG2T = TILES == 8 ? 3 : TILES == 4 ? 2 : TILES == 2 ? 1 : 0;
     static_assert(TILES == 1 || TILES == 2 || TILES == 4 || TILES == 8, "tile count");
     static constexpr int NT = TILES * (L / EPT);
@@ -483,16 +466,32 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
     }
 }
 
+// acc += w g[off] for a row of the fused gather (off < 0: no such row).
+template <typename C> __device__ __forceinline__ void fused_tap(float2& acc, float w, const C* col, int off) {
+    if (off < 0) return;
+    const C g = col[off];
+    acc.x += w * g.x;
+    acc.y += w * g.y;
+}
+
 // Pass 2 for a tile of TILES rows l2: the length-n1 FFTs over i1 of
 // Y[l2 n1 + i1], stored to X[l2 + n2 l1] (natural order of the length-n
 // transform) in the band grid.  For float rows of 2^(4j+3) points the first
 // stage is radix 8 with two butterflies per thread, so each thread reads 8
 // pairs of adjacent elements with 16-byte loads.
+//
+// Fused gather (FP32 forward, bands with B.fused): the grid is not stored.
+// The tile's rows stay in shared memory in natural order, and every entry of
+// the tile's row block -- one node and the taps of its window that fall in
+// these rows, all at one column l1 -- sums phi_rho g[rho][l1] over the rows
+// into its slot of the band's partial sums; the gather kernel adds a node's
+// slots and recombines the right-hand sides.
 template <typename T, int SIGN, int LOG2L>
 __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P2>::NT,
                                   PassTile<T, LOG2L, PassBudget<T>::P2>::MINB)
     k_pass2(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n2,
-            const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst, const C_t<T>* __restrict__ tw) {
+            const C_t<T>* __restrict__ Y, C_t<T>* __restrict__ dst, const C_t<T>* __restrict__ tw,
+            FuseArgs fz) {
     using C = C_t<T>;
     using PT = PassTile<T, LOG2L, PassBudget<T>::P2>;
     constexpr int L = PT::L, TR = PT::TILES, LD = PT::LD;
@@ -536,6 +535,40 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P2>::NT,
         const int row = tid & (TR - 1), t = tid >> PT::LOG2T;
         C v[16];
         fft_last_to_regs<LOG2L, FIRST, SIGN, T>(sm + row * LD, t, v, twr);
+        if constexpr (sizeof(T) == 4 && SIGN > 0) {
+            if (B.fused) {
+                __syncthreads();   // every thread has read its last-stage inputs
+                C* rbuf = sm + row * LD;
+#pragma unroll
+                for (int jb = 0; jb < J; ++jb) {
+                    const int jj = t + jb * (L / 16);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) rbuf[jj + r * NS] = v[jb * R + r];
+                }
+                __syncthreads();
+                // entries of this row block: [e0, e1) of the band's list
+                const int e0 = fz.rbs[B.rbs_off + blockIdx.x], e1 = fz.rbs[B.rbs_off + blockIdx.x + 1];
+                constexpr int NQ = (TR + 3) / 4;   // float4 of window values per entry
+                const int2* ent = fz.ent + B.ent_off;
+                const float4* ph = fz.phi + B.ph_off;
+                float2* pp = fz.pp + B.pp_off + (int64_t)s * B.nodes * B.pparts;
+                for (int e = e0 + tid; e < e1; e += PT::NT) {
+                    const int2 a = __ldg(ent + e);
+                    const C* col = sm + a.y;
+                    float2 acc = {0.f, 0.f};
+#pragma unroll
+                    for (int qd = 0; qd < NQ; ++qd) {
+                        const float4 w4 = __ldg(ph + e * NQ + qd);
+                        fused_tap(acc, w4.x, col, 4 * qd + 0 < TR ? (4 * qd + 0) * LD : -1);
+                        fused_tap(acc, w4.y, col, 4 * qd + 1 < TR ? (4 * qd + 1) * LD : -1);
+                        fused_tap(acc, w4.z, col, 4 * qd + 2 < TR ? (4 * qd + 2) * LD : -1);
+                        fused_tap(acc, w4.w, col, 4 * qd + 3 < TR ? (4 * qd + 3) * LD : -1);
+                    }
+                    pp[a.x] = acc;
+                }
+                return;
+            }
+        }
         C* out = dst + B.grid_off + (int64_t)s * n + l2b + row;
 #pragma unroll
         for (int jb = 0; jb < J; ++jb) {
@@ -568,7 +601,8 @@ static cudaError_t pass1_ct(const PassItem* items, int nitems, const BandDev* ba
 
 template <typename T, int SIGN, int LOG2L>
 static cudaError_t pass2_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n2,
-                            const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw, cudaStream_t st) {
+                            const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw, FuseArgs fz,
+                            cudaStream_t st) {
     using PT = PassTile<T, LOG2L, PassBudget<T>::P2>;
     auto k = k_pass2<T, SIGN, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
@@ -576,7 +610,7 @@ static cudaError_t pass2_ct(const PassItem* items, int nitems, const BandDev* ba
         e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     k<<<dim3((unsigned)((1 << log2n2) / PT::TILES), (unsigned)nitems), PT::NT, PT::SMEM, st>>>(
-        items, bands, log2n2, Y, dst, tw);
+        items, bands, log2n2, Y, dst, tw, fz);
     return cudaGetLastError();
 }
 
@@ -597,11 +631,11 @@ cudaError_t launch_pass1(const PassItem* items, int nitems, const BandDev* bands
 // Pass 2 (length n1 = 2^log2n1, 7..12) over all n2 = 2^log2n2 rows.
 template <typename T, int SIGN>
 cudaError_t launch_pass2(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
-                         int log2n2, const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw,
+                         int log2n2, const C_t<T>* Y, C_t<T>* dst, const C_t<T>* tw, FuseArgs fz,
                          cudaStream_t st) {
     switch (log2n1) {
 #define FL_P2(LG) \
-    case LG: return pass2_ct<T, SIGN, LG>(items, nitems, bands, log2n2, Y, dst, tw, st);
+    case LG: return pass2_ct<T, SIGN, LG>(items, nitems, bands, log2n2, Y, dst, tw, fz, st);
         FL_P2(6) FL_P2(7) FL_P2(8) FL_P2(9) FL_P2(10) FL_P2(11) FL_P2(12)
 #undef FL_P2
         default: return cudaErrorInvalidValue;
@@ -748,7 +782,7 @@ cudaError_t launch_small_fft(const SmallWork* work, int nwork, const BandDev* ba
 #define FL_P1_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, const T*, \
                      const C_t<T>*, C_t<T>*, const C_t<T>*, cudaStream_t
 #define FL_P2_SIG(T) const PassItem*, int, const BandDev*, int, int, const C_t<T>*, C_t<T>*, \
-                     const C_t<T>*, cudaStream_t
+                     const C_t<T>*, FuseArgs, cudaStream_t
 #define FL_FFT_EXTERN(T)                                                   \
     extern template cudaError_t launch_pass1<T, 1, 0, false>(FL_P1_SIG(T)); \
     extern template cudaError_t launch_pass1<T, 1, 0, true>(FL_P1_SIG(T));  \

@@ -522,15 +522,17 @@ static bool lap_params(double eps, int q_in, double y1, double xi1, LapParams* P
     return true;
 }
 
-// Launches moments -> reduce -> couple -> eval on `scratch` (layout above).
+// Launches moments -> reduce -> couple -> eval on `scratch` (layout above),
+// with nblocks moment blocks; the layout reserves partial sums for
+// layout_blocks >= nblocks blocks (0: nblocks).
 template <typename T, bool BANDS_FROM_VALUES = false>
 static cudaError_t lap_run(int64_t N, int64_t M, const double* t, const double* s,
                            const uint8_t* tband, const uint8_t* sband, const LapParams& P,
                            const double* cheb, const T* c, T* f, unsigned char* scratch,
                            int nblocks, cudaStream_t st, Plan* timed,
                            const double* Kt = nullptr, const int64_t* koff = nullptr,
-                           const int32_t* tperm = nullptr) {
-    const LapLayout L = lap_layout(P.levels, P.q, nblocks, sizeof(T));
+                           const int32_t* tperm = nullptr, int layout_blocks = 0) {
+    const LapLayout L = lap_layout(P.levels, P.q, std::max(nblocks, layout_blocks), sizeof(T));
     const int entries = (P.levels + 1) * (P.q + 1);
     T* partial = (T*)(scratch + L.partial);
     double* vS = (double*)(scratch + L.vS);
@@ -1082,11 +1084,13 @@ fl_status fl_laplace_real_noalloc(int64_t N, int64_t M, const double* t_dev, con
     if ((size_t)kLapWarps * (P.levels + 1) * (P.q + 1) * tsz > 200 * 1024)
         return lap_fail(FL_EUNSUPPORTED, "fl_laplace_real_noalloc: moment tables exceed shared memory");
 
-    // [256, 256 + cheb): Chebyshev table; then the Algorithm 1 layout
+    // [256, 256 + cheb): Chebyshev table; then the Algorithm 1 layout with the
+    // partial sums of kLapMaxBlocks moment blocks reserved whatever N is, so
+    // whether a problem fits depends on the number of levels and q alone
     const size_t cheb_off = 256;
     const size_t lap_off = align256(cheb_off + 2 * kMaxQ * sizeof(double));
     const int nblocks = lap_blocks(N);
-    const LapLayout L = lap_layout(P.levels, P.q, nblocks, tsz);
+    const LapLayout L = lap_layout(P.levels, P.q, kLapMaxBlocks, tsz);
     if (lap_off + L.total > kNoAllocScratchBytes) {
         char msg[256];
         snprintf(msg, sizeof(msg),
@@ -1106,10 +1110,12 @@ fl_status fl_laplace_real_noalloc(int64_t N, int64_t M, const double* t_dev, con
     cudaError_t e;
     if (prec == FL_FP64)
         e = lap_run<double, true>(N, M, t_dev, s_dev, nullptr, nullptr, P, cheb, (const double*)c_dev,
-                                  (double*)f_dev, lap, nblocks, st, nullptr);
+                                  (double*)f_dev, lap, nblocks, st, nullptr, nullptr, nullptr, nullptr,
+                                  kLapMaxBlocks);
     else
         e = lap_run<float, true>(N, M, t_dev, s_dev, nullptr, nullptr, P, cheb, (const float*)c_dev,
-                                 (float*)f_dev, lap, nblocks, st, nullptr);
+                                 (float*)f_dev, lap, nblocks, st, nullptr, nullptr, nullptr, nullptr,
+                                 kLapMaxBlocks);
     LAP_CUDA(e, "fl_laplace_real_noalloc");
     return FL_OK;
 }

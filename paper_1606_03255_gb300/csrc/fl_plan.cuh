@@ -27,6 +27,30 @@ struct SmallWork {
     int log2n;
 };
 
+// Thread budgets per CTA of the two passes (float / double).  Pass 2 runs two
+// CTAs per SM so that one CTA's loads overlap the other's shared-memory stages.
+#ifndef FL_P1_THREADS_F32
+#define FL_P1_THREADS_F32 1024
+#endif
+#ifndef FL_P2_THREADS_F32
+#define FL_P2_THREADS_F32 512
+#endif
+#ifndef FL_P1_THREADS_F64
+#define FL_P1_THREADS_F64 512
+#endif
+#ifndef FL_P2_THREADS_F64
+#define FL_P2_THREADS_F64 512
+#endif
+// Columns (pass 1) or rows (pass 2) per CTA: up to 64 contiguous bytes per
+// global row segment within the thread budget TMAX (L/16 threads per FFT);
+// csize = bytes per complex element.  Also used on the host (fused gather).
+__host__ __device__ constexpr int pass_tiles(int csize, int log2L, int tmax) {
+    const int per = (1 << log2L) / 16;                   // threads per FFT
+    const int w0 = 64 / csize;
+    const int wmin = (32 / per > w0) ? 32 / per : w0;    // >= one warp
+    return (wmin * per <= tmax) ? wmin : tmax / per;
+}
+
 // One (band, right-hand side) of a four-step FFT launch, with the offset of
 // its slice of the intermediate buffer.
 struct PassItem {
@@ -39,6 +63,18 @@ struct PassItem {
 // of grid length 2^log2n.
 struct PassGroup {
     int start, count, log2n;
+};
+
+// Device tables of the window gather fused into pass 2 (see k_pass2): per
+// fused band, row-block starts into its entry list; per entry {slot, l1} (the
+// node's partial-sum slot and the grid column of its taps) and the window
+// values of the tile's rows (zero where the window has no tap), in float4
+// groups; and the partial sums the passes write.
+struct FuseArgs {
+    const int32_t* rbs;
+    const int2* ent;
+    const float4* phi;
+    float2* pp;
 };
 
 // Direct route (fl_direct.cu): kDirNodes nodes x one chunk of kDirChunk
@@ -91,6 +127,7 @@ struct BandHost {
     int local = 0;          // band index within its transform (0 = Z^0, 1..levels)
     int64_t nodes = 0;      // nodes of the band
     int64_t node_off = 0;   // first node of the band in sorted order
+    int64_t fentries = 0;   // entries of the fused gather (0: not fused)
     BandDev dev{};
 };
 
@@ -127,6 +164,7 @@ struct Plan {
     std::vector<PassItem> pass_items;
     std::vector<PassGroup> pass_groups;
     int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
+    int fuse_mode = 0;             // window gather in pass 2: 0 by cost, 1 never, 2 wherever possible
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
     int variant = 0;               // 0 Algorithm 2 weights, 1 one-sided interpolation
     // real exponents xi_k >= 1 (fl_plan_xi): the Fourier factor is an NNFFT
@@ -193,6 +231,12 @@ struct Plan {
     DirectAdjItem* d_dadj64 = nullptr;
     void* d_dpart = nullptr;       // direct route: partial sums (complex T)
     void* d_cdir = nullptr;        // direct route adjoint: N complex
+    // fused gather (FuseArgs): row-block starts, entries, window values, partial sums
+    int32_t* d_frbs = nullptr;
+    int2* d_fent = nullptr;
+    float4* d_fphi = nullptr;
+    float2* d_fpp = nullptr;
+    int64_t fused_bands = 0, fused_entries = 0;
     double scratch_bytes = 0;
 
     // Laplace (Algorithm 1)

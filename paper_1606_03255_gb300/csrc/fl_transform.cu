@@ -312,6 +312,46 @@ __device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, c
     return acc;
 }
 
+// FP32 recombination of a node of a fused band (see k_pass2): its partial tap
+// sums a_s = sum_p pp[s][jl P + p] over the row blocks its window spans, with
+// the barycentric weights of gather_rhs_f32 (one right-hand side: a_0).
+__device__ __forceinline__ float2 fused_rhs_f32(const float2* __restrict__ pp, const BandDev& B,
+                                                int64_t jl, double y, int q,
+                                                const float* __restrict__ cheb32) {
+    const int P = B.pparts;
+    const float2* a = pp + B.pp_off + jl * P;
+    const int64_t stride = B.nodes * P;
+    auto part_sum = [&](int s) {
+        float2 v = {0.f, 0.f};
+        for (int k = 0; k < P; ++k) {
+            const float2 w = a[s * stride + k];
+            v.x += w.x;
+            v.y += w.y;
+        }
+        return v;
+    };
+    if (B.nrhs == 1) return part_sum(0);
+    const double tau = (y - B.yc) * B.yh_inv;
+    const float th = (float)tau, tl = (float)(tau - (double)th);
+    float den = 0.f;
+    int hit = -1;
+    for (int s = 0; s < q; ++s) {
+        const float d = (th - cheb32[s]) + (tl - cheb32[q + s]);
+        if (d == 0.f) hit = s;
+        den += cheb32[2 * q + s] / d;
+    }
+    const float inv = 1.f / den;
+    float2 acc = {0.f, 0.f};
+    for (int s = 0; s < q; ++s) {
+        const float d = (th - cheb32[s]) + (tl - cheb32[q + s]);
+        const float L = hit >= 0 ? (s == hit ? 1.f : 0.f) : cheb32[2 * q + s] / d * inv;
+        const float2 v = part_sum(s);
+        acc.x += L * v.x;
+        acc.y += L * v.y;
+    }
+    return acc;
+}
+
 // sum_t phi_t g[(lo + t) mod n] over the 2 m_w taps of one right-hand side.
 template <int MW, typename T, typename C>
 __device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_t nmask, const T* phi) {
@@ -340,6 +380,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
                                                 const float* __restrict__ cheb32, int q, T kb_b,
                                                 const C_t<T>* __restrict__ c, int deriv,
                                                 const C_t<T>* __restrict__ rmul,
+                                                const float2* __restrict__ fpp,
                                                 C_t<T>* __restrict__ f) {
     using C = C_t<T>;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -356,19 +397,27 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     const double2 wv = ws[i];
     const double xs = XI ? 0.5 * wv.x : wv.x;
     const double x = xs - floor(xs);
+    C acc = {(T)0, (T)0};
+    bool done = false;
+    if constexpr (sizeof(T) == 4 && !XI) {
+        if (B.fused) {   // the taps were summed by pass 2
+            acc = fused_rhs_f32(fpp, B, i - B.node_off, kTwoPiD * wv.y, q, cheb32);
+            done = true;
+        }
+    }
     const double t0 = (double)B.n * x;
     const double u = floor(t0);
     const T fr = (T)(t0 - u);
     const int64_t lo = (int64_t)u - (MW - 1);
     T phi[2 * MW];
+    if (!done) {
 #pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+        for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+    }
     const int64_t nmask = B.n - 1;
     const C* g = grid + B.grid_off;
-    C acc = {(T)0, (T)0};
-    bool done = false;
     if constexpr (sizeof(T) == 4) {
-        if (B.nrhs > 1) {
+        if (!done && B.nrhs > 1) {
             acc = gather_rhs_f32<MW>(g, B, lo, nmask, phi, kTwoPiD * wv.y, q, cheb32);
             done = true;
         }
@@ -687,7 +736,16 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         for (int i = 0; i < g.count; ++i) kbytes += (double)p.bands[p.pass_items[g.start + i].band].dev.K;
         const double b1 = (double)g.count * n * sizeof(C) +
                           (MODE == 0 ? kbytes * (sizeof(C) + sizeof(T)) : (double)g.count * n * sizeof(C));
-        const double b2 = (double)g.count * 2.0 * n * sizeof(C);
+        double b2 = 0;   // Y read + grid write, or Y read + entries + partials (fused)
+        for (int i = 0; i < g.count; ++i) {
+            const BandHost& bh = p.bands[p.pass_items[g.start + i].band];
+            if (SIGN > 0 && bh.dev.fused) {
+                const int NQ = (pass_tiles(8, (g.log2n + 1) / 2, FL_P2_THREADS_F32) + 3) / 4;
+                b2 += (double)n * sizeof(C) + (double)bh.fentries * (8.0 + 16.0 * NQ + 8.0);
+            } else {
+                b2 += 2.0 * n * sizeof(C);
+            }
+        }
         int slot;
         timer_begin(p, "fft_pass1", b1, st, &slot);
         e = launch_pass1<T, SIGN, MODE, DERIV>(p.d_pass + g.start, g.count, p.d_bands, l1, l2,
@@ -697,7 +755,8 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         if (e != cudaSuccess) return e;
         timer_begin(p, "fft_pass2", b2, st, &slot);
         e = launch_pass2<T, SIGN>(p.d_pass + g.start, g.count, p.d_bands, l1, l2, (const C*)p.d_Y,
-                                  grid, (const C*)p.d_tw, st);
+                                  grid, (const C*)p.d_tw,
+                                  FuseArgs{p.d_frbs, p.d_fent, p.d_fphi, p.d_fpp}, st);
         timer_end(p, slot, st);
         p.launches += 2;
         if (e != cudaSuccess) return e;
@@ -713,16 +772,20 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
         timer_begin(p, "gather", 0.0, st, &slot);
         k_gather<T, MW, true><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
             p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C_t<T>*)p.d_grid, p.d_cheb,
-            p.d_cheb32, p.q, (T)p.kb_b, (const C_t<T>*)c, 0, nullptr, (C_t<T>*)f);
+            p.d_cheb32, p.q, (T)p.kb_b, (const C_t<T>*)c, 0, nullptr, nullptr, (C_t<T>*)f);
         timer_end(p, slot, st);
         ++p.launches;
         return cudaGetLastError();
     }
     using C = C_t<T>;
     double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(C));
-    for (int b = 1; b <= p.levels; ++b) {
+    for (int b = 1; b < (int)p.bands.size(); ++b) {
         const BandDev& B = p.bands[b].dev;
         if (B.route != 1) continue;
+        if (B.fused) {
+            bytes += (double)p.bands[b].nodes * B.nrhs * B.pparts * sizeof(C);
+            continue;
+        }
         bytes += std::min<double>((double)B.nrhs * B.n * sizeof(C),
                                   (double)p.bands[b].nodes * B.nrhs * 2 * MW * sizeof(C));
     }
@@ -730,7 +793,7 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
     timer_begin(p, "gather", bytes, st, &slot);
     k_gather<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.d_cheb32,
-        p.q, (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, (C*)f);
+        p.q, (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, p.d_fpp, (C*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();

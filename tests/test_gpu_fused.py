@@ -1,0 +1,146 @@
+"""GPU parity of the window gather fused into the FFT's second pass.
+
+With fuse_gather on, a band's grid is never written: pass 2 sums each node's
+taps over the rows of its tile into partial sums, and the gather kernel adds a
+node's partials and recombines the right-hand sides with the barycentric
+weights.  The result is the same NFFT of Algorithm 2 in another summation
+order, so each fused result is checked (a) against the plain FP64 oracle at the
+forward tests' bound, E <= eps + 32 u_32 ||f||_inf / ||c||_1, and (b) against
+the unfused plan on the same inputs to float rounding.  Sizes span four-step
+grids of 2^13 to 2^18 points (pass-2 tiles of 2 to 8 rows), ragged N, nodes on
+the cell and tile boundaries and at the grid's wrap-around, Z^0 nodes, the
+derivative and node-gradient calls, and a batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1606_03255_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def fl():
+    from paper_1606_03255_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1606_03255_gb300 import fl as flmod
+    flmod.load()
+    return flmod
+
+
+def tol(eps, fref, c):
+    return eps + 32 * U32 * np.max(np.abs(fref)) / np.sum(np.abs(c))
+
+
+def _nodes(kind, M, seed):
+    if kind == "clustered":
+        return W.nodes_circle_clustered(M, seed)
+    if kind == "disk":
+        return W.nodes_disk_uniform(M, seed)
+    # boundaries: x on multiples of 1/2^k (cell and tile edges of every grid),
+    # just below 1 (the window wraps around the grid's end) and at 0, with
+    # y spread over the bands; plus two Z^0 nodes
+    rng = np.random.default_rng(seed)
+    k = rng.integers(0, 1 << 18, M)
+    x = k / float(1 << 18)
+    x[:8] = [0.0, 1.0 - 2.0 ** -40, 1.0 - 2.0 ** -20, 0.5, 2.0 ** -18, 1.0 - 2.0 ** -18, 0.25, 0.75]
+    y = 10.0 ** (-6.0 * rng.random(M)) / (2 * np.pi)
+    y[::3] = 0.0
+    w = np.stack([x, y], axis=1)
+    return np.concatenate([w, [[0.3, 9.0], [0.9, 4.0]]])
+
+
+def _plan_run(fl, c, w, eps, fuse, route="nfft", deriv=False, r=None):
+    dev = torch.device("cuda")
+    plan = fl.Plan(len(c), torch.from_numpy(np.ascontiguousarray(w)).to(dev), eps,
+                   precision="fp32", route=route, fuse=fuse)
+    ct = torch.from_numpy(np.asarray(c)).to(torch.complex64).to(dev)
+    if r is not None:
+        f = plan.grad_w(ct, torch.from_numpy(r).to(torch.complex64).to(dev))
+    else:
+        f = plan.execute(ct, deriv=deriv)
+    torch.cuda.synchronize()
+    out = f.cpu().numpy().astype(np.complex128)
+    info = plan.info()
+    plan.close()
+    return out, info
+
+
+@pytest.mark.parametrize("kind", ["clustered", "disk", "edges"])
+@pytest.mark.parametrize("N", [5000, 40000, 70001])
+def test_fused_matches_unfused_and_oracle(fl, kind, N):
+    eps = 1e-6
+    M = 3000
+    c = W.coefficients(N, seed=N % 97)
+    w = _nodes(kind, M, seed=N % 89)
+    f_on, info_on = _plan_run(fl, c, w, eps, "on")
+    f_off, info_off = _plan_run(fl, c, w, eps, "off")
+    assert info_on["n_bands_fused"] > 0 and info_on["fused_entries"] > 0
+    assert info_off["n_bands_fused"] == 0
+    ref = oracle.flt_direct(c, w)
+    assert oracle.error_E(ref, f_on, c) <= tol(eps, ref, c)
+    # the same NFFT summed in another order: float rounding only
+    assert np.max(np.abs(f_on - f_off)) <= 64 * U32 * max(np.max(np.abs(ref)), 1.0)
+
+
+def test_fused_auto_routes(fl):
+    # by cost: a few thousand nodes on 2^18-point grids are fused, and every
+    # band with a grid of 4096 points or fewer is not
+    eps = 1e-6
+    N, M = 1 << 17, 4000
+    c = W.coefficients(N, seed=3)
+    w = W.nodes_circle_clustered(M, seed=4)
+    f, info = _plan_run(fl, c, w, eps, "auto", route="auto")
+    assert info["n_bands_fused"] > 0
+    ref = oracle.flt_direct(c, w)
+    assert oracle.error_E(ref, f, c) <= tol(eps, ref, c)
+
+
+def test_fused_derivative_and_node_gradient(fl):
+    eps = 1e-6
+    N, M = 20000, 2000
+    c = W.coefficients(N, seed=5)
+    w = W.nodes_circle_clustered(M, seed=6)
+    k = np.arange(N)
+    cd = 2j * np.pi * k * c
+    ref = oracle.flt_direct(cd, w)
+    fd, info = _plan_run(fl, c, w, eps, "on", deriv=True)
+    assert info["n_bands_fused"] > 0
+    assert oracle.error_E(ref, fd, cd) <= tol(eps, ref, cd)
+    r = W.targets(M, seed=7)
+    gw, _ = _plan_run(fl, c, w, eps, "on", r=r)
+    # gw_j = r_j conj(f'_j)
+    gref = r * np.conj(ref)
+    assert np.max(np.abs(gw - gref)) <= np.max(np.abs(r)) * tol(eps, ref, cd) * np.sum(np.abs(cd)) * 1.01
+
+
+def test_fused_batched(fl):
+    eps = 1e-6
+    dev = torch.device("cuda")
+    Ns = np.array([3000, 9000, 2500, 17000], dtype=np.int64)
+    Ms = np.array([400, 1200, 0, 900], dtype=np.int64)
+    cs = [W.coefficients(int(n), seed=40 + i) for i, n in enumerate(Ns)]
+    ws = [W.nodes_circle_clustered(int(m), seed=50 + i) for i, m in enumerate(Ms)]
+    outs = {}
+    for fuse in ("on", "off"):
+        bp = fl.BatchedPlan(Ns, Ms, torch.from_numpy(np.concatenate(ws)).to(dev), eps, fuse=fuse,
+                            route="nfft")
+        f = bp.execute(torch.from_numpy(np.concatenate(cs)).to(torch.complex64).to(dev))
+        torch.cuda.synchronize()
+        outs[fuse] = (f.cpu().numpy().astype(np.complex128), bp.info())
+        bp.close()
+    assert outs["on"][1]["n_bands_fused"] > 0 and outs["off"][1]["n_bands_fused"] == 0
+    off = 0
+    for i in range(len(Ns)):
+        m = int(Ms[i])
+        if m == 0:
+            continue
+        ref = oracle.flt_direct(cs[i], ws[i])
+        fi = outs["on"][0][off:off + m]
+        assert oracle.error_E(ref, fi, cs[i]) <= tol(eps, ref, cs[i]), i
+        assert np.max(np.abs(fi - outs["off"][0][off:off + m])) <= 64 * U32 * max(np.max(np.abs(ref)), 1.0)
+        off += m
