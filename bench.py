@@ -144,14 +144,16 @@ def pipe_peaks() -> dict:
 def method_bytes(info: dict, q: int, cs: int = 8, n_min: int = 0) -> float:
     """Bytes the method moves through the band grids per execute (the survey's
     per-unit figure): one grid write and one read per right-hand side of every
-    NFFT band, 2 cs n_m each (cs = bytes per complex); only grids above n_min."""
+    NFFT, 2 cs n each (cs = bytes per complex; a band evaluated as P sub-band
+    NFFTs has P grids of band_n points); only grids above n_min."""
     total = 0.0
     L = info["levels"]
+    parts = info.get("band_parts") or [1] * (L + 1)
     for b in range(1, L + 1):
         if info["band_route"][b] != 1 or info["band_n"][b] <= n_min:
             continue
         nrhs = 1 if b == L else q
-        total += nrhs * 2.0 * cs * info["band_n"][b]
+        total += nrhs * parts[b] * 2.0 * cs * info["band_n"][b]
     return total
 
 
@@ -736,6 +738,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": workload(N), "N": N, "M": M, "eps": EPS32, "q": info["q"],
                    "levels": info["levels"], "m_w": info["m_w"], "sigma": info["sigma"],
+                   "sigma_min": info["sigma_min"],
+                   "split_bands": {b: [pp, info["band_n"][b]] for b, pp in enumerate(info["band_parts"])
+                                   if pp > 1},
+                   "fused_bands": info["n_bands_fused"],
                    "bands_fft": info["n_bands_fft"],
                    "l2": "flushed between steps (256 MiB write); working set > L2",
                    "plan": "built once before the timed region (route bias autotuned)",

@@ -75,7 +75,7 @@ typedef struct {
     int q;                    /* interpolation rank (Definition 3.2) */
     int levels;               /* number of dyadic levels, the paper's M (Definition 3.2) */
     int m_w;                  /* Kaiser-Bessel window half-width (taps = 2 m_w) */
-    int sigma;                /* oversampling of every band grid (2) */
+    int sigma;                /* oversampling of unsplit band grids (2; see sigma_min) */
     double y1, xi1;           /* interval ends of Definition 3.2 */
     int64_t z0_nodes;         /* nodes with |z| < eps (returned as c_0) */
     int batch;                /* transforms in the plan (fl_plan_batched), else 1 */
@@ -94,6 +94,8 @@ typedef struct {
     int kernel;               /* Laplace plans: the fl_kernel */
     int n_bands_fused;        /* bands whose window gather runs inside pass 2 (fuse_gather) */
     int64_t fused_entries;    /* their (node, pass-2 row block) entries */
+    double sigma_min;         /* smallest oversampling n / K_p of the plan's grids (2 if none split) */
+    int band_parts[FL_MAX_LEVELS];    /* NFFTs per band (1, or P sub-bands of band_n points each) */
 } fl_info;
 
 /* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
@@ -168,6 +170,22 @@ typedef struct {
                              0 = for grids above 4096 points whose nodes are
                                  few for the grid (by estimated bytes; default);
                              1 = never; 2 = for every grid above 4096 points. */
+    int oversampling;     /* FL_FP32 plans whose gather can be fused (above):
+                             the oversampling sigma of a band's NFFT.
+                             0 = from the tolerance by estimated cost
+                                 (default): a band with K frequencies may be
+                                 evaluated as P NFFTs over contiguous ranges of
+                                 about K/P frequencies on power-of-two grids of
+                                 sigma K/P points, 1.25 <= sigma < 2, with the
+                                 window half-width m_w that meets eps/3 at the
+                                 smallest sigma used; a split is admitted only
+                                 while the deconvolution's gain
+                                 Phi(0)/Phi(1/(2 sigma)), which scales the FP32
+                                 rounding, stays <= 32 (so sigma >= ~1.5);
+                             1 = sigma = 2 for every band (one NFFT each);
+                             2 = every eligible band split to its fewest grid
+                                 points under the same limits, whatever the
+                                 cost.                                        */
 } fl_options;
 
 /*

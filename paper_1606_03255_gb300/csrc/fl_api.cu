@@ -148,6 +148,8 @@ static fl_status select_bands_xi(Plan& p, Instance& in, int inst_index) {
         bh.inst = inst_index;
         bh.local = b;
         bh.dev.c_off = in.noff;
+        bh.dev.parent = -1;
+        bh.dev.kb = p.kb_b;
         if (b == 0) {
             p.bands.push_back(bh);
             continue;
@@ -221,6 +223,8 @@ static fl_status select_bands(Plan& p, Instance& in, int inst_index) {
         bh.inst = inst_index;
         bh.local = b;
         bh.dev.c_off = in.noff;
+        bh.dev.parent = -1;
+        bh.dev.kb = p.kb_b;
         if (b == 0) {
             p.bands.push_back(bh);
             continue;
@@ -274,7 +278,8 @@ static int route_of(const Plan& p, const BandHost& bh) {
 
 // Four-step work items of the large bands, grouped by grid size into launches
 // of at most rhs_per_launch items (0: a whole size class) and at most
-// kMaxYElems intermediate elements; sets Y_elems.
+// kMaxYElems intermediate elements, a band's items never split between two
+// launches (a launch holding one band may exceed the cap); sets Y_elems.
 constexpr int64_t kMaxYElems = (int64_t)1 << 28;
 
 static void build_pass_groups(Plan& p) {
@@ -282,27 +287,26 @@ static void build_pass_groups(Plan& p) {
     p.pass_groups.clear();
     p.Y_elems = 0;
     for (int lg = kSmallMaxLog2 + 1; lg <= kMaxLog2n; ++lg) {
-        std::vector<PassItem> cls;
-        for (int b : p.large_bands) {
-            const BandDev& d = p.bands[b].dev;
-            if (d.log2n != lg) continue;
-            for (int s = 0; s < d.nrhs; ++s) cls.push_back({b, s, 0});
-        }
-        if (cls.empty()) continue;
         const int64_t n = (int64_t)1 << lg;
         int cap = (int)std::min<int64_t>(65535, std::max<int64_t>(1, kMaxYElems / n));
         if (p.rhs_per_launch > 0) cap = std::min(cap, p.rhs_per_launch);
-        for (size_t i0 = 0; i0 < cls.size(); i0 += cap) {
-            const int cnt = (int)std::min<size_t>(cap, cls.size() - i0);
-            PassGroup g{(int)p.pass_items.size(), cnt, lg};
-            for (int i = 0; i < cnt; ++i) {
-                PassItem it = cls[i0 + i];
-                it.y_off = (int64_t)i * n;
-                p.pass_items.push_back(it);
-            }
-            p.pass_groups.push_back(g);
+        int cnt = 0;
+        auto close = [&]() {
+            if (cnt == 0) return;
+            p.pass_groups.push_back(PassGroup{(int)p.pass_items.size() - cnt, cnt, lg});
             p.Y_elems = std::max<int64_t>(p.Y_elems, (int64_t)cnt * n);
+            cnt = 0;
+        };
+        for (int b : p.large_bands) {
+            const BandDev& d = p.bands[b].dev;
+            if (d.log2n != lg) continue;
+            if (cnt > 0 && cnt + d.nrhs > cap) close();
+            for (int s = 0; s < d.nrhs; ++s) {
+                p.pass_items.push_back({b, s, (int64_t)cnt * n});
+                ++cnt;
+            }
         }
+        close();
     }
 }
 
@@ -310,12 +314,12 @@ static void build_pass_groups(Plan& p) {
 // qualifies when its nodes are few for its grid: per right-hand side the
 // unfused path writes the grid (8 n bytes) and gathers about three 32-byte
 // sectors per node, the fused one reads its entries (8 + 16 NQ bytes: slot,
-// column, window values) and writes and later reads one partial sum per entry.
-// Each node's window of 2 m_w taps at grid indices lo .. lo + 2 m_w - 1
-// (lo = floor(n x) - m_w + 1, mod n) is cut into entries, one per pass-2 row
-// block its taps fall in (tile rows TR of the length-n1 pass, rows l2 = g mod
-// n2, column l1 = g / n2); the window values are those of the gather kernel,
-// phi_t = kb(frac(n x) + m_w - 1 - t), in FP64 rounded once.
+// column, window values) and writes and later reads one partial sum per entry.  Each node's
+// window of 2 m_w taps at grid indices lo .. lo + 2 m_w - 1 (lo = floor(n x) -
+// m_w + 1, mod n) is cut into entries, one per pass-2 row block its taps fall
+// in (tile rows TR of the length-n1 pass, rows l2 = g mod n2, column l1 = g /
+// n2); the window values are those of the gather kernel, phi_t = kb(frac(n x)
+// + m_w - 1 - t), in FP64 rounded once.
 static double kb_window_host(double t, double m, double b) {
     const double s2 = m * m - t * t;
     if (!(s2 > 0.0)) return b;
@@ -335,7 +339,7 @@ static fl_status build_fused(Plan& p, cudaStream_t st) {
         BandHost& bh = p.bands[b];
         BandDev& d = bh.dev;
         d.fused = 0;
-        if (d.route != 1 || d.log2n <= kSmallMaxLog2 || bh.nodes == 0) continue;
+        if (d.route != 1 || d.nsub > 0 || d.log2n <= kSmallMaxLog2 || bh.nodes == 0) continue;
         const int l2 = d.log2n / 2, l1 = (d.log2n + 1) / 2;
         const int TR = pass_tiles(8, l1, FL_P2_THREADS_F32);
         const int P = (taps - 1 + TR - 1) / TR + 1;
@@ -343,7 +347,8 @@ static fl_status build_fused(Plan& p, cudaStream_t st) {
         const double parts = (double)(TR + taps - 1) / TR;
         const double unfused = 8.0 * d.n + std::min<double>(8.0 * d.n, 96.0 * bh.nodes);
         const double fused = bh.nodes * parts * (8.0 + 16.0 * NQ + 8.0) + 8.0 * P * bh.nodes;
-        if (p.fuse_mode == 2 || fused <= 0.5 * unfused) cands.push_back({b, l1, l2, TR, P});
+        // sub-bands (parent >= 0) have no other gather: always fused
+        if (p.fuse_mode == 2 || d.parent >= 0 || fused <= 0.5 * unfused) cands.push_back({b, l1, l2, TR, P});
     }
     if (cands.empty()) return FL_OK;
     std::vector<double2> hw(p.M);
@@ -389,7 +394,7 @@ static fl_status build_fused(Plan& p, cudaStream_t st) {
                     es.push_back(e);
                     cur = rb;
                 }
-                es.back().w[rho % cd.TR] = (float)kb_window_host(fr + (double)(p.mw - 1 - t), (double)p.mw, p.kb_b);
+                es.back().w[rho % cd.TR] = (float)kb_window_host(fr + (double)(p.mw - 1 - t), (double)p.mw, d.kb);
             }
         }
         // bucket by row block (stable: node order within a block)
@@ -414,10 +419,11 @@ static fl_status build_fused(Plan& p, cudaStream_t st) {
             for (int qd = 0; qd < NQ; ++qd)
                 phi[q0 + k * NQ + qd] = make_float4(e.w[4 * qd], e.w[4 * qd + 1], e.w[4 * qd + 2], e.w[4 * qd + 3]);
         }
-        pp += (int64_t)d.nrhs * bh.nodes * cd.P;
+        pp += (int64_t)d.nrhs * bh.nodes * cd.P;   // per right-hand side: one slot per (node, row block)
         ++p.fused_bands;
     }
     p.fused_entries = (int64_t)ent.size();
+
     FL_CUDA(cudaMalloc((void**)&p.d_frbs, rbs.size() * sizeof(int32_t)), "cudaMalloc fused starts");
     FL_CUDA(cudaMalloc((void**)&p.d_fent, ent.size() * sizeof(int2)), "cudaMalloc fused entries");
     FL_CUDA(cudaMalloc((void**)&p.d_fphi, phi.size() * sizeof(float4)), "cudaMalloc fused windows");
@@ -432,6 +438,159 @@ static fl_status build_fused(Plan& p, cudaStream_t st) {
     FL_CUDA(cudaMemsetAsync(p.d_fpp, 0, pp * sizeof(float2), st), "clear fused partials");
     // the host vectors are released on return: finish the copies first
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
+    return FL_OK;
+}
+
+// Oversampling picked from the tolerance (FP32 forward plans).  The NFFT of a
+// band with K frequencies may be computed as P NFFTs over contiguous
+// sub-ranges of about K/P frequencies, each centred on its own range and
+// evaluated on a power-of-two grid n >= sigma_min K_p: e.g. K = 2^20 as 3
+// grids of 2^19 points (sigma = 1.5) or 5 of 2^18 (sigma = 1.25) instead of
+// one of 2^21 (sigma = 2) -- linearity of A~ in its frequency columns.  The
+// window half-width m_w is the smallest meeting the Kaiser-Bessel estimate at
+// eps/3 for the smallest sigma used (one m_w for the plan, every band at least
+// as accurate); each grid gets the window shape b = pi (2 - 1/sigma) of its
+// own sigma.  Split bands always gather inside pass 2 (see build_fused), so
+// only bands that qualify for that are candidates.  For each floor sigma_min
+// in {2, 1.75, 1.5, 1.25} every band takes its cheapest split with sigma >=
+// sigma_min by an estimate of issued instructions (FFT points x (log2 n + 8),
+// fused entries and partial sums, the unfused gather's taps and window
+// values, at the m_w of sigma_min); the cheapest floor wins, and m_w is then
+// set for the smallest sigma it actually chose.
+static double fft_cost(int nrhs, int64_t n, int log2n) { return (double)nrhs * n * (log2n + 8); }
+
+// FP32 rounding of a band grid is amplified by the deconvolution: the weights
+// 1/Phi(nu) of the highest frequency (nu = 1/(2 sigma)) exceed those of the
+// lowest by Phi(0)/Phi(1/(2 sigma)) ~ exp(m_w (b - sqrt(b^2 - (pi/sigma)^2))),
+// b = pi (2 - 1/sigma): about 4 at sigma = 2 (m_w = 5), 29 at sigma = 1.5
+// (m_w = 6), 300 at sigma = 1.31 (m_w = 7).  Sub-bands are used only where
+// it stays <= 32, the factor the FP32 error bound allows for rounding.
+constexpr double kMaxDeconvGain = 32.0;
+
+static double deconv_gain(double sigma, int mw) {
+    const double b = M_PI * (2.0 - 1.0 / sigma), v = M_PI / sigma;
+    return exp((double)mw * (b - sqrt(b * b - v * v)));
+}
+
+static double fused_cost(int64_t nodes, int log2n, int mw) {   // per right-hand side
+    const int TR = pass_tiles(8, (log2n + 1) / 2, FL_P2_THREADS_F32);
+    const double entries = (double)nodes * (TR + 2 * mw - 1) / TR;
+    const int parts = (2 * mw - 1 + TR - 1) / TR + 1;
+    return entries * 24.0 + (double)nodes * parts * 6.0;
+}
+
+static double unfused_cost(int64_t nodes, int nrhs, int mw) {
+    return (double)nodes * ((double)nrhs * 2 * mw * 2 + 2.0 * mw * 20.0);
+}
+
+struct SplitChoice {
+    int P = 1, log2n = 0;
+    int64_t Kp = 0, Nc = 0;
+};
+
+// Best split of band bh at sigma_min >= smin with window half-width mw
+// (P = 1: unsplit); force: fewest grid points regardless of the gather.
+static SplitChoice best_split(const Plan& p, const BandHost& bh, double smin, int mw, bool force,
+                             double* cost) {
+    const BandDev& d = bh.dev;
+    SplitChoice best;
+    const bool four_step = d.log2n > kSmallMaxLog2;
+    double c1 = fft_cost(d.nrhs, d.n, d.log2n) +
+                (four_step ? std::min(d.nrhs * fused_cost(bh.nodes, d.log2n, mw), unfused_cost(bh.nodes, d.nrhs, mw))
+                           : unfused_cost(bh.nodes, d.nrhs, mw));
+    double bc = force ? (double)d.n : c1;
+    const bool eligible = smin < 2.0 && four_step && p.prec == FL_FP32 && !p.xi_mode && p.fuse_mode != 1 &&
+                          bh.nodes > 0;
+    // (the window shape and gain are those of the candidate's own sigma)
+    if (eligible) {
+        for (int P = 2; P <= 9; ++P) {
+            const int64_t Kp = (d.K + P - 1) / P;
+            const int64_t Nc = Kp + (Kp & 1);
+            const int lg = ilog2_ceil((int64_t)ceil(smin * (double)Nc));
+            if (lg <= kSmallMaxLog2 || lg > kMaxLog2n) continue;
+            const int64_t n = (int64_t)1 << lg;
+            if ((double)n >= 2.0 * (double)Nc) continue;   // no gain over sigma = 2
+            // the half-width this sigma needs, and the FP32 limit at it
+            const int mc = std::max(mw, window_width(p.eps_A, (double)n / (double)Nc));
+            if (deconv_gain((double)n / (double)Nc, mc) > kMaxDeconvGain) continue;
+            const double c = force ? (double)P * n
+                                   : P * (fft_cost(d.nrhs, n, lg) + d.nrhs * fused_cost(bh.nodes, lg, mc));
+            if (c < bc) {
+                bc = c;
+                best.P = P;
+                best.log2n = lg;
+                best.Kp = Kp;
+                best.Nc = Nc;
+            }
+        }
+    }
+    *cost = best.P == 1 ? c1 : (force ? 0.0 : bc);
+    return best;
+}
+
+static fl_status plan_splits(Plan& p, const std::vector<int>& nfft, cudaStream_t st) {
+    p.sigma_min = 2.0;
+    if (p.sigma_mode == 1 || p.prec != FL_FP32 || p.xi_mode || p.fuse_mode == 1) return FL_OK;
+    // (sigma_mode 2: every eligible band takes its split of fewest grid points)
+    const double cands[4] = {2.0, 1.75, 1.5, 1.25};   // floors (1.25: only where the gain allows)
+    double best_total = 0.0;
+    std::vector<SplitChoice> best_ch;
+    for (double smin : cands) {
+        if (p.sigma_mode == 2 && smin != 1.25) continue;   // the lowest floor, fewest grid points
+        const int mw = p.mw;   // sigma = 2; a split's own sigma may need more (best_split)
+        std::vector<SplitChoice> ch;
+        double total = 0.0;
+        for (int b : nfft) {
+            double c = 0.0;
+            ch.push_back(best_split(p, p.bands[b], smin, mw, p.sigma_mode >= 2, &c));
+            total += c;
+        }
+        if (best_ch.empty() || total < best_total) {
+            best_total = total;
+            best_ch = ch;
+        }
+    }
+    bool any = false;
+    double smin_used = 2.0;   // the smallest sigma actually chosen fixes m_w
+    for (const SplitChoice& c : best_ch)
+        if (c.P > 1) {
+            any = true;
+            smin_used = std::min(smin_used, ldexp(1.0, c.log2n) / (double)c.Nc);
+        }
+    if (!any) return FL_OK;
+    p.mw = std::max(p.mw, window_width(p.eps_A, smin_used));
+    p.sigma_min = smin_used;
+    for (size_t i = 0; i < nfft.size(); ++i) {
+        const SplitChoice c = best_ch[i];
+        if (c.P == 1) continue;
+        const int b = nfft[i];
+        const int shift = p.bands[b].dev.log2n - c.log2n;   // node cells at the sub-band grid
+        const int64_t n = (int64_t)1 << c.log2n;
+        const double kb = M_PI * (2.0 - (double)c.Nc / (double)n);
+        const int sub0 = (int)p.bands.size();
+        for (int s = 0; s < c.P; ++s) {
+            BandHost ch = p.bands[b];
+            const int64_t k0 = s * c.Kp;
+            ch.dev.parent = b;
+            ch.dev.nsub = 0;
+            ch.dev.k0 = k0;
+            ch.dev.K = std::min<int64_t>(c.Kp, p.bands[b].dev.K - k0);
+            ch.dev.Nm = c.Nc;
+            ch.dev.n = n;
+            ch.dev.log2n = c.log2n;
+            ch.dev.kb = kb;
+            ch.dev.c_off = p.bands[b].dev.c_off + k0;
+            p.bands.push_back(ch);
+        }
+        BandDev& d = p.bands[b].dev;
+        d.nsub = c.P;
+        d.sub0 = sub0;
+        d.n = n;
+        d.log2n = c.log2n;
+        d.kb = kb;
+        cudaError_t e = launch_cell_shift(p.d_cell, p.bands[b].node_off, p.bands[b].nodes, shift, st);
+        if (e != cudaSuccess) return cuda_fail(e, "fl_plan: sub-band cells");
+    }
     return FL_OK;
 }
 
@@ -461,7 +620,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.M = moff;
     p.levels = p.inst[0].levels;
     p.xi1 = p.inst[0].xi1;
-    const int nb = (int)p.bands.size();
+    int nb = (int)p.bands.size();
     FL_CUDA(cudaMalloc((void**)&p.d_bands, nb * sizeof(BandDev)), "cudaMalloc bands");
     std::vector<BandDev> hb(nb);
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
@@ -534,6 +693,7 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.z0_nodes = 0;
     std::vector<DirectItem> small_items;
     std::vector<DirectAdjItem> small_adj;
+    std::vector<int> nfft_bands;   // bands evaluated by an NFFT, in order
     for (int i = 0; i < B; ++i) {
         Instance& in = p.inst[i];
         in.z0_nodes = counts[in.band_base];
@@ -585,7 +745,16 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                 }
                 continue;
             }
-            if (d.route != 1) continue;
+            if (d.route == 1) nfft_bands.push_back(b);
+        }
+    }
+    // oversampling from the tolerance: split sparse bands into sub-bands
+    if ((s = plan_splits(p, nfft_bands, st)) != FL_OK) return s;
+    for (int b : nfft_bands) {
+        const int nsub = p.bands[b].dev.nsub;
+        for (int c = 0; c < std::max(1, nsub); ++c) {
+            const int g = nsub > 0 ? p.bands[b].dev.sub0 + c : b;
+            BandDev& d = p.bands[g].dev;
             d.grid_off = p.grid_elems;
             p.grid_elems += (int64_t)d.nrhs * d.n;
             if (p.xi_mode) {
@@ -602,9 +771,9 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
                 // 4096 points per CTA (256 threads x 16); n = 32 at 8 points per thread
                 const int per = std::max(1, (int)((d.log2n >= 6 ? 4096 : 2048) / d.n));
                 for (int s0 = 0; s0 < d.nrhs; s0 += per)
-                    p.small_work.push_back({b, s0, std::min(per, d.nrhs - s0), d.log2n});
+                    p.small_work.push_back({g, s0, std::min(per, d.nrhs - s0), d.log2n});
             } else {
-                p.large_bands.push_back(b);
+                p.large_bands.push_back(g);
             }
         }
     }
@@ -615,6 +784,14 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     p.dadj_work64.insert(p.dadj_work64.end(), small_adj.begin(), small_adj.end());
     build_pass_groups(p);
     if ((s = build_fused(p, st)) != FL_OK) return s;
+    if ((int)p.bands.size() != nb) {   // sub-bands were appended: a larger table
+        FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
+        FL_CUDA(cudaFree(p.d_bands), "cudaFree bands");
+        p.d_bands = nullptr;
+        nb = (int)p.bands.size();
+        hb.resize(nb);
+        FL_CUDA(cudaMalloc((void**)&p.d_bands, nb * sizeof(BandDev)), "cudaMalloc bands");
+    }
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
@@ -663,14 +840,14 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
         auto dense = [&](const BandHost& bh) { return bh.nodes * 2 * p.mw >= 32 * bh.dev.n; };
         for (int b = 0; b < nb; ++b) {
             const BandDev& d = p.bands[b].dev;
-            if (d.route != 1 || dense(p.bands[b])) continue;
+            if (d.route != 1 || d.nsub > 0 || dense(p.bands[b])) continue;
             p.cell_bands.push_back({b, 0, p.cells_total});
             p.cells_total += d.n;
         }
         p.n_sparse_cb = (int)p.cell_bands.size();
         for (int b = 0; b < nb; ++b) {
             const BandDev& d = p.bands[b].dev;
-            if (d.route != 1 || !dense(p.bands[b])) continue;
+            if (d.route != 1 || d.nsub > 0 || !dense(p.bands[b])) continue;
             p.cell_bands.push_back({b, 0, p.cells_dense});
             p.cells_dense += d.n;
         }
@@ -708,10 +885,10 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     double mb = (double)p.N * cs + (double)p.D_elems * rs + (double)M * (sizeof(double2) + 8 + cs);
     for (int b = 0; b < nb; ++b) {
         const BandDev& d = p.bands[b].dev;
-        if (d.route != 1) continue;
+        if (d.route != 1 || d.nsub > 0) continue;   // split bands: their sub-bands
         const double g = (double)d.nrhs * d.n * cs;
         if (d.fused) {   // Y write + read; entries read, partials written and gathered
-            const int NQ = (d.pparts > 0) ? (pass_tiles(8, (d.log2n + 1) / 2, FL_P2_THREADS_F32) + 3) / 4 : 1;
+            const int NQ = (pass_tiles(8, (d.log2n + 1) / 2, FL_P2_THREADS_F32) + 3) / 4;
             mb += 2.0 * g + (double)d.nrhs * p.bands[b].fentries * (8.0 + 16.0 * NQ + 8.0) +
                   (double)d.nrhs * p.bands[b].nodes * d.pparts * cs;
             continue;
@@ -740,6 +917,7 @@ struct PlanSpec {
     bool use_graph;
     int variant;
     int fuse_mode;
+    int sigma_mode;
 };
 
 static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cudaStream_t st) {
@@ -755,6 +933,7 @@ static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cu
     h->p.use_graph = sp.use_graph;
     h->p.variant = sp.variant;
     h->p.fuse_mode = sp.fuse_mode;
+    h->p.sigma_mode = sp.sigma_mode;
     fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, st);
     if (s != FL_OK) {
         delete h;
@@ -933,7 +1112,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     g_err.clear();
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
                 opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
-                opt->fuse_gather < 0 || opt->fuse_gather > 2))
+                opt->fuse_gather < 0 || opt->fuse_gather > 2 || opt->oversampling < 0 ||
+                opt->oversampling > 2))
         return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
@@ -947,7 +1127,7 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
     PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
                  opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false,
-                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -1109,11 +1289,12 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
     if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
     if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
                 opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
-                opt->fuse_gather < 0 || opt->fuse_gather > 2))
+                opt->fuse_gather < 0 || opt->fuse_gather > 2 || opt->oversampling < 0 ||
+                opt->oversampling > 2))
         return fail(FL_EINVAL, "fl_plan_batched: invalid options");
     PlanSpec sp{B, N_host, M_host, nodes_dev, q, eps, prec, true, opt ? opt->route : 0,
                  opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true,
-                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -1152,7 +1333,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->batch = p.batched ? (int)p.inst.size() : 1;
     if (p.kind == 0) {   // bands of all transforms: routes counted over the batch
         for (const BandHost& bh : p.bands) {
-            if (bh.local == 0) continue;
+            if (bh.local == 0 || bh.dev.parent >= 0) continue;   // sub-bands count with their band
             if (bh.dev.route == 1) ++info->n_bands_fft;
             if (bh.dev.route == 2) ++info->n_bands_direct;
         }
@@ -1165,6 +1346,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
         info->band_nodes[b] = bh.nodes;
         info->band_K[b] = bh.dev.K;
         info->band_n[b] = bh.dev.n;
+        info->band_parts[b] = bh.dev.nsub > 0 ? bh.dev.nsub : 1;
     }
     info->model_bytes = p.model_bytes;
     info->direct_bias = p.tuned_bias > 0 ? p.tuned_bias : p.direct_bias;
@@ -1173,6 +1355,7 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->kernel = p.kind == 1 ? p.lap_kernel : 0;
     info->n_bands_fused = (int)p.fused_bands;
     info->fused_entries = p.fused_entries;
+    info->sigma_min = p.sigma_min;
     return FL_OK;
 }
 

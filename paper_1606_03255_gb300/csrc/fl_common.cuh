@@ -175,6 +175,19 @@ struct BandDev {
     int64_t rbs_off;   // offset of the band's row-block starts (n2 / rows-per-CTA + 1 of them)
     int64_t pp_off;    // offset of the band's partial sums (nrhs x nodes x pparts complex)
     int64_t ph_off;    // offset (in float4) of the band's entry window values
+    // Oversampling below 2: a band whose frequencies 0..K-1 are split into
+    // nsub contiguous sub-bands, each its own NFFT on a power-of-two grid of
+    // n = sigma K_p points (sigma < 2).  The band keeps its nodes (band ids
+    // point to it) but has no grid; its sub-bands are bands[sub0 ..
+    // sub0 + nsub) with parent = the band, frequencies k0 .. k0 + K - 1, the
+    // band's nodes, and the centre frequency k0 + Nm/2.  A split band's n,
+    // log2n and kb are its sub-bands' (the grid of the node cells).
+    int64_t k0;        // first frequency of a sub-band (0 otherwise)
+    int nsub;          // > 0: split band (no grid of its own)
+    int sub0;          // first sub-band of a split band
+    int parent;        // sub-band: its band; -1 otherwise
+    int pad3;
+    double kb;         // Kaiser-Bessel shape b = pi (2 - 1/sigma) of this band's grid
 };
 
 // ---------------------------------------------------------------------------

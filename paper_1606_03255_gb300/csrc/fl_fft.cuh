@@ -37,8 +37,8 @@ __device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
     if (k < 0 || k >= B.K) return C_t<T>{(T)0, (T)0};
     const T d = D[B.D_off + (int64_t)s * B.K + k];
     C_t<T> v = c[k];
-    if (DERIV) {   // (2 pi i k) c_k; float: k < 2^24 exact, one rounding
-        const T w = deriv_weight<T>(k);
+    if (DERIV) {   // (2 pi i k) c_k at the global frequency; float: k < 2^24 exact, one rounding
+        const T w = deriv_weight<T>(k + B.k0);
         v = C_t<T>{-v.y * w, v.x * w};
     }
     return C_t<T>{v.x * d, v.y * d};
@@ -47,9 +47,10 @@ __device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
 // Same with 32-bit grid indices and the band's c/D base pointers resolved,
 // branch-free: the index is clamped into [0, K) so the loads are always in
 // bounds and a thread's loads can all be in flight together; frequencies
-// outside [0, K) are then replaced by zero.
+// outside [0, K) are then replaced by zero.  k0: the band's first frequency
+// (sub-bands; c is already offset by it).
 template <typename T, bool DERIV>
-__device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K,
+__device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K, int k0,
                                                const C_t<T>* __restrict__ c,
                                                const T* __restrict__ Ds) {
     const int kp = (i < (n >> 1)) ? i : i - n;
@@ -59,7 +60,7 @@ __device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K,
     const T d = Ds[kk];
     C_t<T> v = c[kk];
     if (DERIV) {
-        const T w = deriv_weight<T>(kk);
+        const T w = deriv_weight<T>(kk + k0);
         v = C_t<T>{-v.y * w, v.x * w};
     }
     return in ? C_t<T>{v.x * d, v.y * d} : C_t<T>{(T)0, (T)0};
@@ -377,15 +378,24 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
     C v[16];
     if constexpr (MODE == 0) {
         const T* Ds = D + B.D_off + (int64_t)s * B.K;
-        const int K = (int)B.K, half = (int)(B.Nm >> 1);
-        // i2 = t + r L/16 in [n2/4, 3 n2/4) (r = 4..11) holds grid indices in
-        // [n/4, 3n/4): centred frequencies with k >= N_m or k < 0, always zero
+        const int K = (int)B.K, half = (int)(B.Nm >> 1), k0 = (int)B.k0;
+        // with sigma = 2 (half <= n/4 and K - half <= n/4), i2 = t + r L/16 in
+        // [n2/4, 3 n2/4) (r = 4..11) holds grid indices in [n/4, 3n/4):
+        // centred frequencies outside the band, always zero (a sub-band at
+        // sigma < 2 reaches into them)
+        if (4 * half <= n && 4 * (K - half) <= n) {
 #pragma unroll
-        for (int r = 0; r < 16; ++r)
-            v[r] = (r >= 4 && r < 12)
-                       ? C{(T)0, (T)0}
-                       : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K,
-                                                c + B.c_off, Ds);
+            for (int r = 0; r < 16; ++r)
+                v[r] = (r >= 4 && r < 12)
+                           ? C{(T)0, (T)0}
+                           : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, k0,
+                                                    c + B.c_off, Ds);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; ++r)
+                v[r] = prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, k0,
+                                              c + B.c_off, Ds);
+        }
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
 #pragma unroll

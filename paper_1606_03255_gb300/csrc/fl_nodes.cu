@@ -206,4 +206,17 @@ cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, con
     return cudaGetLastError();
 }
 
+__global__ void k_cell_shift(int32_t* __restrict__ cell, int64_t n, int shift) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cell[i] >>= shift;
+}
+
+// floor(x n) >> s = floor(x n / 2^s) for the power-of-two grid sizes n: the
+// cells of the smaller grid, and the sorted order is kept.
+cudaError_t launch_cell_shift(int32_t* cell, int64_t off, int64_t n, int shift, cudaStream_t st) {
+    if (n == 0 || shift == 0) return cudaSuccess;
+    k_cell_shift<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cell + off, n, shift);
+    return cudaGetLastError();
+}
+
 }  // namespace fl

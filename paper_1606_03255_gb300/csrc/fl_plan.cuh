@@ -165,6 +165,8 @@ struct Plan {
     std::vector<PassGroup> pass_groups;
     int rhs_per_launch = 0;        // four-step items per launch (0 = a whole size class)
     int fuse_mode = 0;             // window gather in pass 2: 0 by cost, 1 never, 2 wherever possible
+    int sigma_mode = 0;            // oversampling: 0 by cost, 1 sigma = 2, 2 sub-bands wherever allowed
+    double sigma_min = 2.0;        // smallest oversampling of the plan's grids
     int route_mode = 0;            // 0 by cost, 1 all NFFT, 2 all direct
     int variant = 0;               // 0 Algorithm 2 weights, 1 one-sided interpolation
     // real exponents xi_k >= 1 (fl_plan_xi): the Fourier factor is an NNFFT
@@ -282,6 +284,8 @@ cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
                              cudaStream_t st);
 cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, const uint32_t* keys,
                            const int32_t* vals, cudaStream_t st);
+// cell[off .. off + n) >>= shift (node cells of a band moved to a grid 2^shift times smaller)
+cudaError_t launch_cell_shift(int32_t* cell, int64_t off, int64_t n, int shift, cudaStream_t st);
 
 // Launchers (fl_transform.cu)
 cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st);

@@ -91,11 +91,11 @@ __global__ void k_weights(BandDev B, int ellm, int Lm, int q, double xi1, int le
                           T* __restrict__ D) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= B.K) return;
-    const double xk = xis ? xis[k] : (double)k;
+    const double xk = xis ? xis[k] : (double)(B.k0 + k);   // the band's (sub-band's) frequency
     double inv_phi = 1.0;
-    if (!xis) {
+    if (!xis) {   // the window of this grid: shape B.kb (kb_b for sigma = 2)
         const double nu = (double)(k - B.Nm / 2) / (double)B.n;
-        const double arg = kb_b * kb_b - (kTwoPiD * nu) * (kTwoPiD * nu);
+        const double arg = B.kb * B.kb - (kTwoPiD * nu) * (kTwoPiD * nu);
         inv_phi = 1.0 / (kPi * cyl_bessel_i0((double)mw * sqrt(fmax(arg, 0.0))));
     }
     // entry s of frequency k at Dk[s * ds]
@@ -164,9 +164,13 @@ static cudaError_t build_tables_t(Plan& p, const Instance& in, cudaStream_t st) 
             k_coupling<<<(unsigned)((nk + 255) / 256), 256, 0, st>>>(p.y1, in.xi1, lb, bh.ell, bh.Lm,
                                                                      p.q, p.d_cheb, Kt);
         }
-        k_weights<T><<<(unsigned)((bh.dev.K + 255) / 256), 256, 0, st>>>(
-            bh.dev, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, p.variant,
-            p.xi_mode ? p.d_xis : nullptr, (T*)p.d_D);
+        // a split band: the weights of each sub-band's frequencies (same coupling blocks)
+        for (int c = 0; c < std::max(1, bh.dev.nsub); ++c) {
+            const BandDev& d = bh.dev.nsub > 0 ? p.bands[bh.dev.sub0 + c].dev : bh.dev;
+            k_weights<T><<<(unsigned)((d.K + 255) / 256), 256, 0, st>>>(
+                d, bh.ell, bh.Lm, p.q, in.xi1, in.levels, p.d_cheb, Kt, p.mw, p.kb_b, p.variant,
+                p.xi_mode ? p.d_xis : nullptr, (T*)p.d_D);
+        }
     }
     e = cudaGetLastError();
     if (Kt) {
@@ -352,6 +356,23 @@ __device__ __forceinline__ float2 fused_rhs_f32(const float2* __restrict__ pp, c
     return acc;
 }
 
+// A split band (B.nsub > 0): the sum over its sub-bands S of
+// exp(2 pi i kc_S x) times S's recombined partial sums, kc_S = S.k0 + S.Nm/2
+// the sub-band's centre frequency (kc_S x mod 1 split exactly in FP64).
+__device__ __forceinline__ float2 split_rhs_f32(const float2* __restrict__ pp,
+                                                const BandDev* __restrict__ bands, const BandDev& B,
+                                                int64_t jl, double y, double x, int q,
+                                                const float* __restrict__ cheb32) {
+    float2 acc = {0.f, 0.f};
+    for (int c = 0; c < B.nsub; ++c) {
+        const BandDev S = bands[B.sub0 + c];
+        const float2 a = fused_rhs_f32(pp, S, jl, y, q, cheb32);
+        const double ph = frac_turns((double)(S.k0 + (S.Nm >> 1)), x);
+        acc = cadd(acc, cmul(a, expipi<float>((float)(2.0 * ph))));
+    }
+    return acc;
+}
+
 // sum_t phi_t g[(lo + t) mod n] over the 2 m_w taps of one right-hand side.
 template <int MW, typename T, typename C>
 __device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_t nmask, const T* phi) {
@@ -400,6 +421,11 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     C acc = {(T)0, (T)0};
     bool done = false;
     if constexpr (sizeof(T) == 4 && !XI) {
+        if (B.nsub > 0) {   // sub-bands: their centre phases replace the centring shift
+            const C v = split_rhs_f32(fpp, bands, B, i - B.node_off, kTwoPiD * wv.y, x, q, cheb32);
+            f[j] = rmul ? cmulc(rmul[j], v) : v;
+            return;
+        }
         if (B.fused) {   // the taps were summed by pass 2
             acc = fused_rhs_f32(fpp, B, i - B.node_off, kTwoPiD * wv.y, q, cheb32);
             done = true;
@@ -484,7 +510,9 @@ __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* _
     const double x = xs - floor(xs);
     const double t0 = (double)B.n * x;
     const T fr = (T)(t0 - floor(t0));
-    if constexpr (XI) {
+    if (B.nsub > 0) {   // split band: each sub-band applies its own centre phase
+        sp_rv[i] = r[perm[i]];
+    } else if constexpr (XI) {
         const double ph = frac_turns(B.xc, wv.x);
         const T v = (T)(kTwoPiD * 0.5 * wv.x);
         const T arg = kb_b * kb_b - v * v;
@@ -500,9 +528,10 @@ __global__ void __launch_bounds__(256) k_spread_prep(int64_t M, const double2* _
         if (ph >= 0.5) ph -= 1.0;
         sp_rv[i] = cmulc(r[perm[i]], expipi<T>((T)(2.0 * ph)));
     }
+    const T kb = XI ? kb_b : (T)B.kb;   // the window shape of the band's grid
 #pragma unroll
     for (int t = 0; t < 2 * MW; ++t)
-        sp_phi[i * (2 * MW) + t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+        sp_phi[i * (2 * MW) + t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb);
     if (B.nrhs > 1) {
         T Ls[kMaxQ];
         bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
@@ -531,9 +560,12 @@ __device__ __forceinline__ void spread_cell_sum(const BandDev& B, int64_t l,
                                                 const int32_t* __restrict__ cell,
                                                 const T* __restrict__ sp_phi,
                                                 const T* __restrict__ sp_L,
-                                                const C_t<T>* __restrict__ sp_rv, int q,
+                                                const C_t<T>* __restrict__ sp_rv,
+                                                const double2* __restrict__ ws, int q,
                                                 int lane, int stride, C_t<T>* acc) {
     using C = C_t<T>;
+    // a sub-band: node j's value carries exp(-2 pi i kc x_j), kc its centre
+    const double kc = (double)(B.k0 + (B.Nm >> 1));
     const int64_t n = B.n, nb0 = B.node_off, nend = B.node_off + B.nodes;
     int64_t ra[2][2];
     int nrange = 0;
@@ -557,7 +589,11 @@ __device__ __forceinline__ void spread_cell_sum(const BandDev& B, int64_t l,
         for (int64_t j = j0 + lane; j < j1; j += stride) {
             int64_t t = (l - cell[j] + MW - 1) % n;
             if (t < 0) t += n;
-            const C w = cscale(sp_rv[j], sp_phi[j * (2 * MW) + t]);
+            C w = cscale(sp_rv[j], sp_phi[j * (2 * MW) + t]);
+            if (B.parent >= 0) {
+                const double xj = ws[j].x - floor(ws[j].x);
+                w = cmul(w, expipi<T>((T)(-2.0 * frac_turns(kc, xj))));
+            }
             if (nr == 1) {
                 acc[0] = cadd(acc[0], w);
             } else {
@@ -590,7 +626,8 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
                                                       const int32_t* __restrict__ cell,
                                                       const T* __restrict__ sp_phi,
                                                       const T* __restrict__ sp_L,
-                                                      const C_t<T>* __restrict__ sp_rv, int q,
+                                                      const C_t<T>* __restrict__ sp_rv,
+                                                      const double2* __restrict__ ws, int q,
                                                       C_t<T>* __restrict__ grid) {
     using C = C_t<T>;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -600,7 +637,7 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
     const int64_t l = g - cbs[cb].prefix;
     C acc[kMaxQ];
     for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
-    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, 0, 1, acc);
+    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, ws, q, 0, 1, acc);
     C* gb = grid + B.grid_off + l;
     for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = acc[s];
 }
@@ -617,7 +654,8 @@ __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, con
                                                                     const int32_t* __restrict__ cell,
                                                                     const T* __restrict__ sp_phi,
                                                                     const T* __restrict__ sp_L,
-                                                                    const C_t<T>* __restrict__ sp_rv, int q,
+                                                                    const C_t<T>* __restrict__ sp_rv,
+                                                                    const double2* __restrict__ ws, int q,
                                                                     C_t<T>* __restrict__ grid) {
     using C = C_t<T>;
     __shared__ C red[kSpreadDense / 32][kMaxQ];
@@ -629,7 +667,7 @@ __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, con
     const int64_t l = g - cbs[cb].prefix;
     C acc[kMaxQ];
     for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
-    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, q, threadIdx.x, kSpreadDense, acc);
+    spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, ws, q, threadIdx.x, kSpreadDense, acc);
     for (int s = 0; s < B.nrhs; ++s) {
         T x = acc[s].x, y = acc[s].y;
 #pragma unroll
@@ -684,10 +722,18 @@ __global__ void k_combine(int64_t N, int levels, const BandDev* __restrict__ ban
     C acc = (k == 0) ? *z0sum : C{(T)0, (T)0};
     if (cdir) acc = cadd(acc, cdir[k]);
     for (int b = 1; b <= levels; ++b) {
-        const BandDev B = bands[b];
+        BandDev B = bands[b];
         if (B.route != 1 || k >= B.K) continue;
-        const int64_t i = (k - (B.Nm >> 1)) & (B.n - 1);
-        const T* Dk = D + B.D_off + k;
+        for (int c = 0; c < B.nsub; ++c) {   // split band: the sub-band holding k
+            const BandDev S = bands[B.sub0 + c];
+            if (k >= S.k0 && k < S.k0 + S.K) {
+                B = S;
+                break;
+            }
+        }
+        const int64_t kl = k - B.k0;   // frequency within the (sub-)band
+        const int64_t i = (kl - (B.Nm >> 1)) & (B.n - 1);
+        const T* Dk = D + B.D_off + kl;
         const C* g = grid + B.grid_off + i;
         for (int s = 0; s < B.nrhs; ++s) {
             const T d = Dk[(int64_t)s * B.K];
@@ -739,7 +785,7 @@ static cudaError_t fft_bands(Plan& p, const void* c, cudaStream_t st) {
         double b2 = 0;   // Y read + grid write, or Y read + entries + partials (fused)
         for (int i = 0; i < g.count; ++i) {
             const BandHost& bh = p.bands[p.pass_items[g.start + i].band];
-            if (SIGN > 0 && bh.dev.fused) {
+            if (SIGN > 0 && MODE == 0 && bh.dev.fused) {   // Y read; entries read, partials written
                 const int NQ = (pass_tiles(8, (g.log2n + 1) / 2, FL_P2_THREADS_F32) + 3) / 4;
                 b2 += (double)n * sizeof(C) + (double)bh.fentries * (8.0 + 16.0 * NQ + 8.0);
             } else {
@@ -781,7 +827,7 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
     double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(C));
     for (int b = 1; b < (int)p.bands.size(); ++b) {
         const BandDev& B = p.bands[b].dev;
-        if (B.route != 1) continue;
+        if (B.route != 1 || B.nsub > 0) continue;
         if (B.fused) {
             bytes += (double)p.bands[b].nodes * B.nrhs * B.pparts * sizeof(C);
             continue;
@@ -974,12 +1020,12 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     if (p.cells_total > 0)
         k_spread_cells<T, MW><<<(unsigned)((p.cells_total + 255) / 256), 256, 0, st>>>(
             (int)p.n_sparse_cb, p.d_cell_bands, p.cells_total, p.d_bands, p.d_cell,
-            (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
+            (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.d_ws, p.q, (C*)p.d_grid);
     if (p.cells_dense > 0)
         k_spread_cells_warp<T, MW><<<(unsigned)p.cells_dense, kSpreadDense, 0, st>>>(
             (int)(p.cell_bands.size() - p.n_sparse_cb), p.d_cell_bands + p.n_sparse_cb,
             p.cells_dense, p.d_bands, p.d_cell, (const T*)p.d_sp_phi, (const T*)p.d_sp_L,
-            (const C*)p.d_sp_rv, p.q, (C*)p.d_grid);
+            (const C*)p.d_sp_rv, p.d_ws, p.q, (C*)p.d_grid);
     timer_end(p, slot, st);
     p.launches += 1 + (p.cells_total > 0) + (p.cells_dense > 0);
     return cudaGetLastError();

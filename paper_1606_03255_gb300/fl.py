@@ -57,6 +57,7 @@ class fl_info(ctypes.Structure):
         ("model_bytes", ctypes.c_double), ("direct_bias", ctypes.c_double),
         ("scratch_bytes", ctypes.c_double), ("variant", ctypes.c_int), ("kernel", ctypes.c_int),
         ("n_bands_fused", ctypes.c_int), ("fused_entries", ctypes.c_int64),
+        ("sigma_min", ctypes.c_double), ("band_parts", ctypes.c_int * FL_MAX_LEVELS),
     ]
 
 
@@ -64,12 +65,14 @@ class fl_options(ctypes.Structure):
     _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
                 ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("variant", ctypes.c_int),
-                ("fuse_gather", ctypes.c_int)]
+                ("fuse_gather", ctypes.c_int), ("oversampling", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
 # window gather inside the FFT's second pass (FP32 forward): by cost, never, always
 FUSE = {"auto": 0, "off": 1, "on": 2}
+# oversampling of the band grids: by cost, 2 everywhere, sub-bands wherever allowed
+SIGMA = {"auto": 0, "2": 1, "min": 2}
 # band weights: Algorithm 2 (two-sided interpolation) or the one-sided variant
 VARIANTS = {"alg2": 0, "onesided": 1}
 # kernels of fl_plan_kernel (generalised Algorithm 1)
@@ -321,6 +324,7 @@ def info_dict(info: fl_info) -> dict:
         "variant": {v: k for k, v in VARIANTS.items()}.get(info.variant, info.variant),
         "kernel": {v: k for k, v in KERNELS.items()}.get(info.kernel, info.kernel),
         "n_bands_fused": info.n_bands_fused, "fused_entries": info.fused_entries,
+        "sigma_min": info.sigma_min, "band_parts": list(info.band_parts[:nb]),
     }
 
 
@@ -344,7 +348,7 @@ class Plan:
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
                  rhs_per_launch: int = 0, use_graph: bool = False, autotune: bool = False,
-                 variant: str = "alg2", fuse: str = "auto"):
+                 variant: str = "alg2", fuse: str = "auto", sigma: str = "auto"):
         torch = _torch()
         if nodes.is_complex():
             nodes = torch.view_as_real(nodes.to(torch.complex128))
@@ -355,7 +359,7 @@ class Plan:
         self.cdtype = torch.complex64 if self.prec == FL_FP32 else torch.complex128
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch), int(bool(use_graph)),
-                         int(bool(autotune)), VARIANTS[variant], FUSE[fuse])
+                         int(bool(autotune)), VARIANTS[variant], FUSE[fuse], SIGMA[str(sigma)])
         st, h = fl_plan_ex(self.N, self.M, _ptr(nodes) if self.M else None, q, eps, self.prec,
                            opt, _stream_handle(stream))
         check(st, "fl_plan")
@@ -451,7 +455,7 @@ class BatchedPlan:
     def __init__(self, Ns, Ms, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
                  rhs_per_launch: int = 0, use_graph: bool = True, autotune: bool = False,
-                 variant: str = "alg2", fuse: str = "auto"):
+                 variant: str = "alg2", fuse: str = "auto", sigma: str = "auto"):
         torch = _torch()
         nodes = nodes.to(torch.float64).contiguous()
         self.Ns = [int(x) for x in Ns]
@@ -461,7 +465,8 @@ class BatchedPlan:
         self.cdtype = torch.complex64 if self.prec == FL_FP32 else torch.complex128
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
-                         1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant], FUSE[fuse])
+                         1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant], FUSE[fuse],
+                         SIGMA[str(sigma)])
         st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
                                 self.prec, opt, _stream_handle(stream))
         check(st, "fl_plan_batched")

@@ -56,3 +56,15 @@ def test_traffic_only_for_the_captured_sources_and_size(tmp_path, monkeypatch):
     (tmp_path / "paper_1606_03255_gb300" / "csrc" / "k.cu").write_text("kernel v2\n")
     assert bench.source_hash() != h1
     assert bench.ncu_traffic("fft_pass1", 1 << 20) is None       # sources changed since
+
+
+def test_method_bytes_counts_every_grid_once_per_rhs():
+    # 16 n bytes (complex64: one write and one read) per right-hand side of
+    # every NFFT; a band split into P sub-bands has P grids of band_n points;
+    # direct and empty bands add nothing; the last band has one right-hand side
+    info = {"levels": 4, "band_route": [0, 1, 2, 1, 1], "band_n": [0, 1 << 10, 1 << 12, 1 << 13, 1 << 14],
+            "band_parts": [1, 1, 1, 3, 1]}
+    q = 5
+    expect = q * 16 * (1 << 10) + q * 3 * 16 * (1 << 13) + 1 * 16 * (1 << 14)
+    assert bench.method_bytes(info, q) == expect
+    assert bench.method_bytes(info, q, n_min=4096) == q * 3 * 16 * (1 << 13) + 16 * (1 << 14)
