@@ -67,6 +67,8 @@ def parse():
                     help="comma-separated secondary workloads to run: " + ", ".join(SECONDARY))
     ap.add_argument("--case", default=None, choices=sorted(CASES),
                     help="run one small case only (for kernel profiling): " + ", ".join(sorted(CASES)))
+    ap.add_argument("--save", default=None,
+                    help="with --case: write the case's output vector to this .npy file")
     args = ap.parse_args()
     bad = set(args.workloads.split(",")) - set(SECONDARY)
     if bad:
@@ -444,7 +446,7 @@ def secondary_workloads(dev, flush, rank, names=SECONDARY):
 
 
 CASES = ("disk_2e18_fp32", "disk_2e18_fp64", "adjoint_2e18_fp32", "laplace_2e16_fp64",
-         "laplace_2e16_fp32", "flt_2e20_fp32", "flt_2e18_fp32")
+         "laplace_2e16_fp32", "flt_2e20_fp32", "flt_2e20_fp64ff", "flt_2e18_fp32")
 
 
 def run_case(args):
@@ -470,7 +472,7 @@ def run_case(args):
         N = M = 1 << (20 if "2e20" in name else 18)
         prec = name.rsplit("_", 1)[1]
         cdt = torch.complex64 if prec == "fp32" else torch.complex128
-        if name.startswith("flt"):
+        if name.startswith("flt"):   # the headline inputs (c rounded to complex64 for every form)
             c_np, w_np = rank_workload(N, 0)
         else:
             c_np, w_np = W.coefficients(N, seed=0), W.nodes_disk_uniform(M, seed=200)
@@ -488,6 +490,8 @@ def run_case(args):
         run()
     torch.cuda.synchronize()
     ms = _time_cuda(run, args.steps)
+    if args.save:
+        np.save(args.save, out.cpu().numpy())
     p.close()
     print(json.dumps({"case": name, "ms": ms, "steps": args.steps, "warmup": args.warmup}), flush=True)
     return 0
