@@ -43,7 +43,7 @@ Plan::~Plan() {
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
                     d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm, d_ts, d_tbs,
                     d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi, d_xcs, d_xsb,
-                    d_frbs, d_fent, d_fphi, d_fpp};
+                    d_frbs, d_fent, d_fphi, d_fpp, d_ntab};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -795,6 +795,10 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     for (int b = 0; b < nb; ++b) hb[b] = p.bands[b].dev;
     FL_CUDA(cudaMemcpyAsync(p.d_bands, hb.data(), nb * sizeof(BandDev), cudaMemcpyHostToDevice, st),
             "copy bands");
+    if (p.prec == FL_FP32 && !p.xi_mode && p.M > 0) {
+        FL_CUDA(cudaMalloc((void**)&p.d_ntab, p.M * sizeof(uint4)), "cudaMalloc node records");
+        FL_CUDA(build_node_table(p, st), "fl_plan: node records");
+    }
     // complex128 I/O for FP64 and float pairs; real tables double or float pairs
     const size_t cs = p.prec != FL_FP32 ? 16 : 8, rs = cs / 2;
     if (!p.small_work.empty()) {

@@ -198,6 +198,8 @@ struct Plan {
     int32_t* d_perm = nullptr;     // sorted position -> original index
     int32_t* d_bandid = nullptr;   // band (global index) of each sorted node
     int32_t* d_cell = nullptr;     // grid cell floor(n_m x) of each sorted node
+    uint4* d_ntab = nullptr;       // FP32 plans: per sorted node x 2^64 (64-bit fixed point) and
+                                   // the barycentric tau of its band as a float pair
     void* d_sp_phi = nullptr;      // adjoint: window taps per node (M x 2 m_w, T)
     void* d_sp_L = nullptr;        // adjoint: barycentric weights per node (M x q, T)
     void* d_sp_rv = nullptr;       // adjoint: shifted residual per node (M, complex T)
@@ -289,6 +291,7 @@ cudaError_t launch_cell_shift(int32_t* cell, int64_t off, int64_t n, int shift, 
 
 // Launchers (fl_transform.cu)
 cudaError_t build_tables(Plan& p, const Instance& in, cudaStream_t st);
+cudaError_t build_node_table(Plan& p, cudaStream_t st);   // d_ntab (FP32 forward gather)
 cudaError_t build_cheb(Plan& p, cudaStream_t st);
 cudaError_t build_twiddles(Plan& p, cudaStream_t st);
 // rmul != nullptr: f[j] = rmul[j] * conj(result_j) (the node-gradient epilogue)

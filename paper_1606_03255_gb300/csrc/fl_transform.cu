@@ -235,6 +235,31 @@ cudaError_t build_twiddles(Plan& p, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Per sorted node of an FP32 plan: X = x 2^64 with x = Re w mod 1 (exact for
+// x >= 2^-11, within 2^-64 below), and tau = (2 pi Im w - y_c) / y_h of its
+// band as a float pair (hi = tau rounded, lo = the rest), for gather_node_f32.
+__global__ void k_node_tab(int64_t M, const double2* __restrict__ ws, const int32_t* __restrict__ bandid,
+                           const BandDev* __restrict__ bands, uint4* __restrict__ tab) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const uint64_t X = (uint64_t)ldexp(x, 64);
+    const BandDev B = bands[bandid[i]];
+    float th = 0.f, tl = 0.f;
+    if (B.nrhs > 1) {
+        const double tau = (kTwoPiD * wv.y - B.yc) * B.yh_inv;
+        th = (float)tau;
+        tl = (float)(tau - (double)th);
+    }
+    tab[i] = make_uint4((unsigned)X, (unsigned)(X >> 32), __float_as_uint(th), __float_as_uint(tl));
+}
+
+cudaError_t build_node_table(Plan& p, cudaStream_t st) {
+    k_node_tab<<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(p.M, p.d_ws, p.d_bandid, p.d_bands, p.d_ntab);
+    return cudaGetLastError();
+}
+
 cudaError_t build_cheb(Plan& p, cudaStream_t st) {
     k_cheb<<<1, 64, 0, st>>>(p.q, p.d_cheb, p.d_cheb32);
     return cudaGetLastError();
@@ -276,9 +301,8 @@ __device__ __forceinline__ void bary_weights(double y, const BandDev& B, int q,
 template <int MW>
 __device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, const BandDev& B,
                                                  int64_t lo, int64_t nmask, const float* phi,
-                                                 double y, int q, const float* __restrict__ cheb32) {
-    const double tau = (y - B.yc) * B.yh_inv;
-    const float th = (float)tau, tl = (float)(tau - (double)th);
+                                                 float th, float tl, int q,
+                                                 const float* __restrict__ cheb32) {
     float den = 0.f;
     int hit = -1;
     for (int s = 0; s < q; ++s) {
@@ -316,11 +340,24 @@ __device__ __forceinline__ float2 gather_rhs_f32(const float2* __restrict__ g, c
     return acc;
 }
 
+// sum_t phi_t g[(lo + t) mod n] over the 2 m_w taps of one right-hand side.
+template <int MW, typename T, typename C>
+__device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_t nmask, const T* phi) {
+    C a = {(T)0, (T)0};
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) {
+        const C v = g[(lo + t) & nmask];
+        a.x += phi[t] * v.x;
+        a.y += phi[t] * v.y;
+    }
+    return a;
+}
+
 // FP32 recombination of a node of a fused band (see k_pass2): its partial tap
 // sums a_s = sum_p pp[s][jl P + p] over the row blocks its window spans, with
 // the barycentric weights of gather_rhs_f32 (one right-hand side: a_0).
 __device__ __forceinline__ float2 fused_rhs_f32(const float2* __restrict__ pp, const BandDev& B,
-                                                int64_t jl, double y, int q,
+                                                int64_t jl, float th, float tl, int q,
                                                 const float* __restrict__ cheb32) {
     const int P = B.pparts;
     const float2* a = pp + B.pp_off + jl * P;
@@ -335,8 +372,6 @@ __device__ __forceinline__ float2 fused_rhs_f32(const float2* __restrict__ pp, c
         return v;
     };
     if (B.nrhs == 1) return part_sum(0);
-    const double tau = (y - B.yc) * B.yh_inv;
-    const float th = (float)tau, tl = (float)(tau - (double)th);
     float den = 0.f;
     int hit = -1;
     for (int s = 0; s < q; ++s) {
@@ -356,34 +391,61 @@ __device__ __forceinline__ float2 fused_rhs_f32(const float2* __restrict__ pp, c
     return acc;
 }
 
+// k x mod 1 in turns, in [-1/2, 1/2), for x held as the 64-bit fixed-point
+// X = x 2^64 (exact) and an integer k: the wrapped product k X mod 2^64, whose
+// top 24 bits as a signed value are the turns to 2^-24 (float resolution).
+__device__ __forceinline__ float fixed_turns(uint64_t X, uint64_t k) {
+    return (float)((int64_t)(k * X) >> 40) * 0x1p-24f;
+}
+
 // A split band (B.nsub > 0): the sum over its sub-bands S of
 // exp(2 pi i kc_S x) times S's recombined partial sums, kc_S = S.k0 + S.Nm/2
-// the sub-band's centre frequency (kc_S x mod 1 split exactly in FP64).
+// the sub-band's centre frequency.
 __device__ __forceinline__ float2 split_rhs_f32(const float2* __restrict__ pp,
                                                 const BandDev* __restrict__ bands, const BandDev& B,
-                                                int64_t jl, double y, double x, int q,
+                                                int64_t jl, float th, float tl, uint64_t X, int q,
                                                 const float* __restrict__ cheb32) {
     float2 acc = {0.f, 0.f};
     for (int c = 0; c < B.nsub; ++c) {
         const BandDev S = bands[B.sub0 + c];
-        const float2 a = fused_rhs_f32(pp, S, jl, y, q, cheb32);
-        const double ph = frac_turns((double)(S.k0 + (S.Nm >> 1)), x);
-        acc = cadd(acc, cmul(a, expipi<float>((float)(2.0 * ph))));
+        const float2 a = fused_rhs_f32(pp, S, jl, th, tl, q, cheb32);
+        const float ph = fixed_turns(X, (uint64_t)(S.k0 + (S.Nm >> 1)));
+        acc = cadd(acc, cmul(a, expipi<float>(2.f * ph)));
     }
     return acc;
 }
 
-// sum_t phi_t g[(lo + t) mod n] over the 2 m_w taps of one right-hand side.
-template <int MW, typename T, typename C>
-__device__ __forceinline__ C tap_sum(const C* __restrict__ g, int64_t lo, int64_t nmask, const T* phi) {
-    C a = {(T)0, (T)0};
+// The FP32 gather of one node from its plan-time record (x as X = x 2^64,
+// the barycentric coordinate tau = (y - y_c) / y_h as a float pair): every
+// phase reduction -- the grid cell and its fraction floor/frac(n x), the
+// centring shift (N_m/2) x mod 1, a sub-band's kc x mod 1 -- is an exact
+// shift or wrapped product of X, so no FP64 arithmetic runs per node.
+template <int MW>
+__device__ __forceinline__ float2 gather_node_f32(const uint4 nd, int64_t jl, const BandDev& B,
+                                                  const BandDev* __restrict__ bands,
+                                                  const float2* __restrict__ grid,
+                                                  const float* __restrict__ cheb32, int q, float kb_b,
+                                                  const float2* __restrict__ fpp) {
+    const uint64_t X = ((uint64_t)nd.y << 32) | nd.x;
+    const float th = __uint_as_float(nd.z), tl = __uint_as_float(nd.w);
+    if (B.nsub > 0) return split_rhs_f32(fpp, bands, B, jl, th, tl, X, q, cheb32);
+    float2 acc;
+    if (B.fused) {
+        acc = fused_rhs_f32(fpp, B, jl, th, tl, q, cheb32);
+    } else {
+        const int64_t u = (int64_t)(X >> (64 - B.log2n));
+        const float fr = (float)((X << B.log2n) >> 40) * 0x1p-24f;
+        const int64_t lo = u - (MW - 1);
+        float phi[2 * MW];
 #pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) {
-        const C v = g[(lo + t) & nmask];
-        a.x += phi[t] * v.x;
-        a.y += phi[t] * v.y;
+        for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<float>(fr + (float)(MW - 1 - t), (float)MW, kb_b);
+        const float2* g = grid + B.grid_off;
+        const int64_t nmask = B.n - 1;
+        acc = B.nrhs > 1 ? gather_rhs_f32<MW>(g, B, lo, nmask, phi, th, tl, q, cheb32)
+                         : tap_sum<MW>(g, lo, nmask, phi);
     }
-    return a;
+    // centring shift exp(2 pi i (N_m/2) x), N_m a power of two
+    return cmul(acc, expipi<float>(2.f * fixed_turns(X, (uint64_t)(B.Nm >> 1))));
 }
 
 // Gather + barycentric recombination + centring shift, one thread per node in
@@ -402,6 +464,7 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
                                                 const C_t<T>* __restrict__ c, int deriv,
                                                 const C_t<T>* __restrict__ rmul,
                                                 const float2* __restrict__ fpp,
+                                                const uint4* __restrict__ ntab,
                                                 C_t<T>* __restrict__ f) {
     using C = C_t<T>;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -415,40 +478,32 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     }
     // with rmul: f[j] = rmul[j] * conj(value) (node gradient, see fl_grad_w)
     if (B.route != 1) return;   // direct-route band: written by k_direct_reduce
+    if constexpr (sizeof(T) == 4 && !XI) {
+        const C v = gather_node_f32<MW>(ntab[i], i - B.node_off, B, bands, grid, cheb32, q, kb_b, fpp);
+        f[j] = rmul ? cmulc(rmul[j], v) : v;
+        return;
+    }
     const double2 wv = ws[i];
     const double xs = XI ? 0.5 * wv.x : wv.x;
     const double x = xs - floor(xs);
     C acc = {(T)0, (T)0};
-    bool done = false;
-    if constexpr (sizeof(T) == 4 && !XI) {
-        if (B.nsub > 0) {   // sub-bands: their centre phases replace the centring shift
-            const C v = split_rhs_f32(fpp, bands, B, i - B.node_off, kTwoPiD * wv.y, x, q, cheb32);
-            f[j] = rmul ? cmulc(rmul[j], v) : v;
-            return;
-        }
-        if (B.fused) {   // the taps were summed by pass 2
-            acc = fused_rhs_f32(fpp, B, i - B.node_off, kTwoPiD * wv.y, q, cheb32);
-            done = true;
-        }
-    }
     const double t0 = (double)B.n * x;
     const double u = floor(t0);
     const T fr = (T)(t0 - u);
     const int64_t lo = (int64_t)u - (MW - 1);
     T phi[2 * MW];
-    if (!done) {
 #pragma unroll
-        for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
-    }
+    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
     const int64_t nmask = B.n - 1;
     const C* g = grid + B.grid_off;
-    if constexpr (sizeof(T) == 4) {
-        if (!done && B.nrhs > 1) {
-            acc = gather_rhs_f32<MW>(g, B, lo, nmask, phi, kTwoPiD * wv.y, q, cheb32);
-            done = true;
+    if constexpr (sizeof(T) == 4) {   // XI (real exponents) in FP32
+        if (B.nrhs > 1) {
+            const double tau = (kTwoPiD * wv.y - B.yc) * B.yh_inv;
+            const float th = (float)tau, tl = (float)(tau - (double)th);
+            acc = gather_rhs_f32<MW>(g, B, lo, nmask, phi, th, tl, q, cheb32);
+        } else {
+            acc = tap_sum<MW>(g, lo, nmask, phi);
         }
-    }
-    if (done) {
     } else if (B.nrhs == 1) {
         acc = tap_sum<MW>(g, lo, nmask, phi);
     } else if constexpr (sizeof(T) == 8) {
@@ -818,7 +873,7 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
         timer_begin(p, "gather", 0.0, st, &slot);
         k_gather<T, MW, true><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
             p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C_t<T>*)p.d_grid, p.d_cheb,
-            p.d_cheb32, p.q, (T)p.kb_b, (const C_t<T>*)c, 0, nullptr, nullptr, (C_t<T>*)f);
+            p.d_cheb32, p.q, (T)p.kb_b, (const C_t<T>*)c, 0, nullptr, nullptr, nullptr, (C_t<T>*)f);
         timer_end(p, slot, st);
         ++p.launches;
         return cudaGetLastError();
@@ -839,7 +894,7 @@ static cudaError_t gather_t(Plan& p, const void* c, void* f, bool deriv, const v
     timer_begin(p, "gather", bytes, st, &slot);
     k_gather<T, MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)p.d_grid, p.d_cheb, p.d_cheb32,
-        p.q, (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, p.d_fpp, (C*)f);
+        p.q, (T)p.kb_b, (const C*)c, deriv ? 1 : 0, (const C*)rmul, p.d_fpp, p.d_ntab, (C*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
