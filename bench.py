@@ -256,24 +256,26 @@ def error_E(ref, approx, c) -> float:
     return float(np.max(np.abs(ref - approx)) / np.sum(np.abs(c)))
 
 
-def _time_cuda(fn, reps, flush=None):
-    """Mean milliseconds of fn() over reps calls, CUDA events, optional L2 flush between."""
+def _time_cuda(fn, reps, flush=None, stream=None):
+    """Mean milliseconds of fn() over reps calls, CUDA events (on `stream`, else the
+    current stream), optional L2 flush between."""
     import torch
     ts = []
     for _ in range(reps):
         if flush is not None:
             flush.zero_()
+            torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record()
+        a.record(stream)
         fn()
-        b.record()
+        b.record(stream)
         torch.cuda.synchronize()
         ts.append(a.elapsed_time(b))
     return float(np.mean(ts))
 
 
-SECONDARY = ("disk_1024", "laplace", "batched", "gradients", "real_exponents")
+SECONDARY = ("disk_1024", "laplace", "batched", "shared_nodes", "gradients", "real_exponents")
 
 
 def secondary_workloads(dev, flush, rank, names=SECONDARY):
@@ -391,7 +393,48 @@ def secondary_workloads(dev, flush, rank, names=SECONDARY):
                               "sum_N_i": int(Ns.sum()), "sum_NiMi": evals,
                               "bands_fft": info_b["n_bands_fft"], "bands_direct": info_b["n_bands_direct"],
                               "autotuned_direct_bias": info_b["direct_bias"],
+                              "autotuned": {k: info_b[k] for k in ("oversampling", "fuse_gather",
+                                                                   "rhs_per_launch")},
                               "separate_plans": "512 fl_plan + fl_execute, plain launches, default routes"}
+    if want("shared_nodes"):
+        # 64 coefficient vectors of N = 2^16 on one set of M = 2^16 disk-uniform nodes,
+        # FP32, eps = 1e-6: a batched plan over the shared node set (one sort, one
+        # weight table) against the same batch with the nodes repeated per transform
+        # and against 64 executes of one single plan
+        B, N = 64, 1 << 16
+        w = torch.from_numpy(W.nodes_disk_uniform(N, seed=400 + rank)).to(dev)
+        cb = torch.from_numpy(np.concatenate([W.coefficients(N, seed=500 + i) for i in range(B)])
+                              .astype(np.complex64)).to(dev)
+        fb = torch.empty(B * N, dtype=torch.complex64, device=dev)
+        res = {"B": B, "N": N, "M": N, "unit": "ms"}
+        for mode in ("shared", "repeated"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if mode == "shared":
+                bp = fl.BatchedPlan([N] * B, None, w, 1e-6, shared_nodes=True)
+            else:
+                bp = fl.BatchedPlan([N] * B, [N] * B, w.repeat(B, 1), 1e-6)
+            torch.cuda.synchronize()
+            res[f"plan_s_{mode}"] = time.perf_counter() - t0
+            with torch.cuda.stream(s):
+                for _ in range(3):
+                    bp.execute(cb, out=fb)
+            s.synchronize()
+            res[f"ms_{mode}"] = _time_cuda(lambda: bp.execute(cb, out=fb, stream=s), 10, flush, stream=s)
+            res[f"scratch_GB_{mode}"] = bp.info()["scratch_bytes"] / 1e9
+            bp.close()
+        sp = fl.Plan(N, w, 1e-6)
+
+        def run_single():
+            for i in range(B):
+                sp.execute(cb[i * N:(i + 1) * N], out=fb[i * N:(i + 1) * N])
+        for _ in range(2):
+            run_single()
+        res["ms_single_plan_loop"] = _time_cuda(run_single, 5, flush)
+        sp.close()
+        res["value"] = B * float(N) * N / (res["ms_shared"] * 1e-3)
+        res["value_unit"] = "evals/s"
+        out[f"shared_nodes_{B}x2^16"] = res
     if want("gradients"):
         # gradients: N = M = 2^18, disk-uniform, FP32 (eps 1e-7), loss sum |f - g|^2
         N = M = 1 << 18

@@ -45,7 +45,9 @@ typedef enum {
     FL_EINVAL = 1,        /* invalid argument (sizes, eps, Im w < 0, NaN ...) */
     FL_ENOMEM = 2,        /* device or host allocation failed                 */
     FL_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed      */
-    FL_ETIMEOUT = 4,      /* a bounded device-side wait gave up               */
+    FL_ETIMEOUT = 4,      /* reserved: no kernel of this library waits on
+                             another (every launch's work is independent of
+                             the others in flight), so no call returns it    */
     FL_EUNSUPPORTED = 5   /* size or parameter outside what is implemented    */
 } fl_status;
 
@@ -55,11 +57,14 @@ typedef enum {
  * coefficient weights and twiddles are rounded once from FP64 to pairs, and
  * the window gather, barycentric recombination and direct bands also run in
  * pairs (exponential, sincospi, square root and division written for pairs),
- * with the phases n x mod 1 reduced exactly in double.  Forward only:
- * fl_plan, fl_plan_ex and fl_plan_batched accept it, with fl_execute,
- * fl_execute_host and fl_execute_batched; fl_adjoint,
- * fl_transposed, fl_execute_deriv and fl_grad_w return FL_EUNSUPPORTED on
- * such a plan, and the other plan calls reject it with FL_EINVAL. */
+ * with the phases n x mod 1 reduced exactly in double.  fl_plan, fl_plan_ex
+ * and fl_plan_batched accept it, with fl_execute, fl_execute_host and
+ * fl_execute_batched, and on single plans fl_execute_deriv and fl_grad_w
+ * (Algorithm 2 on the k-weighted coefficients 2 pi i k c_k, formed in double
+ * and rounded to pairs) and fl_adjoint and fl_transposed (the spreading,
+ * direct bands and the final weighting sum_s D[s][k] b_s in double, the
+ * spread grids rounded to pairs for the sign -1 FFTs in pairs).  The other
+ * plan calls reject it with FL_EINVAL. */
 typedef enum { FL_FP32 = 0, FL_FP64 = 1, FL_FP64_FF = 2 } fl_precision;
 
 #define FL_MAX_LEVELS 128
@@ -96,6 +101,11 @@ typedef struct {
     int64_t fused_entries;    /* their (node, pass-2 row block) entries */
     double sigma_min;         /* smallest oversampling n / K_p of the plan's grids (2 if none split) */
     int band_parts[FL_MAX_LEVELS];    /* NFFTs per band (1, or P sub-bands of band_n points each) */
+    int rhs_per_launch;       /* grids per four-step launch pair (0 = all of a size) */
+    int oversampling;         /* fl_options.oversampling the plan was built with */
+    int fuse_gather;          /* fl_options.fuse_gather the plan was built with */
+    int autotuned;            /* 1 if the settings above and direct_bias came from
+                                 the autotuner (fl_options.autotune)            */
 } fl_info;
 
 /* Per-kernel timing gathered while timing is enabled (fl_set_timing). */
@@ -186,6 +196,12 @@ typedef struct {
                              2 = every eligible band split to its fewest grid
                                  points under the same limits, whatever the
                                  cost.                                        */
+    int shared_nodes;     /* fl_plan_batched only: 1 = every transform takes
+                             the same M_0 nodes (nodes_dev holds M_0 rows and
+                             every M_i must equal M_0; N_i may differ).  The
+                             nodes are classified and sorted once per distinct
+                             N_i, and transforms of equal N_i share one weight
+                             table D; 0 = one node set per transform.         */
 } fl_options;
 
 /*
@@ -200,7 +216,8 @@ fl_status fl_plan_ex(fl_plan_t *out, int64_t N, int64_t M, const double *nodes_d
  * fl_plan_batched -- one plan for B independent transforms of sizes
  * N_host[i] x M_host[i] (host arrays), i < B, with the same eps, q and
  * precision.  nodes_dev holds the nodes of transform 0, then 1, ... (sum M_i
- * rows of {Re w, Im w}, float64).  Every kernel launch of fl_execute_batched
+ * rows of {Re w, Im w}, float64), or with fl_options.shared_nodes the M_0
+ * rows that every transform shares.  Every kernel launch of fl_execute_batched
  * covers all B transforms (one global band table; the four-step FFTs of all
  * transforms of one grid size share a launch), and the launches are captured
  * in a CUDA graph and replayed (see fl_options.use_graph).  Forward only.

@@ -599,7 +599,7 @@ static fl_status plan_splits(Plan& p, const std::vector<int>& nfft, cudaStream_t
 // entry of one global band table, and each kernel launch of fl_execute covers
 // all transforms at once.
 static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms,
-                            const double* nodes, int q, cudaStream_t st) {
+                            const double* nodes, int q, bool shared, cudaStream_t st) {
     fl_status s = select_common(p, q);
     if (s != FL_OK) return s;
     p.bands.clear();
@@ -611,6 +611,11 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
         in.M = Ms[i];
         in.noff = noff;
         in.moff = moff;
+        in.src_off = shared ? 0 : moff;
+        // a shared node set: the first transform of the same N is sorted, the
+        // others copy its order (same bands, cells and routes)
+        for (int j = 0; shared && j < i && in.twin < 0; ++j)
+            if (Ns[j] == in.N) in.twin = j;
         noff += in.N;
         moff += in.M;
         maxM = std::max(maxM, in.M);
@@ -659,6 +664,10 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             (e = cudaMemsetAsync(dflag, 0, sizeof(int), st)) == cudaSuccess) {
             for (int i = 0; i < B && e == cudaSuccess; ++i) {
                 const Instance& in = p.inst[i];
+                if (in.twin >= 0) {
+                    e = launch_copy_sorted(p, in, p.inst[in.twin], st);
+                    continue;
+                }
                 if ((e = launch_classify(p, in, nodes, keys, vals, dcount, dflag, st)) == cudaSuccess &&
                     (e = radix_sort_pairs(keys, vals, keys2, vals2, hist, in.M, 32, st)) == cudaSuccess)
                     e = launch_permute(p, in, nodes, keys, vals, st);
@@ -676,6 +685,10 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
         }
         cleanup();
         if (e != cudaSuccess) return cuda_fail(e, "fl_plan: node classification");
+        for (const Instance& in : p.inst)
+            if (in.twin >= 0)
+                for (int lb = 0; lb <= in.levels; ++lb)
+                    counts[in.band_base + lb] = counts[p.inst[in.twin].band_base + lb];
     }
 
     // routes, offsets and work lists
@@ -750,14 +763,25 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     }
     // oversampling from the tolerance: split sparse bands into sub-bands
     if ((s = plan_splits(p, nfft_bands, st)) != FL_OK) return s;
+    // a transform that copies its twin's nodes shares its twin's weight tables
+    // (same N, bands and splits); shares_D[i] records that every band did
+    std::vector<char> shares_D(B, 0);
+    for (int i = 0; i < B; ++i) shares_D[i] = p.inst[i].twin >= 0 && !p.xi_mode;
     for (int b : nfft_bands) {
         const int nsub = p.bands[b].dev.nsub;
+        const Instance& in = p.inst[p.bands[b].inst];
+        const int tb = in.twin >= 0 ? b - in.band_base + p.inst[in.twin].band_base : -1;
+        const bool twin_ok = tb >= 0 && p.bands[tb].dev.route == 1 && p.bands[tb].dev.nsub == nsub &&
+                             p.bands[tb].dev.K == p.bands[b].dev.K;
+        if (tb >= 0 && !twin_ok) shares_D[p.bands[b].inst] = 0;
         for (int c = 0; c < std::max(1, nsub); ++c) {
             const int g = nsub > 0 ? p.bands[b].dev.sub0 + c : b;
             BandDev& d = p.bands[g].dev;
             d.grid_off = p.grid_elems;
             p.grid_elems += (int64_t)d.nrhs * d.n;
-            if (p.xi_mode) {
+            if (twin_ok && !p.xi_mode) {
+                d.D_off = p.bands[nsub > 0 ? p.bands[tb].dev.sub0 + c : tb].dev.D_off;
+            } else if (p.xi_mode) {
                 // exponent-major rows of whole spreading chunks, 16-byte aligned
                 d.dld = d.nrhs == 1 ? 1 : (d.nrhs + p.xqc - 1) / p.xqc * p.xqc;
                 p.D_elems = (p.D_elems + 3) & ~(int64_t)3;
@@ -879,7 +903,8 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
     if (p.prec == FL_FP64_FF)
         FL_CUDA(cudaMalloc(&p.d_cff, (size_t)p.N * sizeof(ffc)), "cudaMalloc float-pair coefficients");
     FL_CUDA(build_cheb(p, st), "fl_plan: tables");
-    for (int i = 0; i < B; ++i) FL_CUDA(build_tables(p, p.inst[i], st), "fl_plan: tables");
+    for (int i = 0; i < B; ++i)
+        if (!shares_D[i]) FL_CUDA(build_tables(p, p.inst[i], st), "fl_plan: tables");
     FL_CUDA(cudaStreamSynchronize(st), "fl_plan: synchronise");
     p.scratch_bytes = (double)p.grid_elems * cs + (double)p.D_elems * rs + (double)p.Y_elems * cs +
                       (double)M * (sizeof(double2) + 8) + (double)p.dpart_elems * cs +
@@ -922,6 +947,7 @@ struct PlanSpec {
     int variant;
     int fuse_mode;
     int sigma_mode;
+    bool shared_nodes;
 };
 
 static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cudaStream_t st) {
@@ -938,7 +964,7 @@ static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cu
     h->p.variant = sp.variant;
     h->p.fuse_mode = sp.fuse_mode;
     h->p.sigma_mode = sp.sigma_mode;
-    fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, st);
+    fl_status s = plan_multi(h->p, sp.B, sp.Ns, sp.Ms, sp.nodes, sp.q, sp.shared_nodes, st);
     if (s != FL_OK) {
         delete h;
         return s;
@@ -947,16 +973,24 @@ static fl_status build_plan(const PlanSpec& sp, double bias, fl_plan_s** out, cu
     return FL_OK;
 }
 
-// Route-bias autotuner: plans the workload for each candidate bias, times
-// three executes of each (CUDA events on the caller's stream, after one
-// warm-up, on zero coefficients: the work does not depend on the values), and
-// keeps the fastest.  The choice is cached for the process by a signature of
-// the workload (sizes, eps, precision and the node count of every band), so
-// planning the same workload again costs one plan.
-static std::vector<std::pair<uint64_t, double>> g_tuned;
+// Autotuner: plans the workload for candidate settings, times three executes
+// of each (CUDA events on the caller's stream, after one warm-up, on zero
+// coefficients: the work does not depend on the values), and keeps the
+// fastest.  Coordinate search, each setting from the best so far: the route
+// bias (route 0), then -- where the caller left them at their defaults -- the
+// oversampling (sigma from the tolerance or 2), the fused gather (by cost or
+// never) and the grids per four-step launch.  The choice is cached for the
+// process by a signature of the workload (sizes, eps, precision, the caller's
+// settings and the node count of every band), so planning the same workload
+// again costs one plan.
+struct Tuned {
+    double bias;
+    int sigma_mode, fuse_mode, rhs;
+};
+static std::vector<std::pair<uint64_t, Tuned>> g_tuned;
 static std::mutex g_tuned_mutex;
 
-static uint64_t plan_signature(const Plan& p) {
+static uint64_t plan_signature(const Plan& p, const PlanSpec& sp) {
     uint64_t h = 1469598103934665603ull;
     auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
     mix((uint64_t)p.N);
@@ -968,6 +1002,11 @@ static uint64_t plan_signature(const Plan& p) {
     mix(e);
     mix((uint64_t)p.q);
     mix((uint64_t)p.variant);
+    mix((uint64_t)sp.route_mode);
+    mix((uint64_t)sp.sigma_mode);
+    mix((uint64_t)sp.fuse_mode);
+    mix((uint64_t)sp.rhs_per_launch);
+    for (const Instance& in : p.inst) mix((uint64_t)(in.twin + 1));
     for (const BandHost& bh : p.bands) mix((uint64_t)bh.nodes * 131 + (uint64_t)bh.local);
     return h;
 }
@@ -999,28 +1038,49 @@ static fl_status time_plan(Plan& p, cudaStream_t st, double* ms) {
     return FL_OK;
 }
 
+static PlanSpec with_tuned(const PlanSpec& sp, const Tuned& t) {
+    PlanSpec r = sp;
+    r.sigma_mode = t.sigma_mode;
+    r.fuse_mode = t.fuse_mode;
+    r.rhs_per_launch = t.rhs;
+    return r;
+}
+
+static void set_tuned(Plan& p, const Tuned& t) {
+    p.tuned_bias = t.bias;
+    p.tuned_sigma_mode = t.sigma_mode;
+    p.tuned_fuse_mode = t.fuse_mode;
+    p.tuned_rhs = t.rhs;
+}
+
 static fl_status build_plan_tuned(const PlanSpec& sp, double bias, bool autotune, fl_plan_s** out,
                                   cudaStream_t st) {
     fl_plan_s* h = nullptr;
     fl_status s = build_plan(sp, bias, &h, st);
-    if (s != FL_OK || !autotune || sp.route_mode != 0) {
+    if (s != FL_OK || !autotune) {
         *out = h;
         return s;
     }
-    const uint64_t sig = plan_signature(h->p);
-    double cached = 0.0;
+    const uint64_t sig = plan_signature(h->p, sp);
+    const Tuned start{bias, sp.sigma_mode, sp.fuse_mode, sp.rhs_per_launch};
+    bool hit = false;
+    Tuned cached = start;
     {
         std::lock_guard<std::mutex> lock(g_tuned_mutex);
         for (const auto& kv : g_tuned)
-            if (kv.first == sig) cached = kv.second;
+            if (kv.first == sig) {
+                cached = kv.second;
+                hit = true;
+            }
     }
-    if (cached > 0.0) {
-        if (cached != bias) {
+    if (hit) {
+        if (cached.bias != start.bias || cached.sigma_mode != start.sigma_mode ||
+            cached.fuse_mode != start.fuse_mode || cached.rhs != start.rhs) {
             delete h;
             h = nullptr;
-            if ((s = build_plan(sp, cached, &h, st)) != FL_OK) return s;
+            if ((s = build_plan(with_tuned(sp, cached), cached.bias, &h, st)) != FL_OK) return s;
         }
-        h->p.tuned_bias = cached;
+        set_tuned(h->p, cached);
         *out = h;
         return FL_OK;
     }
@@ -1029,33 +1089,59 @@ static fl_status build_plan_tuned(const PlanSpec& sp, double bias, bool autotune
         delete h;
         return s;
     }
-    double best_bias = bias;
-    for (double cand : {0.125, 0.25, 0.5, 2.0, 4.0, 8.0}) {
+    Tuned best = start;
+    auto try_cand = [&](const Tuned& t) -> fl_status {
         fl_plan_s* c = nullptr;
-        if ((s = build_plan(sp, cand, &c, st)) != FL_OK) {
-            delete h;
-            return s;
-        }
+        fl_status r = build_plan(with_tuned(sp, t), t.bias, &c, st);
+        if (r != FL_OK) return r;
         double ms = 0;
-        if ((s = time_plan(c->p, st, &ms)) != FL_OK) {
+        if ((r = time_plan(c->p, st, &ms)) != FL_OK) {
             delete c;
-            delete h;
-            return s;
+            return r;
         }
         if (ms < best_ms) {
             delete h;
             h = c;
             best_ms = ms;
-            best_bias = cand;
+            best = t;
         } else {
             delete c;
         }
+        return FL_OK;
+    };
+    std::vector<Tuned> cands;
+    const bool fp32 = sp.prec == FL_FP32;
+    if (sp.route_mode == 0)
+        for (double cand : {0.125, 0.25, 0.5, 2.0, 4.0, 8.0}) {
+            Tuned t = best;
+            t.bias = cand;
+            if ((s = try_cand(t)) != FL_OK) break;
+        }
+    if (s == FL_OK && fp32 && sp.sigma_mode == 0) {
+        Tuned t = best;
+        t.sigma_mode = 1;
+        s = try_cand(t);
+    }
+    if (s == FL_OK && fp32 && sp.fuse_mode == 0) {
+        Tuned t = best;
+        t.fuse_mode = 1;
+        s = try_cand(t);
+    }
+    if (s == FL_OK && sp.rhs_per_launch == 0)
+        for (int r : {12, 36}) {
+            Tuned t = best;
+            t.rhs = r;
+            if ((s = try_cand(t)) != FL_OK) break;
+        }
+    if (s != FL_OK) {
+        delete h;
+        return s;
     }
     {
         std::lock_guard<std::mutex> lock(g_tuned_mutex);
-        g_tuned.push_back({sig, best_bias});
+        g_tuned.push_back({sig, best});
     }
-    h->p.tuned_bias = best_bias;
+    set_tuned(h->p, best);
     *out = h;
     return FL_OK;
 }
@@ -1106,6 +1192,13 @@ const char* fl_last_error(void) { return g_err.c_str(); }
 
 const char* fl_version(void) { return "fastfl 0.1 (sm_103a)"; }
 
+static bool options_valid(const fl_options* opt) {
+    return !opt || (opt->route >= 0 && opt->route <= 2 && opt->direct_bias >= 0.0 &&
+                    opt->rhs_per_launch >= 0 && opt->variant >= 0 && opt->variant <= 1 &&
+                    opt->fuse_gather >= 0 && opt->fuse_gather <= 2 && opt->oversampling >= 0 &&
+                    opt->oversampling <= 2 && opt->shared_nodes >= 0 && opt->shared_nodes <= 1);
+}
+
 fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q, double eps,
                   fl_precision prec, void* stream) {
     return fl_plan_ex(out, N, M, nodes_dev, q, eps, prec, nullptr, stream);
@@ -1114,10 +1207,7 @@ fl_status fl_plan(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev,
 fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_dev, int q,
                      double eps, fl_precision prec, const fl_options* opt, void* stream) {
     g_err.clear();
-    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
-                opt->fuse_gather < 0 || opt->fuse_gather > 2 || opt->oversampling < 0 ||
-                opt->oversampling > 2))
+    if (!options_valid(opt))
         return fail(FL_EINVAL, "fl_plan: invalid options");
     if (!out) return fail(FL_EINVAL, "fl_plan: out is NULL");
     *out = nullptr;
@@ -1131,7 +1221,8 @@ fl_status fl_plan_ex(fl_plan_t* out, int64_t N, int64_t M, const double* nodes_d
     if (M > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan: nodes is NULL");
     PlanSpec sp{1, &N, &M, nodes_dev, q, eps, prec, false,
                  opt ? opt->route : 0, opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph != 0 : false,
-                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0,
+                 false};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -1155,7 +1246,6 @@ fl_status fl_execute_deriv(fl_plan_t h, const void* c_dev, void* f_dev, void* st
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_deriv: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: real-exponent plans are forward only");
-    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_execute_deriv: float-pair plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, f_dev, true, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute_deriv");
     return FL_OK;
@@ -1166,7 +1256,6 @@ fl_status fl_grad_w(fl_plan_t h, const void* c_dev, const void* r_dev, void* gw_
     if (h->p.M > 0 && (!c_dev || !r_dev || !gw_dev)) return fail(FL_EINVAL, "fl_grad_w: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_grad_w: batched plans are forward only");
     if (h->p.xi_mode) return fail(FL_EUNSUPPORTED, "fl_grad_w: real-exponent plans are forward only");
-    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_grad_w: float-pair plans are forward only");
     cudaError_t e = run_forward(h->p, c_dev, gw_dev, true, (cudaStream_t)stream, r_dev);
     if (e != cudaSuccess) return cuda_fail(e, "fl_grad_w");
     return FL_OK;
@@ -1194,7 +1283,6 @@ fl_status fl_adjoint(fl_plan_t h, const void* r_dev, void* c_out_dev, void* stre
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_adjoint: not a Fourier-Laplace plan");
     if (!c_out_dev || (h->p.M > 0 && !r_dev)) return fail(FL_EINVAL, "fl_adjoint: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_adjoint: batched plans are forward only");
-    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_adjoint: float-pair plans are forward only");
     cudaError_t e = run_adjoint(h->p, r_dev, c_out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_adjoint");
     return FL_OK;
@@ -1204,7 +1292,6 @@ fl_status fl_transposed(fl_plan_t h, const void* g_dev, void* out_dev, void* str
     if (!h || h->p.kind != 0) return fail(FL_EINVAL, "fl_transposed: not a Fourier-Laplace plan");
     if (!out_dev || (h->p.M > 0 && !g_dev)) return fail(FL_EINVAL, "fl_transposed: NULL buffer");
     if (h->p.batched) return fail(FL_EUNSUPPORTED, "fl_transposed: batched plans are forward only");
-    if (h->p.prec == FL_FP64_FF) return fail(FL_EUNSUPPORTED, "fl_transposed: float-pair plans are forward only");
     cudaError_t e = run_transposed(h->p, g_dev, out_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_transposed");
     return FL_OK;
@@ -1261,7 +1348,7 @@ fl_status fl_plan_xi(fl_plan_t* out, int64_t N, const double* xi_dev, int64_t M,
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(p.d_xperm, perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "fl_plan_xi: exponents"));
-    fl_status s = plan_multi(p, 1, &N, &M, nodes_dev, q, st);
+    fl_status s = plan_multi(p, 1, &N, &M, nodes_dev, q, false, st);
     if (s != FL_OK) return bail(s);
     e = build_xi_tables(p, st);
     if (e != cudaSuccess) return bail(cuda_fail(e, "fl_plan_xi: tables"));
@@ -1291,14 +1378,16 @@ fl_status fl_plan_batched(fl_plan_t* out, int B, const int64_t* N_host, const in
     if (prec != FL_FP32 && prec != FL_FP64 && prec != FL_FP64_FF)
         return fail(FL_EINVAL, "fl_plan_batched: unknown precision");
     if (Mtot > 0 && !nodes_dev) return fail(FL_EINVAL, "fl_plan_batched: nodes is NULL");
-    if (opt && (opt->route < 0 || opt->route > 2 || !(opt->direct_bias >= 0.0) ||
-                opt->rhs_per_launch < 0 || opt->variant < 0 || opt->variant > 1 ||
-                opt->fuse_gather < 0 || opt->fuse_gather > 2 || opt->oversampling < 0 ||
-                opt->oversampling > 2))
+    if (!options_valid(opt))
         return fail(FL_EINVAL, "fl_plan_batched: invalid options");
+    const bool shared = opt && opt->shared_nodes;
+    for (int i = 1; shared && i < B; ++i)
+        if (M_host[i] != M_host[0])
+            return fail(FL_EINVAL, "fl_plan_batched: shared nodes need every M_i equal to M_0");
     PlanSpec sp{B, N_host, M_host, nodes_dev, q, eps, prec, true, opt ? opt->route : 0,
                  opt ? opt->rhs_per_launch : 0, opt ? opt->use_graph >= 0 : true,
-                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0};
+                 opt ? opt->variant : 0, opt ? opt->fuse_gather : 0, opt ? opt->oversampling : 0,
+                 shared};
     const double bias = (opt && opt->direct_bias > 0.0) ? opt->direct_bias : 1.0;
     fl_plan_s* h = nullptr;
     fl_status s = build_plan_tuned(sp, bias, opt && opt->autotune, &h, (cudaStream_t)stream);
@@ -1360,6 +1449,10 @@ fl_status fl_get_info(fl_plan_t h, fl_info* info) {
     info->n_bands_fused = (int)p.fused_bands;
     info->fused_entries = p.fused_entries;
     info->sigma_min = p.sigma_min;
+    info->rhs_per_launch = p.rhs_per_launch;
+    info->oversampling = p.sigma_mode;
+    info->fuse_gather = p.fuse_mode;
+    info->autotuned = p.tuned_rhs >= 0 ? 1 : 0;
     return FL_OK;
 }
 

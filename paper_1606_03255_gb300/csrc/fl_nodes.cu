@@ -64,7 +64,7 @@ cudaError_t launch_classify(const Plan& p, const Instance& in, const double* nod
     if (in.M == 0) return cudaSuccess;
     const int bs = 256;
     const int64_t grid = (in.M + bs - 1) / bs;
-    k_classify<<<(unsigned)grid, bs, 0, st>>>(in.M, nodes + 2 * in.moff, p.d_bands + in.band_base,
+    k_classify<<<(unsigned)grid, bs, 0, st>>>(in.M, nodes + 2 * in.src_off, p.d_bands + in.band_base,
                                               in.levels, p.y1, (in.N == 1 && !p.xi_mode) ? 1 : 0,
                                               p.xi_mode ? 1 : 0, keys, vals,
                                               (unsigned long long*)(counts + in.band_base), flag);
@@ -201,7 +201,33 @@ cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, con
     if (in.M == 0) return cudaSuccess;
     const int bs = 256;
     k_permute<<<(unsigned)((in.M + bs - 1) / bs), bs, 0, st>>>(
-        in.M, nodes + 2 * in.moff, keys, vals, (int32_t)in.moff, in.band_base, p.d_ws + in.moff,
+        in.M, nodes + 2 * in.src_off, keys, vals, (int32_t)in.moff, in.band_base, p.d_ws + in.moff,
+        p.d_perm + in.moff, p.d_bandid + in.moff, p.d_cell + in.moff);
+    return cudaGetLastError();
+}
+
+// A transform whose nodes and N equal an earlier one's (shared node sets)
+// takes that transform's sorted slice: the same order and cells, its own
+// result indices and band ids.
+__global__ void k_copy_sorted(int64_t M, const double2* __restrict__ ws_src,
+                              const int32_t* __restrict__ perm_src, const int32_t* __restrict__ band_src,
+                              const int32_t* __restrict__ cell_src, int32_t dm, int32_t db,
+                              double2* __restrict__ ws, int32_t* __restrict__ perm,
+                              int32_t* __restrict__ bandid, int32_t* __restrict__ cell) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    ws[i] = ws_src[i];
+    perm[i] = perm_src[i] + dm;
+    bandid[i] = band_src[i] + db;
+    cell[i] = cell_src[i];
+}
+
+cudaError_t launch_copy_sorted(Plan& p, const Instance& in, const Instance& twin, cudaStream_t st) {
+    if (in.M == 0) return cudaSuccess;
+    const int bs = 256;
+    k_copy_sorted<<<(unsigned)((in.M + bs - 1) / bs), bs, 0, st>>>(
+        in.M, p.d_ws + twin.moff, p.d_perm + twin.moff, p.d_bandid + twin.moff, p.d_cell + twin.moff,
+        (int32_t)(in.moff - twin.moff), in.band_base - twin.band_base, p.d_ws + in.moff,
         p.d_perm + in.moff, p.d_bandid + in.moff, p.d_cell + in.moff);
     return cudaGetLastError();
 }

@@ -136,6 +136,8 @@ struct BandHost {
 struct Instance {
     int64_t N = 0, M = 0;
     int64_t noff = 0, moff = 0;   // offsets of its coefficients and nodes/results
+    int64_t src_off = 0;          // first row of its nodes in the caller's array
+    int twin = -1;                // an earlier transform with the same N and nodes
     int band_base = 0;
     int levels = 1;
     double xi1 = 0;
@@ -186,6 +188,7 @@ struct Plan {
     int64_t xiphi_elems = 0;
     double direct_bias = 1.0;
     double tuned_bias = 0.0;       // bias chosen by the autotuner (0: not tuned)
+    int tuned_sigma_mode = -1, tuned_fuse_mode = -1, tuned_rhs = -1;   // its other choices
     std::vector<DirectItem> direct_work;   // items of the larger-K bands, then n_direct_small
     int64_t n_direct_small = 0;            // items of the bands with K <= kDirSmallK (at the end)
     std::vector<DirectRange> direct_ranges;
@@ -286,6 +289,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_tmp,
                              cudaStream_t st);
 cudaError_t launch_permute(Plan& p, const Instance& in, const double* nodes, const uint32_t* keys,
                            const int32_t* vals, cudaStream_t st);
+cudaError_t launch_copy_sorted(Plan& p, const Instance& in, const Instance& twin, cudaStream_t st);
 // cell[off .. off + n) >>= shift (node cells of a band moved to a grid 2^shift times smaller)
 cudaError_t launch_cell_shift(int32_t* cell, int64_t off, int64_t n, int shift, cudaStream_t st);
 

@@ -22,7 +22,7 @@ from . import build as _build
 
 FL_OK, FL_EINVAL, FL_ENOMEM, FL_ECUDA, FL_ETIMEOUT, FL_EUNSUPPORTED = range(6)
 FL_FP32, FL_FP64, FL_FP64_FF = 0, 1, 2
-# "fp64ff": complex128 in and out, band-grid FFTs in float pairs (forward only)
+# "fp64ff": complex128 in and out, band-grid FFTs in float pairs
 PRECISIONS = {"fp32": FL_FP32, "fp64": FL_FP64, "fp64ff": FL_FP64_FF}
 FL_MAX_LEVELS = 128
 FL_MAX_TIMED_KERNELS = 16
@@ -58,14 +58,16 @@ class fl_info(ctypes.Structure):
         ("scratch_bytes", ctypes.c_double), ("variant", ctypes.c_int), ("kernel", ctypes.c_int),
         ("n_bands_fused", ctypes.c_int), ("fused_entries", ctypes.c_int64),
         ("sigma_min", ctypes.c_double), ("band_parts", ctypes.c_int * FL_MAX_LEVELS),
-    ]
+        ("rhs_per_launch", ctypes.c_int), ("oversampling", ctypes.c_int),
+        ("fuse_gather", ctypes.c_int), ("autotuned", ctypes.c_int)]
 
 
 class fl_options(ctypes.Structure):
     _fields_ = [("route", ctypes.c_int), ("direct_bias", ctypes.c_double),
                 ("rhs_per_launch", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("variant", ctypes.c_int),
-                ("fuse_gather", ctypes.c_int), ("oversampling", ctypes.c_int)]
+                ("fuse_gather", ctypes.c_int), ("oversampling", ctypes.c_int),
+                ("shared_nodes", ctypes.c_int)]
 
 
 ROUTES = {"auto": 0, "nfft": 1, "direct": 2}
@@ -325,6 +327,10 @@ def info_dict(info: fl_info) -> dict:
         "kernel": {v: k for k, v in KERNELS.items()}.get(info.kernel, info.kernel),
         "n_bands_fused": info.n_bands_fused, "fused_entries": info.fused_entries,
         "sigma_min": info.sigma_min, "band_parts": list(info.band_parts[:nb]),
+        "rhs_per_launch": info.rhs_per_launch,
+        "oversampling": {v: k for k, v in SIGMA.items()}.get(info.oversampling, info.oversampling),
+        "fuse_gather": {v: k for k, v in FUSE.items()}.get(info.fuse_gather, info.fuse_gather),
+        "autotuned": bool(info.autotuned),
     }
 
 
@@ -342,7 +348,7 @@ class Plan:
 
     nodes: CUDA float64 tensor (M, 2) of (Re w, Im w), or complex128 (M,).
     precision: "fp32" (complex64 c/f), "fp64" (complex128 c/f) or "fp64ff"
-    (complex128 c/f, band-grid FFTs in float pairs; forward only).
+    (complex128 c/f, band-grid FFTs in float pairs; batched plans forward only).
     """
 
     def __init__(self, N: int, nodes, eps: float, precision: str = "fp32", q: int = 0,
@@ -448,17 +454,22 @@ class BatchedPlan:
     """B independent transforms f_i = C_i c_i in one plan (fl_plan_batched).
 
     Ns, Ms: sizes per transform; nodes: CUDA float64 (sum Ms, 2), the nodes of
-    transform 0, 1, ... in order.  execute(c) takes the coefficients of all
-    transforms concatenated (sum Ns) and returns the results concatenated.
+    transform 0, 1, ... in order, or with shared_nodes=True the (M, 2) node
+    set of every transform (Ms may then be omitted: M for each).  execute(c)
+    takes the coefficients of all transforms concatenated (sum Ns) and returns
+    the results concatenated.
     """
 
     def __init__(self, Ns, Ms, nodes, eps: float, precision: str = "fp32", q: int = 0,
                  stream=None, route: str = "auto", direct_bias: float = 1.0,
                  rhs_per_launch: int = 0, use_graph: bool = True, autotune: bool = False,
-                 variant: str = "alg2", fuse: str = "auto", sigma: str = "auto"):
+                 variant: str = "alg2", fuse: str = "auto", sigma: str = "auto",
+                 shared_nodes: bool = False):
         torch = _torch()
         nodes = nodes.to(torch.float64).contiguous()
         self.Ns = [int(x) for x in Ns]
+        if shared_nodes and Ms is None:
+            Ms = [int(nodes.shape[0])] * len(self.Ns)
         self.Ms = [int(x) for x in Ms]
         self.N, self.M = sum(self.Ns), sum(self.Ms)
         self.prec = _precision(precision)
@@ -466,7 +477,7 @@ class BatchedPlan:
         self._handle = None
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
                          1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant], FUSE[fuse],
-                         SIGMA[str(sigma)])
+                         SIGMA[str(sigma)], int(bool(shared_nodes)))
         st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
                                 self.prec, opt, _stream_handle(stream))
         check(st, "fl_plan_batched")

@@ -73,3 +73,29 @@ def test_null_handles(fl):
     assert fl.fl_adjoint(None, None, None, None) == fl.FL_EINVAL
     assert fl.fl_set_timing(None, 1) == fl.FL_EINVAL
     fl.fl_destroy(None)
+
+
+def _options(fl, **kw):
+    opt = fl.fl_options()
+    for k, v in kw.items():
+        setattr(opt, k, v)
+    return opt
+
+
+@pytest.mark.parametrize("field,value", [("shared_nodes", 2), ("shared_nodes", -1),
+                                         ("oversampling", 3), ("fuse_gather", 3), ("route", 3)])
+def test_invalid_options_rejected_on_host(fl, field, value):
+    nodes = (ctypes.c_double * 4)()   # never read: the options are checked first
+    ptr = ctypes.cast(nodes, ctypes.c_void_p)
+    st, h = fl.fl_plan_ex(4, 2, ptr, 0, 1e-6, 0, _options(fl, **{field: value}), None)
+    assert st == fl.FL_EINVAL and not h.value
+    st, h = fl.fl_plan_batched([4, 4], [2, 2], ptr, 0, 1e-6, 0, _options(fl, **{field: value}), None)
+    assert st == fl.FL_EINVAL and not h.value
+
+
+def test_shared_nodes_need_equal_node_counts(fl):
+    nodes = (ctypes.c_double * 8)()
+    ptr = ctypes.cast(nodes, ctypes.c_void_p)
+    st, h = fl.fl_plan_batched([4, 8, 4], [2, 3, 2], ptr, 0, 1e-6, 0, _options(fl, shared_nodes=1), None)
+    assert st == fl.FL_EINVAL and not h.value
+    assert "shared nodes" in fl.fl_last_error()

@@ -6,7 +6,13 @@
 * the batched workload of 512 transforms with log-uniform degrees
   N_i = floor(2^U), U ~ U[8, 16], M_i = N_i, disk-uniform nodes, on a seeded
   sample of transforms;
-* CUDA-graph replay: repeated and re-targeted executes give the same results.
+* CUDA-graph replay: repeated and re-targeted executes give the same results;
+* shared node sets (one node array for every transform, sorted once per
+  distinct N_i, weight tables shared by transforms of equal N_i): each
+  transform against the oracle, and bitwise equal to the same batch planned
+  with the node set repeated per transform;
+* the autotuner's choices (route bias, oversampling, fused gather, grids per
+  launch) stay within the accuracy bound and are reused from its cache.
 """
 import numpy as np
 import pytest
@@ -158,8 +164,11 @@ def test_autotuned_plans(fl):
     dev = torch.device("cuda")
     nodes = torch.from_numpy(np.concatenate(ws)).to(dev)
     plan = fl.BatchedPlan(Ns, Ns, nodes, 1e-6, autotune=True)
-    bias = plan.info()["direct_bias"]
+    inf = plan.info()
+    bias = inf["direct_bias"]
     assert bias in (0.125, 0.25, 0.5, 1.0, 2.0, 4.0, 8.0)
+    assert inf["autotuned"] and inf["oversampling"] in ("auto", "2")
+    assert inf["fuse_gather"] in ("auto", "off") and inf["rhs_per_launch"] in (0, 12, 36)
     f = plan.execute(torch.from_numpy(np.concatenate(cs)).to(torch.complex64).to(dev)).cpu().numpy()
     moff = 0
     for c, w, M in zip(cs, ws, Ns):
@@ -169,10 +178,47 @@ def test_autotuned_plans(fl):
         moff += M
     # the same workload again: the cached choice is reused
     plan2 = fl.BatchedPlan(Ns, Ns, nodes, 1e-6, autotune=True)
-    assert plan2.info()["direct_bias"] == bias
+    inf2 = plan2.info()
+    for k in ("direct_bias", "oversampling", "fuse_gather", "rhs_per_launch"):
+        assert inf2[k] == inf[k], k
     single = fl.Plan(int(Ns[0]), torch.from_numpy(ws[0]).to(dev), 1e-6, autotune=True)
     fs = single.execute(torch.from_numpy(cs[0]).to(torch.complex64).to(dev)).cpu().numpy()
     ref = oracle.flt_direct(cs[0], ws[0])
     assert oracle.error_E(ref, fs, cs[0]) <= _tol(1e-6, "fp32", ref, cs[0])
     for p in (plan, plan2, single):
         p.close()
+
+
+@pytest.mark.parametrize("prec,eps", [("fp32", 1e-6), ("fp64", 1e-12)])
+def test_shared_nodes(fl, prec, eps):
+    # six transforms on one node set, three distinct N (grids from 2^9 to 2^16
+    # points, fused and split bands in FP32); nodes of both distributions and a
+    # Z^0 node
+    Ns = [20000, 5000, 20000, 300, 5000, 20000]
+    M = 3000
+    w = np.concatenate([W.nodes_circle_clustered(M // 2, seed=61),
+                        W.nodes_disk_uniform(M - M // 2 - 1, seed=62), [[0.4, 7.0]]])
+    cs = [W.coefficients(N, seed=70 + i) for i, N in enumerate(Ns)]
+    dev = torch.device("cuda")
+    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    c = torch.from_numpy(np.concatenate(cs)).to(cdt).to(dev)
+    shared = fl.BatchedPlan(Ns, None, torch.from_numpy(w).to(dev), eps, precision=prec,
+                            shared_nodes=True)
+    rep = fl.BatchedPlan(Ns, [M] * len(Ns), torch.from_numpy(np.concatenate([w] * len(Ns))).to(dev),
+                         eps, precision=prec)
+    fs = shared.execute(c)
+    fr = rep.execute(c)
+    torch.cuda.synchronize()
+    inf_s, inf_r = shared.info(), rep.info()
+    assert inf_s["batch"] == len(Ns) and inf_s["M"] == M * len(Ns)
+    # one weight table per distinct N
+    assert inf_s["scratch_bytes"] < inf_r["scratch_bytes"]
+    fs = fs.cpu().numpy()
+    assert np.array_equal(fs, fr.cpu().numpy())
+    fs = fs.astype(np.complex128)
+    for i, N in enumerate(Ns):
+        ref = oracle.flt_direct(cs[i], w)
+        E = oracle.error_E(ref, fs[i * M:(i + 1) * M], cs[i])
+        assert E <= _tol(eps, prec, ref, cs[i]), (i, N, E)
+    shared.close()
+    rep.close()
