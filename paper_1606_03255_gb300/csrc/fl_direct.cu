@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict_
 __global__ void k_direct_reduce_ff(int nranges, const DirectRange* __restrict__ ranges,
                                    int64_t total, const BandDev* __restrict__ bands,
                                    const int32_t* __restrict__ perm, const ffc* __restrict__ part,
-                                   double2* __restrict__ f) {
+                                   const double2* __restrict__ rmul, double2* __restrict__ f) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
     int r = 0;
@@ -369,10 +369,15 @@ __global__ void k_direct_reduce_ff(int nranges, const DirectRange* __restrict__ 
     const ffc* p = part + B.dslot + local * B.nchunk;
     ffc acc = {ff(0), ff(0)};
     for (int ch = 0; ch < B.nchunk; ++ch) acc = cadd(acc, p[ch]);
-    f[perm[B.node_off + local]] = double2{(double)acc.x, (double)acc.y};
+    const int32_t j = perm[B.node_off + local];
+    const double2 v = double2{(double)acc.x, (double)acc.y};
+    // with rmul: rmul[j] conj(v) (node gradient)
+    f[j] = rmul ? cmulc(rmul[j], v) : v;
 }
 
-static cudaError_t direct_forward_ff(Plan& p, void* f, cudaStream_t st) {
+// (the coefficients are read as pairs from p.d_cff, k-weighted by the caller
+// for the derivative)
+static cudaError_t direct_forward_ff(Plan& p, void* f, const void* rmul, cudaStream_t st) {
     if (p.direct_work.empty()) return cudaSuccess;
     const size_t smem = (size_t)kDirChunk * sizeof(ffc);
     cudaError_t e = cudaFuncSetAttribute(k_direct_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -384,7 +389,7 @@ static cudaError_t direct_forward_ff(Plan& p, void* f, cudaStream_t st) {
     timer_end(p, slot, st);
     k_direct_reduce_ff<<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
         (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
-        (const ffc*)p.d_dpart, (double2*)f);
+        (const ffc*)p.d_dpart, (const double2*)rmul, (double2*)f);
     p.launches += 2;
     return cudaGetLastError();
 }
@@ -486,7 +491,7 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
 cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
                                cudaStream_t st) {
     if (p.prec == FL_FP64_FF)   // reads the coefficients as pairs (converted by the caller)
-        return deriv || rmul ? cudaErrorNotSupported : direct_forward_ff(p, f, st);
+        return direct_forward_ff(p, f, rmul, st);
     return p.prec == FL_FP64 ? direct_forward_t<double>(p, c, f, deriv, rmul, st)
                              : direct_forward_t<float>(p, c, f, deriv, rmul, st);
 }
@@ -517,8 +522,9 @@ static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// (the float-pair form: in double, on its complex128 r)
 cudaError_t run_direct_adjoint(Plan& p, const void* r, cudaStream_t st) {
-    return p.prec == FL_FP64 ? direct_adjoint_t<double>(p, r, st) : direct_adjoint_t<float>(p, r, st);
+    return p.prec != FL_FP32 ? direct_adjoint_t<double>(p, r, st) : direct_adjoint_t<float>(p, r, st);
 }
 
 }  // namespace fl

@@ -13,5 +13,6 @@ FL_SMALL_INST(float)
 FL_SMALL_INST(double)
 #undef FL_SMALL_INST
 template cudaError_t launch_small_fft<ff, 1, 0, false>(FL_SMALL_SIG(ff));
+template cudaError_t launch_small_fft<ff, -1, 1, false>(FL_SMALL_SIG(ff));
 
 }  // namespace fl

@@ -673,9 +673,16 @@ __device__ __forceinline__ int find_cell_band(const Plan::CellBand* __restrict__
     return lo;
 }
 
+// A spread grid value as stored: C_t<T>, or rounded to a float pair (the grids
+// of the float-pair form, whose spreading runs in double).
+template <typename G, typename C> __device__ __forceinline__ G grid_value(const C& v) {
+    if constexpr (std::is_same<G, ffc>::value) return ffc{ff(v.x), ff(v.y)};
+    else return v;
+}
+
 // k_spread_cells: one thread per (sparse NFFT band, grid cell l); writes a_s[l]
 // for every right-hand side s.
-template <typename T, int MW>
+template <typename T, int MW, typename G = C_t<T>>
 __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellBand* __restrict__ cbs,
                                                       int64_t total, const BandDev* __restrict__ bands,
                                                       const int32_t* __restrict__ cell,
@@ -683,7 +690,7 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
                                                       const T* __restrict__ sp_L,
                                                       const C_t<T>* __restrict__ sp_rv,
                                                       const double2* __restrict__ ws, int q,
-                                                      C_t<T>* __restrict__ grid) {
+                                                      G* __restrict__ grid) {
     using C = C_t<T>;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= total) return;
@@ -693,8 +700,8 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
     C acc[kMaxQ];
     for (int s = 0; s < B.nrhs; ++s) acc[s] = C{(T)0, (T)0};
     spread_cell_sum<T, MW>(B, l, cell, sp_phi, sp_L, sp_rv, ws, q, 0, 1, acc);
-    C* gb = grid + B.grid_off + l;
-    for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = acc[s];
+    G* gb = grid + B.grid_off + l;
+    for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = grid_value<G>(acc[s]);
 }
 
 // Dense NFFT bands (many nodes per cell): one CTA of kSpreadDense threads per
@@ -702,7 +709,7 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
 // in a fixed order (a shuffle tree per warp, then the warps in order).
 constexpr int kSpreadDense = 256;
 
-template <typename T, int MW>
+template <typename T, int MW, typename G = C_t<T>>
 __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, const Plan::CellBand* __restrict__ cbs,
                                                                     int64_t total,
                                                                     const BandDev* __restrict__ bands,
@@ -711,7 +718,7 @@ __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, con
                                                                     const T* __restrict__ sp_L,
                                                                     const C_t<T>* __restrict__ sp_rv,
                                                                     const double2* __restrict__ ws, int q,
-                                                                    C_t<T>* __restrict__ grid) {
+                                                                    G* __restrict__ grid) {
     using C = C_t<T>;
     __shared__ C red[kSpreadDense / 32][kMaxQ];
     const int64_t g = blockIdx.x;
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, con
     if (s < B.nrhs) {
         C sum = red[0][s];
         for (int ww = 1; ww < kSpreadDense / 32; ++ww) sum = cadd(sum, red[ww][s]);
-        grid[B.grid_off + l + (int64_t)s * B.n] = sum;
+        grid[B.grid_off + l + (int64_t)s * B.n] = grid_value<G>(sum);
     }
 }
 
@@ -765,10 +772,12 @@ __global__ void k_z0_sum(int64_t z0, const int32_t* __restrict__ perm,
     if (threadIdx.x == 0) *out = C_t<T>{sx[0], sy[0]};
 }
 
-// c_out[k] = [k == 0] z0sum + sum_bands sum_s D[s][k] b_s[(k - N_m/2) mod n].
-template <typename T>
+// c_out[k] = [k == 0] z0sum + sum_bands sum_s D[s][k] b_s[(k - N_m/2) mod n],
+// accumulated in T (double for the float-pair form, whose grids G and weights
+// DT are float pairs).
+template <typename T, typename G = C_t<T>, typename DT = T>
 __global__ void k_combine(int64_t N, int levels, const BandDev* __restrict__ bands,
-                          const T* __restrict__ D, const C_t<T>* __restrict__ grid,
+                          const DT* __restrict__ D, const G* __restrict__ grid,
                           const C_t<T>* __restrict__ z0sum, const C_t<T>* __restrict__ cdir,
                           C_t<T>* __restrict__ cout) {
     using C = C_t<T>;
@@ -788,13 +797,13 @@ __global__ void k_combine(int64_t N, int levels, const BandDev* __restrict__ ban
         }
         const int64_t kl = k - B.k0;   // frequency within the (sub-)band
         const int64_t i = (kl - (B.Nm >> 1)) & (B.n - 1);
-        const T* Dk = D + B.D_off + kl;
-        const C* g = grid + B.grid_off + i;
+        const DT* Dk = D + B.D_off + kl;
+        const G* g = grid + B.grid_off + i;
         for (int s = 0; s < B.nrhs; ++s) {
-            const T d = Dk[(int64_t)s * B.K];
-            const C v = g[(int64_t)s * B.n];
-            acc.x += d * v.x;
-            acc.y += d * v.y;
+            const T d = (T)Dk[(int64_t)s * B.K];
+            const G v = g[(int64_t)s * B.n];
+            acc.x += d * (T)v.x;
+            acc.y += d * (T)v.y;
         }
     }
     cout[k] = acc;
@@ -942,9 +951,17 @@ cudaError_t run_forward_xi(Plan& p, const void* c, void* f, cudaStream_t st) {
 // FP64-accuracy form in float pairs: c converted once to pairs; the FFTs of
 // the band grids, the direct bands and the gather (window, barycentric
 // weights, shift) in float pairs, with the phases reduced exactly in double.
-__global__ void k_to_ff(int64_t n, const double2* __restrict__ in, ffc* __restrict__ out) {
+// (deriv: the k-weighted coefficients 2 pi i k c_k, formed in double and then
+// rounded to pairs)
+__global__ void k_to_ff(int64_t n, const double2* __restrict__ in, int deriv, ffc* __restrict__ out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = ffc{ff(in[i].x), ff(in[i].y)};
+    if (i >= n) return;
+    double2 v = in[i];
+    if (deriv) {
+        const double w = kTwoPiD * (double)i;
+        v = double2{-w * v.y, w * v.x};
+    }
+    out[i] = ffc{ff(v.x), ff(v.y)};
 }
 
 // The gather of the float-pair form: k_gather's steps with the window values,
@@ -961,14 +978,15 @@ __global__ void __launch_bounds__(256) k_gather_ff(int64_t M, const double2* __r
                                                    const ffc* __restrict__ grid,
                                                    const float* __restrict__ cheb32, int q,
                                                    double kb_b, const double2* __restrict__ c,
+                                                   int deriv, const double2* __restrict__ rmul,
                                                    double2* __restrict__ f) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     const int b = bandid[i];
     const int32_t j = perm[i];
     const BandDev B = bands[b];
-    if (B.K == 0 && B.n == 0) {   // Z^0: c_0
-        f[j] = c[B.c_off];
+    if (B.K == 0 && B.n == 0) {   // Z^0: c_0 (its k-weighted term is 0)
+        f[j] = (deriv || rmul) ? double2{0.0, 0.0} : c[B.c_off];
         return;
     }
     if (B.route != 1) return;     // direct-route band: written by the direct kernels
@@ -1015,11 +1033,14 @@ __global__ void __launch_bounds__(256) k_gather_ff(int64_t M, const double2* __r
     ffc e;
     ff_sincospi(ff(2.0 * ph), &e.y, &e.x);
     const ffc v = cmul(acc, e);
-    f[j] = double2{(double)v.x, (double)v.y};
+    const double2 out = double2{(double)v.x, (double)v.y};
+    // with rmul: rmul[j] conj(f'_j) (node gradient, see fl_grad_w)
+    f[j] = rmul ? cmulc(rmul[j], out) : out;
 }
 
 template <int MW>
-static cudaError_t gather_ff_t(Plan& p, const void* c, void* f, cudaStream_t st) {
+static cudaError_t gather_ff_t(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                               cudaStream_t st) {
     double bytes = (double)p.M * (sizeof(double2) + 4 + 1 + sizeof(double2));
     for (int b = 1; b <= p.levels; ++b) {
         const BandDev& B = p.bands[b].dev;
@@ -1031,22 +1052,26 @@ static cudaError_t gather_ff_t(Plan& p, const void* c, void* f, cudaStream_t st)
     timer_begin(p, "gather", bytes, st, &slot);
     k_gather_ff<MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const ffc*)p.d_grid, p.d_cheb32, p.q,
-        p.kb_b, (const double2*)c, (double2*)f);
+        p.kb_b, (const double2*)c, deriv ? 1 : 0, (const double2*)rmul, (double2*)f);
     timer_end(p, slot, st);
     ++p.launches;
     return cudaGetLastError();
 }
 
-static cudaError_t forward_ff(Plan& p, const void* c, void* f, cudaStream_t st) {
+// (deriv: Algorithm 2 on the k-weighted coefficients, the derivative in w;
+// rmul: the node gradient rmul_j conj(f'_j))
+static cudaError_t forward_ff(Plan& p, const void* c, void* f, bool deriv, const void* rmul,
+                              cudaStream_t st) {
     if (p.M == 0) return cudaSuccess;
-    k_to_ff<<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, (const double2*)c, (ffc*)p.d_cff);
+    k_to_ff<<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, (const double2*)c, deriv ? 1 : 0,
+                                                           (ffc*)p.d_cff);
     ++p.launches;
     cudaError_t e = fft_bands<ff, +1, 0, false>(p, p.d_cff, st);
     if (e != cudaSuccess) return e;
-    if ((e = run_direct_forward(p, c, f, false, nullptr, st)) != cudaSuccess) return e;
+    if ((e = run_direct_forward(p, c, f, deriv, rmul, st)) != cudaSuccess) return e;
     switch (p.mw) {
 #define FL_MW_CASE(W) \
-    case W: return gather_ff_t<W>(p, c, f, st);
+    case W: return gather_ff_t<W>(p, c, f, deriv, rmul, st);
         FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
         FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
 #undef FL_MW_CASE
@@ -1056,13 +1081,12 @@ static cudaError_t forward_ff(Plan& p, const void* c, void* f, cudaStream_t st) 
 
 cudaError_t run_forward(Plan& p, const void* c, void* f, bool deriv, cudaStream_t st,
                         const void* rmul) {
-    if (p.prec == FL_FP64_FF)
-        return deriv || rmul ? cudaErrorNotSupported : forward_ff(p, c, f, st);
+    if (p.prec == FL_FP64_FF) return forward_ff(p, c, f, deriv, rmul, st);
     return p.prec == FL_FP64 ? forward_t<double>(p, c, f, deriv, rmul, st)
                              : forward_t<float>(p, c, f, deriv, rmul, st);
 }
 
-template <typename T, int MW>
+template <typename T, int MW, typename G = C_t<T>>
 static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     using C = C_t<T>;
     if (p.cell_bands.empty()) return cudaSuccess;
@@ -1073,41 +1097,46 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
         p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q, (T)p.kb_b,
         (T*)p.d_sp_phi, (T*)p.d_sp_L, (C*)p.d_sp_rv);
     if (p.cells_total > 0)
-        k_spread_cells<T, MW><<<(unsigned)((p.cells_total + 255) / 256), 256, 0, st>>>(
+        k_spread_cells<T, MW, G><<<(unsigned)((p.cells_total + 255) / 256), 256, 0, st>>>(
             (int)p.n_sparse_cb, p.d_cell_bands, p.cells_total, p.d_bands, p.d_cell,
-            (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.d_ws, p.q, (C*)p.d_grid);
+            (const T*)p.d_sp_phi, (const T*)p.d_sp_L, (const C*)p.d_sp_rv, p.d_ws, p.q, (G*)p.d_grid);
     if (p.cells_dense > 0)
-        k_spread_cells_warp<T, MW><<<(unsigned)p.cells_dense, kSpreadDense, 0, st>>>(
+        k_spread_cells_warp<T, MW, G><<<(unsigned)p.cells_dense, kSpreadDense, 0, st>>>(
             (int)(p.cell_bands.size() - p.n_sparse_cb), p.d_cell_bands + p.n_sparse_cb,
             p.cells_dense, p.d_bands, p.d_cell, (const T*)p.d_sp_phi, (const T*)p.d_sp_L,
-            (const C*)p.d_sp_rv, p.d_ws, p.q, (C*)p.d_grid);
+            (const C*)p.d_sp_rv, p.d_ws, p.q, (G*)p.d_grid);
     timer_end(p, slot, st);
     p.launches += 1 + (p.cells_total > 0) + (p.cells_dense > 0);
     return cudaGetLastError();
 }
 
-template <typename T>
+// T: the arithmetic of the spreading, direct bands and combine; FT: that of the
+// FFTs (T, or float pairs ff with T = double for the float-pair form, whose
+// spread grids are rounded to pairs and whose combine reads pair grids and
+// weights).
+template <typename T, typename FT = T>
 static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st) {
     using C = C_t<T>;
+    using G = C_t<FT>;
     cudaError_t e;
     switch (p.mw) {
 #define FL_MW_CASE(W) \
-    case W: e = spread_t<T, W>(p, r, st); break;
+    case W: e = spread_t<T, W, G>(p, r, st); break;
         FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
         FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
 #undef FL_MW_CASE
         default: e = cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    if ((e = fft_bands<T, -1, 1, false>(p, nullptr, st)) != cudaSuccess) return e;
+    if ((e = fft_bands<FT, -1, 1, false>(p, nullptr, st)) != cudaSuccess) return e;
     if (p.xi_mode) return launch_xi_combine(p, cout, st);   // no direct bands, Z^0 adds 0
     if ((e = run_direct_adjoint(p, r, st)) != cudaSuccess) return e;
     C* z0sum = (C*)p.d_z0;
     k_z0_sum<T><<<1, 256, 0, st>>>(p.z0_nodes, p.d_perm, (const C*)r, z0sum);
     int slot;
     timer_begin(p, "combine", 0.0, st, &slot);
-    k_combine<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
-        p.N, p.levels, p.d_bands, (const T*)p.d_D, (const C*)p.d_grid, z0sum,
+    k_combine<T, G, FT><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(
+        p.N, p.levels, p.d_bands, (const FT*)p.d_D, (const G*)p.d_grid, z0sum,
         p.direct_ranges.empty() ? nullptr : (const C*)p.d_cdir, (C*)cout);
     timer_end(p, slot, st);
     p.launches += 2;
@@ -1115,6 +1144,7 @@ static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st
 }
 
 cudaError_t run_adjoint(Plan& p, const void* r, void* cout, cudaStream_t st) {
+    if (p.prec == FL_FP64_FF) return adjoint_t<double, ff>(p, r, cout, st);
     return p.prec == FL_FP64 ? adjoint_t<double>(p, r, cout, st) : adjoint_t<float>(p, r, cout, st);
 }
 
@@ -1128,7 +1158,7 @@ __global__ void k_conj(int64_t n, const C_t<T>* in, C_t<T>* out) {
     }
 }
 
-template <typename T>
+template <typename T, typename FT = T>
 static cudaError_t transposed_t(Plan& p, const void* g, void* out, cudaStream_t st) {
     using C = C_t<T>;
     if (p.M > 0) {
@@ -1139,7 +1169,7 @@ static cudaError_t transposed_t(Plan& p, const void* g, void* out, cudaStream_t 
         k_conj<T><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(p.M, (const C*)g, (C*)p.d_stage_r);
         ++p.launches;
     }
-    cudaError_t e = adjoint_t<T>(p, p.M > 0 ? p.d_stage_r : g, out, st);
+    cudaError_t e = adjoint_t<T, FT>(p, p.M > 0 ? p.d_stage_r : g, out, st);
     if (e != cudaSuccess) return e;
     k_conj<T><<<(unsigned)((p.N + 255) / 256), 256, 0, st>>>(p.N, (const C*)out, (C*)out);
     ++p.launches;
@@ -1148,6 +1178,7 @@ static cudaError_t transposed_t(Plan& p, const void* g, void* out, cudaStream_t 
 
 // g_k = sum_j ghat_j z_j^k, k = 0..N-1 (C^T ghat = conj(C^* conj(ghat))).
 cudaError_t run_transposed(Plan& p, const void* g, void* out, cudaStream_t st) {
+    if (p.prec == FL_FP64_FF) return transposed_t<double, ff>(p, g, out, st);
     return p.prec == FL_FP64 ? transposed_t<double>(p, g, out, st) : transposed_t<float>(p, g, out, st);
 }
 
