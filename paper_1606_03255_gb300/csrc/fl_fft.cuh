@@ -44,26 +44,29 @@ __device__ __forceinline__ C_t<T> prep_value(int64_t i, const BandDev& B, int s,
     return C_t<T>{v.x * d, v.y * d};
 }
 
-// Same with 32-bit grid indices and the band's c/D base pointers resolved,
-// branch-free: the index is clamped into [0, K) so the loads are always in
-// bounds and a thread's loads can all be in flight together; frequencies
-// outside [0, K) are then replaced by zero.  k0: the band's first frequency
-// (sub-bands; c is already offset by it).
-template <typename T, bool DERIV>
+// Same with 32-bit grid indices and the band's c/D base pointers resolved, for
+// an element of pass-1 row r: the row holds grid indices i in [r n/16,
+// (r+1) n/16), so whether i is a negative centred frequency (i >= n/2) is
+// known at compile time (HI = r >= 8) and k = i (- n) + N_m/2 lies in the band
+// iff 0 <= k < K, one unsigned comparison.  Branch-free: outside the band the
+// loads read index 0 (in bounds, so a thread's loads can all be in flight
+// together) and the weight is replaced by zero.  k0: the band's first
+// frequency (sub-bands; c is already offset by it).
+template <typename T, bool DERIV, bool HI>
 __device__ __forceinline__ C_t<T> prep_value32(int i, int n, int half_Nm, int K, int k0,
                                                const C_t<T>* __restrict__ c,
                                                const T* __restrict__ Ds) {
-    const int kp = (i < (n >> 1)) ? i : i - n;
-    const int k = kp + half_Nm;
-    const bool in = k >= 0 && k < K;
-    const int kk = min(max(k, 0), K - 1);
-    const T d = Ds[kk];
+    const int k = HI ? i - n + half_Nm : i + half_Nm;
+    const bool in = (unsigned)k < (unsigned)K;
+    const int kk = in ? k : 0;
+    const T dl = Ds[kk];
+    const T d = in ? dl : (T)0;
     C_t<T> v = c[kk];
     if (DERIV) {
         const T w = deriv_weight<T>(kk + k0);
         v = C_t<T>{-v.y * w, v.x * w};
     }
-    return in ? C_t<T>{v.x * d, v.y * d} : C_t<T>{(T)0, (T)0};
+    return C_t<T>{v.x * d, v.y * d};
 }
 
 // ---------------------------------------------------------------------------
@@ -383,18 +386,19 @@ __global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
         // [n2/4, 3 n2/4) (r = 4..11) holds grid indices in [n/4, 3n/4):
         // centred frequencies outside the band, always zero (a sub-band at
         // sigma < 2 reaches into them)
+        const C* cb = c + B.c_off;
+        const int i0 = i1 + (t << log2n1), di = (L / 16) << log2n1;   // row r: i0 + r di
         if (4 * half <= n && 4 * (K - half) <= n) {
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                v[r] = (r >= 4 && r < 12)
-                           ? C{(T)0, (T)0}
-                           : prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, k0,
-                                                    c + B.c_off, Ds);
+                v[r] = (r >= 4 && r < 12) ? C{(T)0, (T)0}
+                       : r < 8 ? prep_value32<T, DERIV, false>(i0 + r * di, n, half, K, k0, cb, Ds)
+                               : prep_value32<T, DERIV, true>(i0 + r * di, n, half, K, k0, cb, Ds);
         } else {
 #pragma unroll
             for (int r = 0; r < 16; ++r)
-                v[r] = prep_value32<T, DERIV>(i1 + ((t + r * (L / 16)) << log2n1), n, half, K, k0,
-                                              c + B.c_off, Ds);
+                v[r] = r < 8 ? prep_value32<T, DERIV, false>(i0 + r * di, n, half, K, k0, cb, Ds)
+                             : prep_value32<T, DERIV, true>(i0 + r * di, n, half, K, k0, cb, Ds);
         }
     } else {
         const C* in = src + B.grid_off + (int64_t)s * n;
