@@ -192,6 +192,20 @@ __global__ void __launch_bounds__(kDirSmallNodes) k_direct_small(const DirectIte
 
 // f[perm[i]] = sum over the node's chunks (in chunk order); with rmul,
 // rmul[perm[i]] * conj(sum) (the node-gradient epilogue).
+// The direct band holding flattened node t: the last range whose prefix is
+// <= t (prefixes ascend; binary search, so batches of thousands of direct
+// bands cost log2 of that per node).
+__device__ __forceinline__ int find_direct_range(const DirectRange* __restrict__ ranges, int nranges,
+                                                 int64_t t) {
+    int lo = 0, hi = nranges;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (ranges[mid].prefix <= t) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 template <typename T>
 __global__ void k_direct_reduce(int nranges, const DirectRange* __restrict__ ranges,
                                 int64_t total, const BandDev* __restrict__ bands,
@@ -200,9 +214,7 @@ __global__ void k_direct_reduce(int nranges, const DirectRange* __restrict__ ran
     using C = C_t<T>;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
-    int r = 0;
-    while (r + 1 < nranges && ranges[r + 1].prefix <= t) ++r;
-    const DirectRange R = ranges[r];
+    const DirectRange R = ranges[find_direct_range(ranges, nranges, t)];
     const BandDev B = bands[R.band];
     const int64_t local = t - R.prefix;
     const C* p = part + B.dslot + local * B.nchunk;
@@ -361,9 +373,7 @@ __global__ void k_direct_reduce_ff(int nranges, const DirectRange* __restrict__ 
                                    const double2* __restrict__ rmul, double2* __restrict__ f) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= total) return;
-    int r = 0;
-    while (r + 1 < nranges && ranges[r + 1].prefix <= t) ++r;
-    const DirectRange R = ranges[r];
+    const DirectRange R = ranges[find_direct_range(ranges, nranges, t)];
     const BandDev B = bands[R.band];
     const int64_t local = t - R.prefix;
     const ffc* p = part + B.dslot + local * B.nchunk;
@@ -386,10 +396,10 @@ static cudaError_t direct_forward_ff(Plan& p, void* f, const void* rmul, cudaStr
     timer_begin(p, "direct", (double)p.direct_terms * sizeof(ffc) / 32.0, st, &slot);
     k_direct_ff<<<(unsigned)p.direct_work.size(), 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws,
                                                                   (const ffc*)p.d_cff, (ffc*)p.d_dpart);
-    timer_end(p, slot, st);
     k_direct_reduce_ff<<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
         (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
         (const ffc*)p.d_dpart, (const double2*)rmul, (double2*)f);
+    timer_end(p, slot, st);
     p.launches += 2;
     return cudaGetLastError();
 }
@@ -480,10 +490,10 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
                                                                   (const C*)c, (C*)p.d_dpart);
         ++p.launches;
     }
-    timer_end(p, slot, st);
     k_direct_reduce<T><<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
         (int)p.direct_ranges.size(), p.d_dranges, p.direct_nodes, p.d_bands, p.d_perm,
         (const C*)p.d_dpart, (const C*)rmul, (C*)f);
+    timer_end(p, slot, st);
     p.launches += 1 + (nbig > 0);
     return cudaGetLastError();
 }
