@@ -16,6 +16,13 @@ namespace fl {
 
 constexpr double kTwoPiDir = 6.283185307179586476925286766559;
 
+// Shared-memory stride of a staged Horner block: one element of padding, so
+// the 32 lanes of a warp, each on its own block, read 32 different bank
+// offsets instead of one (blocks of 32 complex values are 256 or 512 bytes
+// apart, a whole number of bank rows).
+constexpr int kDirBlockLd = kDirBlock + 1;
+constexpr int kDirTile = kDirChunk / kDirBlock * kDirBlockLd;
+
 // frac(k x) in [-1/2, 1/2) for the FP64 form and the float pairs: k x = p + e
 // exactly (FMA), one rounding.  (The FP32 form uses dir_f32_power below.)
 template <typename T> __device__ __forceinline__ double dir_phase(double k, double x);
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
                 v = C{-v.y * wgt, v.x * wgt};
             }
         }
-        tile[i] = v;
+        tile[i + i / kDirBlock] = v;
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -117,7 +124,7 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
             if (ykb > 745.0) break;
             zk = cscale(expipi<T>((T)(2.0 * dir_phase<T>((double)kb, x))), dir_exp<T>((T)(-ykb)));
         }
-        const C* cb = tile + b * kDirBlock;
+        const C* cb = tile + b * kDirBlockLd;
         C P = cb[kDirBlock - 1];
 #pragma unroll
         for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
@@ -190,8 +197,6 @@ __global__ void __launch_bounds__(kDirSmallNodes) k_direct_small(const DirectIte
     part[B.dslot + (i - B.node_off) * B.nchunk] = acc;
 }
 
-// f[perm[i]] = sum over the node's chunks (in chunk order); with rmul,
-// rmul[perm[i]] * conj(sum) (the node-gradient epilogue).
 // The direct band holding flattened node t: the last range whose prefix is
 // <= t (prefixes ascend; binary search, so batches of thousands of direct
 // bands cost log2 of that per node).
@@ -206,6 +211,8 @@ __device__ __forceinline__ int find_direct_range(const DirectRange* __restrict__
     return lo;
 }
 
+// f[perm[i]] = sum over the node's chunks (in chunk order); with rmul,
+// rmul[perm[i]] * conj(sum) (the node-gradient epilogue).
 template <typename T>
 __global__ void k_direct_reduce(int nranges, const DirectRange* __restrict__ ranges,
                                 int64_t total, const BandDev* __restrict__ bands,
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict_
     const int nst = (int)((kend - k0 + kDirBlock - 1) / kDirBlock) * kDirBlock;
     for (int i = threadIdx.x; i < nst; i += blockDim.x) {
         const int64_t k = k0 + i;
-        tile[i] = k < kend ? c[B.c_off + k] : ffc{ff(0), ff(0)};
+        tile[i + i / kDirBlock] = k < kend ? c[B.c_off + k] : ffc{ff(0), ff(0)};
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict_
         if (kb >= kend) break;
         const double ykb = y * (double)kb;
         if (ykb > 104.0) break;     // below 2^-150 |c|: so are the later blocks
-        const ffc* cb = tile + b * kDirBlock;
+        const ffc* cb = tile + b * kDirBlockLd;
         ffc P = cb[kDirBlock - 1];
 #pragma unroll
         for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
@@ -389,7 +396,7 @@ __global__ void k_direct_reduce_ff(int nranges, const DirectRange* __restrict__ 
 // for the derivative)
 static cudaError_t direct_forward_ff(Plan& p, void* f, const void* rmul, cudaStream_t st) {
     if (p.direct_work.empty()) return cudaSuccess;
-    const size_t smem = (size_t)kDirChunk * sizeof(ffc);
+    const size_t smem = (size_t)kDirTile * sizeof(ffc);
     cudaError_t e = cudaFuncSetAttribute(k_direct_ff, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int slot;
@@ -475,7 +482,7 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
                                     cudaStream_t st) {
     using C = C_t<T>;
     if (p.direct_work.empty()) return cudaSuccess;
-    const size_t smem = (size_t)kDirChunk * sizeof(C);
+    const size_t smem = (size_t)kDirTile * sizeof(C);
     auto kern = deriv ? k_direct<T, true> : k_direct<T, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
