@@ -65,41 +65,13 @@ __device__ __forceinline__ bool dir_f32_power(const DirF32Node& d, int64_t k, fl
     return true;
 }
 
-// One CTA per work item: up to kDirNodes consecutive sorted nodes of one band
-// against one chunk of kDirChunk coefficients staged in shared memory.  Warp w
-// takes node w; lane l takes the Horner blocks l, l + 32, ... of the chunk.
-template <typename T, bool DERIV>
-__global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ items,
-                                                const BandDev* __restrict__ bands,
-                                                const double2* __restrict__ ws,
-                                                const C_t<T>* __restrict__ c,
-                                                C_t<T>* __restrict__ part) {
+// Warp part of k_direct for node w of the item: lane l sums the Horner blocks
+// l, l + 32, ... of the staged chunk; lane 0 writes the node's partial.
+template <typename T>
+__device__ __forceinline__ void direct_node(const DirectItem& it, const BandDev& B, const C_t<T>* tile,
+                                            const double2* __restrict__ ws, int64_t k0, int64_t kend,
+                                            int w, int lane, C_t<T>* __restrict__ part) {
     using C = C_t<T>;
-    extern __shared__ unsigned char smem_raw[];
-    C* tile = reinterpret_cast<C*>(smem_raw);
-    const DirectItem it = items[blockIdx.x];
-    const BandDev B = bands[it.band];
-    const int64_t k0 = (int64_t)it.chunk * kDirChunk;
-    const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
-    // the chunk's terms rounded up to whole Horner blocks (zeros past kend)
-    const int nst = (int)((kend - k0 + kDirBlock - 1) / kDirBlock) * kDirBlock;
-    for (int i = threadIdx.x; i < nst; i += blockDim.x) {
-        const int64_t k = k0 + i;
-        C v = C{(T)0, (T)0};
-        if (k < kend) {
-            v = c[B.c_off + k];
-            if (DERIV) {
-                T wgt;
-                if constexpr (sizeof(T) == 4) wgt = (float)k * 6.28318530717958647692f;   // k < 2^24: one rounding
-                else wgt = kTwoPiDir * (double)k;
-                v = C{-v.y * wgt, v.x * wgt};
-            }
-        }
-        tile[i + i / kDirBlock] = v;
-    }
-    __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w >= it.nnodes) return;
     const int64_t i = it.node0 + w;
     const double2 wv = ws[i];
     const double x = wv.x - floor(wv.x);
@@ -136,6 +108,45 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
     }
     if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
+}
+
+// One CTA per work item: up to kDirNodes consecutive sorted nodes of one band
+// against one chunk of kDirChunk coefficients staged in shared memory.  Warp w
+// takes nodes w, w + 8, ...; lane l the Horner blocks l, l + 32, ... of the
+// chunk.
+template <typename T, bool DERIV>
+__global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ items,
+                                                const BandDev* __restrict__ bands,
+                                                const double2* __restrict__ ws,
+                                                const C_t<T>* __restrict__ c,
+                                                C_t<T>* __restrict__ part) {
+    using C = C_t<T>;
+    extern __shared__ unsigned char smem_raw[];
+    C* tile = reinterpret_cast<C*>(smem_raw);
+    const DirectItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int64_t k0 = (int64_t)it.chunk * kDirChunk;
+    const int64_t kend = min(B.K, k0 + (int64_t)kDirChunk);
+    // the chunk's terms rounded up to whole Horner blocks (zeros past kend)
+    const int nst = (int)((kend - k0 + kDirBlock - 1) / kDirBlock) * kDirBlock;
+    for (int i = threadIdx.x; i < nst; i += blockDim.x) {
+        const int64_t k = k0 + i;
+        C v = C{(T)0, (T)0};
+        if (k < kend) {
+            v = c[B.c_off + k];
+            if (DERIV) {
+                T wgt;
+                if constexpr (sizeof(T) == 4) wgt = (float)k * 6.28318530717958647692f;   // k < 2^24: one rounding
+                else wgt = kTwoPiDir * (double)k;
+                v = C{-v.y * wgt, v.x * wgt};
+            }
+        }
+        tile[i + i / kDirBlock] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int w = threadIdx.x >> 5; w < it.nnodes; w += 8)
+        direct_node<T>(it, B, tile, ws, k0, kend, w, lane, part);
 }
 
 // Bands with K <= kDirSmallK: one thread per node (up to kDirSmallNodes per

@@ -78,10 +78,15 @@ struct FuseArgs {
 };
 
 // Direct route (fl_direct.cu): kDirNodes nodes x one chunk of kDirChunk
-// coefficients per CTA, Horner blocks of kDirBlock terms.
+// coefficients per CTA (its 8 warps take kDirNodes / 8 nodes each, so the
+// staged chunk serves them all), Horner blocks of kDirBlock terms.
+#ifndef FL_DIR_NODES
+#define FL_DIR_NODES 16
+#endif
 constexpr int kDirBlock = 32;
 constexpr int kDirChunk = 4096;
-constexpr int kDirNodes = 8;
+constexpr int kDirNodes = FL_DIR_NODES;
+static_assert(kDirNodes % 8 == 0, "whole nodes per warp");
 // FP32 bands with K <= kDirSmallK and at least kDirSmallMinNodes nodes: one
 // thread per node, up to kDirSmallNodes nodes per CTA, all K terms per thread
 // (see k_direct_small).  Fewer nodes, or FP64 (whose serial chains are long),
