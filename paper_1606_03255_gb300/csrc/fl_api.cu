@@ -801,6 +801,17 @@ static fl_status plan_multi(Plan& p, int B, const int64_t* Ns, const int64_t* Ms
             }
         }
     }
+    // few direct items (a handful of sparse bands): half as many nodes per
+    // item, so the launch still covers the GPU several times over
+    if (!p.direct_work.empty() && (int64_t)p.direct_work.size() < kDirFewItems) {
+        std::vector<DirectItem> halves;
+        for (const DirectItem& it : p.direct_work) {
+            const int h = std::min(it.nnodes, kDirNodes / 2);
+            halves.push_back({it.band, it.chunk, it.node0, h, 0});
+            if (it.nnodes > h) halves.push_back({it.band, it.chunk, it.node0 + h, it.nnodes - h, 0});
+        }
+        p.direct_work.swap(halves);
+    }
     p.n_direct_small = (int64_t)small_items.size();
     p.direct_work.insert(p.direct_work.end(), small_items.begin(), small_items.end());
     p.n_dadj_small = (int64_t)small_adj.size();

@@ -344,44 +344,45 @@ __global__ void __launch_bounds__(256) k_direct_ff(const DirectItem* __restrict_
         tile[i + i / kDirBlock] = k < kend ? c[B.c_off + k] : ffc{ff(0), ff(0)};
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (w >= it.nnodes) return;
-    const int64_t i = it.node0 + w;
-    const double2 wv = ws[i];
-    const double x = wv.x - floor(wv.x);
-    const double y = kTwoPiDir * wv.y;
-    double xr = x;
-    if (xr >= 0.5) xr -= 1.0;
-    ffc z;
-    ff_sincospi(ff(2.0 * xr), &z.y, &z.x);
-    const ff mag = ff_exp(ff(-y));
-    z = ffc{z.x * mag, z.y * mag};
-    ffc acc = {ff(0), ff(0)};
+    const int lane = threadIdx.x & 31;
+    for (int w = threadIdx.x >> 5; w < it.nnodes; w += 8) {   // nodes w, w + 8, ...
+        const int64_t i = it.node0 + w;
+        const double2 wv = ws[i];
+        const double x = wv.x - floor(wv.x);
+        const double y = kTwoPiDir * wv.y;
+        double xr = x;
+        if (xr >= 0.5) xr -= 1.0;
+        ffc z;
+        ff_sincospi(ff(2.0 * xr), &z.y, &z.x);
+        const ff mag = ff_exp(ff(-y));
+        z = ffc{z.x * mag, z.y * mag};
+        ffc acc = {ff(0), ff(0)};
 #pragma unroll 1
-    for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
-        const int b = bb * 32 + lane;
-        const int64_t kb = k0 + (int64_t)b * kDirBlock;
-        if (kb >= kend) break;
-        const double ykb = y * (double)kb;
-        if (ykb > 104.0) break;     // below 2^-150 |c|: so are the later blocks
-        const ffc* cb = tile + b * kDirBlockLd;
-        ffc P = cb[kDirBlock - 1];
+        for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
+            const int b = bb * 32 + lane;
+            const int64_t kb = k0 + (int64_t)b * kDirBlock;
+            if (kb >= kend) break;
+            const double ykb = y * (double)kb;
+            if (ykb > 104.0) break;     // below 2^-150 |c|: so are the later blocks
+            const ffc* cb = tile + b * kDirBlockLd;
+            ffc P = cb[kDirBlock - 1];
 #pragma unroll
-        for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
-        ffc zk;
-        ff_sincospi(ff(2.0 * dir_phase<double>((double)kb, x)), &zk.y, &zk.x);
-        const ff mk = ff_exp(ff(-ykb));
-        acc = cadd(acc, cmul(ffc{zk.x * mk, zk.y * mk}, P));
-    }
+            for (int t = kDirBlock - 2; t >= 0; --t) P = cadd(cmul(P, z), cb[t]);
+            ffc zk;
+            ff_sincospi(ff(2.0 * dir_phase<double>((double)kb, x)), &zk.y, &zk.x);
+            const ff mk = ff_exp(ff(-ykb));
+            acc = cadd(acc, cmul(ffc{zk.x * mk, zk.y * mk}, P));
+        }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const ffc o = {ff(__shfl_xor_sync(0xffffffffu, acc.x.hi, off),
-                          __shfl_xor_sync(0xffffffffu, acc.x.lo, off)),
-                       ff(__shfl_xor_sync(0xffffffffu, acc.y.hi, off),
-                          __shfl_xor_sync(0xffffffffu, acc.y.lo, off))};
-        acc = cadd(acc, o);
+        for (int off = 16; off > 0; off >>= 1) {
+            const ffc o = {ff(__shfl_xor_sync(0xffffffffu, acc.x.hi, off),
+                              __shfl_xor_sync(0xffffffffu, acc.x.lo, off)),
+                           ff(__shfl_xor_sync(0xffffffffu, acc.y.hi, off),
+                              __shfl_xor_sync(0xffffffffu, acc.y.lo, off))};
+            acc = cadd(acc, o);
+        }
+        if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
     }
-    if (lane == 0) part[B.dslot + (i - B.node_off) * B.nchunk + it.chunk] = acc;
 }
 
 // f[perm[i]] = sum over the node's chunks (in chunk order), rounded to double.

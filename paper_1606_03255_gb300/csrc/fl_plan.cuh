@@ -87,6 +87,9 @@ constexpr int kDirBlock = 32;
 constexpr int kDirChunk = 4096;
 constexpr int kDirNodes = FL_DIR_NODES;
 static_assert(kDirNodes % 8 == 0, "whole nodes per warp");
+// below this many direct items (8 CTAs per SM of the 152) a plan halves the
+// nodes per item
+constexpr int64_t kDirFewItems = 8 * 152;
 // FP32 bands with K <= kDirSmallK and at least kDirSmallMinNodes nodes: one
 // thread per node, up to kDirSmallNodes nodes per CTA, all K terms per thread
 // (see k_direct_small).  Fewer nodes, or FP64 (whose serial chains are long),
