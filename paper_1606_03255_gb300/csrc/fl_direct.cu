@@ -525,8 +525,79 @@ cudaError_t run_direct_forward(Plan& p, const void* c, void* f, bool deriv, cons
                              : direct_forward_t<float>(p, c, f, deriv, rmul, st);
 }
 
+// The float-pair form's adjoint of the direct bands with K > kDirSmallK:
+// k_direct_adj's steps (same work items, KL = 16 frequencies per lane) with
+// conj(z_j), the restart power conj(z_j)^k0 and the frequency steps in float
+// pairs; the restart phase k0 x mod 1 is still reduced exactly in double.
+// Each lane's sums, rounded to double, meet in cdir through atomics.
+__global__ void __launch_bounds__(32) k_direct_adj_ff(const DirectAdjItem* __restrict__ items,
+                                                      const BandDev* __restrict__ bands,
+                                                      const double2* __restrict__ ws,
+                                                      const int32_t* __restrict__ perm,
+                                                      const double2* __restrict__ r,
+                                                      double2* __restrict__ cdir) {
+    constexpr int KL = 16;
+    const DirectAdjItem it = items[blockIdx.x];
+    const BandDev B = bands[it.band];
+    const int lane = threadIdx.x;
+    const int64_t k0 = (int64_t)it.kchunk * (32 * KL) + (int64_t)lane * KL;
+    const bool active = k0 < B.K;
+    ffc acc[KL];
+#pragma unroll
+    for (int t = 0; t < KL; ++t) acc[t] = ffc{ff(0), ff(0)};
+    for (int nb = 0; nb < it.nnodes; nb += 32) {
+        // lane loads node nb + lane: x, y, r_j and conj(z_j) as pairs
+        double xl = 0.0, yl = 0.0;
+        ffc rl = {ff(0), ff(0)}, zl = {ff(0), ff(0)};
+        if (nb + lane < it.nnodes) {
+            const int64_t i = it.node0 + nb + lane;
+            const double2 wv = ws[i];
+            xl = wv.x - floor(wv.x);
+            yl = kTwoPiDir * wv.y;
+            const double2 rv = r[perm[i]];
+            rl = ffc{ff(rv.x), ff(rv.y)};
+            const double xr = xl >= 0.5 ? xl - 1.0 : xl;
+            ff_sincospi(ff(-2.0 * xr), &zl.y, &zl.x);
+            const ff mag = ff_exp(ff(-yl));
+            zl = ffc{zl.x * mag, zl.y * mag};
+        }
+        const int cnt = min(32, it.nnodes - nb);
+        for (int q = 0; q < cnt; ++q) {
+            const ffc rq = {ff(__shfl_sync(0xffffffffu, rl.x.hi, q), __shfl_sync(0xffffffffu, rl.x.lo, q)),
+                            ff(__shfl_sync(0xffffffffu, rl.y.hi, q), __shfl_sync(0xffffffffu, rl.y.lo, q))};
+            const ffc zq = {ff(__shfl_sync(0xffffffffu, zl.x.hi, q), __shfl_sync(0xffffffffu, zl.x.lo, q)),
+                            ff(__shfl_sync(0xffffffffu, zl.y.hi, q), __shfl_sync(0xffffffffu, zl.y.lo, q))};
+            const double x = __shfl_sync(0xffffffffu, xl, q);
+            const double y = __shfl_sync(0xffffffffu, yl, q);
+            if (!active) continue;
+            const double yk = y * (double)k0;
+            if (yk > 104.0) continue;   // below 2^-150 |r_j|
+            ffc w0;
+            ff_sincospi(ff(-2.0 * dir_phase<double>((double)k0, x)), &w0.y, &w0.x);
+            const ff mk = ff_exp(ff(-yk));
+            ffc rw = cmul(rq, ffc{w0.x * mk, w0.y * mk});
+#pragma unroll
+            for (int t = 0; t < KL; ++t) {
+                acc[t] = cadd(acc[t], rw);
+                rw = cmul(rw, zq);
+            }
+        }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int t = 0; t < KL; ++t) {
+        const int64_t k = k0 + t;
+        if (k < B.K) {
+            atomicAdd(&cdir[k].x, (double)acc[t].x);
+            atomicAdd(&cdir[k].y, (double)acc[t].y);
+        }
+    }
+}
+
+// (pairs: the float-pair form, T = double, whose bands with K > kDirSmallK
+// take k_direct_adj_ff)
 template <typename T>
-static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
+static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st, bool pairs = false) {
     using C = C_t<T>;
     if (p.direct_ranges.empty()) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(p.d_cdir, 0, p.N * sizeof(C), st);
@@ -537,7 +608,11 @@ static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
     int slot;
     timer_begin(p, "direct_adj", 0.0, st, &slot);
     const int64_t nbig = (int64_t)items.size() - p.n_dadj_small;
-    if (nbig > 0) {
+    if (nbig > 0 && pairs) {
+        k_direct_adj_ff<<<(unsigned)nbig, 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
+                                                      (const double2*)r, (double2*)p.d_cdir);
+        ++p.launches;
+    } else if (nbig > 0) {
         k_direct_adj<T><<<(unsigned)nbig, 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
                                                        (const C*)r, (C*)p.d_cdir);
         ++p.launches;
@@ -551,9 +626,10 @@ static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// (the float-pair form: in double, on its complex128 r)
+// (the float-pair form on its complex128 r: bands with K <= kDirSmallK in double)
 cudaError_t run_direct_adjoint(Plan& p, const void* r, cudaStream_t st) {
-    return p.prec != FL_FP32 ? direct_adjoint_t<double>(p, r, st) : direct_adjoint_t<float>(p, r, st);
+    if (p.prec == FL_FP64_FF) return direct_adjoint_t<double>(p, r, st, true);
+    return p.prec == FL_FP64 ? direct_adjoint_t<double>(p, r, st) : direct_adjoint_t<float>(p, r, st);
 }
 
 }  // namespace fl
