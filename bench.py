@@ -48,7 +48,7 @@ def workload(N: int) -> str:
     """The headline workload's description at N = M (2^20 by default)."""
     size = f"2^{N.bit_length() - 1}" if N > 0 and N & (N - 1) == 0 else str(N)
     return (f"N=M={size} Fourier-Laplace transform: c complex64 N(0,1); nodes half on |z|=1, "
-            "half with 1-|z|=10^(-6U); eps=1e-6 FP32 form (FP64 phase reduction)")
+            "half with 1-|z|=10^(-6U); eps=1e-6 FP32 form (phases reduced exactly from the FP64 nodes)")
 
 
 def parse():
@@ -462,6 +462,26 @@ def secondary_workloads(dev, flush, rank, names=SECONDARY):
         tr = _time_cuda(lambda: op._plan.transposed(r), 10, flush)
         out["adjoint_transposed_2^18_fp32"] = {"ms_adjoint": adj, "ms_transposed": tr,
                                                "value_transposed": N * M / (tr * 1e-3), "unit": "ms"}
+        # the same loss at eps = 1e-12: the FP64 form and the float-pair form
+        for prec in ("fp64", "fp64ff"):
+            c2 = c.detach().to(torch.complex128).requires_grad_(True)
+            w2 = w.detach().clone().requires_grad_(True)
+            g2 = g.to(torch.complex128)
+            op2 = FourierLaplace(N, eps=1e-12, precision=prec)
+            op2.plan_for(w2)
+
+            def fwd_bwd2():
+                c2.grad = None
+                w2.grad = None
+                loss = torch.sum(torch.abs(op2(c2, w2) - g2) ** 2)
+                loss.backward()
+            for _ in range(2):
+                fwd_bwd2()
+            out[f"gradients_2^18_{prec}_eps1e-12"] = {
+                "ms_fwd_bwd": _time_cuda(fwd_bwd2, 4, flush),
+                "ms_fwd": _time_cuda(lambda: op2(c2.detach(), w2.detach()), 4, flush),
+                "ms_adjoint": _time_cuda(lambda: op2._plan.adjoint(g2), 4, flush), "unit": "ms"}
+            op2._plan.close()
     if want("real_exponents"):
         # real exponents: N = M = 2^18, xi_k ~ U[1, N], nodes as the headline
         # workload shifted to Re w in [-1/2, 1/2), FP32, eps = 1e-6
