@@ -383,8 +383,7 @@ fl_status fl_laplace_real(fl_plan_t p, const void *c_dev, void *f_dev, void *str
  * entry of the (levels + 1) x (q + 1) moment table.  A problem that needs more
  * returns FL_EUNSUPPORTED with the bytes needed in fl_last_error().
  * The first call on each device does a one-time set-up (it looks up the
- * array's device address); make that first call before any stream capture.
- * The call synchronises `stream` once (it reads max t and max s back to choose
+ * array's device address).  The call synchronises `stream` once (it reads max t and max s back to choose
  * the levels).  Every call on a device shares the one array, which keeps the
  * last call's contents: calls that overlap on the GPU (two streams, two host
  * threads) race and give wrong results, so serialise them.
