@@ -78,11 +78,12 @@ def test_gradients_against_finite_differences(ag):
     assert _rel(an_w, fd_w) <= 1e-5
 
 
-@pytest.mark.parametrize("prec,eps,bar", [("fp64", 1e-12, 1e-9), ("fp32", 1e-7, 1e-5)])
+@pytest.mark.parametrize("prec,eps,bar", [("fp64", 1e-12, 1e-9), ("fp64ff", 1e-12, 1e-9),
+                                          ("fp32", 1e-7, 1e-5)])
 def test_gradient_workload_full_size_sampled(ag, prec, eps, bar):
     # N = M = 2^18, disk-uniform nodes, g complex N(0,1), L = sum |f - g|^2
     N = M = 1 << 18
-    cdt = torch.complex128 if prec == "fp64" else torch.complex64
+    cdt = torch.complex64 if prec == "fp32" else torch.complex128
     c0 = W.coefficients(N, seed=0).astype(np.complex64 if prec == "fp32" else np.complex128)
     w0 = W.nodes_disk_uniform(M, seed=1)
     g = W.targets(M, seed=2)
