@@ -635,7 +635,10 @@ def run_ours(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    plan.set_timing(True)
+    # K steps timed as a whole (step events only), then K more with the
+    # library's per-kernel events (two per launch, which add a few percent to
+    # a step) for the kernel table and the roofline: one timed region
+    plan.set_timing(False)   # (also zeroes the plan's launch counter)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
@@ -643,6 +646,11 @@ def run_ours(args):
         starts[i].record(stream)
         plan.execute(c, out=f)
         ends[i].record(stream)
+    untimed_launches = plan.timing()["total_launches"]
+    plan.set_timing(True)
+    for i in range(args.steps):
+        flush.zero_()
+        plan.execute(c, out=f)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -650,6 +658,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = float(np.mean(step_ms))
     timing = plan.timing()
+    timing["total_launches"] += untimed_launches
     plan.set_timing(False)
     ms = max_over_ranks(ms, dist, dev)
     value = job_value(world, N, M, ms)
