@@ -509,19 +509,29 @@ def secondary_workloads(dev, flush, rank, names=SECONDARY):
 
 
 CASES = ("disk_2e18_fp32", "disk_2e18_fp64", "adjoint_2e18_fp32", "laplace_2e16_fp64",
-         "laplace_2e16_fp32", "flt_2e20_fp32", "flt_2e20_fp64ff", "flt_2e18_fp32")
+         "laplace_2e16_fp32", "flt_2e20_fp32", "flt_2e20_fp64ff", "flt_2e18_fp32", "batched_512_fp32")
 
 
 def run_case(args):
     """One small case on cuda:0, `--warmup` untimed and `--steps` timed calls,
     for profiling single kernels: the disk-uniform forward at 2^18 (its bands
     are mostly summed directly), its adjoint, the Laplace transform at 2^16, and
-    the headline workload at 2^20 or 2^18."""
+    the headline workload at 2^20 or 2^18, and the 512-transform batch (plain
+    launches, route bias 1)."""
     import torch
     from paper_1606_03255_gb300 import fl
     dev = torch.device("cuda", 0)
     name = args.case
-    if name.startswith("laplace"):
+    if name.startswith("batched"):
+        Ns = W.batched_degrees(512, seed=0)
+        cs = np.concatenate([W.coefficients(int(n), seed=7 + i).astype(np.complex64)
+                             for i, n in enumerate(Ns)])
+        ws = np.concatenate([W.nodes_disk_uniform(int(n), seed=9000 + i) for i, n in enumerate(Ns)])
+        p = fl.BatchedPlan(Ns, Ns, torch.from_numpy(ws).to(dev), 1e-6, use_graph=False)
+        cb = torch.from_numpy(cs).to(dev)
+        out = torch.empty(int(Ns.sum()), dtype=torch.complex64, device=dev)
+        run = lambda: p.execute(cb, out=out)   # noqa: E731
+    elif name.startswith("laplace"):
         N = M = 1 << 16
         prec = name.rsplit("_", 1)[1]
         dt = torch.float64 if prec == "fp64" else torch.float32

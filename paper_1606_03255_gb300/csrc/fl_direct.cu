@@ -50,6 +50,19 @@ __device__ __forceinline__ DirF32Node dir_f32_node(double x, double y) {
     d.yl = (float)(y - (double)d.yh);
     return d;
 }
+
+// The same from the plan's node record (k_node_tab: X, and y as a float pair),
+// with z = exp(-y) e^(2 pi i x) in float: x - [x >= 1/2] is the signed X 2^-64,
+// rounded once to float (the value the double path rounds).
+__device__ __forceinline__ DirF32Node dir_f32_record(uint4 rec, float2* z) {
+    DirF32Node d;
+    d.X = ((uint64_t)rec.y << 32) | (uint64_t)rec.x;
+    d.yh = __uint_as_float(rec.z);
+    d.yl = __uint_as_float(rec.w);
+    const float xr = (float)(int64_t)d.X * 0x1p-64f;
+    *z = cscale(expipi<float>(2.f * xr), expf(-d.yh));
+    return d;
+}
 // z^k = exp(-y k) e^(2 pi i frac(k x)) for 0 <= k < 2^24 (SIGN = -1: the conjugate
 // phase); false when y k > lim (the power underflows: so do all later ones).
 template <int SIGN>
@@ -69,19 +82,24 @@ __device__ __forceinline__ bool dir_f32_power(const DirF32Node& d, int64_t k, fl
 // l, l + 32, ... of the staged chunk; lane 0 writes the node's partial.
 template <typename T>
 __device__ __forceinline__ void direct_node(const DirectItem& it, const BandDev& B, const C_t<T>* tile,
-                                            const double2* __restrict__ ws, int64_t k0, int64_t kend,
+                                            const double2* __restrict__ ws,
+                                            const uint4* __restrict__ ntab, int64_t k0, int64_t kend,
                                             int w, int lane, C_t<T>* __restrict__ part) {
     using C = C_t<T>;
     const int64_t i = it.node0 + w;
-    const double2 wv = ws[i];
-    const double x = wv.x - floor(wv.x);
-    const double y = kTwoPiDir * wv.y;
-    // z = exp(-y) exp(2 pi i x) in T
-    double xr = x;
-    if (xr >= 0.5) xr -= 1.0;
-    const C z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    // z = exp(-y) exp(2 pi i x) in T (FP32: from the node record)
+    C z;
     DirF32Node nd;
-    if constexpr (sizeof(T) == 4) nd = dir_f32_node(x, y);
+    double x = 0.0, y = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        nd = dir_f32_record(ntab[i], &z);
+    } else {
+        const double2 wv = ws[i];
+        x = wv.x - floor(wv.x);
+        y = kTwoPiDir * wv.y;
+        const double xr = x >= 0.5 ? x - 1.0 : x;
+        z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    }
     C acc = C{(T)0, (T)0};
 #pragma unroll 1
     for (int bb = 0; bb < kDirChunk / (32 * kDirBlock); ++bb) {
@@ -118,6 +136,7 @@ template <typename T, bool DERIV>
 __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ items,
                                                 const BandDev* __restrict__ bands,
                                                 const double2* __restrict__ ws,
+                                                const uint4* __restrict__ ntab,
                                                 const C_t<T>* __restrict__ c,
                                                 C_t<T>* __restrict__ part) {
     using C = C_t<T>;
@@ -146,7 +165,7 @@ __global__ void __launch_bounds__(256) k_direct(const DirectItem* __restrict__ i
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int w = threadIdx.x >> 5; w < it.nnodes; w += 8)
-        direct_node<T>(it, B, tile, ws, k0, kend, w, lane, part);
+        direct_node<T>(it, B, tile, ws, ntab, k0, kend, w, lane, part);
 }
 
 // Bands with K <= kDirSmallK: one thread per node (up to kDirSmallNodes per
@@ -157,6 +176,7 @@ template <typename T, bool DERIV>
 __global__ void __launch_bounds__(kDirSmallNodes) k_direct_small(const DirectItem* __restrict__ items,
                                                                  const BandDev* __restrict__ bands,
                                                                  const double2* __restrict__ ws,
+                                                                 const uint4* __restrict__ ntab,
                                                                  const C_t<T>* __restrict__ c,
                                                                  C_t<T>* __restrict__ part) {
     using C = C_t<T>;
@@ -181,14 +201,18 @@ __global__ void __launch_bounds__(kDirSmallNodes) k_direct_small(const DirectIte
     __syncthreads();
     if ((int)threadIdx.x >= it.nnodes) return;
     const int64_t i = it.node0 + threadIdx.x;
-    const double2 wv = ws[i];
-    const double x = wv.x - floor(wv.x);
-    const double y = kTwoPiDir * wv.y;
-    double xr = x;
-    if (xr >= 0.5) xr -= 1.0;
-    const C z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    C z;
     DirF32Node nd;
-    if constexpr (sizeof(T) == 4) nd = dir_f32_node(x, y);
+    double x = 0.0, y = 0.0;
+    if constexpr (sizeof(T) == 4) {
+        nd = dir_f32_record(ntab[i], &z);
+    } else {
+        const double2 wv = ws[i];
+        x = wv.x - floor(wv.x);
+        y = kTwoPiDir * wv.y;
+        const double xr = x >= 0.5 ? x - 1.0 : x;
+        z = cscale(expipi<T>((T)(2.0 * xr)), dir_exp<T>((T)(-y)));
+    }
     C acc = C{(T)0, (T)0};
     for (int kb = 0; kb < K; kb += kDirBlock) {
         C zk;
@@ -255,6 +279,7 @@ template <typename T>
 __global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restrict__ items,
                                                    const BandDev* __restrict__ bands,
                                                    const double2* __restrict__ ws,
+                                                   const uint4* __restrict__ ntab,
                                                    const int32_t* __restrict__ perm,
                                                    const C_t<T>* __restrict__ r,
                                                    C_t<T>* __restrict__ cdir) {
@@ -275,13 +300,17 @@ __global__ void __launch_bounds__(32) k_direct_adj(const DirectAdjItem* __restri
         DirF32Node nl = {0ull, 0.f, 0.f};
         if (nb + lane < it.nnodes) {
             const int64_t i = it.node0 + nb + lane;
-            const double2 wv = ws[i];
-            xl = wv.x - floor(wv.x);
-            yl = kTwoPiDir * wv.y;
             rl = r[perm[i]];
-            double xr = xl >= 0.5 ? xl - 1.0 : xl;
-            zl = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-yl)));
-            if constexpr (sizeof(T) == 4) nl = dir_f32_node(xl, yl);
+            if constexpr (sizeof(T) == 4) {   // from the node record; conj(z)
+                nl = dir_f32_record(ntab[i], &zl);
+                zl.y = -zl.y;
+            } else {
+                const double2 wv = ws[i];
+                xl = wv.x - floor(wv.x);
+                yl = kTwoPiDir * wv.y;
+                const double xr = xl >= 0.5 ? xl - 1.0 : xl;
+                zl = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-yl)));
+            }
         }
         const int cnt = min(32, it.nnodes - nb);
         for (int q = 0; q < cnt; ++q) {
@@ -433,6 +462,7 @@ template <typename T>
 __global__ void __launch_bounds__(32) k_direct_adj_small(const DirectAdjItem* __restrict__ items,
                                                          const BandDev* __restrict__ bands,
                                                          const double2* __restrict__ ws,
+                                                         const uint4* __restrict__ ntab,
                                                          const int32_t* __restrict__ perm,
                                                          const C_t<T>* __restrict__ r,
                                                          C_t<T>* __restrict__ cdir) {
@@ -451,15 +481,18 @@ __global__ void __launch_bounds__(32) k_direct_adj_small(const DirectAdjItem* __
     for (int t = 0; t < KL; ++t) acc[t] = C{(T)0, (T)0};
     for (int jn = g; active && jn < it.nnodes; jn += G) {
         const int64_t i = it.node0 + jn;
-        const double2 wv = ws[i];
-        const double x = wv.x - floor(wv.x);
-        const double y = kTwoPiDir * wv.y;
-        const double xr = x >= 0.5 ? x - 1.0 : x;
-        const C zq = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-y)));
-        C w0;
-        if constexpr (sizeof(T) == 4) {
-            if (!dir_f32_power<-1>(dir_f32_node(x, y), k0, 104.f, &w0)) continue;
+        C zq, w0;
+        double x = 0.0, y = 0.0;
+        if constexpr (sizeof(T) == 4) {   // from the node record; conj(z)
+            const DirF32Node nd = dir_f32_record(ntab[i], &zq);
+            zq.y = -zq.y;
+            if (!dir_f32_power<-1>(nd, k0, 104.f, &w0)) continue;
         } else {
+            const double2 wv = ws[i];
+            x = wv.x - floor(wv.x);
+            y = kTwoPiDir * wv.y;
+            const double xr = x >= 0.5 ? x - 1.0 : x;
+            zq = cscale(expipi<T>((T)(-2.0 * xr)), dir_exp<T>((T)(-y)));
             const double yk = y * (double)k0;
             if (yk > 745.0) continue;
             w0 = cscale(expipi<T>((T)(-2.0 * dir_phase<T>((double)k0, x))), dir_exp<T>((T)(-yk)));
@@ -502,11 +535,12 @@ static cudaError_t direct_forward_t(Plan& p, const void* c, void* f, bool deriv,
     timer_begin(p, "direct", (double)p.direct_terms * sizeof(C) / 32.0, st, &slot);
     const int64_t nbig = (int64_t)p.direct_work.size() - p.n_direct_small;
     if (nbig > 0)
-        kern<<<(unsigned)nbig, 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws, (const C*)c, (C*)p.d_dpart);
+        kern<<<(unsigned)nbig, 256, smem, st>>>(p.d_direct, p.d_bands, p.d_ws, p.d_ntab, (const C*)c,
+                                                (C*)p.d_dpart);
     if (p.n_direct_small > 0) {
         auto ks = deriv ? k_direct_small<T, true> : k_direct_small<T, false>;
         ks<<<(unsigned)p.n_direct_small, kDirSmallNodes, 0, st>>>(p.d_direct + nbig, p.d_bands, p.d_ws,
-                                                                  (const C*)c, (C*)p.d_dpart);
+                                                                  p.d_ntab, (const C*)c, (C*)p.d_dpart);
         ++p.launches;
     }
     k_direct_reduce<T><<<(unsigned)((p.direct_nodes + 255) / 256), 256, 0, st>>>(
@@ -613,13 +647,13 @@ static cudaError_t direct_adjoint_t(Plan& p, const void* r, cudaStream_t st, boo
                                                       (const double2*)r, (double2*)p.d_cdir);
         ++p.launches;
     } else if (nbig > 0) {
-        k_direct_adj<T><<<(unsigned)nbig, 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_perm,
+        k_direct_adj<T><<<(unsigned)nbig, 32, 0, st>>>(d_items, p.d_bands, p.d_ws, p.d_ntab, p.d_perm,
                                                        (const C*)r, (C*)p.d_cdir);
         ++p.launches;
     }
     if (p.n_dadj_small > 0) {
         k_direct_adj_small<T><<<(unsigned)p.n_dadj_small, 32, 0, st>>>(
-            d_items + nbig, p.d_bands, p.d_ws, p.d_perm, (const C*)r, (C*)p.d_cdir);
+            d_items + nbig, p.d_bands, p.d_ws, p.d_ntab, p.d_perm, (const C*)r, (C*)p.d_cdir);
         ++p.launches;
     }
     timer_end(p, slot, st);

@@ -237,7 +237,9 @@ cudaError_t build_twiddles(Plan& p, cudaStream_t st) {
 
 // Per sorted node of an FP32 plan: X = x 2^64 with x = Re w mod 1 (exact for
 // x >= 2^-11, within 2^-64 below), and tau = (2 pi Im w - y_c) / y_h of its
-// band as a float pair (hi = tau rounded, lo = the rest), for gather_node_f32.
+// band as a float pair (hi = tau rounded, lo = the rest), for gather_node_f32;
+// for a node of a direct-route band y = 2 pi Im w as a float pair instead, for
+// the direct kernels (no FP64 arithmetic per node there).
 __global__ void k_node_tab(int64_t M, const double2* __restrict__ ws, const int32_t* __restrict__ bandid,
                            const BandDev* __restrict__ bands, uint4* __restrict__ tab) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,7 +249,11 @@ __global__ void k_node_tab(int64_t M, const double2* __restrict__ ws, const int3
     const uint64_t X = (uint64_t)ldexp(x, 64);
     const BandDev B = bands[bandid[i]];
     float th = 0.f, tl = 0.f;
-    if (B.nrhs > 1) {
+    if (B.route == 2) {
+        const double y = kTwoPiD * wv.y;
+        th = (float)y;
+        tl = (float)(y - (double)th);
+    } else if (B.nrhs > 1) {
         const double tau = (kTwoPiD * wv.y - B.yc) * B.yh_inv;
         th = (float)tau;
         tl = (float)(tau - (double)th);
