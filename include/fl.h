@@ -180,8 +180,10 @@ typedef struct {
                              0 = for grids above 4096 points whose nodes are
                                  few for the grid (by estimated bytes; default);
                              1 = never; 2 = for every grid above 4096 points. */
-    int oversampling;     /* FL_FP32 plans whose gather can be fused (above):
-                             the oversampling sigma of a band's NFFT.
+    int oversampling;     /* FL_FP32 plans whose gather can be fused (above)
+                             and FL_FP64 plans (whose sub-bands are gathered
+                             from their grids): the oversampling sigma of a
+                             band's NFFT.
                              0 = from the tolerance by estimated cost
                                  (default): a band with K frequencies may be
                                  evaluated as P NFFTs over contiguous ranges of
@@ -190,8 +192,11 @@ typedef struct {
                                  window half-width m_w that meets eps/3 at the
                                  smallest sigma used; a split is admitted only
                                  while the deconvolution's gain
-                                 Phi(0)/Phi(1/(2 sigma)), which scales the FP32
-                                 rounding, stays <= 32 (so sigma >= ~1.5);
+                                 Phi(0)/Phi(1/(2 sigma)), which scales the
+                                 grids' rounding, stays <= 32 in FP32 (so
+                                 sigma >= ~1.5) and <= 2^47 eps/3 in FP64
+                                 (sigma >= 1.75 at eps = 1e-12); float-pair
+                                 plans keep sigma = 2;
                              1 = sigma = 2 for every band (one NFFT each);
                              2 = every eligible band split to its fewest grid
                                  points under the same limits, whatever the

@@ -472,6 +472,11 @@ static double deconv_gain(double sigma, int mw) {
     return exp((double)mw * (b - sqrt(b * b - v * v)));
 }
 
+// FP64 plans: the gain times the grids' rounding, 2^6 units of 2^-53, stays
+// below the NFFT's share of the tolerance (e.g. <= 47 at eps = 1e-12, so
+// sigma >= 1.75 there; no practical limit at 1e-6).
+static double deconv_gain_limit64(double eps_A) { return eps_A * ldexp(1.0, 47); }
+
 static double fused_cost(int64_t nodes, int log2n, int mw) {   // per right-hand side
     const int TR = pass_tiles(8, (log2n + 1) / 2, FL_P2_THREADS_F32);
     const double entries = (double)nodes * (TR + 2 * mw - 1) / TR;
@@ -495,12 +500,16 @@ static SplitChoice best_split(const Plan& p, const BandHost& bh, double smin, in
     const BandDev& d = bh.dev;
     SplitChoice best;
     const bool four_step = d.log2n > kSmallMaxLog2;
+    // FP32: sub-bands gather inside pass 2 (fused); FP64: from their grids
+    const bool fusable = p.prec == FL_FP32 && p.fuse_mode != 1;
     double c1 = fft_cost(d.nrhs, d.n, d.log2n) +
-                (four_step ? std::min(d.nrhs * fused_cost(bh.nodes, d.log2n, mw), unfused_cost(bh.nodes, d.nrhs, mw))
-                           : unfused_cost(bh.nodes, d.nrhs, mw));
+                (four_step && fusable
+                     ? std::min(d.nrhs * fused_cost(bh.nodes, d.log2n, mw), unfused_cost(bh.nodes, d.nrhs, mw))
+                     : unfused_cost(bh.nodes, d.nrhs, mw));
     double bc = force ? (double)d.n : c1;
-    const bool eligible = smin < 2.0 && four_step && p.prec == FL_FP32 && !p.xi_mode && p.fuse_mode != 1 &&
-                          bh.nodes > 0;
+    const bool eligible = smin < 2.0 && four_step && !p.xi_mode && bh.nodes > 0 &&
+                          (fusable || p.prec == FL_FP64);
+    const double gain_max = p.prec == FL_FP32 ? kMaxDeconvGain : deconv_gain_limit64(p.eps_A);
     // (the window shape and gain are those of the candidate's own sigma)
     if (eligible) {
         for (int P = 2; P <= 9; ++P) {
@@ -512,9 +521,9 @@ static SplitChoice best_split(const Plan& p, const BandHost& bh, double smin, in
             if ((double)n >= 2.0 * (double)Nc) continue;   // no gain over sigma = 2
             // the half-width this sigma needs, and the FP32 limit at it
             const int mc = std::max(mw, window_width(p.eps_A, (double)n / (double)Nc));
-            if (deconv_gain((double)n / (double)Nc, mc) > kMaxDeconvGain) continue;
-            const double c = force ? (double)P * n
-                                   : P * (fft_cost(d.nrhs, n, lg) + d.nrhs * fused_cost(bh.nodes, lg, mc));
+            if (deconv_gain((double)n / (double)Nc, mc) > gain_max) continue;
+            const double gather = fusable ? d.nrhs * fused_cost(bh.nodes, lg, mc) : unfused_cost(bh.nodes, d.nrhs, mc);
+            const double c = force ? (double)P * n : P * (fft_cost(d.nrhs, n, lg) + gather);
             if (c < bc) {
                 bc = c;
                 best.P = P;
@@ -530,7 +539,8 @@ static SplitChoice best_split(const Plan& p, const BandHost& bh, double smin, in
 
 static fl_status plan_splits(Plan& p, const std::vector<int>& nfft, cudaStream_t st) {
     p.sigma_min = 2.0;
-    if (p.sigma_mode == 1 || p.prec != FL_FP32 || p.xi_mode || p.fuse_mode == 1) return FL_OK;
+    if (p.sigma_mode == 1 || p.xi_mode || p.prec == FL_FP64_FF || (p.prec == FL_FP32 && p.fuse_mode == 1))
+        return FL_OK;
     // (sigma_mode 2: every eligible band takes its split of fewest grid points)
     const double cands[4] = {2.0, 1.75, 1.5, 1.25};   // floors (1.25: only where the gain allows)
     double best_total = 0.0;

@@ -498,10 +498,32 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
     const T fr = (T)(t0 - u);
     const int64_t lo = (int64_t)u - (MW - 1);
     T phi[2 * MW];
+    const T kb = XI ? kb_b : (T)B.kb;   // the window shape of the band's grids
 #pragma unroll
-    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb_b);
+    for (int t = 0; t < 2 * MW; ++t) phi[t] = kb_window<T>(fr + (T)(MW - 1 - t), (T)MW, kb);
     const int64_t nmask = B.n - 1;
     const C* g = grid + B.grid_off;
+    if constexpr (sizeof(T) == 8 && !XI) {
+        if (B.nsub > 0) {   // split band (FP64): its sub-bands' grids, each with its centre phase
+            T Ls[kMaxQ];
+            if (B.nrhs > 1) bary_weights<T>(kTwoPiD * wv.y, B, q, cheb, Ls);
+            else Ls[0] = (T)1;   // the Y_M band: one right-hand side
+            for (int sb = 0; sb < B.nsub; ++sb) {
+                const BandDev S = bands[B.sub0 + sb];
+                const C* gs = grid + S.grid_off;
+                C a = {(T)0, (T)0};
+                for (int s = 0; s < S.nrhs; ++s) {
+                    const C v = tap_sum<MW>(gs + (int64_t)s * S.n, lo, nmask, phi);
+                    a.x += Ls[s] * v.x;
+                    a.y += Ls[s] * v.y;
+                }
+                const double ph = frac_turns((double)(S.k0 + (S.Nm >> 1)), x);
+                acc = cadd(acc, cmul(a, expipi<T>((T)(2.0 * ph))));
+            }
+            f[j] = rmul ? cmulc(rmul[j], acc) : acc;
+            return;
+        }
+    }
     if constexpr (sizeof(T) == 4) {   // XI (real exponents) in FP32
         if (B.nrhs > 1) {
             const double tau = (kTwoPiD * wv.y - B.yc) * B.yh_inv;

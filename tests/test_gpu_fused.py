@@ -16,7 +16,8 @@ into P contiguous sub-bands, each an NFFT on a power-of-two grid of about
 sigma K/P points, whose partial sums the gather combines with the sub-bands'
 centre phases.  A different NFFT (grids, windows), so those plans are checked
 against the oracle at the same bound, forward, derivative, node gradient,
-adjoint and transposed evaluation, and in a batch.
+adjoint and transposed evaluation, and in a batch; FP64 plans, whose
+sub-bands are gathered from their grids, at the FP64 bar E <= eps.
 """
 import numpy as np
 import pytest
@@ -249,10 +250,59 @@ def test_split_batched(fl):
         off += m
 
 
-def test_split_not_used_in_fp64(fl):
+def _fp64_split_plan(fl, N, w, eps, sigma, route="nfft"):
+    plan = fl.Plan(N, torch.from_numpy(np.ascontiguousarray(w)).cuda(), eps, precision="fp64",
+                   route=route, sigma=sigma)
+    info = plan.info()
+    assert info["sigma_min"] < 2.0 and max(info["band_parts"]) > 1, info["band_parts"]
+    # the FP64 limit on the deconvolution's gain: <= 2^47 eps/3
+    b = np.pi * (2 - 1 / info["sigma_min"])
+    gain = np.exp(info["m_w"] * (b - np.sqrt(b * b - (np.pi / info["sigma_min"]) ** 2)))
+    assert gain <= 2.0 ** 47 * eps / 3 * (1 + 1e-12), (info["sigma_min"], info["m_w"])
+    return plan, info
+
+
+@pytest.mark.parametrize("sigma", ["min", "auto"])
+@pytest.mark.parametrize("eps", [1e-10, 1e-6])
+@pytest.mark.parametrize("kind,N", [("clustered", 40000), ("edges", 1 << 17)])
+def test_fp64_split_forward(fl, sigma, eps, kind, N):
+    # FP64 plans gather the sub-bands from their grids; the FP64 bar: E <= eps
+    c = W.coefficients(N, seed=N % 53)
+    w = _nodes(kind, 2500, seed=N % 47)
+    plan, info = _fp64_split_plan(fl, N, w, eps, sigma)
+    f = plan.execute(torch.from_numpy(c).cuda()).cpu().numpy()
+    plan.close()
+    ref = oracle.flt_direct(c, w)
+    assert oracle.error_E(ref, f, c) <= eps, (info["m_w"], info["sigma_min"])
+
+
+def test_fp64_split_adjoint_transposed_and_gradients(fl):
+    eps, N, M = 1e-10, 50000, 2000
+    c = W.coefficients(N, seed=18)
+    w = W.nodes_circle_clustered(M, seed=19)
+    r = W.targets(M, seed=20)
+    plan, _ = _fp64_split_plan(fl, N, w, eps, "min")
+    ct, rt = torch.from_numpy(c).cuda(), torch.from_numpy(r).cuda()
+    adj = plan.adjoint(rt).cpu().numpy()
+    tr = plan.transposed(rt).cpu().numpy()
+    fd = plan.execute(ct, deriv=True).cpu().numpy()
+    gw = plan.grad_w(ct, rt).cpu().numpy()
+    plan.close()
+    aref = oracle.flt_adjoint(r, w, N)
+    assert oracle.error_E(aref, adj, r) <= eps
+    tref = np.conj(oracle.flt_adjoint(np.conj(r), w, N))
+    assert oracle.error_E(tref, tr, r) <= eps
+    cd = 2j * np.pi * np.arange(N) * c
+    dref = oracle.flt_direct(cd, w)
+    assert oracle.error_E(dref, fd, cd) <= eps
+    assert np.max(np.abs(gw - r * np.conj(dref))) <= np.max(np.abs(r)) * eps * np.sum(np.abs(cd))
+
+
+def test_split_not_used_in_float_pairs(fl):
+    # the float pairs' 48-bit grids would lose eps = 1e-12 to the gain
     dev = torch.device("cuda")
     w = W.nodes_circle_clustered(500, seed=1)
-    plan = fl.Plan(40000, torch.from_numpy(w).to(dev), 1e-10, precision="fp64", route="nfft",
+    plan = fl.Plan(40000, torch.from_numpy(w).to(dev), 1e-10, precision="fp64ff", route="nfft",
                    sigma="min")
     info = plan.info()
     plan.close()
