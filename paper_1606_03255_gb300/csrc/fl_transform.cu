@@ -569,6 +569,57 @@ __global__ void __launch_bounds__(256) k_gather(int64_t M, const double2* __rest
 // ---------------------------------------------------------------------------
 // Adjoint: spread (transpose of the gather), FFT with sign -, combine.
 
+// The float-pair form's spreading preparation: k_spread_prep's per-node
+// window taps, barycentric weights and shifted r_j in pairs (the window from
+// one pair exponential, the weights as in k_gather_ff); the phase (N_m/2) x
+// mod 1 is reduced exactly in double.
+template <int MW>
+__global__ void __launch_bounds__(256) k_spread_prep_ff(int64_t M, const double2* __restrict__ ws,
+                                                        const int32_t* __restrict__ perm,
+                                                        const int32_t* __restrict__ bandid,
+                                                        const BandDev* __restrict__ bands,
+                                                        const double2* __restrict__ r,
+                                                        const float* __restrict__ cheb32, int q,
+                                                        ff* __restrict__ sp_phi, ff* __restrict__ sp_L,
+                                                        ffc* __restrict__ sp_rv) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const BandDev B = bands[bandid[i]];
+    if (B.route != 1) return;
+    const double2 wv = ws[i];
+    const double x = wv.x - floor(wv.x);
+    const double t0 = (double)B.n * x;
+    const ff fr = ff(t0 - floor(t0));
+    double ph = (double)(B.Nm >> 1) * x;   // N_m a power of two: exact
+    ph -= floor(ph);
+    if (ph >= 0.5) ph -= 1.0;
+    ffc e;
+    ff_sincospi(ff(2.0 * ph), &e.y, &e.x);
+    const double2 rj = r[perm[i]];
+    sp_rv[i] = cmulc(ffc{ff(rj.x), ff(rj.y)}, e);
+    const ff kb = ff(B.kb);
+#pragma unroll
+    for (int t = 0; t < 2 * MW; ++t) sp_phi[i * (2 * MW) + t] = ff_kb_window(fr + ff(MW - 1 - t), (float)MW, kb);
+    if (B.nrhs > 1) {
+        const ff tf = ff((kTwoPiD * wv.y - B.yc) * B.yh_inv);
+        ff L[kMaxQ];
+        ff den = ff(0);
+        int hit = -1;
+        for (int s = 0; s < q; ++s) {
+            const ff d = tf - ff(cheb32[s], cheb32[q + s]);
+            if (d.hi == 0.f && d.lo == 0.f) {
+                hit = s;
+                L[s] = ff(0);
+                continue;
+            }
+            L[s] = ff_div(ff(cheb32[2 * q + s], cheb32[3 * q + s]), d);
+            den += L[s];
+        }
+        for (int s = 0; s < q; ++s)
+            sp_L[i * q + s] = hit >= 0 ? (s == hit ? ff(1) : ff(0)) : ff_div(L[s], den);
+    }
+}
+
 // Adjoint spreading, the transpose of the gather, without atomics in two
 // steps.  k_spread_prep: for every sorted node of an NFFT band its 2 m_w window
 // taps, its barycentric weights L_s(y_j) and rv_j = r_j exp(-2 pi i (N_m/2) x_j).
@@ -673,9 +724,11 @@ __device__ __forceinline__ void spread_cell_sum(const BandDev& B, int64_t l,
             int64_t t = (l - cell[j] + MW - 1) % n;
             if (t < 0) t += n;
             C w = cscale(sp_rv[j], sp_phi[j * (2 * MW) + t]);
-            if (B.parent >= 0) {
-                const double xj = ws[j].x - floor(ws[j].x);
-                w = cmul(w, expipi<T>((T)(-2.0 * frac_turns(kc, xj))));
+            if constexpr (!std::is_same<T, ff>::value) {   // (no sub-bands in float pairs)
+                if (B.parent >= 0) {
+                    const double xj = ws[j].x - floor(ws[j].x);
+                    w = cmul(w, expipi<T>((T)(-2.0 * frac_turns(kc, xj))));
+                }
             }
             if (nr == 1) {
                 acc[0] = cadd(acc[0], w);
@@ -732,6 +785,12 @@ __global__ void __launch_bounds__(256) k_spread_cells(int ncb, const Plan::CellB
     for (int s = 0; s < B.nrhs; ++s) gb[(int64_t)s * B.n] = grid_value<G>(acc[s]);
 }
 
+__device__ __forceinline__ float shfl_xor_t(float v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ double shfl_xor_t(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ ff shfl_xor_t(ff v, int off) {
+    return ff(__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off));
+}
+
 // Dense NFFT bands (many nodes per cell): one CTA of kSpreadDense threads per
 // cell, threads strided over the covering nodes; the thread sums are combined
 // in a fixed order (a shuffle tree per warp, then the warps in order).
@@ -762,8 +821,8 @@ __global__ void __launch_bounds__(kSpreadDense) k_spread_cells_warp(int ncb, con
         T x = acc[s].x, y = acc[s].y;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
-            x += __shfl_xor_sync(0xffffffffu, x, off);
-            y += __shfl_xor_sync(0xffffffffu, y, off);
+            x += shfl_xor_t(x, off);
+            y += shfl_xor_t(y, off);
         }
         if (lane == 0) red[w][s] = C{x, y};
     }
@@ -1120,10 +1179,16 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     if (p.cell_bands.empty()) return cudaSuccess;
     int slot;
     timer_begin(p, "spread", 0.0, st, &slot);
-    auto prep = p.xi_mode ? k_spread_prep<T, MW, true> : k_spread_prep<T, MW, false>;
-    prep<<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
-        p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q, (T)p.kb_b,
-        (T*)p.d_sp_phi, (T*)p.d_sp_L, (C*)p.d_sp_rv);
+    if constexpr (std::is_same<T, ff>::value) {
+        k_spread_prep_ff<MW><<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+            p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const double2*)r, p.d_cheb32, p.q,
+            (ff*)p.d_sp_phi, (ff*)p.d_sp_L, (ffc*)p.d_sp_rv);
+    } else {
+        auto prep = p.xi_mode ? k_spread_prep<T, MW, true> : k_spread_prep<T, MW, false>;
+        prep<<<(unsigned)((p.M + 255) / 256), 256, 0, st>>>(
+            p.M, p.d_ws, p.d_perm, p.d_bandid, p.d_bands, (const C*)r, p.d_cheb, p.q, (T)p.kb_b,
+            (T*)p.d_sp_phi, (T*)p.d_sp_L, (C*)p.d_sp_rv);
+    }
     if (p.cells_total > 0)
         k_spread_cells<T, MW, G><<<(unsigned)((p.cells_total + 255) / 256), 256, 0, st>>>(
             (int)p.n_sparse_cb, p.d_cell_bands, p.cells_total, p.d_bands, p.d_cell,
@@ -1138,10 +1203,9 @@ static cudaError_t spread_t(Plan& p, const void* r, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// T: the arithmetic of the spreading, direct bands and combine; FT: that of the
-// FFTs (T, or float pairs ff with T = double for the float-pair form, whose
-// spread grids are rounded to pairs and whose combine reads pair grids and
-// weights).
+// T: the arithmetic of the direct bands and the combine; FT: that of the
+// spreading and the FFTs (T, or float pairs ff with T = double for the
+// float-pair form, whose combine reads pair grids and weights in double).
 template <typename T, typename FT = T>
 static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st) {
     using C = C_t<T>;
@@ -1149,7 +1213,7 @@ static cudaError_t adjoint_t(Plan& p, const void* r, void* cout, cudaStream_t st
     cudaError_t e;
     switch (p.mw) {
 #define FL_MW_CASE(W) \
-    case W: e = spread_t<T, W, G>(p, r, st); break;
+    case W: e = spread_t<FT, W, G>(p, r, st); break;
         FL_MW_CASE(2) FL_MW_CASE(3) FL_MW_CASE(4) FL_MW_CASE(5) FL_MW_CASE(6) FL_MW_CASE(7)
         FL_MW_CASE(8) FL_MW_CASE(9) FL_MW_CASE(10) FL_MW_CASE(11) FL_MW_CASE(12)
 #undef FL_MW_CASE
