@@ -332,6 +332,11 @@ template <typename T> struct PassBudget {
 };
 
 // Columns (pass 1) or rows (pass 2) per CTA: pass_tiles (fl_plan.cuh).
+// FL_PASS_REGT_F32: threads per SM the FP32 passes' register budget is sized
+// for (65536 registers / this = registers per thread).
+#ifndef FL_PASS_REGT_F32
+#define FL_PASS_REGT_F32 1024
+#endif
 template <typename T, int LOG2L, int TMAX>
 struct PassTile {
     static constexpr int L = 1 << LOG2L;
@@ -348,7 +353,7 @@ struct PassTile {
     static constexpr size_t SMEM = (size_t)TILES * LD * sizeof(C_t<T>);
     // register budget: 64 per thread for float (1024 threads per SM), 128 for
     // double (512)
-    static constexpr int REGT = sizeof(T) == 4 ? 1024 : 512;
+    static constexpr int REGT = sizeof(T) == 4 ? FL_PASS_REGT_F32 : 512;
     static constexpr int MINB = (REGT / NT) > 0 ? (REGT / NT) : 1;
 };
 
