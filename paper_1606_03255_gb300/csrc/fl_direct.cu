@@ -43,17 +43,11 @@ struct DirF32Node {
     uint64_t X;
     float yh, yl;
 };
-__device__ __forceinline__ DirF32Node dir_f32_node(double x, double y) {
-    DirF32Node d;
-    d.X = (uint64_t)ldexp(x, 64);
-    d.yh = (float)y;
-    d.yl = (float)(y - (double)d.yh);
-    return d;
-}
 
-// The same from the plan's node record (k_node_tab: X, and y as a float pair),
-// with z = exp(-y) e^(2 pi i x) in float: x - [x >= 1/2] is the signed X 2^-64,
-// rounded once to float (the value the double path rounds).
+// A node from the plan's record (k_node_tab: X = x 2^64, and y = 2 pi Im w as
+// a float pair, formed once at plan time in double), with z = exp(-y)
+// e^(2 pi i x) in float: x - [x >= 1/2] is the signed X 2^-64, rounded once
+// to float.
 __device__ __forceinline__ DirF32Node dir_f32_record(uint4 rec, float2* z) {
     DirF32Node d;
     d.X = ((uint64_t)rec.y << 32) | (uint64_t)rec.x;
@@ -63,6 +57,7 @@ __device__ __forceinline__ DirF32Node dir_f32_record(uint4 rec, float2* z) {
     *z = cscale(expipi<float>(2.f * xr), expf(-d.yh));
     return d;
 }
+
 // z^k = exp(-y k) e^(2 pi i frac(k x)) for 0 <= k < 2^24 (SIGN = -1: the conjugate
 // phase); false when y k > lim (the power underflows: so do all later ones).
 template <int SIGN>
