@@ -337,13 +337,15 @@ template <typename T> struct PassBudget {
 #ifndef FL_PASS_REGT_F32
 #define FL_PASS_REGT_F32 1024
 #endif
-template <typename T, int LOG2L, int TMAX>
+template <typename T, int LOG2L, int TMAX, int SEG = 64>
 struct PassTile {
     static constexpr int L = 1 << LOG2L;
     static constexpr int EPT = 16;                       // elements per thread
-    static constexpr int TILES = pass_tiles((int)sizeof(C_t<T>), LOG2L, TMAX);
-    static constexpr int LOG2T = TILES == 8 ? 3 : TILES == 4 ? 2 : TILES == 2 ? 1 : 0;
-    static_assert(TILES == 1 || TILES == 2 || TILES == 4 || TILES == 8, "tile count");
+    static constexpr int TILES = pass_tiles((int)sizeof(C_t<T>), LOG2L, TMAX, SEG);
+    static constexpr int LOG2T = TILES == 32 ? 5 : TILES == 16 ? 4 : TILES == 8 ? 3 : TILES == 4 ? 2
+                                 : TILES == 2 ? 1 : 0;
+    static_assert(TILES == 1 || TILES == 2 || TILES == 4 || TILES == 8 || TILES == 16 || TILES == 32,
+                  "tile count");
     static constexpr int NT = TILES * (L / EPT);
     // offset between tiles: P/TILES bank groups (P = 128 bytes / element
     // size), so the transposing load/store loops (consecutive threads on
@@ -362,13 +364,13 @@ struct PassTile {
 // stored to Y[l2 n1 + i1].  MODE 0: x generated by prep_value (forward);
 // MODE 1: x read from the band grid (adjoint).
 template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
-__global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1>::NT,
-                                  PassTile<T, LOG2L, PassBudget<T>::P1>::MINB)
+__global__ void __launch_bounds__(PassTile<T, LOG2L, PassBudget<T>::P1, FL_P1_SEG_BYTES>::NT,
+                                  PassTile<T, LOG2L, PassBudget<T>::P1, FL_P1_SEG_BYTES>::MINB)
     k_pass1(const PassItem* __restrict__ items, const BandDev* __restrict__ bands, int log2n1,
             const C_t<T>* __restrict__ c, const T* __restrict__ D, const C_t<T>* __restrict__ src,
             C_t<T>* __restrict__ Y, const C_t<T>* __restrict__ tw) {
     using C = C_t<T>;
-    using PT = PassTile<T, LOG2L, PassBudget<T>::P1>;
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P1, FL_P1_SEG_BYTES>;
     using SP = StagePlan<LOG2L>;
     constexpr int L = PT::L, TC = PT::TILES, LD = PT::LD;
     extern __shared__ unsigned char smem_raw[];
@@ -607,7 +609,7 @@ template <typename T, int SIGN, int MODE, bool DERIV, int LOG2L>
 static cudaError_t pass1_ct(const PassItem* items, int nitems, const BandDev* bands, int log2n1,
                             const C_t<T>* c, const T* D, const C_t<T>* src, C_t<T>* Y,
                             const C_t<T>* tw, cudaStream_t st) {
-    using PT = PassTile<T, LOG2L, PassBudget<T>::P1>;
+    using PT = PassTile<T, LOG2L, PassBudget<T>::P1, FL_P1_SEG_BYTES>;
     auto k = k_pass1<T, SIGN, MODE, DERIV, LOG2L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PT::SMEM);
     if (e == cudaSuccess)
