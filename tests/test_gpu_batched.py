@@ -222,3 +222,26 @@ def test_shared_nodes(fl, prec, eps):
         assert E <= _tol(eps, prec, ref, cs[i]), (i, N, E)
     shared.close()
     rep.close()
+
+
+def test_shared_nodes_edge_cases(fl):
+    dev = torch.device("cuda")
+    # an empty shared node set: nothing to evaluate
+    bp = fl.BatchedPlan([100, 200], None, torch.zeros((0, 2), dtype=torch.float64, device=dev), 1e-6,
+                        shared_nodes=True)
+    assert bp.info()["M"] == 0
+    f = bp.execute(torch.zeros(300, dtype=torch.complex64, device=dev))
+    assert f.numel() == 0
+    bp.close()
+    # one transform, and several of one size: the same as a single plan
+    w = W.nodes_disk_uniform(700, seed=81)
+    c = W.coefficients(5000, seed=82)
+    sp = fl.Plan(5000, torch.from_numpy(w).to(dev), 1e-6)
+    ref = sp.execute(torch.from_numpy(c).to(torch.complex64).to(dev)).cpu().numpy()
+    sp.close()
+    for B in (1, 3):
+        bp = fl.BatchedPlan([5000] * B, None, torch.from_numpy(w).to(dev), 1e-6, shared_nodes=True)
+        f = bp.execute(torch.from_numpy(np.tile(c, B)).to(torch.complex64).to(dev)).cpu().numpy()
+        bp.close()
+        for i in range(B):
+            assert np.array_equal(f[i * 700:(i + 1) * 700], ref), (B, i)
