@@ -144,8 +144,8 @@ def pipe_peaks() -> dict:
 
 
 def method_bytes(info: dict, q: int, cs: int = 8, n_min: int = 0) -> float:
-    """Bytes the method moves through the band grids per execute (the survey's
-    per-unit figure): one grid write and one read per right-hand side of every
+    """Bytes the method moves through the band grids per execute (its per-unit
+    figure): one grid write and one read per right-hand side of every
     NFFT, 2 cs n each (cs = bytes per complex; a band evaluated as P sub-band
     NFFTs has P grids of band_n points); only grids above n_min."""
     total = 0.0
@@ -684,7 +684,7 @@ def run_ours(args):
                               "avg_launch_ms": per, "bytes_per_launch": kd["bytes"] / max(kd["launches"], 1),
                               "GBps": gbs, "share": kd["total_ms"] / max(sum(v["total_ms"] for v in kern.values()), 1e-12)}
     # Roofline of the dominant work, the four-step FFTs of the band grids (pass
-    # 1 and pass 2 together: the survey's per-unit figure, one grid write and
+    # 1 and pass 2 together: the method's per-unit figure, one grid write and
     # one read per right-hand side, cannot be credited to either pass alone),
     # and of the whole step on the method's bytes.
     passes = sorted(k for k in kernel_table if k.startswith("fft_pass"))
