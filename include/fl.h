@@ -239,6 +239,30 @@ fl_status fl_plan_batched(fl_plan_t *out, int B, const int64_t *N_host, const in
 fl_status fl_execute_batched(fl_plan_t p, const void *c_dev, void *f_dev, void *stream);
 
 /*
+ * fl_plan_batched_ptrs -- fl_plan_batched with one node array per transform:
+ * nodes_host is a host array of B device pointers, entry i holding M_i rows
+ * of {Re w, Im w} (NULL allowed where M_i = 0); with
+ * fl_options.shared_nodes only entry 0 is read (the M_0 shared rows).  The
+ * node sets are copied into one temporary device array for planning, which
+ * is freed before the call returns (the call synchronises `stream`).
+ */
+fl_status fl_plan_batched_ptrs(fl_plan_t *out, int B, const int64_t *N_host, const int64_t *M_host,
+                               const double *const *nodes_host, int q, double eps, fl_precision prec,
+                               const fl_options *opt, void *stream);
+
+/*
+ * fl_execute_batched_ptrs -- fl_execute_batched on per-transform buffers:
+ * c_host and f_host are host arrays of B device pointers (transform i: N_i
+ * and M_i complex of the plan's precision; f entries may be NULL where
+ * M_i = 0).  One kernel gathers the coefficients into the plan's staging
+ * array, the batched transform runs on it, and one kernel scatters the
+ * results; the pointer arrays are read before the call returns.
+ * Asynchronous on `stream`.
+ */
+fl_status fl_execute_batched_ptrs(fl_plan_t p, const void *const *c_host, void *const *f_host,
+                                  void *stream);
+
+/*
  * fl_execute -- f~ ~= C c with C = (z_j^k), Algorithm 2.
  *   c_dev : device, N complex (plan precision).
  *   f_dev : device, M complex (plan precision), fully overwritten.

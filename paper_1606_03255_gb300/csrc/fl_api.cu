@@ -43,7 +43,7 @@ Plan::~Plan() {
                     d_dranges, d_dpart, d_cdir, d_dadj32, d_dadj64, d_cell, d_sp_phi,
                     d_sp_L, d_sp_rv, d_cell_bands, d_lapK, d_lapKoff, d_tw, d_nearT, d_cheb32, d_cff, d_tperm, d_ts, d_tbs,
                     d_xis, d_xperm, d_xbk, d_xstart, d_xwin, d_xiphi, d_xcs, d_xsb,
-                    d_frbs, d_fent, d_fphi, d_fpp, d_ntab};
+                    d_frbs, d_fent, d_fphi, d_fpp, d_ntab, d_boff, d_bptr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     for (Timer& t : timers) {
@@ -1203,6 +1203,64 @@ static cudaError_t forward_graphed(Plan& p, const void* c, void* f, cudaStream_t
     return cudaGraphLaunch(p.gexec, st);
 }
 
+// Batched plans with per-transform buffers: element e of the concatenation
+// belongs to transform b with off[b] <= e < off[b + 1] (binary search);
+// pack copies the callers' arrays into the concatenation, unpack back out.
+template <typename E>
+__global__ void k_batch_pack(int B, const int64_t* __restrict__ off, const E* const* __restrict__ src,
+                             int64_t total, E* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int lo = 0, hi = B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    dst[e] = src[lo][e - off[lo]];
+}
+
+template <typename E>
+__global__ void k_batch_unpack(int B, const int64_t* __restrict__ off, const E* __restrict__ src,
+                               int64_t total, E* const* __restrict__ dst) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    int lo = 0, hi = B;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    dst[lo][e - off[lo]] = src[e];
+}
+
+// pack: c pointers -> d_stage_c; else d_stage_f -> f pointers (offsets and
+// pointers from d_boff / d_bptr).
+static cudaError_t launch_batch_pack(Plan& p, size_t cs, bool pack, cudaStream_t st) {
+    const int B = (int)p.inst.size();
+    const int64_t total = pack ? p.N : p.M;
+    if (total == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((total + 255) / 256);
+    const int64_t* off = pack ? p.d_boff : p.d_boff + B + 1;
+    if (cs == 16) {
+        if (pack)
+            k_batch_pack<double2><<<grid, 256, 0, st>>>(B, off, (const double2* const*)p.d_bptr, total,
+                                                        (double2*)p.d_stage_c);
+        else
+            k_batch_unpack<double2><<<grid, 256, 0, st>>>(B, off, (const double2*)p.d_stage_f, total,
+                                                          (double2* const*)(p.d_bptr + B));
+    } else {
+        if (pack)
+            k_batch_pack<float2><<<grid, 256, 0, st>>>(B, off, (const float2* const*)p.d_bptr, total,
+                                                       (float2*)p.d_stage_c);
+        else
+            k_batch_unpack<float2><<<grid, 256, 0, st>>>(B, off, (const float2*)p.d_stage_f, total,
+                                                         (float2* const*)(p.d_bptr + B));
+    }
+    ++p.launches;
+    return cudaGetLastError();
+}
+
 }  // namespace fl
 
 using namespace fl;
@@ -1423,6 +1481,96 @@ fl_status fl_execute_batched(fl_plan_t h, const void* c_dev, void* f_dev, void* 
     if (h->p.M > 0 && (!c_dev || !f_dev)) return fail(FL_EINVAL, "fl_execute_batched: NULL buffer");
     cudaError_t e = forward_graphed(h->p, c_dev, f_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "fl_execute_batched");
+    return FL_OK;
+}
+
+fl_status fl_plan_batched_ptrs(fl_plan_t* out, int B, const int64_t* N_host, const int64_t* M_host,
+                               const double* const* nodes_host, int q, double eps, fl_precision prec,
+                               const fl_options* opt, void* stream) {
+    g_err.clear();
+    if (!out) return fail(FL_EINVAL, "fl_plan_batched_ptrs: out is NULL");
+    *out = nullptr;
+    if (B < 1 || !N_host || !M_host) return fail(FL_EINVAL, "fl_plan_batched_ptrs: need B >= 1 and sizes");
+    if (opt && opt->shared_nodes)   // one node set: the first pointer
+        return fl_plan_batched(out, B, N_host, M_host, nodes_host ? nodes_host[0] : nullptr, q, eps, prec,
+                               opt, stream);
+    int64_t Mtot = 0;
+    for (int i = 0; i < B; ++i) {
+        if (M_host[i] < 0) return fail(FL_EINVAL, "fl_plan_batched_ptrs: need M_i >= 0");
+        if (M_host[i] > 0 && (!nodes_host || !nodes_host[i]))
+            return fail(FL_EINVAL, "fl_plan_batched_ptrs: nodes of a transform with M_i > 0 is NULL");
+        Mtot += M_host[i];
+    }
+    if (Mtot > ((int64_t)1 << 31) - 1) return fail(FL_EUNSUPPORTED, "fl_plan_batched_ptrs: sum of M_i above 2^31 - 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    double* cat = nullptr;   // the node sets concatenated, for planning only
+    if (Mtot > 0) {
+        FL_CUDA(cudaMalloc(&cat, Mtot * 2 * sizeof(double)), "cudaMalloc nodes");
+        int64_t off = 0;
+        for (int i = 0; i < B; ++i) {
+            if (M_host[i] > 0) {
+                const cudaError_t e = cudaMemcpyAsync(cat + 2 * off, nodes_host[i], M_host[i] * 2 * sizeof(double),
+                                                      cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) {
+                    cudaFree(cat);
+                    return cuda_fail(e, "fl_plan_batched_ptrs: copy nodes");
+                }
+            }
+            off += M_host[i];
+        }
+    }
+    fl_status s = fl_plan_batched(out, B, N_host, M_host, cat, q, eps, prec, opt, stream);
+    if (cat) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        cudaFree(cat);
+        if (e != cudaSuccess && s == FL_OK) {
+            fl_destroy(*out);
+            *out = nullptr;
+            return cuda_fail(e, "fl_plan_batched_ptrs: synchronise");
+        }
+    }
+    return s;
+}
+
+fl_status fl_execute_batched_ptrs(fl_plan_t h, const void* const* c_host, void* const* f_host, void* stream) {
+    if (!h || h->p.kind != 0 || !h->p.batched)
+        return fail(FL_EINVAL, "fl_execute_batched_ptrs: not a batched Fourier-Laplace plan");
+    Plan& p = h->p;
+    const int B = (int)p.inst.size();
+    if (!c_host || (p.M > 0 && !f_host)) return fail(FL_EINVAL, "fl_execute_batched_ptrs: NULL pointer array");
+    for (int i = 0; i < B; ++i) {
+        if (!c_host[i]) return fail(FL_EINVAL, "fl_execute_batched_ptrs: NULL coefficients");
+        if (p.inst[i].M > 0 && !f_host[i]) return fail(FL_EINVAL, "fl_execute_batched_ptrs: NULL result");
+    }
+    const size_t cs = p.prec != FL_FP32 ? 16 : 8;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!p.d_stage_c) FL_CUDA(cudaMalloc(&p.d_stage_c, p.N * cs), "cudaMalloc staging");
+    if (!p.d_stage_f && p.M > 0) FL_CUDA(cudaMalloc(&p.d_stage_f, p.M * cs), "cudaMalloc staging");
+    if (!p.d_boff) {   // instance offsets, fixed for the plan
+        std::vector<int64_t> off(2 * (B + 1));
+        for (int i = 0; i < B; ++i) {
+            off[i] = p.inst[i].noff;
+            off[B + 1 + i] = p.inst[i].moff;
+        }
+        off[B] = p.N;
+        off[2 * B + 1] = p.M;
+        FL_CUDA(cudaMalloc((void**)&p.d_boff, off.size() * sizeof(int64_t)), "cudaMalloc offsets");
+        FL_CUDA(cudaMemcpy(p.d_boff, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice),
+                "copy offsets");
+        FL_CUDA(cudaMalloc((void**)&p.d_bptr, 2 * (size_t)B * sizeof(void*)), "cudaMalloc pointer table");
+    }
+    // the caller's pointers (pageable host memory: the copy is staged before
+    // the call returns, so the arrays may be reused at once)
+    std::vector<const void*> ptrs(2 * (size_t)B, nullptr);
+    for (int i = 0; i < B; ++i) {
+        ptrs[i] = c_host[i];
+        ptrs[B + i] = p.M > 0 ? f_host[i] : nullptr;
+    }
+    FL_CUDA(cudaMemcpyAsync(p.d_bptr, ptrs.data(), ptrs.size() * sizeof(void*), cudaMemcpyHostToDevice, st),
+            "copy pointer table");
+    FL_CUDA(launch_batch_pack(p, cs, true, st), "fl_execute_batched_ptrs: gather coefficients");
+    FL_CUDA(forward_graphed(p, p.d_stage_c, p.d_stage_f, st), "fl_execute_batched_ptrs");
+    if (p.M > 0) FL_CUDA(launch_batch_pack(p, cs, false, st), "fl_execute_batched_ptrs: scatter results");
     return FL_OK;
 }
 

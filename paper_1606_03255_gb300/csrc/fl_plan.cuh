@@ -244,8 +244,10 @@ struct Plan {
     void* d_Y = nullptr;           // four-step intermediate (complex T)
     void* d_tw = nullptr;          // four-step stage twiddles (complex T, kTwEntries;
                                    // float pairs: + 8192 pass-1 output twiddles)
-    void* d_stage_c = nullptr;     // staging for fl_execute_host
+    void* d_stage_c = nullptr;     // staging for fl_execute_host and fl_execute_batched_ptrs
     void* d_stage_f = nullptr;
+    int64_t* d_boff = nullptr;     // batched: instance offsets of c (B + 1) then of f (B + 1)
+    void** d_bptr = nullptr;       // batched: the caller's c pointers (B) then f pointers (B)
     void* d_stage_r = nullptr;     // fl_transposed: conj of the node values
     void* d_cff = nullptr;         // FL_FP64_FF: the coefficients as float pairs (N)
     void* d_z0 = nullptr;          // one complex: sum of r over Z^0 (adjoint)

@@ -32,7 +32,8 @@ STATUS_NAMES = {FL_OK: "FL_OK", FL_EINVAL: "FL_EINVAL", FL_ENOMEM: "FL_ENOMEM",
                 FL_EUNSUPPORTED: "FL_EUNSUPPORTED"}
 
 # Every symbol include/fl.h declares.
-EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
+EXPORTED = ["fl_plan", "fl_plan_ex", "fl_plan_batched", "fl_execute_batched", "fl_plan_batched_ptrs",
+            "fl_execute_batched_ptrs", "fl_execute", "fl_execute_deriv", "fl_grad_w", "fl_execute_host",
             "fl_adjoint", "fl_transposed", "fl_plan_xi",
             "fl_plan_laplace", "fl_plan_kernel", "fl_laplace_real", "fl_laplace_real_noalloc", "fl_get_info",
             "fl_set_timing", "fl_get_timing", "fl_destroy", "fl_last_error", "fl_version"]
@@ -122,6 +123,9 @@ def load(path: str | None = None):
         "fl_plan_batched": [pp, ci, ctypes.POINTER(i64), ctypes.POINTER(i64), vp, ci, cd, ci,
                             ctypes.POINTER(fl_options), vp],
         "fl_execute_batched": [vp, vp, vp, vp],
+        "fl_plan_batched_ptrs": [pp, ci, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp), ci, cd,
+                                 ci, ctypes.POINTER(fl_options), vp],
+        "fl_execute_batched_ptrs": [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp],
         "fl_execute": [vp, vp, vp, vp],
         "fl_execute_deriv": [vp, vp, vp, vp],
         "fl_grad_w": [vp, vp, vp, vp, vp],
@@ -182,6 +186,24 @@ def fl_plan_batched(Ns, Ms, nodes_ptr, q, eps, prec, options, stream):
 
 def fl_execute_batched(plan, c_ptr, f_ptr, stream):
     return load().fl_execute_batched(plan, c_ptr, f_ptr, stream)
+
+
+def fl_plan_batched_ptrs(Ns, Ms, node_ptrs, q, eps, prec, options, stream):
+    h = ctypes.c_void_p()
+    B = len(Ns)
+    na = (ctypes.c_int64 * B)(*[int(x) for x in Ns])
+    ma = (ctypes.c_int64 * B)(*[int(x) for x in Ms])
+    pa = (ctypes.c_void_p * B)(*node_ptrs)
+    opt = ctypes.byref(options) if options is not None else None
+    st = load().fl_plan_batched_ptrs(ctypes.byref(h), B, na, ma, pa, int(q), float(eps), int(prec), opt, stream)
+    return st, h
+
+
+def fl_execute_batched_ptrs(plan, c_ptrs, f_ptrs, stream):
+    B = len(c_ptrs)
+    ca = (ctypes.c_void_p * B)(*c_ptrs)
+    fa = (ctypes.c_void_p * B)(*f_ptrs)
+    return load().fl_execute_batched_ptrs(plan, ca, fa, stream)
 
 
 def fl_execute(plan, c_ptr, f_ptr, stream):
@@ -466,10 +488,14 @@ class BatchedPlan:
                  variant: str = "alg2", fuse: str = "auto", sigma: str = "auto",
                  shared_nodes: bool = False):
         torch = _torch()
-        nodes = nodes.to(torch.float64).contiguous()
+        per_transform = isinstance(nodes, (list, tuple))
+        if per_transform:
+            nodes = [w.to(torch.float64).contiguous() for w in nodes]
+        else:
+            nodes = nodes.to(torch.float64).contiguous()
         self.Ns = [int(x) for x in Ns]
         if shared_nodes and Ms is None:
-            Ms = [int(nodes.shape[0])] * len(self.Ns)
+            Ms = [int((nodes[0] if per_transform else nodes).shape[0])] * len(self.Ns)
         self.Ms = [int(x) for x in Ms]
         self.N, self.M = sum(self.Ns), sum(self.Ms)
         self.prec = _precision(precision)
@@ -478,9 +504,14 @@ class BatchedPlan:
         opt = fl_options(ROUTES[route], float(direct_bias), int(rhs_per_launch),
                          1 if use_graph else -1, int(bool(autotune)), VARIANTS[variant], FUSE[fuse],
                          SIGMA[str(sigma)], int(bool(shared_nodes)))
-        st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
-                                self.prec, opt, _stream_handle(stream))
-        check(st, "fl_plan_batched")
+        if per_transform:   # one node tensor per transform (fl_plan_batched_ptrs)
+            st, h = fl_plan_batched_ptrs(self.Ns, self.Ms, [_ptr(w) if w.numel() else None for w in nodes],
+                                         q, eps, self.prec, opt, _stream_handle(stream))
+            check(st, "fl_plan_batched_ptrs")
+        else:
+            st, h = fl_plan_batched(self.Ns, self.Ms, _ptr(nodes) if self.M else None, q, eps,
+                                    self.prec, opt, _stream_handle(stream))
+            check(st, "fl_plan_batched")
         self._handle = h
 
     @property
@@ -496,6 +527,24 @@ class BatchedPlan:
         check(fl_execute_batched(self._handle, _ptr(c), _ptr(out) if self.M else None,
                                  _stream_handle(stream)), "fl_execute_batched")
         return out
+
+    def execute_list(self, cs, outs=None, stream=None):
+        """The batch on per-transform tensors (fl_execute_batched_ptrs): cs[i]
+        holds N_i coefficients; returns (or fills) one result tensor per
+        transform."""
+        torch = _torch()
+        if len(cs) != len(self.Ns):
+            raise ValueError("execute_list: one coefficient tensor per transform")
+        for c, n in zip(cs, self.Ns):
+            _require(c, self.cdtype, n, "c")
+        if outs is None:
+            outs = [torch.empty(m, dtype=self.cdtype, device=cs[0].device) for m in self.Ms]
+        for o, m in zip(outs, self.Ms):
+            _require(o, self.cdtype, m, "out")
+        check(fl_execute_batched_ptrs(self._handle, [_ptr(c) for c in cs],
+                                      [_ptr(o) if o.numel() else None for o in outs],
+                                      _stream_handle(stream)), "fl_execute_batched_ptrs")
+        return outs
 
     def info(self) -> dict:
         st, inf = fl_get_info(self._handle)

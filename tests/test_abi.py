@@ -99,3 +99,13 @@ def test_shared_nodes_need_equal_node_counts(fl):
     st, h = fl.fl_plan_batched([4, 8, 4], [2, 3, 2], ptr, 0, 1e-6, 0, _options(fl, shared_nodes=1), None)
     assert st == fl.FL_EINVAL and not h.value
     assert "shared nodes" in fl.fl_last_error()
+
+
+def test_pointer_batched_calls_check_arguments_on_host(fl):
+    # a transform with nodes and a NULL node pointer, and a NULL plan
+    st, h = fl.fl_plan_batched_ptrs([4, 4], [2, 3], [None, None], 0, 1e-6, 0, None, None)
+    assert st == fl.FL_EINVAL and not h.value
+    assert "NULL" in fl.fl_last_error()
+    st, h = fl.fl_plan_batched_ptrs([4, 4], [-1, 3], [None, None], 0, 1e-6, 0, None, None)
+    assert st == fl.FL_EINVAL and not h.value
+    assert fl.fl_execute_batched_ptrs(None, [None], [None], None) == fl.FL_EINVAL

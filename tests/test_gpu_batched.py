@@ -245,3 +245,30 @@ def test_shared_nodes_edge_cases(fl):
         bp.close()
         for i in range(B):
             assert np.array_equal(f[i * 700:(i + 1) * 700], ref), (B, i)
+
+
+def test_per_transform_pointers(fl):
+    # one node tensor and one coefficient / result tensor per transform
+    # (fl_plan_batched_ptrs, fl_execute_batched_ptrs): the same numbers as
+    # the concatenated calls, bit for bit; a transform without nodes included
+    Ns = [3000, 700, 12000, 50]
+    Ms = [800, 0, 2500, 40]
+    cs, ws = _batch(Ns, Ms, seed=90, kinds=("clustered", "disk"))
+    dev = torch.device("cuda")
+    bp = fl.BatchedPlan(Ns, Ms, [torch.from_numpy(w).to(dev) for w in ws], 1e-6)
+    ref_plan = fl.BatchedPlan(Ns, Ms, torch.from_numpy(np.concatenate(ws)).to(dev), 1e-6)
+    ct = [torch.from_numpy(c).to(torch.complex64).to(dev) for c in cs]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        outs = bp.execute_list(ct)
+        outs2 = bp.execute_list([2 * c for c in ct])     # the pointer table re-read per call
+        ref = ref_plan.execute(torch.cat(ct))
+    s.synchronize()
+    moff = 0
+    for i, m in enumerate(Ms):
+        assert outs[i].numel() == m
+        assert torch.equal(outs[i], ref[moff:moff + m])
+        assert torch.allclose(outs2[i], 2 * ref[moff:moff + m], rtol=1e-5, atol=1e-3)
+        moff += m
+    bp.close()
+    ref_plan.close()
